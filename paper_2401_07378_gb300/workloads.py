@@ -1,0 +1,219 @@
+"""Seeded synthetic inputs shaped like the NNS-EMD paper's workloads.
+
+This module holds no NNS-EMD arithmetic: it only draws point sets and raw
+weights.  Both the CUDA path (through the tests and the benchmark) and the
+CPU oracle are fed from here, so the two sides always see the same inputs.
+
+The paper's datasets (MNIST, CIFAR-10, DOTmark, 20news, Amazon, NUS-WIDE,
+Paris-6k and the seasonal colour-transfer set) are not available; each
+generator below stands in for one of them with the shape, size and value
+distribution the paper describes (Sec. IV-A "Histogram Initialization",
+Table "Datasets description"):
+
+* ``single_pair``       -- a spatial-location histogram pair (pixels as bins).
+* ``color_transfer``    -- colour-intensity histograms of two RGB images
+                           (Sec. IV-D), 8 colour clusters.
+* ``doc_knn``           -- word-embedding histograms of documents
+                           (Sec. IV-B, document classification).
+* ``retrieval``         -- signatures of image descriptors (Sec. IV-C).
+* ``gmm``               -- large Gaussian-mixture clouds in d=64.
+
+Coordinates are float32 (row-major ``[points, d]``); weights are float64 and
+not normalised (the solver normalises them, Sec. II-A).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+_ONE_MINUS = np.float32(np.nextafter(np.float32(1.0), np.float32(0.0)))
+
+
+@dataclass
+class Pair:
+    """One EMD problem: suppliers ``x``/``a`` and consumers ``y``/``b``."""
+
+    x: np.ndarray  # float32 [m, d]  suppliers S
+    a: np.ndarray  # float64 [m]
+    y: np.ndarray  # float32 [n, d]  consumers C
+    b: np.ndarray  # float64 [n]
+
+    @property
+    def m(self) -> int:
+        return int(self.x.shape[0])
+
+    @property
+    def n(self) -> int:
+        return int(self.y.shape[0])
+
+    @property
+    def d(self) -> int:
+        return int(self.x.shape[1])
+
+
+@dataclass
+class Batch:
+    """Many EMD problems packed back to back (CSR-style offsets)."""
+
+    x: np.ndarray      # float32 [sum m, d]
+    a: np.ndarray      # float64 [sum m]
+    x_off: np.ndarray  # int64 [P+1]
+    y: np.ndarray      # float32 [sum n, d]
+    b: np.ndarray      # float64 [sum n]
+    y_off: np.ndarray  # int64 [P+1]
+
+    @property
+    def num_pairs(self) -> int:
+        return int(self.x_off.shape[0] - 1)
+
+    @property
+    def d(self) -> int:
+        return int(self.x.shape[1])
+
+    def pair(self, p: int) -> Pair:
+        xs, xe = int(self.x_off[p]), int(self.x_off[p + 1])
+        ys, ye = int(self.y_off[p]), int(self.y_off[p + 1])
+        return Pair(self.x[xs:xe], self.a[xs:xe], self.y[ys:ye], self.b[ys:ye])
+
+    @staticmethod
+    def pack(pairs: list[Pair]) -> "Batch":
+        d = pairs[0].d
+        x_off = np.zeros(len(pairs) + 1, np.int64)
+        y_off = np.zeros(len(pairs) + 1, np.int64)
+        x_off[1:] = np.cumsum([p.m for p in pairs])
+        y_off[1:] = np.cumsum([p.n for p in pairs])
+        x = np.ascontiguousarray(np.concatenate([p.x for p in pairs]).reshape(-1, d), np.float32)
+        y = np.ascontiguousarray(np.concatenate([p.y for p in pairs]).reshape(-1, d), np.float32)
+        a = np.ascontiguousarray(np.concatenate([p.a for p in pairs]), np.float64)
+        b = np.ascontiguousarray(np.concatenate([p.b for p in pairs]), np.float64)
+        return Batch(x, a, x_off, y, b, y_off)
+
+
+def _clip01(v: np.ndarray) -> np.ndarray:
+    return np.clip(v.astype(np.float32), np.float32(0.0), _ONE_MINUS)
+
+
+def uniform_pair(m: int, n: int, d: int, seed: int, weights: str = "uniform") -> Pair:
+    """Points iid Uniform[0,1)^d; weights uniform (1 each) or Dirichlet(1)."""
+    rng = np.random.default_rng(seed)
+    x = rng.random((m, d), dtype=np.float32)
+    y = rng.random((n, d), dtype=np.float32)
+    if weights == "uniform":
+        a = np.ones(m, np.float64)
+        b = np.ones(n, np.float64)
+    elif weights == "dirichlet":
+        a = rng.exponential(1.0, m)
+        b = rng.exponential(1.0, n)
+    else:
+        raise ValueError(weights)
+    return Pair(x, a, y, b)
+
+
+def single_pair(seed: int = 0, n: int = 256, d: int = 2) -> Pair:
+    """Spatial-location histogram pair: n=m=256 points in d=2, Uniform[0,1),
+    uniform weights (the paper's grayscale-pixel formulation, Sec. II-A)."""
+    return uniform_pair(n, n, d, seed)
+
+
+def color_transfer(seed: int = 0, n: int = 65536, clusters: int = 8, sigma: float = 0.08) -> Pair:
+    """Colour-intensity histograms of two RGB images (Sec. IV-D): 65,536
+    points each in d=3.  Cluster centres ~ Uniform[0,1)^3 (drawn first, shared
+    by both images), points = centre + N(0, sigma^2 I) clipped to [0,1),
+    uniform weights."""
+    rng = np.random.default_rng(seed)
+    centres = rng.random((clusters, 3))
+    pts = []
+    for _ in range(2):
+        lab = rng.integers(0, clusters, n)
+        p = centres[lab] + rng.normal(0.0, sigma, (n, 3))
+        pts.append(_clip01(p))
+    return Pair(pts[0], np.ones(n), pts[1], np.ones(n))
+
+
+def gmm_pair(seed: int = 0, n: int = 262144, d: int = 64, components: int = 256,
+             mixture_seed: int = 12345, alpha: float = 0.5) -> Pair:
+    """Gaussian-mixture clouds: means ~ N(0, 4I) (fixed mixture seed), points
+    ~ N(mu, 0.25 I), Dirichlet(alpha) weights (as normalised Gamma draws)."""
+    mrng = np.random.default_rng(mixture_seed)
+    means = mrng.normal(0.0, 2.0, (components, d))
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(2):
+        lab = rng.integers(0, components, n)
+        p = means[lab] + rng.normal(0.0, 0.5, (n, d))
+        w = rng.gamma(alpha, 1.0, n)
+        out.append((p.astype(np.float32), w))
+    return Pair(out[0][0], out[0][1], out[1][0], out[1][1])
+
+
+# --------------------------------------------------------------------------
+# document kNN (Sec. IV-B): 1 query document against many documents
+# --------------------------------------------------------------------------
+
+def vocabulary(size: int = 50000, d: int = 300, seed: int = 0) -> np.ndarray:
+    """Word vectors iid N(0,1) then L2-normalised (float32)."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal((size, d))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return v.astype(np.float32)
+
+
+def _zipf_probs(size: int, s: float) -> np.ndarray:
+    p = np.arange(1, size + 1, dtype=np.float64) ** (-s)
+    return p / p.sum()
+
+
+def _document(rng: np.random.Generator, vocab: np.ndarray, probs: np.ndarray,
+              median: float, sigma: float, lo: int, hi: int, s: float):
+    length = int(np.clip(np.round(rng.lognormal(np.log(median), sigma)), lo, hi))
+    ids = rng.choice(vocab.shape[0], size=length, replace=False, p=probs)
+    w = (ids.astype(np.float64) + 1.0) ** (-s)  # term weight ~ vocab rank^-s
+    return vocab[ids], w
+
+
+def doc_knn(num_docs: int = 4096, seed: int = 0, vocab_size: int = 50000, d: int = 300,
+            median: float = 60.0, sigma: float = 0.6, lo: int = 20, hi: int = 500,
+            s: float = 1.1, vocab_seed: int = 0) -> Batch:
+    """One query document (consumer) against ``num_docs`` documents
+    (suppliers).  Document lengths are LogNormal(ln median, sigma) clipped to
+    [lo, hi]; words are distinct ids drawn with probability ~ rank^-s; a
+    word's weight is ~ rank^-s (a Zipf term frequency)."""
+    vocab = vocabulary(vocab_size, d, vocab_seed)
+    probs = _zipf_probs(vocab_size, s)
+    rng = np.random.default_rng(seed)
+    qy, qb = _document(rng, vocab, probs, median, sigma, lo, hi, s)
+    pairs = []
+    for _ in range(num_docs):
+        dx, da = _document(rng, vocab, probs, median, sigma, lo, hi, s)
+        pairs.append(Pair(dx, da, qy, qb))
+    return Batch.pack(pairs)
+
+
+def retrieval(num_pairs: int = 10000, seed: int = 0, d: int = 128, lo: int = 256, hi: int = 2048) -> Batch:
+    """Signature pairs of SIFT-like descriptors: m, n ~ Uniform{lo..hi}
+    independently; descriptors |N(0,1)| then L2-normalised and scaled by 512;
+    weights Dirichlet(1) (normalised Exp(1) draws)."""
+    rng = np.random.default_rng(seed)
+    pairs = []
+    for _ in range(num_pairs):
+        m = int(rng.integers(lo, hi + 1))
+        n = int(rng.integers(lo, hi + 1))
+        sig = []
+        for k in (m, n):
+            v = np.abs(rng.standard_normal((k, d)))
+            v = v / np.linalg.norm(v, axis=1, keepdims=True) * 512.0
+            sig.append(v.astype(np.float32))
+        pairs.append(Pair(sig[0], rng.exponential(1.0, m), sig[1], rng.exponential(1.0, n)))
+    return Batch.pack(pairs)
+
+
+def random_batch(num_pairs: int, seed: int, d: int, lo: int, hi: int, weights: str = "dirichlet") -> Batch:
+    """Small uneven batches of uniform point sets (test cases)."""
+    rng = np.random.default_rng(seed)
+    pairs = []
+    for p in range(num_pairs):
+        m = int(rng.integers(lo, hi + 1))
+        n = int(rng.integers(lo, hi + 1))
+        pairs.append(uniform_pair(m, n, d, seed * 100003 + p, weights))
+    return Batch.pack(pairs)
