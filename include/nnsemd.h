@@ -1,0 +1,181 @@
+/*
+ * nnsemd.h -- C ABI of the GB300 (sm_103a) NNS-EMD solver.
+ *
+ * NNS-EMD approximates the Earth Mover's Distance between two weighted point
+ * sets (Sec. II-A, Eq. objective/inflow/outflow): suppliers S (points x_i,
+ * weights a_i, i < m) and consumers C (points y_j, weights b_j, j < n).  The
+ * solver runs the paper's Algorithm 1 (Sec. III-A, greedy protocol) in
+ * rounds until one side has no mass left:
+ *   1. every active consumer finds its nearest active supplier (NNS op.);
+ *   2. each supplier serves the consumers that picked it in ascending
+ *      distance, moving f = min(s_i, c_j) until s_i is spent (greedy
+ *      protocol), and the transport cost f * D_ij is accumulated;
+ *   3. points whose residual weight is exactly 0 retire (weights update).
+ * It returns R = sum f * D_ij and, optionally, the sparse plan F*.
+ *
+ * Conventions fixed by this library (the paper leaves them open):
+ *  - Weights are normalised to unit mass (Sec. II-A) by dividing each by the
+ *    correctly rounded sum of its side.  Zero weights are allowed (the point
+ *    never takes part and its coordinates are not read); negative or
+ *    non-finite weights are errors.
+ *  - Argmin ties go to the lowest supplier index, greedy-order ties to the
+ *    lowest consumer index.
+ *  - Metric NNSEMD_L2 (Euclidean, the paper's choice) and NNSEMD_SQL2 order
+ *    candidates by the squared distance; NNSEMD_L1 by the L1 sum.  The cost
+ *    uses the metric itself (sqrt for L2), evaluated in FP64.
+ *  - Decisions (argmin, greedy order) are taken on FP32 distances computed
+ *    by direct differences in a fixed order: t_k = x_k - y_k (FP32),
+ *    acc = t_0*t_0, acc = fma(t_k, t_k, acc) for k = 1..d-1 (L1: the
+ *    running FP32 sum of |t_k|).  Mass bookkeeping is FP64 and sequential
+ *    per supplier exactly as in Algorithm 1.  R is the correctly rounded sum
+ *    of the per-flow FP64 terms f * D_ij.
+ *  - Reduced precision (BF16/FP16/FP8) only proposes candidates; the final
+ *    choice is re-ranked in FP32 and certified, so results equal the FP32
+ *    path's (uncertified consumers fall back to the FP32 scan).
+ *
+ * Memory: every array argument is caller-owned.  Pointers are DEVICE
+ * pointers unless the name or comment says host.  The context owns only its
+ * workspace (grown on demand, freed by nnsemd_destroy).  Coordinates are
+ * float32 row-major [points][d] (4-byte aligned); weights are float64
+ * (8-byte aligned).
+ *
+ * Errors: every function returns an nnsemd_status; nothing throws across
+ * the ABI.  nnsemd_last_error(ctx) gives a message for the last failure on
+ * that context.  A context is not thread-safe: use one per host thread.
+ */
+#ifndef NNSEMD_H
+#define NNSEMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NNSEMD_ABI_VERSION 1
+
+typedef enum {
+  NNSEMD_OK = 0,
+  NNSEMD_ERR_INVALID_ARG = 1,  /* bad size, pointer, alignment or option */
+  NNSEMD_ERR_NONFINITE = 2,    /* a coordinate or weight is NaN or Inf */
+  NNSEMD_ERR_ZERO_MASS = 3,    /* a side's weights sum to zero, or a weight is negative */
+  NNSEMD_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+  NNSEMD_ERR_OOM = 5,          /* the workspace could not be allocated */
+  NNSEMD_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up */
+  NNSEMD_ERR_ITER_LIMIT = 7,   /* more than m + n rounds (cannot happen unless corrupted) */
+  NNSEMD_ERR_UNSUPPORTED = 8,  /* d or a size beyond what the chosen path serves */
+  NNSEMD_ERR_CAPACITY = 9      /* the caller's plan arrays are too small */
+} nnsemd_status;
+
+typedef enum { NNSEMD_L2 = 0, NNSEMD_SQL2 = 1, NNSEMD_L1 = 2 } nnsemd_metric;
+
+typedef enum {
+  NNSEMD_FP32 = 0,  /* direct-difference FP32 distances on CUDA cores (d <= 8) or tiles (d > 8) */
+  NNSEMD_BF16 = 1,  /* tcgen05 BF16 contraction proposes candidates, FP32 re-rank decides */
+  NNSEMD_FP16 = 2,  /* the same with FP16 operands */
+  NNSEMD_FP8 = 3    /* the same with E4M3 operands and a per-row scale */
+} nnsemd_precision;
+
+typedef struct nnsemd_ctx nnsemd_ctx;
+
+typedef struct {
+  int32_t device;               /* CUDA device ordinal */
+  void *stream;                 /* cudaStream_t the context launches on; NULL = default stream */
+  size_t workspace_bytes_hint;  /* preallocate this much workspace (0 = on demand) */
+} nnsemd_config;
+
+/* nnsemd_options.flags bits */
+#define NNSEMD_FLAG_TIME_KERNELS 1  /* time the NNS and tail kernels with CUDA events (fills the *_ms stats) */
+
+typedef struct {
+  int32_t metric;               /* nnsemd_metric */
+  int32_t precision;            /* nnsemd_precision */
+  int32_t rerank_k;             /* candidates per consumer kept by a reduced-precision scan (0 = default 8) */
+  int32_t flags;                /* NNSEMD_FLAG_* bits, 0 for none */
+  const void *proposal;         /* learned candidate proposal, NULL = full scan */
+} nnsemd_options;
+
+typedef struct {
+  int64_t capacity;             /* in: entries i, j, f can hold; m + n - 1 always suffices */
+  int64_t nnz;                  /* out: entries written (order unspecified, (i, j) unique) */
+  int32_t *i;                   /* supplier index of each flow */
+  int32_t *j;                   /* consumer index of each flow */
+  double *f;                    /* flow amount (normalised mass) */
+} nnsemd_plan;
+
+typedef struct {
+  int64_t rounds;               /* NNS rounds run (Alg. 1 iterations); batched: summed over pairs */
+  int64_t pair_evals;           /* sum over rounds of m_t * n_t (the paper's NNS work, Thm. 3) */
+  double leftover_mass;         /* residual mass left on both sides (rounding only) */
+  int64_t certified;            /* reduced precision: consumer searches settled by the re-rank */
+  int64_t fallbacks;            /* reduced precision: consumer searches redone by the FP32 scan */
+  int64_t kernel_launches;      /* CUDA kernels this call launched */
+  double nns_kernel_ms;         /* NNSEMD_FLAG_TIME_KERNELS: summed duration of the multi-CTA NNS launches */
+  int64_t nns_kernel_launches;  /* number of those launches */
+  int64_t nns_kernel_pairs;     /* sum of m_t * n_t they evaluated */
+  double tail_kernel_ms;        /* NNSEMD_FLAG_TIME_KERNELS: duration of the one-CTA tail kernel */
+} nnsemd_stats;
+
+/* Create a context bound to cfg->device and cfg->stream.  *out receives the
+ * handle (NULL on failure).  cfg may be NULL (device 0, default stream). */
+int nnsemd_create(nnsemd_ctx **out, const nnsemd_config *cfg);
+
+/* Free the context and its workspace.  Waits for its stream.  NULL is a no-op. */
+int nnsemd_destroy(nnsemd_ctx *ctx);
+
+/* Re-bind the context to another stream of the same device. */
+int nnsemd_set_stream(nnsemd_ctx *ctx, void *stream);
+
+/* Solve one pair (Alg. 1, Sec. III-A).
+ *   x [m][d], a [m]: suppliers S (device); y [n][d], b [n]: consumers C (device).
+ *   1 <= d; d <= 8 runs on CUDA cores, larger d on the tiled / tensor-core path.
+ *   cost_out: HOST pointer receiving R; the call returns when R is known.
+ *   plan (nullable): device arrays i/j/f of plan->capacity entries; plan->nnz set.
+ *   stats (nullable, host): filled on return.
+ * Errors: INVALID_ARG (sizes, null or misaligned pointers, bad options),
+ * NONFINITE, ZERO_MASS, CAPACITY, UNSUPPORTED, CUDA, OOM, TIMEOUT. */
+int nnsemd_solve(nnsemd_ctx *ctx,
+                 const float *x, const double *a, int64_t m,
+                 const float *y, const double *b, int64_t n,
+                 int32_t d, const nnsemd_options *opt,
+                 double *cost_out, nnsemd_plan *plan, nnsemd_stats *stats);
+
+/* The same solve from HOST buffers: x, a, y, b and the plan arrays are host
+ * memory (pinned memory gives the fastest copies).  The inputs are copied to
+ * the context's device workspace, solved, and the plan copied back. */
+int nnsemd_solve_host(nnsemd_ctx *ctx,
+                      const float *x, const double *a, int64_t m,
+                      const float *y, const double *b, int64_t n,
+                      int32_t d, const nnsemd_options *opt,
+                      double *cost_out, nnsemd_plan *plan, nnsemd_stats *stats);
+
+/* Solve P independent pairs packed back to back (Sec. III-D, batch
+ * processing).  Pair p's suppliers are rows x_off[p] .. x_off[p+1]-1 of
+ * x_packed / a_packed, its consumers rows y_off[p] .. y_off[p+1]-1 of
+ * y_packed / b_packed.  x_off and y_off are HOST arrays of P+1 entries
+ * starting at 0; every pair needs >= 1 point on each side.  costs_out is a
+ * DEVICE array of P doubles.  The call is asynchronous on the context's
+ * stream unless stats is non-NULL (then it waits to fill stats). */
+int nnsemd_solve_batched(nnsemd_ctx *ctx, int32_t num_pairs,
+                         const float *x_packed, const double *a_packed, const int64_t *x_off,
+                         const float *y_packed, const double *b_packed, const int64_t *y_off,
+                         int32_t d, const nnsemd_options *opt,
+                         double *costs_out, nnsemd_stats *stats);
+
+/* Message for the last failure on ctx (never NULL; "" after success).  The
+ * string stays valid until the next call on ctx.  ctx may be NULL for
+ * failures of nnsemd_create. */
+const char *nnsemd_last_error(const nnsemd_ctx *ctx);
+
+/* Static name of a status code. */
+const char *nnsemd_status_string(int status);
+
+/* NNSEMD_ABI_VERSION of the loaded library. */
+int nnsemd_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NNSEMD_H */

@@ -1,0 +1,532 @@
+// C-ABI entry points of the NNS-EMD library (declared in include/nnsemd.h):
+// context and workspace management, argument checks, and the host-side
+// orchestration of the rounds of Alg. 1 (Sec. III-A).
+//
+// A single-pair solve runs
+//   setup    exact totals of a and b, normalisation (Sec. II-A), packing of
+//            the initial active sets (positive weight);
+//   rounds   while both active sets are larger than one CTA can hold: the
+//            multi-CTA round (K1 NNS, grouping, greedy flow, compaction);
+//   tail     once they fit, every remaining round in one CTA (k_finish);
+//   final    R and the leftover mass as correctly rounded sums.
+// The host reads the two active counts after each multi-CTA round (a few
+// bytes from pinned memory) to size the next round's grids.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "nnsemd.h"
+
+using namespace nnsemd;
+
+struct nnsemd_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  DevState* hstate = nullptr;  // pinned mirror of the device state
+  std::string err;
+  long long launches = 0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // kernel timing (NNSEMD_FLAG_TIME_KERNELS)
+};
+
+namespace {
+
+constexpr int64_t FIN_PAIRS = 1LL << 19;  // tail threshold on m_t * n_t
+thread_local std::string g_create_err;
+
+int fail(nnsemd_ctx* ctx, int status, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(nnsemd_ctx* ctx, int status, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  else g_create_err = buf;
+  return status;
+}
+
+int cuda_fail(nnsemd_ctx* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, NNSEMD_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
+  } while (0)
+
+// Bump allocator over the context workspace (256-byte aligned slices).
+struct Carve {
+  char* base;
+  size_t off = 0;
+  explicit Carve(void* b) : base((char*)b) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+int ensure_ws(nnsemd_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return NNSEMD_OK;
+  if (ctx->ws) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+  }
+  size_t want = bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(&ctx->ws, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->ws = nullptr;
+    return fail(ctx, NNSEMD_ERR_OOM, "workspace of %zu bytes: %s", want, cudaGetErrorString(e));
+  }
+  ctx->ws_bytes = want;
+  return NNSEMD_OK;
+}
+
+// Lay out the buffers of a single-pair solve; with base == nullptr only the
+// size is computed.
+size_t layout_solve(void* base, int64_t m, int64_t n, int d, SolveBufs& B) {
+  Carve C(base);
+  const int dp = padded_dim(d);
+  B.st = C.take<DevState>(1);
+  B.xs_acc = C.take<unsigned long long>(4 * XS_LIMBS);
+  B.s = C.take<double>(m);
+  B.c = C.take<double>(n);
+  for (int k = 0; k < 2; ++k) {
+    B.xa[k] = C.take<float>(pad_points(m) * dp);
+    B.ia[k] = C.take<int>(m);
+    B.ya[k] = C.take<float>(pad_points(n) * dp);
+    B.ja[k] = C.take<int>(n);
+  }
+  B.nnkey = C.take<unsigned long long>(n);
+  B.cnt = C.take<int>(m);
+  B.seg = C.take<int2>(m);
+  B.seglist = C.take<int>(m);
+  B.biglist = C.take<int>(m);
+  B.member = C.take<unsigned long long>(n);
+  B.terms = C.take<double>(m + n);
+  B.blockcounts = C.take<int>((m + n) / 1024 + 8);
+  return C.off + 256;
+}
+
+int map_err_bits(nnsemd_ctx* ctx, unsigned bits) {
+  if (!bits) return NNSEMD_OK;
+  if (bits & EF_NONFINITE) return fail(ctx, NNSEMD_ERR_NONFINITE, "a coordinate or weight is not finite");
+  if (bits & EF_NEGATIVE) return fail(ctx, NNSEMD_ERR_ZERO_MASS, "a weight is negative");
+  if (bits & EF_ZERO_MASS) return fail(ctx, NNSEMD_ERR_ZERO_MASS, "a side's weights sum to zero");
+  if (bits & EF_CAPACITY) return fail(ctx, NNSEMD_ERR_CAPACITY, "plan capacity too small");
+  if (bits & EF_TIMEOUT) return fail(ctx, NNSEMD_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (bits & EF_ITER) return fail(ctx, NNSEMD_ERR_ITER_LIMIT, "round limit m + n exceeded");
+  return fail(ctx, NNSEMD_ERR_CUDA, "internal consistency check failed on the device (0x%x)", bits);
+}
+
+int check_opts(nnsemd_ctx* ctx, const nnsemd_options* opt, int d, int& metric) {
+  metric = NNSEMD_L2;
+  if (opt) {
+    metric = opt->metric;
+    if (opt->flags & ~NNSEMD_FLAG_TIME_KERNELS) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "unknown options.flags bits");
+    if (opt->precision != NNSEMD_FP32) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "reduced precision needs d > 8");
+  }
+  if (metric < 0 || metric > 2) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "unknown metric %d", metric);
+  if (d < 1) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "d must be >= 1");
+  if (d > 8) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "d = %d: only d <= 8 is served", d);
+  return NNSEMD_OK;
+}
+
+// The device part of a single-pair solve on buffers that are already laid
+// out; writes R to *cost and fills the counters.
+int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, double* cost, int64_t* nnz,
+              nnsemd_stats* stats, int flags = 0) {
+  cudaStream_t st = ctx->stream;
+  long long L = 0;
+  const bool timed = (flags & NNSEMD_FLAG_TIME_KERNELS) != 0;
+  if (timed && !ctx->ev[0])
+    for (int k = 0; k < 4; ++k) CK(cudaEventCreate(&ctx->ev[k]));
+  double nns_ms = 0.0, tail_ms = 0.0;
+  long long nns_launches = 0, nns_pairs = 0;
+  bool tail_ran = false;
+  CK(cudaMemsetAsync(B.st, 0, sizeof(DevState), st));
+  CK(cudaMemsetAsync(B.xs_acc, 0, 4 * XS_LIMBS * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(B.cnt, 0, B.m * sizeof(int), st));
+  launch_xs_accum(a, B.m, B.xs_acc, &B.st->err, true, st);
+  launch_xs_accum(b, B.n, B.xs_acc + XS_LIMBS, &B.st->err, true, st);
+  launch_normalise(a, B.m, B.xs_acc, &B.st->total_a, B.s, &B.st->err, st);
+  launch_normalise(b, B.n, B.xs_acc + XS_LIMBS, &B.st->total_b, B.c, &B.st->err, st);
+  B.cur = 0;
+  launch_initial_pack(B, st);
+  L += 6;
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(ctx->hstate, B.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  int rc = map_err_bits(ctx, ctx->hstate->err);
+  if (rc) return rc;
+  int mt = ctx->hstate->mt, nt = ctx->hstate->nt;
+  long long rounds = 0, pair_evals = 0;
+  const long long round_limit = B.m + B.n;
+  while (mt > 0 && nt > 0) {
+    if (mt <= FIN_MAX && nt <= FIN_MAX && (int64_t)mt * nt <= FIN_PAIRS) {
+      if (timed) CK(cudaEventRecord(ctx->ev[2], st));
+      if (launch_finish(B, round_limit - rounds, st)) return fail(ctx, NNSEMD_ERR_CUDA, "finisher launch");
+      if (timed) CK(cudaEventRecord(ctx->ev[3], st));
+      tail_ran = true;
+      L += 1;
+      break;
+    }
+    if (rounds >= round_limit) return fail(ctx, NNSEMD_ERR_ITER_LIMIT, "round limit m + n exceeded");
+    CK(cudaMemsetAsync(B.nnkey, 0xff, (size_t)nt * sizeof(unsigned long long), st));
+    if (timed) CK(cudaEventRecord(ctx->ev[0], st));
+    if (launch_nns_lowd(B, mt, nt, st)) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "no NNS kernel for d=%d", B.d);
+    if (timed) CK(cudaEventRecord(ctx->ev[1], st));
+    launch_big_round(B, mt, nt, st);
+    L += 10;
+    CK(cudaGetLastError());
+    B.cur ^= 1;
+    rounds += 1;
+    pair_evals += (long long)mt * nt;
+    nns_launches += 1;
+    nns_pairs += (long long)mt * nt;
+    CK(cudaMemcpyAsync(ctx->hstate, B.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (timed) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
+      nns_ms += ms;
+    }
+    rc = map_err_bits(ctx, ctx->hstate->err);
+    if (rc) return rc;
+    mt = ctx->hstate->mt;
+    nt = ctx->hstate->nt;
+  }
+  launch_leftover(B, st);
+  L += 8;
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(ctx->hstate, B.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  rc = map_err_bits(ctx, ctx->hstate->err);
+  if (rc) return rc;
+  *cost = ctx->hstate->cost;
+  *nnz = (int64_t)ctx->hstate->nnz;
+  ctx->launches += L;
+  if (timed && tail_ran) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]));
+    tail_ms = ms;
+  }
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->rounds = rounds + ctx->hstate->rounds;
+    stats->pair_evals = pair_evals + ctx->hstate->pair_evals;
+    stats->leftover_mass = ctx->hstate->leftover;
+    stats->kernel_launches = L;
+    stats->nns_kernel_ms = nns_ms;
+    stats->nns_kernel_launches = nns_launches;
+    stats->nns_kernel_pairs = nns_pairs;
+    stats->tail_kernel_ms = tail_ms;
+  }
+  return NNSEMD_OK;
+}
+
+int check_sizes(nnsemd_ctx* ctx, int64_t m, int64_t n) {
+  if (m < 1 || n < 1) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "m and n must be >= 1 (m=%lld n=%lld)",
+                                  (long long)m, (long long)n);
+  if (m > (1LL << 30) || n > (1LL << 30)) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "m or n above 2^30");
+  return NNSEMD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nnsemd_create(nnsemd_ctx** out, const nnsemd_config* cfg) {
+  if (!out) return fail(nullptr, NNSEMD_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  nnsemd_ctx* ctx = new (std::nothrow) nnsemd_ctx();
+  if (!ctx) return fail(nullptr, NNSEMD_ERR_OOM, "context allocation");
+  ctx->device = cfg ? cfg->device : 0;
+  ctx->stream = cfg ? (cudaStream_t)cfg->stream : nullptr;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e == cudaSuccess) e = cudaMallocHost(&ctx->hstate, sizeof(DevState));
+  if (e != cudaSuccess) {
+    int rc = fail(nullptr, NNSEMD_ERR_CUDA, "device %d: %s", ctx->device, cudaGetErrorString(e));
+    delete ctx;
+    return rc;
+  }
+  if (cfg && cfg->workspace_bytes_hint) {
+    int rc = ensure_ws(ctx, cfg->workspace_bytes_hint);
+    if (rc) {
+      g_create_err = ctx->err;
+      cudaFreeHost(ctx->hstate);
+      delete ctx;
+      return rc;
+    }
+  }
+  *out = ctx;
+  return NNSEMD_OK;
+}
+
+int nnsemd_destroy(nnsemd_ctx* ctx) {
+  if (!ctx) return NNSEMD_OK;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->hstate) cudaFreeHost(ctx->hstate);
+  for (cudaEvent_t e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  delete ctx;
+  return NNSEMD_OK;
+}
+
+int nnsemd_set_stream(nnsemd_ctx* ctx, void* stream) {
+  if (!ctx) return NNSEMD_ERR_INVALID_ARG;
+  ctx->stream = (cudaStream_t)stream;
+  return NNSEMD_OK;
+}
+
+int nnsemd_solve(nnsemd_ctx* ctx, const float* x, const double* a, int64_t m, const float* y, const double* b,
+                 int64_t n, int32_t d, const nnsemd_options* opt, double* cost_out, nnsemd_plan* plan,
+                 nnsemd_stats* stats) {
+  if (!ctx) return NNSEMD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  int metric;
+  int rc = check_opts(ctx, opt, d, metric);
+  if (rc) return rc;
+  if ((rc = check_sizes(ctx, m, n))) return rc;
+  if (!x || !a || !y || !b || !cost_out) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "null pointer argument");
+  if (((uintptr_t)x & 3) || ((uintptr_t)y & 3) || ((uintptr_t)a & 7) || ((uintptr_t)b & 7))
+    return fail(ctx, NNSEMD_ERR_INVALID_ARG, "misaligned input pointer");
+  if (plan && (!plan->i || !plan->j || !plan->f || plan->capacity < 0))
+    return fail(ctx, NNSEMD_ERR_INVALID_ARG, "plan arrays");
+  CK(cudaSetDevice(ctx->device));
+  SolveBufs B{};
+  size_t bytes = layout_solve(nullptr, m, n, d, B);
+  if ((rc = ensure_ws(ctx, bytes))) return rc;
+  layout_solve(ctx->ws, m, n, d, B);
+  B.x = x;
+  B.y = y;
+  B.m = m;
+  B.n = n;
+  B.d = d;
+  B.dp = padded_dim(d);
+  B.metric = metric;
+  B.plan_i = plan ? plan->i : nullptr;
+  B.plan_j = plan ? plan->j : nullptr;
+  B.plan_f = plan ? plan->f : nullptr;
+  B.plan_cap = plan ? plan->capacity : 0;
+  int64_t nnz = 0;
+  rc = run_solve(ctx, B, a, b, cost_out, &nnz, stats, opt ? opt->flags : 0);
+  if (plan) plan->nnz = rc ? 0 : nnz;
+  return rc;
+}
+
+int nnsemd_solve_host(nnsemd_ctx* ctx, const float* x, const double* a, int64_t m, const float* y,
+                      const double* b, int64_t n, int32_t d, const nnsemd_options* opt, double* cost_out,
+                      nnsemd_plan* plan, nnsemd_stats* stats) {
+  if (!ctx) return NNSEMD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  int metric;
+  int rc = check_opts(ctx, opt, d, metric);
+  if (rc) return rc;
+  if ((rc = check_sizes(ctx, m, n))) return rc;
+  if (!x || !a || !y || !b || !cost_out) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "null pointer argument");
+  if (plan && (!plan->i || !plan->j || !plan->f || plan->capacity < 0))
+    return fail(ctx, NNSEMD_ERR_INVALID_ARG, "plan arrays");
+  CK(cudaSetDevice(ctx->device));
+  // device staging for the inputs and the plan, placed after the solve buffers
+  SolveBufs B{};
+  size_t solve_bytes = layout_solve(nullptr, m, n, d, B);
+  const int64_t cap = plan ? std::min<int64_t>(plan->capacity, m + n) : 0;
+  auto stage_layout = [&](void* base, float** xd, double** ad, float** yd, double** bd, int32_t** pi, int32_t** pj,
+                          double** pf) {
+    Carve C(base);
+    C.off = solve_bytes;
+    *xd = C.take<float>((size_t)m * d);
+    *ad = C.take<double>(m);
+    *yd = C.take<float>((size_t)n * d);
+    *bd = C.take<double>(n);
+    *pi = C.take<int32_t>(cap);
+    *pj = C.take<int32_t>(cap);
+    *pf = C.take<double>(cap);
+    return C.off + 256;
+  };
+  float *xd, *yd;
+  double *ad, *bd, *pf;
+  int32_t *pi, *pj;
+  size_t bytes = stage_layout(nullptr, &xd, &ad, &yd, &bd, &pi, &pj, &pf);
+  if ((rc = ensure_ws(ctx, bytes))) return rc;
+  layout_solve(ctx->ws, m, n, d, B);
+  stage_layout(ctx->ws, &xd, &ad, &yd, &bd, &pi, &pj, &pf);
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemcpyAsync(xd, x, (size_t)m * d * sizeof(float), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ad, a, (size_t)m * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(yd, y, (size_t)n * d * sizeof(float), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(bd, b, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st));
+  B.x = xd;
+  B.y = yd;
+  B.m = m;
+  B.n = n;
+  B.d = d;
+  B.dp = padded_dim(d);
+  B.metric = metric;
+  B.plan_i = plan ? pi : nullptr;
+  B.plan_j = plan ? pj : nullptr;
+  B.plan_f = plan ? pf : nullptr;
+  B.plan_cap = cap;
+  int64_t nnz = 0;
+  rc = run_solve(ctx, B, ad, bd, cost_out, &nnz, stats, opt ? opt->flags : 0);
+  if (rc) {
+    if (plan) plan->nnz = 0;
+    return rc;
+  }
+  if (plan) {
+    if (nnz > plan->capacity) return fail(ctx, NNSEMD_ERR_CAPACITY, "plan capacity too small");
+    CK(cudaMemcpyAsync(plan->i, pi, (size_t)nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(plan->j, pj, (size_t)nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(plan->f, pf, (size_t)nnz * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    plan->nnz = nnz;
+  }
+  return NNSEMD_OK;
+}
+
+int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_packed, const double* a_packed,
+                         const int64_t* x_off, const float* y_packed, const double* b_packed, const int64_t* y_off,
+                         int32_t d, const nnsemd_options* opt, double* costs_out, nnsemd_stats* stats) {
+  if (!ctx) return NNSEMD_ERR_INVALID_ARG;
+  ctx->err.clear();
+  int metric;
+  int rc = check_opts(ctx, opt, d, metric);
+  if (rc) return rc;
+  if (num_pairs < 0) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "num_pairs < 0");
+  if (num_pairs == 0) {
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    return NNSEMD_OK;
+  }
+  if (!x_packed || !a_packed || !x_off || !y_packed || !b_packed || !y_off || !costs_out)
+    return fail(ctx, NNSEMD_ERR_INVALID_ARG, "null pointer argument");
+  if (x_off[0] != 0 || y_off[0] != 0) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "offsets must start at 0");
+  std::vector<int> small, large;
+  for (int p = 0; p < num_pairs; ++p) {
+    const int64_t m = x_off[p + 1] - x_off[p], n = y_off[p + 1] - y_off[p];
+    if (m < 1 || n < 1) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "pair %d has an empty side", p);
+    ((m <= FIN_MAX && n <= FIN_MAX) ? small : large).push_back(p);
+  }
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  // workspace: offsets, pair list, queue, per-pair counters, error word
+  Carve C(nullptr);
+  C.take<int64_t>(num_pairs + 1);
+  C.take<int64_t>(num_pairs + 1);
+  C.take<int>(small.size() + 1);
+  C.take<unsigned>(4);
+  C.take<long long>(num_pairs);
+  C.take<long long>(num_pairs);
+  const size_t head = (C.off + 511) & ~(size_t)255;  // keeps the solve buffers 256-byte aligned
+  size_t bytes = head;
+  int64_t maxm = 0, maxn = 0;
+  for (int p : large) {
+    maxm = std::max(maxm, x_off[p + 1] - x_off[p]);
+    maxn = std::max(maxn, y_off[p + 1] - y_off[p]);
+  }
+  SolveBufs B{};
+  if (!large.empty()) bytes += layout_solve(nullptr, maxm, maxn, d, B);
+  if ((rc = ensure_ws(ctx, bytes))) return rc;
+  Carve W(ctx->ws);
+  int64_t* xo_d = W.take<int64_t>(num_pairs + 1);
+  int64_t* yo_d = W.take<int64_t>(num_pairs + 1);
+  int* ids_d = W.take<int>(small.size() + 1);
+  unsigned* q_d = W.take<unsigned>(4);
+  long long* rounds_d = W.take<long long>(num_pairs);
+  long long* pe_d = W.take<long long>(num_pairs);
+  CK(cudaMemcpyAsync(xo_d, x_off, (num_pairs + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(yo_d, y_off, (num_pairs + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  if (!small.empty())
+    CK(cudaMemcpyAsync(ids_d, small.data(), small.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(q_d, 0, 4 * sizeof(unsigned), st));
+  CK(cudaMemsetAsync(rounds_d, 0, num_pairs * sizeof(long long), st));
+  CK(cudaMemsetAsync(pe_d, 0, num_pairs * sizeof(long long), st));
+  long long L = 0;
+  if (!small.empty()) {
+    BatchArgs A{x_packed, a_packed, xo_d, y_packed, b_packed, yo_d, ids_d, (int)small.size(), d, metric,
+                costs_out, rounds_d, pe_d, q_d, q_d + 1};
+    const int grid = (int)std::min<size_t>(small.size(), 152);
+    if (launch_batched_lowd(A, grid, st)) return fail(ctx, NNSEMD_ERR_CUDA, "batched launch");
+    CK(cudaGetLastError());
+    L += 1;
+  }
+  long long extra_rounds = 0, extra_pe = 0;
+  for (int p : large) {
+    layout_solve((char*)ctx->ws + head, maxm, maxn, d, B);
+    B.x = x_packed + x_off[p] * d;
+    B.y = y_packed + y_off[p] * d;
+    B.m = x_off[p + 1] - x_off[p];
+    B.n = y_off[p + 1] - y_off[p];
+    B.d = d;
+    B.dp = padded_dim(d);
+    B.metric = metric;
+    double cost = 0;
+    int64_t nnz = 0;
+    nnsemd_stats s1{};
+    rc = run_solve(ctx, B, a_packed + x_off[p], b_packed + y_off[p], &cost, &nnz, &s1);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(costs_out + p, &B.st->cost, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    extra_rounds += s1.rounds;
+    extra_pe += s1.pair_evals;
+    L += s1.kernel_launches;
+  }
+  ctx->launches += L;
+  if (stats) {
+    unsigned err = 0;
+    std::vector<long long> r(num_pairs), pe(num_pairs);
+    CK(cudaMemcpyAsync(&err, q_d + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(r.data(), rounds_d, num_pairs * sizeof(long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(pe.data(), pe_d, num_pairs * sizeof(long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if ((rc = map_err_bits(ctx, err))) return rc;
+    std::memset(stats, 0, sizeof(*stats));
+    for (int p : small) {
+      stats->rounds += r[p];
+      stats->pair_evals += pe[p];
+    }
+    stats->rounds += extra_rounds;
+    stats->pair_evals += extra_pe;
+    stats->kernel_launches = L;
+  }
+  return NNSEMD_OK;
+}
+
+const char* nnsemd_last_error(const nnsemd_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+const char* nnsemd_status_string(int status) {
+  switch (status) {
+    case NNSEMD_OK: return "NNSEMD_OK";
+    case NNSEMD_ERR_INVALID_ARG: return "NNSEMD_ERR_INVALID_ARG";
+    case NNSEMD_ERR_NONFINITE: return "NNSEMD_ERR_NONFINITE";
+    case NNSEMD_ERR_ZERO_MASS: return "NNSEMD_ERR_ZERO_MASS";
+    case NNSEMD_ERR_CUDA: return "NNSEMD_ERR_CUDA";
+    case NNSEMD_ERR_OOM: return "NNSEMD_ERR_OOM";
+    case NNSEMD_ERR_TIMEOUT: return "NNSEMD_ERR_TIMEOUT";
+    case NNSEMD_ERR_ITER_LIMIT: return "NNSEMD_ERR_ITER_LIMIT";
+    case NNSEMD_ERR_UNSUPPORTED: return "NNSEMD_ERR_UNSUPPORTED";
+    case NNSEMD_ERR_CAPACITY: return "NNSEMD_ERR_CAPACITY";
+    default: return "NNSEMD_ERR_UNKNOWN";
+  }
+}
+
+int nnsemd_abi_version(void) { return NNSEMD_ABI_VERSION; }
+
+}  // extern "C"

@@ -1,0 +1,255 @@
+// Device-side building blocks shared by the NNS-EMD kernels (sm_103a).
+//
+//  * the FP32 decision distance and the FP64 cost distance, each with one
+//    fixed operation order (intrinsics only, so nothing is re-associated or
+//    contracted by the compiler);
+//  * an exact accumulator for sums of non-negative doubles, used for the
+//    normalisation totals (Sec. II-A) and for R = sum f * D_ij (Alg. 1), so
+//    both are correctly rounded whatever the order of accumulation;
+//  * thin wrappers over mbarrier and the 1-D TMA bulk copy, with bounded
+//    waits that raise an error flag instead of hanging.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define NNS_DEV __device__ __forceinline__
+
+namespace nnsemd {
+
+enum Metric : int { METRIC_L2 = 0, METRIC_SQL2 = 1, METRIC_L1 = 2 };
+
+// Error bits raised on the device and read by the host after a call.
+enum ErrFlag : unsigned {
+  EF_NONFINITE = 1u,
+  EF_NEGATIVE = 2u,
+  EF_TIMEOUT = 4u,
+  EF_CAPACITY = 8u,
+  EF_ITER = 16u,
+  EF_INTERNAL = 32u,
+  EF_ZERO_MASS = 64u,
+};
+
+// Per-solve state in device memory; the host reads it through a pinned copy.
+struct DevState {
+  int mt, nt;                    // active supplier / consumer counts (written by compaction)
+  unsigned long long nnz;        // flows (plan entries, cost terms) written
+  unsigned err;                  // ErrFlag bits
+  int nseg;                      // non-empty supplier groups this round
+  int nbig;                      // groups longer than a warp this round
+  unsigned seg_cursor;           // member slots handed out this round
+  long long rounds;              // rounds run on the device (finisher)
+  long long pair_evals;          // sum of m_t * n_t over device-run rounds
+  double total_a, total_b;       // normalisation totals (correctly rounded)
+  double cost;                   // R (correctly rounded)
+  double leftover;               // residual mass after the solve
+};
+
+// --------------------------------------------------------------------------
+// distances
+// --------------------------------------------------------------------------
+
+// FP32 decision key: squared Euclidean for L2 / SQL2, L1 sum for L1.
+// t_k = x_k - y_k; acc = t_0 * t_0; acc = fma(t_k, t_k, acc) (k ascending).
+template <int METRIC>
+NNS_DEV float key32(const float* x, const float* y, int d) {
+  if (METRIC == METRIC_L1) {
+    float acc = fabsf(__fsub_rn(x[0], y[0]));
+    for (int k = 1; k < d; ++k) acc = __fadd_rn(acc, fabsf(__fsub_rn(x[k], y[k])));
+    return acc;
+  }
+  float t = __fsub_rn(x[0], y[0]);
+  float acc = __fmul_rn(t, t);
+  for (int k = 1; k < d; ++k) {
+    float u = __fsub_rn(x[k], y[k]);
+    acc = __fmaf_rn(u, u, acc);
+  }
+  return acc;
+}
+
+// FP64 ground distance D_ij of the cost: the same steps in double, sqrt for L2.
+NNS_DEV double cost_dist64(const float* x, const float* y, int d, int metric) {
+  double acc;
+  if (metric == METRIC_L1) {
+    acc = fabs(__dsub_rn((double)x[0], (double)y[0]));
+    for (int k = 1; k < d; ++k) acc = __dadd_rn(acc, fabs(__dsub_rn((double)x[k], (double)y[k])));
+    return acc;
+  }
+  double t = __dsub_rn((double)x[0], (double)y[0]);
+  acc = __dmul_rn(t, t);
+  for (int k = 1; k < d; ++k) {
+    double u = __dsub_rn((double)x[k], (double)y[k]);
+    acc = __fma_rn(u, u, acc);
+  }
+  return metric == METRIC_L2 ? __dsqrt_rn(acc) : acc;
+}
+
+// Greedy-order and argmin key: (float bits of the FP32 key) << 32 | index.
+// Non-negative floats order like their bit patterns, so a 64-bit unsigned
+// minimum picks the smallest distance and then the smallest index.
+NNS_DEV unsigned long long pack_key(float k, unsigned idx) {
+  return ((unsigned long long)__float_as_uint(k) << 32) | idx;
+}
+
+// --------------------------------------------------------------------------
+// exact sum of non-negative finite doubles
+//
+// A double v = M * 2^(E-1075) (M < 2^53) is M << (E-1) in units of 2^-1074.
+// That integer is split into 32-bit digits and added into 64-bit limbs
+// (limb L holds digit weight 2^(32L) * 2^-1074); 64-bit limbs absorb 2^32
+// additions of 32-bit digits without overflow.  The final carry propagation
+// and round-to-nearest-even run in one thread.
+// --------------------------------------------------------------------------
+
+constexpr int XS_LIMBS = 68;
+
+NNS_DEV void xs_digits(double v, int& limb, unsigned long long& c0, unsigned long long& c1,
+                       unsigned long long& c2) {
+  unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  int e = (int)((bits >> 52) & 0x7ff);
+  unsigned long long mant = bits & 0xfffffffffffffULL;
+  if (e) mant |= 1ULL << 52; else e = 1;
+  int b = e - 1;
+  limb = b >> 5;
+  int sh = b & 31;
+  unsigned long long lo = mant << sh;
+  unsigned long long hi = sh ? (mant >> (64 - sh)) : 0ULL;
+  c0 = lo & 0xffffffffULL;
+  c1 = lo >> 32;
+  c2 = hi;
+}
+
+// Add v (>= 0, finite) into an accumulator (shared or global memory).
+NNS_DEV void xs_add(unsigned long long* acc, double v) {
+  if (!(v > 0.0)) return;
+  int L;
+  unsigned long long c0, c1, c2;
+  xs_digits(v, L, c0, c1, c2);
+  if (c0) atomicAdd(acc + L, c0);
+  if (c1) atomicAdd(acc + L + 1, c1);
+  if (c2) atomicAdd(acc + L + 2, c2);
+}
+
+NNS_DEV unsigned long long xs_limb(const unsigned long long* a, int L) {
+  return (L >= 0 && L < XS_LIMBS) ? a[L] : 0ULL;
+}
+
+// 64 bits of the normalised accumulator starting at bit position pos.
+NNS_DEV unsigned long long xs_bits64(const unsigned long long* a, int pos) {
+  int L = pos >> 5, r = pos & 31;
+  unsigned long long lo = xs_limb(a, L) | (xs_limb(a, L + 1) << 32);
+  unsigned long long hi = xs_limb(a, L + 2) | (xs_limb(a, L + 3) << 32);
+  return r ? ((lo >> r) | (hi << (64 - r))) : lo;
+}
+
+// Correctly rounded value of the accumulator (single thread; a is modified).
+NNS_DEV double xs_round(unsigned long long* a) {
+  unsigned long long carry = 0;
+  for (int L = 0; L < XS_LIMBS; ++L) {
+    unsigned long long v = a[L] + carry;
+    a[L] = v & 0xffffffffULL;
+    carry = v >> 32;
+  }
+  int top = -1;
+  for (int L = XS_LIMBS - 1; L >= 0; --L)
+    if (a[L]) { top = L * 32 + (63 - __clzll((long long)a[L])); break; }
+  if (top < 0) return 0.0;
+  if (top <= 52) return __longlong_as_double((long long)xs_bits64(a, 0));
+  int shift = top - 52;
+  unsigned long long mant = xs_bits64(a, shift) & ((1ULL << 53) - 1);
+  int rpos = shift - 1;
+  unsigned long long round = (xs_bits64(a, rpos) & 1ULL);
+  bool sticky = false;
+  int Lr = rpos >> 5;
+  for (int L = 0; L < Lr && !sticky; ++L) sticky = a[L] != 0;
+  if (!sticky && (rpos & 31)) sticky = (a[Lr] & ((1ULL << (rpos & 31)) - 1)) != 0;
+  if (round && (sticky || (mant & 1ULL))) {
+    ++mant;
+    if (mant >> 53) { mant >>= 1; ++shift; }
+  }
+  int E = shift + 1;
+  if (E >= 2047) return __longlong_as_double(0x7ff0000000000000LL);
+  return __longlong_as_double((long long)(((unsigned long long)E << 52) | (mant & ((1ULL << 52) - 1))));
+}
+
+// --------------------------------------------------------------------------
+// mbarrier + 1-D bulk copy (TMA) helpers
+// --------------------------------------------------------------------------
+
+NNS_DEV unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+NNS_DEV void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+NNS_DEV void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+NNS_DEV void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+NNS_DEV bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for a phase with an iteration limit; returns false if it gave up.
+NNS_DEV bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned limit = 1u << 22) {
+  for (unsigned it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from
+// global to this CTA's shared memory, completing on `bar`.
+NNS_DEV void tma_load_1d(void* dst_smem, const void* src_gmem, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst_smem)),
+      "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// --------------------------------------------------------------------------
+// packed FP32x2 arithmetic (sm_100+): two IEEE single-precision operations
+// per instruction, lane-wise identical to the scalar _rn intrinsics.
+// --------------------------------------------------------------------------
+
+NNS_DEV unsigned long long f2_pack(float lo, float hi) {
+  return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+NNS_DEV float f2_lo(unsigned long long v) { return __uint_as_float((unsigned)(v & 0xffffffffULL)); }
+NNS_DEV float f2_hi(unsigned long long v) { return __uint_as_float((unsigned)(v >> 32)); }
+
+NNS_DEV unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+NNS_DEV unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+NNS_DEV unsigned long long f2_fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+NNS_DEV float fmin3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+}  // namespace nnsemd

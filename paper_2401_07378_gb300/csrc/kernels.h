@@ -1,0 +1,87 @@
+// Host-side launchers of the NNS-EMD kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace nnsemd {
+
+// Supplier tile staged in shared memory by K1, and the granularity every
+// packed active list is padded to (with NaN coordinates) so that a tile
+// never reads past its buffer.
+constexpr int K1_TS = 256;
+constexpr int PAD_POINTS = K1_TS;
+// Largest active set the single-CTA solver keeps in shared memory.
+constexpr int FIN_MAX = 1024;
+
+__host__ __device__ inline int padded_dim(int d) { return d <= 2 ? 2 : (d <= 4 ? 4 : 8); }
+__host__ __device__ inline int64_t pad_points(int64_t n) { return (n + PAD_POINTS - 1) / PAD_POINTS * PAD_POINTS; }
+
+// Buffers of one single-pair solve (device pointers inside the workspace).
+struct SolveBufs {
+  const float* x;  // original coordinates [m][d]
+  const float* y;  // [n][d]
+  int64_t m, n;
+  int d, dp, metric;
+  double* s;       // residual supplier weights [m] (original index)
+  double* c;       // residual consumer weights [n]
+  float* xa[2];    // packed active supplier coordinates [pad(m)][dp]
+  int* ia[2];      // their original indices
+  float* ya[2];
+  int* ja[2];
+  int cur;         // which of the double buffers is current
+  unsigned long long* nnkey;  // [n] per active consumer: key32 bits << 32 | supplier position
+  int* cnt;        // [m] consumers per supplier position
+  int2* seg;       // [m] (offset, length) of each supplier's group
+  int* seglist;    // [m] non-empty groups
+  int* biglist;    // [m] groups longer than a warp
+  unsigned long long* member;  // [n] group members: key32 bits << 32 | consumer position
+  double* terms;   // [m+n] per-flow cost terms f * D_ij
+  int* blockcounts;            // compaction scratch
+  unsigned long long* xs_acc;  // 4 exact-sum accumulators of XS_LIMBS limbs
+  DevState* st;
+  // caller's plan arrays (nullable) and capacity
+  int32_t* plan_i;
+  int32_t* plan_j;
+  double* plan_f;
+  int64_t plan_cap;
+};
+
+// setup.cu / rounds.cu ----------------------------------------------------
+void launch_xs_clear(unsigned long long* acc, int count, cudaStream_t st);
+void launch_xs_accum(const double* v, int64_t n, unsigned long long* acc, unsigned* err, bool check,
+                     cudaStream_t st);
+// total = round(acc); if (w) out[i] = w[i] / total (0 if total == 0 -> EF_ZERO_MASS)
+void launch_normalise(const double* w, int64_t n, unsigned long long* acc, double* total, double* out,
+                      unsigned* err, cudaStream_t st);
+void launch_xs_round(unsigned long long* acc, double* out, cudaStream_t st);
+// sum of residuals (leftover mass) into st->leftover
+void launch_leftover(const SolveBufs& B, cudaStream_t st);
+// Initial packing of both sides: active = positive weight, coordinates checked.
+int launch_initial_pack(SolveBufs& B, cudaStream_t st);
+// One multi-CTA round on the current active lists (mt, nt known on the host).
+int launch_big_round(SolveBufs& B, int mt, int nt, cudaStream_t st);
+
+// lowd.cu ------------------------------------------------------------------
+int launch_nns_lowd(const SolveBufs& B, int mt, int nt, cudaStream_t st);
+// Run all remaining rounds of the current active lists in one CTA.
+int launch_finish(const SolveBufs& B, int64_t round_limit, cudaStream_t st);
+
+// Batched small pairs (all in one persistent launch), low d.
+struct BatchArgs {
+  const float* x; const double* a; const int64_t* x_off;
+  const float* y; const double* b; const int64_t* y_off;
+  const int* pair_ids;   // pairs handled by the CTA solver
+  int num;               // number of entries in pair_ids
+  int d, metric;
+  double* costs;         // [P]
+  long long* rounds;     // [P] rounds per pair (nullable)
+  long long* pair_evals; // [P] (nullable)
+  unsigned* queue;       // work-queue counter (device, zeroed)
+  unsigned* err;
+};
+int launch_batched_lowd(const BatchArgs& A, int grid, cudaStream_t st);
+
+}  // namespace nnsemd

@@ -1,0 +1,615 @@
+// Low-dimension (d <= 8) NNS-EMD kernels for sm_103a.
+//
+// K1  k_nns_lowd   -- the NNS operation of Alg. 1 (Sec. III-A) over the
+//                     active sets, fused distance + argmin.  Supplier tiles
+//                     are staged in shared memory by 1-D TMA bulk copies
+//                     (double-buffered on mbarriers); each thread keeps P
+//                     consumers in registers and evaluates two of them per
+//                     packed FP32x2 instruction.  The argmin runs on groups
+//                     of 8 suppliers (3-input min), and the winning group is
+//                     re-scanned once at the end to recover the lowest index
+//                     attaining the minimum.  Partial results of different
+//                     supplier chunks merge through a 64-bit atomicMin on
+//                     (key bits, position), which keeps the lowest-index
+//                     tie-break.
+// cta_rounds       -- all steps of a round (NNS, grouping, greedy flow,
+//                     weights update, compaction) for active sets of at most
+//                     FIN_MAX points per side, entirely in one CTA's shared
+//                     memory.  Used for the tail rounds of a large solve and,
+//                     one pair per CTA, for batches of small pairs (Sec. III-D
+//                     batch processing).
+#include <math_constants.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace nnsemd {
+
+// --------------------------------------------------------------------------
+// K1: fused FP32 distance + argmin, d <= 8
+// --------------------------------------------------------------------------
+
+constexpr int K1_THREADS = 256;
+// consumers per thread (two per packed register): fewer at larger d so that
+// the consumer coordinates stay in registers
+__host__ __device__ constexpr int k1_p(int D) { return D <= 3 ? 8 : 4; }
+
+template <int D, int DP, bool L1>
+__global__ void __launch_bounds__(K1_THREADS, 2)
+    k_nns_lowd(const float* __restrict__ xa, int mt, int chunk, const float* __restrict__ ya, int nt,
+               unsigned long long* __restrict__ nnkey, unsigned* __restrict__ err) {
+  static_assert(K1_TS % 8 == 0, "tile must hold whole groups");
+  constexpr int K1_P = k1_p(D);
+  __shared__ __align__(128) float tile[2][K1_TS * DP];
+  __shared__ __align__(8) uint64_t bar[2];
+
+  const int tid = threadIdx.x;
+  const int q0 = blockIdx.x * (K1_THREADS * K1_P);
+  const int p0 = blockIdx.y * chunk;
+  const int p1 = min(p0 + chunk, mt);
+  if (p0 >= p1) return;
+
+  // this thread's consumers, packed two per 64-bit register
+  unsigned long long yy[K1_P / 2][D];
+#pragma unroll
+  for (int c = 0; c < K1_P / 2; ++c) {
+    const int qa = q0 + (2 * c) * K1_THREADS + tid;
+    const int qb = q0 + (2 * c + 1) * K1_THREADS + tid;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      float va = qa < nt ? ya[(size_t)qa * DP + k] : 0.f;
+      float vb = qb < nt ? ya[(size_t)qb * DP + k] : 0.f;
+      yy[c][k] = f2_pack(va, vb);
+    }
+  }
+  float best[K1_P];
+  int bestg[K1_P];
+#pragma unroll
+  for (int c = 0; c < K1_P; ++c) { best[c] = CUDART_INF_F; bestg[c] = -1; }
+
+  const int ntile = (p1 - p0 + K1_TS - 1) / K1_TS;
+  const unsigned bytes = K1_TS * DP * sizeof(float);
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    mbar_expect_tx(&bar[0], bytes);
+    tma_load_1d(tile[0], xa + (size_t)p0 * DP, bytes, &bar[0]);
+  }
+  bool ok = true;
+  for (int t = 0; t < ntile; ++t) {
+    const int buf = t & 1;
+    if (tid == 0 && t + 1 < ntile) {
+      mbar_expect_tx(&bar[buf ^ 1], bytes);
+      tma_load_1d(tile[buf ^ 1], xa + (size_t)(p0 + (t + 1) * K1_TS) * DP, bytes, &bar[buf ^ 1]);
+    }
+    if (ok) ok = mbar_wait_bounded(&bar[buf], (t >> 1) & 1);
+    if (ok) {
+      const int base = p0 + t * K1_TS;
+      const int ng = (min(p1, base + K1_TS) - base + 7) >> 3;
+      const float* xt = tile[buf];
+      for (int g = 0; g < ng; ++g) {
+        float gmin[K1_P];
+#pragma unroll
+        for (int c = 0; c < K1_P; ++c) gmin[c] = CUDART_INF_F;
+#pragma unroll
+        for (int s = 0; s < 8; s += 2) {
+          float xv0[DP], xv1[DP];
+#pragma unroll
+          for (int k = 0; k < DP; ++k) {
+            xv0[k] = xt[(g * 8 + s) * DP + k];
+            xv1[k] = xt[(g * 8 + s + 1) * DP + k];
+          }
+#pragma unroll
+          for (int c = 0; c < K1_P / 2; ++c) {
+            float da0, db0, da1, db1;
+            if (L1) {
+              unsigned long long t0 = f2_sub(f2_pack(xv0[0], xv0[0]), yy[c][0]);
+              unsigned long long u0 = f2_sub(f2_pack(xv1[0], xv1[0]), yy[c][0]);
+              da0 = fabsf(f2_lo(t0)); db0 = fabsf(f2_hi(t0));
+              da1 = fabsf(f2_lo(u0)); db1 = fabsf(f2_hi(u0));
+#pragma unroll
+              for (int k = 1; k < D; ++k) {
+                unsigned long long tk = f2_sub(f2_pack(xv0[k], xv0[k]), yy[c][k]);
+                unsigned long long uk = f2_sub(f2_pack(xv1[k], xv1[k]), yy[c][k]);
+                da0 = __fadd_rn(da0, fabsf(f2_lo(tk))); db0 = __fadd_rn(db0, fabsf(f2_hi(tk)));
+                da1 = __fadd_rn(da1, fabsf(f2_lo(uk))); db1 = __fadd_rn(db1, fabsf(f2_hi(uk)));
+              }
+            } else {
+              unsigned long long t0 = f2_sub(f2_pack(xv0[0], xv0[0]), yy[c][0]);
+              unsigned long long u0 = f2_sub(f2_pack(xv1[0], xv1[0]), yy[c][0]);
+              unsigned long long acc0 = f2_mul(t0, t0);
+              unsigned long long acc1 = f2_mul(u0, u0);
+#pragma unroll
+              for (int k = 1; k < D; ++k) {
+                unsigned long long tk = f2_sub(f2_pack(xv0[k], xv0[k]), yy[c][k]);
+                unsigned long long uk = f2_sub(f2_pack(xv1[k], xv1[k]), yy[c][k]);
+                acc0 = f2_fma(tk, tk, acc0);
+                acc1 = f2_fma(uk, uk, acc1);
+              }
+              da0 = f2_lo(acc0); db0 = f2_hi(acc0);
+              da1 = f2_lo(acc1); db1 = f2_hi(acc1);
+            }
+            gmin[2 * c] = fmin3(gmin[2 * c], da0, da1);
+            gmin[2 * c + 1] = fmin3(gmin[2 * c + 1], db0, db1);
+          }
+        }
+        const int G = (base >> 3) + g;
+#pragma unroll
+        for (int c = 0; c < K1_P; ++c) {
+          if (gmin[c] < best[c]) { best[c] = gmin[c]; bestg[c] = G; }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (__syncthreads_or(!ok)) {
+    // a copy never landed: give the last copy of each buffer a bounded
+    // chance to complete before the CTA exits, then report
+    if (tid == 0) {
+      for (int b = 0; b < 2 && b < ntile; ++b) {
+        const int uses = (ntile - b + 1) / 2;
+        mbar_wait_bounded(&bar[b], (unsigned)(uses - 1) & 1);
+      }
+      atomicOr(err, EF_TIMEOUT);
+    }
+    return;
+  }
+
+  // resolve the lowest position inside the winning group and merge
+#pragma unroll
+  for (int c = 0; c < K1_P; ++c) {
+    const int q = q0 + c * K1_THREADS + tid;
+    if (q >= nt) continue;
+    float yv[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) yv[k] = (c & 1) ? f2_hi(yy[c >> 1][k]) : f2_lo(yy[c >> 1][k]);
+    unsigned long long key;
+    if (bestg[c] >= 0) {
+      const float* xg = xa + (size_t)bestg[c] * 8 * DP;
+      int kk = 0;
+      for (int s = 0; s < 8; ++s) {
+        float v = L1 ? key32<METRIC_L1>(xg + s * DP, yv, D) : key32<METRIC_SQL2>(xg + s * DP, yv, D);
+        if (v == best[c]) { kk = s; break; }
+      }
+      key = pack_key(best[c], (unsigned)(bestg[c] * 8 + kk));
+    } else {
+      key = pack_key(CUDART_INF_F, (unsigned)p0);
+    }
+    atomicMin(nnkey + q, key);
+  }
+}
+
+template <int D, int DP, bool L1>
+static void nns_lowd_t(const SolveBufs& B, int mt, int nt, cudaStream_t st) {
+  const int per_cta = K1_THREADS * k1_p(D);
+  const int gx = (nt + per_cta - 1) / per_cta;
+  // enough CTAs for several waves over the 152 SMs; chunks stay whole tiles
+  const int target = 152 * 8;
+  int gy = (target + gx - 1) / gx;
+  int tiles = (mt + K1_TS - 1) / K1_TS;
+  if (gy > tiles) gy = tiles;
+  int chunk_tiles = (tiles + gy - 1) / gy;
+  int chunk = chunk_tiles * K1_TS;
+  gy = (mt + chunk - 1) / chunk;
+  dim3 grid(gx, gy);
+  k_nns_lowd<D, DP, L1><<<grid, K1_THREADS, 0, st>>>(B.xa[B.cur], mt, chunk, B.ya[B.cur], nt, B.nnkey,
+                                                     &B.st->err);
+}
+
+int launch_nns_lowd(const SolveBufs& B, int mt, int nt, cudaStream_t st) {
+  const bool l1 = B.metric == METRIC_L1;
+#define NNS_CASE(DD, DPP)                                             \
+  case DD:                                                            \
+    if (l1) nns_lowd_t<DD, DPP, true>(B, mt, nt, st);                 \
+    else nns_lowd_t<DD, DPP, false>(B, mt, nt, st);                   \
+    break;
+  switch (B.d) {
+    NNS_CASE(1, 2) NNS_CASE(2, 2) NNS_CASE(3, 4) NNS_CASE(4, 4)
+    NNS_CASE(5, 8) NNS_CASE(6, 8) NNS_CASE(7, 8) NNS_CASE(8, 8)
+    default: return -1;
+  }
+#undef NNS_CASE
+  return 0;
+}
+
+// --------------------------------------------------------------------------
+// the single-CTA solver
+// --------------------------------------------------------------------------
+
+constexpr int FIN_THREADS = 1024;
+
+template <int DP>
+struct FinSmem {
+  float xs[FIN_MAX * DP];
+  float ys[FIN_MAX * DP];
+  double sres[FIN_MAX];
+  double cres[FIN_MAX];
+  int iidx[FIN_MAX];
+  int jidx[FIN_MAX];
+  unsigned long long nnk[FIN_MAX];
+  unsigned long long mem[FIN_MAX];
+  unsigned long long mem2[FIN_MAX];
+  int cnt[FIN_MAX + 1];
+  int off[FIN_MAX + 1];
+  unsigned long long acc[XS_LIMBS];
+  int wt[33];
+  int mt, nt;
+  unsigned nflow;
+  double total;
+};
+
+// Exclusive prefix sum over the block; `total` receives the block sum.
+NNS_DEV int block_scan_excl(int v, int* wt, int& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += t;
+  }
+  if (lane == 31) wt[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    int t = lane < nw ? wt[lane] : 0;
+    int y = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int u = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += u;
+    }
+    wt[lane] = y - t;
+    if (lane == 31) wt[32] = y;
+  }
+  __syncthreads();
+  total = wt[32];
+  const int r = wt[w] + x - v;
+  __syncthreads();
+  return r;
+}
+
+// Stable compaction of both active lists to the points with weight left.
+template <int DP>
+NNS_DEV void cta_compact(FinSmem<DP>& S) {
+  const int tid = threadIdx.x;
+  const int mt = S.mt, nt = S.nt;
+  const bool ks = tid < mt && S.sres[tid] > 0.0;
+  const bool kc = tid < nt && S.cres[tid] > 0.0;
+  float xv[DP], yv[DP];
+  double sv = 0.0, cv = 0.0;
+  int iv = 0, jv = 0;
+  if (ks) {
+#pragma unroll
+    for (int k = 0; k < DP; ++k) xv[k] = S.xs[tid * DP + k];
+    sv = S.sres[tid];
+    iv = S.iidx[tid];
+  }
+  if (kc) {
+#pragma unroll
+    for (int k = 0; k < DP; ++k) yv[k] = S.ys[tid * DP + k];
+    cv = S.cres[tid];
+    jv = S.jidx[tid];
+  }
+  int tot;
+  const int ex = block_scan_excl((ks ? 1 : 0) | (kc ? (1 << 16) : 0), S.wt, tot);
+  if (ks) {
+    const int p = ex & 0xffff;
+#pragma unroll
+    for (int k = 0; k < DP; ++k) S.xs[p * DP + k] = xv[k];
+    S.sres[p] = sv;
+    S.iidx[p] = iv;
+  }
+  if (kc) {
+    const int q = ex >> 16;
+#pragma unroll
+    for (int k = 0; k < DP; ++k) S.ys[q * DP + k] = yv[k];
+    S.cres[q] = cv;
+    S.jidx[q] = jv;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    S.mt = tot & 0xffff;
+    S.nt = tot >> 16;
+  }
+  __syncthreads();
+}
+
+struct CtaOut {
+  double* terms;                 // global per-flow terms (nullable)
+  unsigned long long* acc;       // exact accumulator for R (shared, nullable)
+  int32_t* plan_i;               // plan (nullable)
+  int32_t* plan_j;
+  double* plan_f;
+  long long plan_cap;
+  double* s_glob;                // residual write-back by original index (nullable)
+  double* c_glob;
+  unsigned* err;
+};
+
+// Rounds of Alg. 1 until one active side is empty.  nnz, rounds and
+// pair_evals are running totals owned by thread 0 (valid in every thread on
+// return).
+template <int D, int DP, bool L1>
+NNS_DEV void cta_rounds(FinSmem<DP>& S, int metric, const CtaOut& O, unsigned long long& nnz, long long& rounds,
+                        long long& pair_evals, long long round_limit) {
+  const int tid = threadIdx.x;
+  const int T = blockDim.x;
+  for (;;) {
+    const int mt = S.mt, nt = S.nt;
+    if (mt == 0 || nt == 0) break;
+    if (rounds >= round_limit) {
+      if (tid == 0) atomicOr(O.err, EF_ITER);
+      break;
+    }
+    // ---- NNS: nearest active supplier of every active consumer
+    int split = 1;
+    while (split < 32 && nt * split * 2 <= T) split <<= 1;
+    {
+      const int q = tid / split, part = tid & (split - 1);
+      unsigned long long bk = ~0ULL;
+      if (q < nt) {
+        float yv[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) yv[k] = S.ys[q * DP + k];
+        float best = CUDART_INF_F;
+        int bp = -1;
+        for (int p = part; p < mt; p += split) {
+          const float v = L1 ? key32<METRIC_L1>(S.xs + p * DP, yv, D) : key32<METRIC_SQL2>(S.xs + p * DP, yv, D);
+          if (bp < 0 || v < best) { best = v; bp = p; }
+        }
+        if (bp >= 0) bk = pack_key(best, (unsigned)bp);
+      }
+      for (int o = 1; o < split; o <<= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, bk, o);
+        bk = other < bk ? other : bk;
+      }
+      if (q < nt && part == 0) S.nnk[q] = bk;
+    }
+    for (int p = tid; p < mt; p += T) S.cnt[p] = 0;
+    if (tid == 0) S.nflow = 0;
+    __syncthreads();
+    // ---- group the consumers by their supplier
+    for (int q = tid; q < nt; q += T) atomicAdd(&S.cnt[(int)(S.nnk[q] & 0xffffffffULL)], 1);
+    __syncthreads();
+    {
+      int tot;
+      const int v = tid < mt ? S.cnt[tid] : 0;
+      const int ex = block_scan_excl(v, S.wt, tot);
+      if (tid < mt) S.off[tid] = ex;
+      if (tid == 0) S.off[mt] = tot;
+    }
+    __syncthreads();
+    for (int q = tid; q < nt; q += T) {
+      const unsigned long long key = S.nnk[q];
+      const int p = (int)(key & 0xffffffffULL);
+      const int slot = S.off[p] + atomicSub(&S.cnt[p], 1) - 1;
+      S.mem[slot] = (key & 0xffffffff00000000ULL) | (unsigned)q;
+    }
+    __syncthreads();
+    // ---- greedy order: rank of each member inside its group
+    for (int r = tid; r < nt; r += T) {
+      const unsigned long long e = S.mem[r];
+      const int q = (int)(e & 0xffffffffULL);
+      const int p = (int)(S.nnk[q] & 0xffffffffULL);
+      const int b = S.off[p], en = S.off[p + 1];
+      int rank = 0;
+      for (int u = b; u < en; ++u) rank += S.mem[u] < e;
+      S.mem2[b + rank] = e;
+    }
+    __syncthreads();
+    // ---- flow & cost (greedy protocol), one supplier per thread
+    for (int p = tid; p < mt; p += T) {
+      const int b = S.off[p], en = S.off[p + 1];
+      if (b == en) continue;
+      double s = S.sres[p];
+      for (int r = b; r < en; ++r) {
+        if (!(s > 0.0)) break;
+        const int q = (int)(S.mem2[r] & 0xffffffffULL);
+        const double c = S.cres[q];
+        const double f = s < c ? s : c;
+        s = __dsub_rn(s, f);
+        const double cn = __dsub_rn(c, f);
+        S.cres[q] = cn;
+        const double Dij = cost_dist64(S.xs + p * DP, S.ys + q * DP, D, metric);
+        const double term = __dmul_rn(f, Dij);
+        const unsigned long long slot = nnz + atomicAdd(&S.nflow, 1u);
+        if (O.terms) O.terms[slot] = term;
+        if (O.acc) xs_add(O.acc, term);
+        if (O.plan_i) {
+          if ((long long)slot < O.plan_cap) {
+            O.plan_i[slot] = S.iidx[p];
+            O.plan_j[slot] = S.jidx[q];
+            O.plan_f[slot] = f;
+          } else {
+            atomicOr(O.err, EF_CAPACITY);
+          }
+        }
+        if (O.c_glob) O.c_glob[S.jidx[q]] = cn;
+      }
+      S.sres[p] = s;
+      if (O.s_glob) O.s_glob[S.iidx[p]] = s;
+    }
+    __syncthreads();
+    nnz += S.nflow;
+    rounds += 1;
+    pair_evals += (long long)mt * nt;
+    // ---- weights update: retire spent points, compact
+    cta_compact(S);
+  }
+}
+
+// Tail of a single large solve: load the current active lists and finish.
+template <int D, int DP, bool L1>
+__global__ void __launch_bounds__(FIN_THREADS, 1) k_finish(SolveBufs B, long long round_limit) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FinSmem<DP>& S = *reinterpret_cast<FinSmem<DP>*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int mt = B.st->mt, nt = B.st->nt;
+  if (mt > FIN_MAX || nt > FIN_MAX) {
+    if (tid == 0) atomicOr(&B.st->err, EF_INTERNAL);
+    return;
+  }
+  const float* xa = B.xa[B.cur];
+  const float* ya = B.ya[B.cur];
+  for (int p = tid; p < mt; p += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < DP; ++k) S.xs[p * DP + k] = xa[(size_t)p * DP + k];
+    S.iidx[p] = B.ia[B.cur][p];
+    S.sres[p] = B.s[S.iidx[p]];
+  }
+  for (int q = tid; q < nt; q += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < DP; ++k) S.ys[q * DP + k] = ya[(size_t)q * DP + k];
+    S.jidx[q] = B.ja[B.cur][q];
+    S.cres[q] = B.c[S.jidx[q]];
+  }
+  if (tid == 0) {
+    S.mt = mt;
+    S.nt = nt;
+  }
+  __syncthreads();
+  CtaOut O{B.terms, nullptr, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, B.s, B.c, &B.st->err};
+  unsigned long long nnz = B.st->nnz;
+  long long rounds = B.st->rounds, pe = B.st->pair_evals;
+  cta_rounds<D, DP, L1>(S, B.metric, O, nnz, rounds, pe, round_limit);
+  if (tid == 0) {
+    B.st->nnz = nnz;
+    B.st->rounds = rounds;
+    B.st->pair_evals = pe;
+    B.st->mt = S.mt;
+    B.st->nt = S.nt;
+  }
+}
+
+template <int D, int DP, bool L1>
+static int finish_t(const SolveBufs& B, long long round_limit, cudaStream_t st) {
+  const size_t smem = sizeof(FinSmem<DP>);
+  cudaError_t e = cudaFuncSetAttribute(k_finish<D, DP, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return -1;
+  k_finish<D, DP, L1><<<1, FIN_THREADS, smem, st>>>(B, round_limit);
+  return 0;
+}
+
+int launch_finish(const SolveBufs& B, int64_t round_limit, cudaStream_t st) {
+  const bool l1 = B.metric == METRIC_L1;
+#define FIN_CASE(DD, DPP) \
+  case DD:                \
+    return l1 ? finish_t<DD, DPP, true>(B, round_limit, st) : finish_t<DD, DPP, false>(B, round_limit, st);
+  switch (B.d) {
+    FIN_CASE(1, 2) FIN_CASE(2, 2) FIN_CASE(3, 4) FIN_CASE(4, 4)
+    FIN_CASE(5, 8) FIN_CASE(6, 8) FIN_CASE(7, 8) FIN_CASE(8, 8)
+    default: return -1;
+  }
+#undef FIN_CASE
+}
+
+// --------------------------------------------------------------------------
+// batched small pairs: one persistent launch, a work queue of pairs, each
+// pair solved start to finish by one CTA (Sec. III-D batch processing)
+// --------------------------------------------------------------------------
+
+template <int DP>
+NNS_DEV bool cta_load_side(const float* pts, const double* w, int cnt, int d, float* dst, double* res, int* idx,
+                           unsigned long long* acc, double* total_slot, unsigned* err) {
+  const int tid = threadIdx.x;
+  for (int i = tid; i < XS_LIMBS; i += blockDim.x) acc[i] = 0ULL;
+  __syncthreads();
+  bool bad = false;
+  for (int p = tid; p < cnt; p += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < DP; ++k) {
+      const float v = k < d ? pts[(size_t)p * d + k] : 0.f;
+      if (!isfinite(v)) bad = true;
+      dst[p * DP + k] = v;
+    }
+    const double wv = w[p];
+    if (!isfinite(wv) || wv < 0.0) bad = true;
+    res[p] = wv;
+    idx[p] = p;
+    if (isfinite(wv)) xs_add(acc, wv);
+  }
+  bad = __syncthreads_or(bad);
+  if (tid == 0) *total_slot = xs_round(acc);
+  __syncthreads();
+  const double total = *total_slot;
+  if (bad || !(total > 0.0)) {
+    if (tid == 0) atomicOr(err, bad ? EF_NONFINITE : EF_ZERO_MASS);
+    return false;
+  }
+  for (int p = tid; p < cnt; p += blockDim.x) res[p] = __ddiv_rn(res[p], total);
+  __syncthreads();
+  return true;
+}
+
+template <int D, int DP, bool L1>
+__global__ void __launch_bounds__(FIN_THREADS, 1) k_batched_lowd(BatchArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FinSmem<DP>& S = *reinterpret_cast<FinSmem<DP>*>(smem_raw);
+  __shared__ int s_item;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) s_item = (int)atomicAdd(A.queue, 1u);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= A.num) break;
+    const int pr = A.pair_ids[item];
+    const int64_t xo = A.x_off[pr], yo = A.y_off[pr];
+    const int m = (int)(A.x_off[pr + 1] - xo), n = (int)(A.y_off[pr + 1] - yo);
+    bool ok = cta_load_side<DP>(A.x + xo * A.d, A.a + xo, m, A.d, S.xs, S.sres, S.iidx, S.acc, &S.total, A.err);
+    if (ok)
+      ok = cta_load_side<DP>(A.y + yo * A.d, A.b + yo, n, A.d, S.ys, S.cres, S.jidx, S.acc, &S.total, A.err);
+    if (!ok) {
+      if (tid == 0) A.costs[pr] = CUDART_NAN;
+      __syncthreads();
+      continue;
+    }
+    if (tid == 0) {
+      S.mt = m;
+      S.nt = n;
+    }
+    for (int i = tid; i < XS_LIMBS; i += blockDim.x) S.acc[i] = 0ULL;
+    __syncthreads();
+    cta_compact(S);  // drop zero weights
+    CtaOut O{nullptr, S.acc, nullptr, nullptr, nullptr, 0, nullptr, nullptr, A.err};
+    unsigned long long nnz = 0;
+    long long rounds = 0, pe = 0;
+    cta_rounds<D, DP, L1>(S, A.metric, O, nnz, rounds, pe, (long long)m + n);
+    __syncthreads();
+    if (tid == 0) {
+      A.costs[pr] = xs_round(S.acc);
+      if (A.rounds) A.rounds[pr] = rounds;
+      if (A.pair_evals) A.pair_evals[pr] = pe;
+    }
+    __syncthreads();
+  }
+}
+
+template <int D, int DP, bool L1>
+static int batched_t(const BatchArgs& A, int grid, cudaStream_t st) {
+  const size_t smem = sizeof(FinSmem<DP>);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_batched_lowd<D, DP, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return -1;
+  k_batched_lowd<D, DP, L1><<<grid, FIN_THREADS, smem, st>>>(A);
+  return 0;
+}
+
+int launch_batched_lowd(const BatchArgs& A, int grid, cudaStream_t st) {
+  const bool l1 = A.metric == METRIC_L1;
+#define BAT_CASE(DD, DPP) \
+  case DD:                \
+    return l1 ? batched_t<DD, DPP, true>(A, grid, st) : batched_t<DD, DPP, false>(A, grid, st);
+  switch (A.d) {
+    BAT_CASE(1, 2) BAT_CASE(2, 2) BAT_CASE(3, 4) BAT_CASE(4, 4)
+    BAT_CASE(5, 8) BAT_CASE(6, 8) BAT_CASE(7, 8) BAT_CASE(8, 8)
+    default: return -1;
+  }
+#undef BAT_CASE
+}
+
+}  // namespace nnsemd

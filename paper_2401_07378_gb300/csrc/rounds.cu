@@ -1,0 +1,540 @@
+// Round kernels of a multi-CTA NNS-EMD solve (sm_103a), one per step of
+// Alg. 1 (Sec. III-A) after the NNS operation:
+//
+//   k_group_count / k_group_alloc / k_group_scatter
+//       a_i^(t): bucket the active consumers by the supplier they picked,
+//       with one 64-bit member key (key32 bits << 32 | consumer position)
+//       per consumer, so that sorting a group orders it by distance and
+//       then by consumer index (the greedy protocol's order).
+//   k_flow_small / k_flow_big
+//       sort each group (a warp-register bitonic network for groups of at
+//       most 32, a CTA network in shared or global memory beyond that), then
+//       walk it in FP64 exactly as the algorithm does: f = min(s_i, c_j),
+//       s_i -= f, c_j -= f, until s_i is spent; each flow writes its plan
+//       entry and its cost term f * D_ij (FP64 ground distance).
+//   k_compact_count / k_compact_scatter
+//       weights update: stable compaction of both active lists to the points
+//       whose residual is still positive, gathering their coordinates into
+//       the other half of a double buffer.
+//   k_xs_* exact sums (normalisation totals, R, leftover mass).
+#include <math_constants.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace nnsemd {
+
+// --------------------------------------------------------------------------
+// exact sums
+// --------------------------------------------------------------------------
+
+__global__ void k_xs_clear(unsigned long long* acc, int count) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) acc[i] = 0ULL;
+}
+
+// Accumulate v[0..n) (n from n_dev when given).  With `check`, non-finite or
+// negative values raise error bits and are skipped.
+__global__ void k_xs_accum(const double* __restrict__ v, int64_t n, const unsigned long long* n_dev,
+                           unsigned long long* gacc, unsigned* err, int check) {
+  __shared__ unsigned long long sacc[XS_LIMBS];
+  for (int i = threadIdx.x; i < XS_LIMBS; i += blockDim.x) sacc[i] = 0ULL;
+  __syncthreads();
+  const int64_t cnt = n_dev ? (int64_t)*n_dev : n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+    const double w = v[i];
+    if (check) {
+      if (!isfinite(w)) { atomicOr(err, EF_NONFINITE); continue; }
+      if (w < 0.0) { atomicOr(err, EF_NEGATIVE); continue; }
+    }
+    xs_add(sacc, w);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < XS_LIMBS; i += blockDim.x)
+    if (sacc[i]) atomicAdd(gacc + i, sacc[i]);
+}
+
+__global__ void k_xs_round(unsigned long long* acc, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = xs_round(acc);
+}
+
+// out[i] = w[i] / total, the total rounded from acc by the first thread of
+// every block (each block rounds its own copy: no inter-block ordering).
+__global__ void k_normalise(const double* __restrict__ w, int64_t n, const unsigned long long* __restrict__ acc,
+                            double* total_out, double* __restrict__ out, unsigned* err) {
+  __shared__ unsigned long long a[XS_LIMBS];
+  __shared__ double total;
+  for (int i = threadIdx.x; i < XS_LIMBS; i += blockDim.x) a[i] = acc[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    total = xs_round(a);
+    if (blockIdx.x == 0) {
+      *total_out = total;
+      if (!(total > 0.0)) atomicOr(err, EF_ZERO_MASS);
+    }
+  }
+  __syncthreads();
+  const double t = total;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double wi = w[i];
+    out[i] = (t > 0.0 && isfinite(wi) && wi > 0.0) ? __ddiv_rn(wi, t) : 0.0;
+  }
+}
+
+static int xs_grid(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 4) g = 152 * 4;
+  return (int)(g < 1 ? 1 : g);
+}
+
+void launch_xs_clear(unsigned long long* acc, int count, cudaStream_t st) {
+  k_xs_clear<<<1, 256, 0, st>>>(acc, count);
+}
+
+void launch_xs_accum(const double* v, int64_t n, unsigned long long* acc, unsigned* err, bool check,
+                     cudaStream_t st) {
+  k_xs_accum<<<xs_grid(n), 256, 0, st>>>(v, n, nullptr, acc, err, check ? 1 : 0);
+}
+
+void launch_normalise(const double* w, int64_t n, unsigned long long* acc, double* total, double* out,
+                      unsigned* err, cudaStream_t st) {
+  k_normalise<<<xs_grid(n), 256, 0, st>>>(w, n, acc, total, out, err);
+}
+
+void launch_xs_round(unsigned long long* acc, double* out, cudaStream_t st) { k_xs_round<<<1, 32, 0, st>>>(acc, out); }
+
+void launch_leftover(const SolveBufs& B, cudaStream_t st) {
+  unsigned long long* acc = B.xs_acc + 3 * XS_LIMBS;
+  k_xs_clear<<<1, 256, 0, st>>>(acc, XS_LIMBS);
+  k_xs_accum<<<xs_grid(B.m), 256, 0, st>>>(B.s, B.m, nullptr, acc, &B.st->err, 0);
+  k_xs_accum<<<xs_grid(B.n), 256, 0, st>>>(B.c, B.n, nullptr, acc, &B.st->err, 0);
+  k_xs_round<<<1, 32, 0, st>>>(acc, &B.st->leftover);
+  // R: the exact sum of the nnz cost terms
+  unsigned long long* cacc = B.xs_acc + 2 * XS_LIMBS;
+  k_xs_clear<<<1, 256, 0, st>>>(cacc, XS_LIMBS);
+  k_xs_accum<<<152 * 2, 256, 0, st>>>(B.terms, 0, &B.st->nnz, cacc, &B.st->err, 0);
+  k_xs_round<<<1, 32, 0, st>>>(cacc, &B.st->cost);
+}
+
+// --------------------------------------------------------------------------
+// compaction (initial packing and the weights update of every round)
+// --------------------------------------------------------------------------
+
+constexpr int CP_THREADS = 256;
+constexpr int CP_ITEMS = 4;
+constexpr int CP_BLOCK = CP_THREADS * CP_ITEMS;
+
+struct CompactSide {
+  const float* pts_in;  // input coordinates, in_stride floats per point
+  int in_stride;
+  const int* idx_in;    // original index of each input point (nullptr: identity)
+  const double* resid;  // residual weight by original index
+  float* pts_out;       // packed output, DP floats per point
+  int* idx_out;
+  int count;            // input points
+  int* count_out;       // survivors
+  int nblocks;
+  int check;            // check coordinates for finiteness
+};
+
+struct CompactArgs {
+  CompactSide side[2];
+  int* blockcounts;     // [side0 blocks + side1 blocks]
+  unsigned* err;
+};
+
+NNS_DEV int cp_block_side(const CompactArgs& A, int b, int& local) {
+  if (b < A.side[0].nblocks) { local = b; return 0; }
+  local = b - A.side[0].nblocks;
+  return 1;
+}
+
+__global__ void __launch_bounds__(CP_THREADS) k_compact_count(CompactArgs A) {
+  int lb;
+  const int sd = cp_block_side(A, blockIdx.x, lb);
+  const CompactSide& S = A.side[sd];
+  int c = 0;
+  const int base = lb * CP_BLOCK + threadIdx.x * CP_ITEMS;
+#pragma unroll
+  for (int k = 0; k < CP_ITEMS; ++k) {
+    const int pos = base + k;
+    if (pos < S.count) {
+      const int orig = S.idx_in ? S.idx_in[pos] : pos;
+      c += S.resid[orig] > 0.0;
+    }
+  }
+  // block reduction
+  __shared__ int red[CP_THREADS / 32];
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < CP_THREADS / 32; ++w) t += red[w];
+    A.blockcounts[blockIdx.x] = t;
+  }
+}
+
+template <int DP>
+__global__ void __launch_bounds__(CP_THREADS) k_compact_scatter(CompactArgs A) {
+  int lb;
+  const int sd = cp_block_side(A, blockIdx.x, lb);
+  const CompactSide& S = A.side[sd];
+  const int first = sd == 0 ? 0 : A.side[0].nblocks;
+  __shared__ int s_off;
+  __shared__ int wsum[CP_THREADS / 32 + 1];
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int b = first; b < first + lb; ++b) o += A.blockcounts[b];
+    s_off = o;
+  }
+  // flags of this thread's items
+  int flags[CP_ITEMS];
+  int origs[CP_ITEMS];
+  int mine = 0;
+  const int base = lb * CP_BLOCK + threadIdx.x * CP_ITEMS;
+#pragma unroll
+  for (int k = 0; k < CP_ITEMS; ++k) {
+    const int pos = base + k;
+    flags[k] = 0;
+    origs[k] = 0;
+    if (pos < S.count) {
+      const int orig = S.idx_in ? S.idx_in[pos] : pos;
+      origs[k] = orig;
+      flags[k] = S.resid[orig] > 0.0;
+    }
+    mine += flags[k];
+  }
+  // block exclusive scan of per-thread counts
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += t;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int i = 0; i < CP_THREADS / 32; ++i) {
+      int t = wsum[i];
+      wsum[i] = run;
+      run += t;
+    }
+    wsum[CP_THREADS / 32] = run;
+  }
+  __syncthreads();
+  int pos_out = s_off + wsum[w] + x - mine;
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < CP_ITEMS; ++k) {
+    if (!flags[k]) continue;
+    const int pos = base + k;
+    float v[DP];
+#pragma unroll
+    for (int e = 0; e < DP; ++e) {
+      float t = e < S.in_stride ? S.pts_in[(size_t)pos * S.in_stride + e] : 0.f;
+      if (S.check && !isfinite(t)) bad = true;
+      v[e] = t;
+    }
+    if (DP == 2) {
+      reinterpret_cast<float2*>(S.pts_out)[pos_out] = make_float2(v[0], v[1]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < DP; e += 4)
+        reinterpret_cast<float4*>(S.pts_out + (size_t)pos_out * DP)[e / 4] = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+    }
+    S.idx_out[pos_out] = origs[k];
+    ++pos_out;
+  }
+  if (bad) atomicOr(A.err, EF_NONFINITE);
+  // the last block of a side publishes the count and NaN-pads the tail
+  if (lb == S.nblocks - 1) {
+    const int total = s_off + wsum[CP_THREADS / 32];
+    if (threadIdx.x == 0) *S.count_out = total;
+    const int padded = (int)pad_points(total);
+    for (int p = total + threadIdx.x; p < padded; p += CP_THREADS)
+#pragma unroll
+      for (int e = 0; e < DP; ++e) S.pts_out[(size_t)p * DP + e] = CUDART_NAN_F;
+  }
+}
+
+static void compact_launch(CompactArgs& A, int dp, cudaStream_t st) {
+  for (int s = 0; s < 2; ++s) A.side[s].nblocks = (A.side[s].count + CP_BLOCK - 1) / CP_BLOCK;
+  const int nb = A.side[0].nblocks + A.side[1].nblocks;
+  if (nb == 0) return;
+  k_compact_count<<<nb, CP_THREADS, 0, st>>>(A);
+  if (dp == 2) k_compact_scatter<2><<<nb, CP_THREADS, 0, st>>>(A);
+  else if (dp == 4) k_compact_scatter<4><<<nb, CP_THREADS, 0, st>>>(A);
+  else k_compact_scatter<8><<<nb, CP_THREADS, 0, st>>>(A);
+}
+
+int launch_initial_pack(SolveBufs& B, cudaStream_t st) {
+  CompactArgs A{};
+  A.side[0] = CompactSide{B.x, B.d, nullptr, B.s, B.xa[B.cur], B.ia[B.cur], (int)B.m, &B.st->mt, 0, 1};
+  A.side[1] = CompactSide{B.y, B.d, nullptr, B.c, B.ya[B.cur], B.ja[B.cur], (int)B.n, &B.st->nt, 0, 1};
+  A.blockcounts = B.blockcounts;
+  A.err = &B.st->err;
+  compact_launch(A, B.dp, st);
+  return 0;
+}
+
+// --------------------------------------------------------------------------
+// grouping
+// --------------------------------------------------------------------------
+
+__global__ void k_group_count(const unsigned long long* __restrict__ nnkey, int nt, int mt, int* __restrict__ cnt,
+                              unsigned* err) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nt) return;
+  const unsigned p = (unsigned)(nnkey[q] & 0xffffffffULL);
+  if (p >= (unsigned)mt) { atomicOr(err, EF_INTERNAL); return; }
+  atomicAdd(cnt + p, 1);
+}
+
+__global__ void k_group_alloc(const int* __restrict__ cnt, int mt, int2* __restrict__ seg, int* __restrict__ seglist,
+                              int* __restrict__ biglist, DevState* st) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int L = p < mt ? cnt[p] : 0;
+  int x = L;
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += t;
+  }
+  unsigned base = 0;
+  if (lane == 31 && x) base = atomicAdd(&st->seg_cursor, (unsigned)x);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  const unsigned lt = (1u << lane) - 1u;
+  const unsigned ne = __ballot_sync(0xffffffffu, L > 0);
+  unsigned sb = 0;
+  if (lane == 0 && ne) sb = atomicAdd((unsigned*)&st->nseg, (unsigned)__popc(ne));
+  sb = __shfl_sync(0xffffffffu, sb, 0);
+  const unsigned big = __ballot_sync(0xffffffffu, L > 32);
+  unsigned bb = 0;
+  if (lane == 0 && big) bb = atomicAdd((unsigned*)&st->nbig, (unsigned)__popc(big));
+  bb = __shfl_sync(0xffffffffu, bb, 0);
+  if (p < mt) {
+    seg[p] = make_int2((int)(base + x - L), L);
+    if (L > 0) seglist[sb + __popc(ne & lt)] = p;
+    if (L > 32) biglist[bb + __popc(big & lt)] = p;
+  }
+}
+
+__global__ void k_group_scatter(const unsigned long long* __restrict__ nnkey, int nt, int* __restrict__ cnt,
+                                const int2* __restrict__ seg, unsigned long long* __restrict__ member) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nt) return;
+  const unsigned long long key = nnkey[q];
+  const int p = (int)(key & 0xffffffffULL);
+  const int slot = seg[p].x + atomicSub(cnt + p, 1) - 1;
+  member[slot] = (key & 0xffffffff00000000ULL) | (unsigned)q;
+}
+
+// --------------------------------------------------------------------------
+// greedy flow
+// --------------------------------------------------------------------------
+
+struct FlowArgs {
+  const float* x;  // original coordinates
+  const float* y;
+  int d, metric;
+  const int* ia;   // current active lists
+  const int* ja;
+  const int2* seg;
+  const int* seglist;
+  const int* biglist;
+  unsigned long long* member;
+  double* s;
+  double* c;
+  double* terms;
+  int32_t* plan_i;
+  int32_t* plan_j;
+  double* plan_f;
+  long long plan_cap;
+  DevState* st;
+};
+
+// Warp-wide ascending sort of one 64-bit key per lane (bitonic network in
+// which every comparator puts the smaller key on the lower lane).
+NNS_DEV unsigned long long warp_sort_u64(unsigned long long key) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+    {
+      const int partner = lane ^ (k - 1);
+      const unsigned long long o = __shfl_sync(0xffffffffu, key, partner);
+      key = lane < partner ? (o < key ? o : key) : (o > key ? o : key);
+    }
+#pragma unroll
+    for (int j = k >> 2; j > 0; j >>= 1) {
+      const int partner = lane ^ j;
+      const unsigned long long o = __shfl_sync(0xffffffffu, key, partner);
+      key = lane < partner ? (o < key ? o : key) : (o > key ? o : key);
+    }
+  }
+  return key;
+}
+
+// Serve up to 32 sorted members (one per lane, `cnt` valid) from supplier i
+// whose residual is `s` (uniform).  Returns how many were served.
+NNS_DEV int warp_serve(const FlowArgs& A, int i, double& s, unsigned long long key, int cnt) {
+  const int lane = threadIdx.x & 31;
+  int j = 0;
+  double c = 0.0;
+  if (lane < cnt) {
+    const int q = (int)(key & 0xffffffffULL);
+    j = A.ja[q];
+    c = A.c[j];
+  }
+  double myf = 0.0, mycn = 0.0;
+  int served = 0;
+  for (int l = 0; l < cnt; ++l) {
+    if (!(s > 0.0)) break;
+    const double cl = __shfl_sync(0xffffffffu, c, l);
+    const double f = s < cl ? s : cl;
+    s = __dsub_rn(s, f);
+    if (lane == l) {
+      myf = f;
+      mycn = __dsub_rn(cl, f);
+    }
+    served = l + 1;
+  }
+  unsigned long long base = 0;
+  if (lane == 0 && served) base = atomicAdd(&A.st->nnz, (unsigned long long)served);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (lane < served) {
+    A.c[j] = mycn;
+    const double Dij = cost_dist64(A.x + (size_t)i * A.d, A.y + (size_t)j * A.d, A.d, A.metric);
+    const unsigned long long slot = base + lane;
+    A.terms[slot] = __dmul_rn(myf, Dij);
+    if (A.plan_i) {
+      if ((long long)slot < A.plan_cap) {
+        A.plan_i[slot] = i;
+        A.plan_j[slot] = j;
+        A.plan_f[slot] = myf;
+      } else {
+        atomicOr(&A.st->err, EF_CAPACITY);
+      }
+    }
+  }
+  return served;
+}
+
+__global__ void k_flow_small(FlowArgs A) {
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const int nseg = A.st->nseg;
+  for (int w = blockIdx.x * wpb + (threadIdx.x >> 5); w < nseg; w += gridDim.x * wpb) {
+    const int p = A.seglist[w];
+    const int2 sg = A.seg[p];
+    if (sg.y > 32) continue;
+    unsigned long long key = lane < sg.y ? A.member[sg.x + lane] : ~0ULL;
+    key = warp_sort_u64(key);
+    const int i = A.ia[p];
+    double s = A.s[i];
+    warp_serve(A, i, s, key, sg.y);
+    if (lane == 0) A.s[i] = s;
+  }
+}
+
+constexpr int BIG_THREADS = 256;
+constexpr int BIG_SMEM_KEYS = 4096;
+
+// Ascending bitonic sort of a[0..L) in place (virtual +inf padding up to a
+// power of two; every comparator puts the smaller key at the lower index,
+// so padding never moves).  All threads of the block call this.
+template <typename Ptr>
+NNS_DEV void block_sort_u64(Ptr a, int L) {
+  int N = 1;
+  while (N < L) N <<= 1;
+  for (int k = 2; k <= N; k <<= 1) {
+    for (int idx = threadIdx.x; idx < N / 2; idx += blockDim.x) {
+      const int h = k >> 1;
+      const int i = (idx / h) * k + (idx % h);
+      const int pr = i ^ (k - 1);
+      if (pr < L) {
+        const unsigned long long u = a[i], v = a[pr];
+        if (v < u) { a[i] = v; a[pr] = u; }
+      }
+    }
+    __syncthreads();
+    for (int j = k >> 2; j > 0; j >>= 1) {
+      for (int idx = threadIdx.x; idx < N / 2; idx += blockDim.x) {
+        const int i = (idx / j) * (2 * j) + (idx % j);
+        const int pr = i + j;
+        if (pr < L) {
+          const unsigned long long u = a[i], v = a[pr];
+          if (v < u) { a[i] = v; a[pr] = u; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(BIG_THREADS) k_flow_big(FlowArgs A) {
+  __shared__ unsigned long long keys[BIG_SMEM_KEYS];
+  const int nbig = A.st->nbig;
+  for (int b = blockIdx.x; b < nbig; b += gridDim.x) {
+    const int p = A.biglist[b];
+    const int2 sg = A.seg[p];
+    const int L = sg.y;
+    unsigned long long* g = A.member + sg.x;
+    const bool in_smem = L <= BIG_SMEM_KEYS;
+    if (in_smem) {
+      for (int r = threadIdx.x; r < L; r += blockDim.x) keys[r] = g[r];
+      __syncthreads();
+      block_sort_u64(keys, L);
+    } else {
+      block_sort_u64(g, L);
+    }
+    if (threadIdx.x < 32) {
+      const int i = A.ia[p];
+      double s = A.s[i];
+      for (int base = 0; base < L && s > 0.0; base += 32) {
+        const int cntc = min(32, L - base);
+        const unsigned long long key =
+            (int)threadIdx.x < cntc ? (in_smem ? keys[base + threadIdx.x] : g[base + threadIdx.x]) : ~0ULL;
+        const int served = warp_serve(A, i, s, key, cntc);
+        if (served < cntc) break;
+      }
+      if (threadIdx.x == 0) A.s[i] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------------------
+// one multi-CTA round (the NNS operation is launched by the caller)
+// --------------------------------------------------------------------------
+
+__global__ void k_round_reset(DevState* st) {
+  st->nseg = 0;
+  st->nbig = 0;
+  st->seg_cursor = 0;
+}
+
+int launch_big_round(SolveBufs& B, int mt, int nt, cudaStream_t st) {
+  const int cur = B.cur;
+  k_round_reset<<<1, 1, 0, st>>>(B.st);
+  k_group_count<<<(nt + 255) / 256, 256, 0, st>>>(B.nnkey, nt, mt, B.cnt, &B.st->err);
+  k_group_alloc<<<(mt + 255) / 256, 256, 0, st>>>(B.cnt, mt, B.seg, B.seglist, B.biglist, B.st);
+  k_group_scatter<<<(nt + 255) / 256, 256, 0, st>>>(B.nnkey, nt, B.cnt, B.seg, B.member);
+  FlowArgs F{B.x, B.y, B.d, B.metric, B.ia[cur], B.ja[cur], B.seg, B.seglist, B.biglist, B.member,
+             B.s, B.c, B.terms, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, B.st};
+  int warps = (nt + 31) / 32;
+  int blocks = (warps + 7) / 8;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_flow_small<<<blocks, 256, 0, st>>>(F);
+  k_flow_big<<<152, BIG_THREADS, 0, st>>>(F);
+  // weights update: compact into the other buffer
+  CompactArgs A{};
+  A.side[0] = CompactSide{B.xa[cur], B.dp, B.ia[cur], B.s, B.xa[cur ^ 1], B.ia[cur ^ 1], mt, &B.st->mt, 0, 0};
+  A.side[1] = CompactSide{B.ya[cur], B.dp, B.ja[cur], B.c, B.ya[cur ^ 1], B.ja[cur ^ 1], nt, &B.st->nt, 0, 0};
+  A.blockcounts = B.blockcounts;
+  A.err = &B.st->err;
+  compact_launch(A, B.dp, st);
+  return 0;
+}
+
+}  // namespace nnsemd

@@ -1,0 +1,65 @@
+"""Host-side logic of bench.py without a GPU: the multi-rank reductions
+(world size 2 over gloo on CPU) and the reference arm's JSON line."""
+import json
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    import bench
+    bench.dist_init("gloo")
+    assert bench.world() == (rank, world, rank)
+    mx = bench.dist_reduce(10.0 + rank, "max", "cpu")
+    sm = bench.dist_reduce(float(rank + 1), "sum", "cpu")
+    bench.dist_barrier()
+    with open(os.path.join(out_dir, f"r{rank}.json"), "w") as fh:
+        json.dump({"max": mx, "sum": sm}, fh)
+    import torch.distributed as dist
+    dist.destroy_process_group()
+
+
+def test_two_rank_reductions_over_gloo(tmp_path):
+    import torch.multiprocessing as mp
+    port = _free_port()
+    mp.spawn(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    for r in range(2):
+        got = json.load(open(tmp_path / f"r{r}.json"))
+        assert got == {"max": 11.0, "sum": 3.0}
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    import bench
+    monkeypatch.setattr(bench, "ORACLE_SAMPLE_N", 1024)
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    bench.main(["--impl", "reference", "--steps", "2", "--warmup", "0"])
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "pairs/s" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_reference_arm_non_zero_rank_prints_nothing(monkeypatch, capsys):
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    bench.main(["--impl", "reference", "--steps", "1", "--warmup", "0"])
+    assert capsys.readouterr().out.strip() == ""

@@ -1,0 +1,197 @@
+"""Parity of the CUDA path with the CPU oracle (through the C ABI).
+
+The FP32 path takes its decisions (argmin, greedy order) on FP32 distances
+with the same fixed operation order as the oracle's ``decide="fp32"`` mode,
+keeps the mass bookkeeping in FP64 in the algorithm's own order, and returns
+R as a correctly rounded sum.  So everything is compared bit for bit: the
+cost, the plan (as a set of (i, j, f)), the number of rounds and the NNS work.
+The oracle also checks, on the CPU, that every FP32 decision agrees with the
+FP64 one up to a documented near-tie (gap < 1e-6 relative).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from golden_io import all_golden
+from paper_2401_07378_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2401_07378_gb300 import nnsemd
+    c = nnsemd.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a, dt):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dt).cuda()
+
+
+def gpu_solve(ctx, x, a, y, b, metric, plan=True):
+    return ctx.solve(dev(x, torch.float32), dev(a, torch.float64), dev(y, torch.float32), dev(b, torch.float64),
+                     metric=metric, plan=plan)
+
+
+def plan_set(i, j, f):
+    i = np.asarray(i.cpu() if hasattr(i, "cpu") else i)
+    j = np.asarray(j.cpu() if hasattr(j, "cpu") else j)
+    f = np.asarray(f.cpu() if hasattr(f, "cpu") else f)
+    order = np.lexsort((j, i))
+    return i[order], j[order], f[order]
+
+
+def assert_parity(res, ref):
+    assert res.cost == ref.cost, (res.cost, ref.cost)
+    gi, gj, gf = plan_set(res.plan_i, res.plan_j, res.plan_f)
+    oi, oj, of = plan_set(ref.plan_i, ref.plan_j, ref.plan_f)
+    assert np.array_equal(gi, oi) and np.array_equal(gj, oj)
+    assert np.array_equal(gf, of)
+    assert res.stats["rounds"] == ref.rounds
+    assert res.stats["pair_evals"] == ref.pair_evals
+    assert ref.violations == 0
+    assert abs(res.stats["leftover_mass"] - ref.leftover) <= 1e-15
+
+
+@pytest.mark.parametrize("g", all_golden(GOLDEN), ids=lambda g: g.name)
+def test_golden_examples_on_gpu(ctx, g):
+    ref = oracle.solve(g.x, g.a, g.y, g.b, g.metric, "fp32")
+    res = gpu_solve(ctx, g.x, g.a, g.y, g.b, g.metric)
+    assert_parity(res, ref)
+    assert res.cost == pytest.approx(g.cost, rel=2e-16)
+
+
+def test_single_pair_256_d2(ctx):
+    p = wl.single_pair(0)
+    ref = oracle.solve_pair(p, "l2")
+    assert_parity(gpu_solve(ctx, p.x, p.a, p.y, p.b, "l2"), ref)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 8])
+@pytest.mark.parametrize("metric", ["l2", "sql2", "l1"])
+def test_random_pairs_all_d(ctx, d, metric):
+    rng = np.random.default_rng(100 + d)
+    for m, n, w in ((1, 1, "uniform"), (1, 37, "dirichlet"), (53, 1, "dirichlet"), (300, 700, "dirichlet"),
+                    (1500, 1100, "uniform"), (2500, 3100, "dirichlet")):
+        p = wl.uniform_pair(m, n, d, int(rng.integers(1 << 30)), w)
+        ref = oracle.solve_pair(p, metric)
+        assert_parity(gpu_solve(ctx, p.x, p.a, p.y, p.b, metric), ref)
+
+
+def test_multi_round_colour_clusters(ctx):
+    # large enough for several multi-CTA rounds before the one-CTA tail;
+    # sizes not multiples of any tile
+    p = wl.color_transfer(seed=3, n=20011)
+    ref = oracle.solve_pair(p, "sql2")
+    assert_parity(gpu_solve(ctx, p.x, p.a, p.y, p.b, "sql2"), ref)
+
+
+def test_zero_weights_and_duplicates(ctx):
+    rng = np.random.default_rng(5)
+    x = rng.integers(0, 4, (3000, 2)).astype(np.float32)   # many exact ties / duplicates
+    y = rng.integers(0, 4, (2000, 2)).astype(np.float32)
+    a = rng.exponential(1.0, 3000)
+    b = rng.exponential(1.0, 2000)
+    a[rng.random(3000) < 0.4] = 0.0
+    b[rng.random(2000) < 0.4] = 0.0
+    for metric in ("l2", "l1"):
+        ref = oracle.solve(x, a, y, b, metric)
+        assert_parity(gpu_solve(ctx, x, a, y, b, metric), ref)
+
+
+def test_identical_sets_cost_zero(ctx):
+    p = wl.color_transfer(seed=1, n=5000)
+    res = gpu_solve(ctx, p.x, p.a, p.x, p.a, "l2")
+    assert res.cost == 0.0
+
+
+def test_one_heavy_supplier_long_groups(ctx):
+    # one supplier holds most of the mass: its group spans far more than a
+    # warp, which exercises the CTA-level sort of long groups
+    rng = np.random.default_rng(6)
+    x = rng.random((40, 3)).astype(np.float32)
+    y = rng.random((9000, 3)).astype(np.float32)
+    a = np.full(40, 1e-3)
+    a[7] = 50.0
+    b = np.ones(9000)
+    ref = oracle.solve(x, a, y, b, "l2")
+    assert_parity(gpu_solve(ctx, x, a, y, b, "l2"), ref)
+
+
+def test_host_entry_point_matches_device(ctx):
+    p = wl.uniform_pair(4000, 3500, 3, 9, "dirichlet")
+    dev_res = gpu_solve(ctx, p.x, p.a, p.y, p.b, "l2")
+    host_res = ctx.solve_host(p.x, p.a, p.y, p.b, metric="l2", plan=True)
+    assert host_res.cost == dev_res.cost
+    a = plan_set(host_res.plan_i, host_res.plan_j, host_res.plan_f)
+    b = plan_set(dev_res.plan_i, dev_res.plan_j, dev_res.plan_f)
+    assert all(np.array_equal(u, v) for u, v in zip(a, b))
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_batched_small_pairs(ctx, d):
+    batch = wl.random_batch(40, seed=d, d=d, lo=1, hi=1024)
+    costs, stats = ctx.solve_batched(dev(batch.x, torch.float32), dev(batch.a, torch.float64), batch.x_off,
+                                     dev(batch.y, torch.float32), dev(batch.b, torch.float64), batch.y_off,
+                                     metric="l2")
+    costs = costs.cpu().numpy()
+    rounds = 0
+    for p in range(batch.num_pairs):
+        ref = oracle.solve_pair(batch.pair(p), "l2")
+        assert costs[p] == ref.cost, p
+        rounds += ref.rounds
+    assert stats["rounds"] == rounds
+
+
+def test_batched_mixes_small_and_large_pairs(ctx):
+    pairs = [wl.uniform_pair(m, n, 2, s, "dirichlet") for s, (m, n) in
+             enumerate([(10, 20), (1500, 900), (1024, 1024), (3000, 2500), (1, 1)])]
+    batch = wl.Batch.pack(pairs)
+    costs, _ = ctx.solve_batched(dev(batch.x, torch.float32), dev(batch.a, torch.float64), batch.x_off,
+                                 dev(batch.y, torch.float32), dev(batch.b, torch.float64), batch.y_off,
+                                 metric="sql2")
+    costs = costs.cpu().numpy()
+    for p, pr in enumerate(pairs):
+        assert costs[p] == oracle.solve_pair(pr, "sql2").cost
+
+
+def test_errors_are_reported(ctx):
+    from paper_2401_07378_gb300.nnsemd import NNSEMDError
+    x = np.zeros((4, 2), np.float32)
+    w = np.ones(4)
+    bad = x.copy()
+    bad[1, 1] = np.nan
+    with pytest.raises(NNSEMDError) as e:
+        gpu_solve(ctx, bad, w, x, w, "l2")
+    assert e.value.status == 2
+    with pytest.raises(NNSEMDError) as e:
+        gpu_solve(ctx, x, np.array([1.0, -1.0, 1.0, 1.0]), x, w, "l2")
+    assert e.value.status == 3
+    with pytest.raises(NNSEMDError) as e:
+        gpu_solve(ctx, x, np.zeros(4), x, w, "l2")
+    assert e.value.status == 3
+    with pytest.raises(NNSEMDError) as e:
+        gpu_solve(ctx, np.zeros((4, 9), np.float32), w, np.zeros((4, 9), np.float32), w, "l2")
+    assert e.value.status == 8
+    # the context stays usable after errors
+    p = wl.single_pair(2)
+    assert gpu_solve(ctx, p.x, p.a, p.y, p.b, "l2").cost == oracle.solve_pair(p, "l2").cost
+
+
+def test_colour_transfer_full_size(ctx):
+    """The benchmark's workload (65,536 colours per image, d=3, squared
+    Euclidean, full plan) in the benchmark's launch configuration, compared
+    bit for bit with the oracle."""
+    p = wl.color_transfer(seed=0)
+    res = gpu_solve(ctx, p.x, p.a, p.y, p.b, "sql2")
+    # properties that hold at any size, checked first
+    gi, gj, gf = plan_set(res.plan_i, res.plan_j, res.plan_f)
+    assert gf.size == 65536 and np.all(gf == 1.0 / 65536)
+    assert np.array_equal(np.sort(gi), np.arange(65536)) and np.array_equal(np.sort(gj), np.arange(65536))
+    ref = oracle.solve_pair(p, "sql2")
+    assert_parity(res, ref)
