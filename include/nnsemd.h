@@ -163,6 +163,30 @@ int nnsemd_solve_batched(nnsemd_ctx *ctx, int32_t num_pairs,
                          int32_t d, const nnsemd_options *opt,
                          double *costs_out, nnsemd_stats *stats);
 
+/* Solve one small pair without allocating any memory.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc (a plugin
+ * running inside another framework's launch callback, a process whose device
+ * memory a caching allocator has already claimed, a latency-critical path
+ * that cannot take cudaMalloc's implicit synchronisation).
+ *   x [m][d], a [m], y [n][d], b [n]: device inputs as for nnsemd_solve;
+ *   1 <= m, n <= NNSEMD_NOALLOC_MAX_POINTS, 1 <= d <= NNSEMD_NOALLOC_MAX_D,
+ *   larger sizes return NNSEMD_ERR_UNSUPPORTED;
+ *   metric: an nnsemd_metric;  cost_out: DEVICE pointer to one double (R);
+ *   stream: cudaStream_t to launch on (NULL = default); the call returns
+ *   after the stream has finished the solve (it reads back an error word).
+ * No context is needed.  Scratch (a few error and counter words) lives in a
+ * 256-byte __device__ array of the library, held by every GPU that loads it
+ * until the process exits; the kernel clears it at the start of each call.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current: make the first call on each
+ * device before any stream capture.  All calls share the array, so calls that
+ * overlap on the GPU race: serialise them.  R equals nnsemd_solve's. */
+#define NNSEMD_NOALLOC_MAX_POINTS 1024
+#define NNSEMD_NOALLOC_MAX_D 8
+int nnsemd_solve_small_noalloc(const float *x, const double *a, int64_t m,
+                               const float *y, const double *b, int64_t n,
+                               int32_t d, int32_t metric, double *cost_out, void *stream);
+
 /* Message for the last failure on ctx (never NULL; "" after success).  The
  * string stays valid until the next call on ctx.  ctx may be NULL for
  * failures of nnsemd_create. */

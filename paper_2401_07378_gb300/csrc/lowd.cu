@@ -613,3 +613,146 @@ int launch_batched_lowd(const BatchArgs& A, int grid, cudaStream_t st) {
 }
 
 }  // namespace nnsemd
+
+// --------------------------------------------------------------------------
+// nnsemd_solve_small_noalloc: one small pair solved by the one-CTA solver
+// without any memory allocation.
+//
+// Some callers cannot call cudaMalloc: a plugin that runs inside another
+// framework's launch callback, where allocating is not allowed; a process
+// whose device memory is already claimed in full by a caching allocator; a
+// latency-critical path that cannot afford cudaMalloc's implicit device
+// synchronisation.  For them this entry point keeps its few words of scratch
+// (error bits and round counters) in a file-scope __device__ array that is
+// part of the loaded module, so a call allocates nothing.  Everything else
+// lives in the CTA's shared memory, as in the batched kernel above.
+//
+// Every GPU that loads the library holds this array until the process exits.
+// All calls share it and it keeps the last call's contents; the kernel clears
+// it itself before use.  Calls that overlap on the GPU (different streams, or
+// several host threads) race on it: serialise them.
+// --------------------------------------------------------------------------
+
+#include <mutex>
+
+#include "nnsemd.h"
+
+namespace nnsemd {
+
+struct NoAllocScratch {
+  unsigned err;          // ErrFlag bits of the last call
+  unsigned pad;
+  long long rounds;      // rounds of the last call
+  long long pair_evals;  // sum of m_t * n_t of the last call
+};
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = 256;
+static_assert(sizeof(NoAllocScratch) <= NOALLOC_SCRATCH_BYTES, "scratch too small");
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+template <int D, int DP, bool L1>
+__global__ void __launch_bounds__(FIN_THREADS, 1)
+    k_small_noalloc(const float* x, const double* a, int m, const float* y, const double* b, int n, int d,
+                    int metric, double* cost_out, NoAllocScratch* scr) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FinSmem<DP>& S = *reinterpret_cast<FinSmem<DP>*>(smem_raw);
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    scr->err = 0;
+    scr->rounds = 0;
+    scr->pair_evals = 0;
+  }
+  __syncthreads();
+  bool ok = cta_load_side<DP>(x, a, m, d, S.xs, S.sres, S.iidx, S.acc, &S.total, &scr->err);
+  if (ok) ok = cta_load_side<DP>(y, b, n, d, S.ys, S.cres, S.jidx, S.acc, &S.total, &scr->err);
+  if (!ok) {
+    if (tid == 0) *cost_out = CUDART_NAN;
+    return;
+  }
+  if (tid == 0) {
+    S.mt = m;
+    S.nt = n;
+  }
+  for (int i = tid; i < XS_LIMBS; i += blockDim.x) S.acc[i] = 0ULL;
+  __syncthreads();
+  cta_compact(S);
+  CtaOut O{nullptr, S.acc, nullptr, nullptr, nullptr, 0, nullptr, nullptr, &scr->err};
+  unsigned long long nnz = 0;
+  long long rounds = 0, pe = 0;
+  cta_rounds<D, DP, L1>(S, metric, O, nnz, rounds, pe, (long long)m + n);
+  __syncthreads();
+  if (tid == 0) {
+    *cost_out = xs_round(S.acc);
+    scr->rounds = rounds;
+    scr->pair_evals = pe;
+  }
+}
+
+template <int D, int DP, bool L1>
+static cudaError_t small_noalloc_t(const float* x, const double* a, int m, const float* y, const double* b, int n,
+                                   int metric, double* cost_out, NoAllocScratch* scr, cudaStream_t st) {
+  const size_t smem = sizeof(FinSmem<DP>);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_small_noalloc<D, DP, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_small_noalloc<D, DP, L1><<<1, FIN_THREADS, smem, st>>>(x, a, m, y, b, n, D, metric, cost_out, scr);
+  return cudaGetLastError();
+}
+
+// Device address of the scratch array, looked up once per device with that
+// device current (in host code the array's name is only a stand-in).
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[256];
+
+static cudaError_t noalloc_scratch_address(int device, NoAllocScratch** out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (device < 0 || device >= 256) return cudaErrorInvalidDevice;
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[device] = p;
+  }
+  *out = static_cast<NoAllocScratch*>(g_noalloc_addr[device]);
+  return cudaSuccess;
+}
+
+}  // namespace nnsemd
+
+extern "C" int nnsemd_solve_small_noalloc(const float* x, const double* a, int64_t m, const float* y,
+                                          const double* b, int64_t n, int32_t d, int32_t metric, double* cost_out,
+                                          void* stream) {
+  using namespace nnsemd;
+  if (!x || !a || !y || !b || !cost_out) return NNSEMD_ERR_INVALID_ARG;
+  if (m < 1 || n < 1 || d < 1 || metric < 0 || metric > 2) return NNSEMD_ERR_INVALID_ARG;
+  if (m > NNSEMD_NOALLOC_MAX_POINTS || n > NNSEMD_NOALLOC_MAX_POINTS || d > NNSEMD_NOALLOC_MAX_D)
+    return NNSEMD_ERR_UNSUPPORTED;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return NNSEMD_ERR_CUDA;
+  NoAllocScratch* scr = nullptr;
+  if (noalloc_scratch_address(device, &scr) != cudaSuccess) return NNSEMD_ERR_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool l1 = metric == METRIC_L1;
+  const int mi = (int)m, ni = (int)n;
+  cudaError_t e;
+#define NOALLOC_CASE(DD, DPP)                                                                              \
+  case DD:                                                                                                 \
+    e = l1 ? small_noalloc_t<DD, DPP, true>(x, a, mi, y, b, ni, metric, cost_out, scr, st)                 \
+           : small_noalloc_t<DD, DPP, false>(x, a, mi, y, b, ni, metric, cost_out, scr, st);               \
+    break;
+  switch (d) {
+    NOALLOC_CASE(1, 2) NOALLOC_CASE(2, 2) NOALLOC_CASE(3, 4) NOALLOC_CASE(4, 4)
+    NOALLOC_CASE(5, 8) NOALLOC_CASE(6, 8) NOALLOC_CASE(7, 8) NOALLOC_CASE(8, 8)
+    default: return NNSEMD_ERR_UNSUPPORTED;
+  }
+#undef NOALLOC_CASE
+  if (e != cudaSuccess) return NNSEMD_ERR_CUDA;
+  NoAllocScratch h{};
+  if (cudaMemcpyAsync(&h, scr, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return NNSEMD_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return NNSEMD_ERR_CUDA;
+  if (h.err & EF_NONFINITE) return NNSEMD_ERR_NONFINITE;
+  if (h.err & (EF_ZERO_MASS | EF_NEGATIVE)) return NNSEMD_ERR_ZERO_MASS;
+  if (h.err & EF_ITER) return NNSEMD_ERR_ITER_LIMIT;
+  if (h.err) return NNSEMD_ERR_CUDA;
+  return NNSEMD_OK;
+}
