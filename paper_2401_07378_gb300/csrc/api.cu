@@ -38,7 +38,8 @@ struct nnsemd_ctx {
 
 namespace {
 
-constexpr int64_t FIN_PAIRS = 1LL << 19;  // tail threshold on m_t * n_t
+constexpr int64_t FIN_PAIRS = 1LL << 19;     // d <= 8 tail threshold on m_t * n_t
+constexpr int64_t FIN_HD_WORK = 1LL << 23;   // d > 8 tail threshold on m_t * n_t * d
 thread_local std::string g_create_err;
 
 int fail(nnsemd_ctx* ctx, int status, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
@@ -100,7 +101,7 @@ int ensure_ws(nnsemd_ctx* ctx, size_t bytes) {
 // size is computed.
 size_t layout_solve(void* base, int64_t m, int64_t n, int d, SolveBufs& B) {
   Carve C(base);
-  const int dp = padded_dim(d);
+  const int dp = d <= 8 ? padded_dim(d) : 0;
   B.st = C.take<DevState>(1);
   B.xs_acc = C.take<unsigned long long>(4 * XS_LIMBS);
   B.s = C.take<double>(m);
@@ -142,9 +143,12 @@ int check_opts(nnsemd_ctx* ctx, const nnsemd_options* opt, int d, int& metric) {
   }
   if (metric < 0 || metric > 2) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "unknown metric %d", metric);
   if (d < 1) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "d must be >= 1");
-  if (d > 8) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "d = %d: only d <= 8 is served", d);
+  if (d > 65536) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "d = %d: above 65536", d);
   return NNSEMD_OK;
 }
+
+// Packed coordinate width of the d <= 8 path; 0 for d > 8 (index-only lists).
+int packed_dim(int d) { return d <= 8 ? padded_dim(d) : 0; }
 
 // The device part of a single-pair solve on buffers that are already laid
 // out; writes R to *cost and fills the counters.
@@ -176,10 +180,14 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
   int mt = ctx->hstate->mt, nt = ctx->hstate->nt;
   long long rounds = 0, pair_evals = 0;
   const long long round_limit = B.m + B.n;
+  const bool lowd = B.dp > 0;
   while (mt > 0 && nt > 0) {
-    if (mt <= FIN_MAX && nt <= FIN_MAX && (int64_t)mt * nt <= FIN_PAIRS) {
+    const bool tail = lowd ? (mt <= FIN_MAX && nt <= FIN_MAX && (int64_t)mt * nt <= FIN_PAIRS)
+                           : (mt <= FIN_MAX_HD && nt <= FIN_MAX_HD && (int64_t)mt * nt * B.d <= FIN_HD_WORK);
+    if (tail) {
       if (timed) CK(cudaEventRecord(ctx->ev[2], st));
-      if (launch_finish(B, round_limit - rounds, st)) return fail(ctx, NNSEMD_ERR_CUDA, "finisher launch");
+      const int lrc = lowd ? launch_finish(B, round_limit - rounds, st) : launch_finish_hd(B, round_limit - rounds, st);
+      if (lrc) return fail(ctx, NNSEMD_ERR_CUDA, "finisher launch");
       if (timed) CK(cudaEventRecord(ctx->ev[3], st));
       tail_ran = true;
       L += 1;
@@ -188,7 +196,8 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
     if (rounds >= round_limit) return fail(ctx, NNSEMD_ERR_ITER_LIMIT, "round limit m + n exceeded");
     CK(cudaMemsetAsync(B.nnkey, 0xff, (size_t)nt * sizeof(unsigned long long), st));
     if (timed) CK(cudaEventRecord(ctx->ev[0], st));
-    if (launch_nns_lowd(B, mt, nt, st)) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "no NNS kernel for d=%d", B.d);
+    const int nrc = lowd ? launch_nns_lowd(B, mt, nt, st) : launch_nns_f32(B, mt, nt, nullptr, nullptr, st);
+    if (nrc) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "no NNS kernel for d=%d", B.d);
     if (timed) CK(cudaEventRecord(ctx->ev[1], st));
     launch_big_round(B, mt, nt, st);
     L += 10;
@@ -319,7 +328,7 @@ int nnsemd_solve(nnsemd_ctx* ctx, const float* x, const double* a, int64_t m, co
   B.m = m;
   B.n = n;
   B.d = d;
-  B.dp = padded_dim(d);
+  B.dp = packed_dim(d);
   B.metric = metric;
   B.plan_i = plan ? plan->i : nullptr;
   B.plan_j = plan ? plan->j : nullptr;
@@ -378,7 +387,7 @@ int nnsemd_solve_host(nnsemd_ctx* ctx, const float* x, const double* a, int64_t 
   B.m = m;
   B.n = n;
   B.d = d;
-  B.dp = padded_dim(d);
+  B.dp = packed_dim(d);
   B.metric = metric;
   B.plan_i = plan ? pi : nullptr;
   B.plan_j = plan ? pj : nullptr;
@@ -421,7 +430,8 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
   for (int p = 0; p < num_pairs; ++p) {
     const int64_t m = x_off[p + 1] - x_off[p], n = y_off[p + 1] - y_off[p];
     if (m < 1 || n < 1) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "pair %d has an empty side", p);
-    ((m <= FIN_MAX && n <= FIN_MAX) ? small : large).push_back(p);
+    const int cap = d <= 8 ? FIN_MAX : FIN_MAX_HD;
+    ((m <= cap && n <= cap) ? small : large).push_back(p);
   }
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
@@ -462,7 +472,8 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
     BatchArgs A{x_packed, a_packed, xo_d, y_packed, b_packed, yo_d, ids_d, (int)small.size(), d, metric,
                 costs_out, rounds_d, pe_d, q_d, q_d + 1};
     const int grid = (int)std::min<size_t>(small.size(), 152);
-    if (launch_batched_lowd(A, grid, st)) return fail(ctx, NNSEMD_ERR_CUDA, "batched launch");
+    const int brc = d <= 8 ? launch_batched_lowd(A, grid, st) : launch_batched_hd(A, grid, st);
+    if (brc) return fail(ctx, NNSEMD_ERR_CUDA, "batched launch");
     CK(cudaGetLastError());
     L += 1;
   }
@@ -474,7 +485,7 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
     B.m = x_off[p + 1] - x_off[p];
     B.n = y_off[p + 1] - y_off[p];
     B.d = d;
-    B.dp = padded_dim(d);
+    B.dp = packed_dim(d);
     B.metric = metric;
     double cost = 0;
     int64_t nnz = 0;

@@ -1,0 +1,494 @@
+// The one-CTA NNS-EMD solver: every step of a round of Alg. 1 (Sec. III-A)
+// for active sets of at most CAP points per side, with all per-point state in
+// one CTA's shared memory.  Used for the tail rounds of a large solve, for
+// batches of small pairs (one pair per CTA) and by the allocation-free entry
+// point.
+//
+// The coordinates are a policy:
+//   GeoSmem   (d <= 8)  coordinates of the active points live in shared
+//                       memory and move with the compaction;
+//   GeoGlobal (d > 8)   coordinates stay in global memory (L2) and are read
+//                       by original index; the NNS step runs 64 x 64 tiles
+//                       staged in shared memory by 256-thread groups.
+// Grouping, greedy order, flow and compaction are the same for both.
+#pragma once
+
+#include <math_constants.h>
+
+#include "common.cuh"
+
+namespace nnsemd {
+
+constexpr int FIN_THREADS = 1024;
+
+// Exclusive prefix sum over the block; `total` receives the block sum.
+NNS_DEV int block_scan_excl(int v, int* wt, int& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += t;
+  }
+  if (lane == 31) wt[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    int t = lane < nw ? wt[lane] : 0;
+    int y = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int u = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += u;
+    }
+    wt[lane] = y - t;
+    if (lane == 31) wt[32] = y;
+  }
+  __syncthreads();
+  total = wt[32];
+  const int r = wt[w] + x - v;
+  __syncthreads();
+  return r;
+}
+
+// Per-point state of a pair solved in one CTA (no coordinates).
+template <int CAP>
+struct CtaCore {
+  double sres[CAP];
+  double cres[CAP];
+  int iidx[CAP];
+  int jidx[CAP];
+  unsigned long long nnk[CAP];
+  unsigned long long mem[CAP];
+  unsigned long long mem2[CAP];
+  int cnt[CAP + 1];
+  int off[CAP + 1];
+  unsigned long long acc[XS_LIMBS];
+  int wt[33];
+  int mt, nt;
+  unsigned nflow;
+  double total;
+};
+
+struct CtaOut {
+  double* terms;                 // global per-flow terms (nullable)
+  unsigned long long* acc;       // exact accumulator for R (shared, nullable)
+  int32_t* plan_i;               // plan (nullable)
+  int32_t* plan_j;
+  double* plan_f;
+  long long plan_cap;
+  double* s_glob;                // residual write-back by original index (nullable)
+  double* c_glob;
+  unsigned* err;
+};
+
+// --------------------------------------------------------------------------
+// coordinate policies
+// --------------------------------------------------------------------------
+
+template <int D, int DP, bool L1, int CAP>
+struct GeoSmem {
+  static constexpr int kDP = DP;
+  float xs[CAP * DP];
+  float ys[CAP * DP];
+  struct PX { float v[DP]; };
+
+  NNS_DEV void load_x(int p, PX& r) const {
+#pragma unroll
+    for (int k = 0; k < DP; ++k) r.v[k] = xs[p * DP + k];
+  }
+  NNS_DEV void store_x(int p, const PX& r) {
+#pragma unroll
+    for (int k = 0; k < DP; ++k) xs[p * DP + k] = r.v[k];
+  }
+  NNS_DEV void load_y(int q, PX& r) const {
+#pragma unroll
+    for (int k = 0; k < DP; ++k) r.v[k] = ys[q * DP + k];
+  }
+  NNS_DEV void store_y(int q, const PX& r) {
+#pragma unroll
+    for (int k = 0; k < DP; ++k) ys[q * DP + k] = r.v[k];
+  }
+  template <int C>
+  NNS_DEV double dist64(const CtaCore<C>& S, int p, int q, int metric) const {
+    return cost_dist64(xs + p * DP, ys + q * DP, D, metric);
+  }
+  // S.nnk[q] = (key32 bits << 32 | p) of the nearest active supplier
+  template <int C>
+  NNS_DEV void nns(CtaCore<C>& S, int mt, int nt) const {
+    const int tid = threadIdx.x, T = blockDim.x;
+    int split = 1;
+    while (split < 32 && nt * split * 2 <= T) split <<= 1;
+    for (int base = 0; base < nt; base += T / split) {
+      const int q = base + tid / split, part = tid & (split - 1);
+      unsigned long long bk = ~0ULL;
+      if (q < nt) {
+        float yv[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) yv[k] = ys[q * DP + k];
+        float best = CUDART_INF_F;
+        int bp = -1;
+        for (int p = part; p < mt; p += split) {
+          const float v = L1 ? key32<METRIC_L1>(xs + p * DP, yv, D) : key32<METRIC_SQL2>(xs + p * DP, yv, D);
+          if (bp < 0 || v < best) { best = v; bp = p; }
+        }
+        if (bp >= 0) bk = pack_key(best, (unsigned)bp);
+      }
+      for (int o = 1; o < split; o <<= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, bk, o);
+        bk = other < bk ? other : bk;
+      }
+      if (q < nt && part == 0) S.nnk[q] = bk;
+    }
+    __syncthreads();
+  }
+};
+
+// ---- tiled FP32 NNS for d > 8 ---------------------------------------------
+
+constexpr int TG_M = 64;        // consumers per tile
+constexpr int TG_N = 64;        // suppliers per tile
+constexpr int TG_K = 32;        // coordinates per staged chunk
+constexpr int TG_THREADS = 256; // threads per group (4 x 4 pairs each)
+constexpr int TG_PAD = 68;
+
+struct __align__(16) TileSmem {
+  float Xs[TG_K][TG_PAD];
+  float Ys[TG_K][TG_PAD];
+};
+
+NNS_DEV void group_sync(int bar) {
+  if (bar == 0) __syncthreads();
+  else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(TG_THREADS) : "memory");
+}
+
+// One 256-thread group: for the consumers cons[c0 .. c0+nc) (positions in the
+// active consumer list, or c0.. directly when cons is null) and the suppliers
+// at positions [p0, p1), the lowest (key32 bits << 32 | position).  Each
+// thread owns 4 consumers x 4 suppliers of a tile; the key of every pair is
+// accumulated over k = 0..d-1 in order (fma from +0, which equals the
+// definition's first product), so it is bit-identical to key32.  Returns, in
+// the threads with tx == 0, the keys of their 4 consumers (others: ~0).
+template <bool L1>
+NNS_DEV void group_nns_tile(const float* __restrict__ x, const int* __restrict__ ia, int p0, int p1,
+                            const float* __restrict__ y, const int* __restrict__ ja, const int* __restrict__ cons,
+                            int c0, int nc, int d, TileSmem& T, int gt, int bar, unsigned long long out[4]) {
+  const int tx = gt & 15, ty = gt >> 4;
+  float best[4];
+  int bpos[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) { best[i] = CUDART_INF_F; bpos[i] = -1; }
+  // loader mapping: row r of the tile, 8 consecutive coordinates
+  const int lr = gt & 63, lk = (gt >> 6) * 8;
+  const int cq = c0 + lr;
+  const float* yrow = nullptr;
+  if (lr < nc) yrow = y + (size_t)ja[cons ? cons[cq] : cq] * d;
+  for (int pt = p0; pt < p1; pt += TG_N) {
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    const int sp = pt + lr;
+    const float* xrow = sp < p1 ? x + (size_t)ia[sp] * d : nullptr;
+    for (int k0 = 0; k0 < d; k0 += TG_K) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = k0 + lk + e;
+        T.Ys[lk + e][lr] = (yrow && k < d) ? yrow[k] : 0.f;
+        T.Xs[lk + e][lr] = xrow ? (k < d ? xrow[k] : 0.f) : CUDART_NAN_F;
+      }
+      group_sync(bar);
+#pragma unroll 8
+      for (int k = 0; k < TG_K; ++k) {
+        const float4 xv = *reinterpret_cast<const float4*>(&T.Xs[k][tx * 4]);
+        const float4 yv = *reinterpret_cast<const float4*>(&T.Ys[k][ty * 4]);
+        const float xa[4] = {xv.x, xv.y, xv.z, xv.w};
+        const float ya[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float t = __fsub_rn(xa[j], ya[i]);
+            acc[i][j] = L1 ? __fadd_rn(acc[i][j], fabsf(t)) : __fmaf_rn(t, t, acc[i][j]);
+          }
+      }
+      group_sync(bar);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (acc[i][j] < best[i]) { best[i] = acc[i][j]; bpos[i] = pt + tx * 4 + j; }
+  }
+  // reduce over the 16 threads sharing each consumer (adjacent lanes)
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    unsigned long long k = bpos[i] >= 0 ? pack_key(best[i], (unsigned)bpos[i]) : ~0ULL;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+      const unsigned long long other = __shfl_xor_sync(0xffffffffu, k, o);
+      k = other < k ? other : k;
+    }
+    out[i] = k;
+  }
+}
+
+template <bool L1, int CAP>
+struct GeoGlobal {
+  static constexpr int kDP = 0;
+  const float* x;  // [m][d] original coordinates (global)
+  const float* y;  // [n][d]
+  int d;
+  TileSmem tiles[FIN_THREADS / TG_THREADS];
+  struct PX {};
+  NNS_DEV void load_x(int, PX&) const {}
+  NNS_DEV void store_x(int, const PX&) {}
+  NNS_DEV void load_y(int, PX&) const {}
+  NNS_DEV void store_y(int, const PX&) {}
+  template <int C>
+  NNS_DEV double dist64(const CtaCore<C>& S, int p, int q, int metric) const {
+    return cost_dist64(x + (size_t)S.iidx[p] * d, y + (size_t)S.jidx[q] * d, d, metric);
+  }
+  template <int C>
+  NNS_DEV void nns(CtaCore<C>& S, int mt, int nt) {
+    const int g = threadIdx.x / TG_THREADS, gt = threadIdx.x % TG_THREADS;
+    const int ngroups = blockDim.x / TG_THREADS;
+    for (int c0 = g * TG_M; c0 < nt; c0 += ngroups * TG_M) {
+      unsigned long long out[4];
+      group_nns_tile<L1>(x, S.iidx, 0, mt, y, S.jidx, nullptr, c0, min(TG_M, nt - c0), d, tiles[g], gt, 1 + g,
+                         out);
+      const int tx = gt & 15, ty = gt >> 4;
+      if (tx == 0)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int q = c0 + ty * 4 + i;
+          if (q < nt) S.nnk[q] = out[i];
+        }
+    }
+    __syncthreads();
+  }
+};
+
+// Note: GeoGlobal passes the CTA's own index arrays (iidx, jidx) as the
+// "position -> original index" maps, so positions are CTA-local.
+
+// --------------------------------------------------------------------------
+// compaction and rounds
+// --------------------------------------------------------------------------
+
+// Stable compaction of both active lists to the points with weight left.
+template <int CAP, class Geo>
+NNS_DEV void cta_compact(CtaCore<CAP>& S, Geo& G) {
+  constexpr int IT = CAP / FIN_THREADS;
+  const int tid = threadIdx.x;
+  const int mt = S.mt, nt = S.nt;
+  bool ks[IT], kc[IT];
+  double sv[IT], cv[IT];
+  int iv[IT], jv[IT];
+  typename Geo::PX px[IT], py[IT];
+  int ns = 0, nc = 0;
+#pragma unroll
+  for (int k = 0; k < IT; ++k) {
+    const int p = tid * IT + k;
+    ks[k] = p < mt && S.sres[p] > 0.0;
+    kc[k] = p < nt && S.cres[p] > 0.0;
+    if (ks[k]) { sv[k] = S.sres[p]; iv[k] = S.iidx[p]; G.load_x(p, px[k]); }
+    if (kc[k]) { cv[k] = S.cres[p]; jv[k] = S.jidx[p]; G.load_y(p, py[k]); }
+    ns += ks[k];
+    nc += kc[k];
+  }
+  int tot;
+  const int ex = block_scan_excl(ns | (nc << 16), S.wt, tot);
+  int ps = ex & 0xffff, pc = ex >> 16;
+#pragma unroll
+  for (int k = 0; k < IT; ++k) {
+    if (ks[k]) { S.sres[ps] = sv[k]; S.iidx[ps] = iv[k]; G.store_x(ps, px[k]); ++ps; }
+    if (kc[k]) { S.cres[pc] = cv[k]; S.jidx[pc] = jv[k]; G.store_y(pc, py[k]); ++pc; }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    S.mt = tot & 0xffff;
+    S.nt = tot >> 16;
+  }
+  __syncthreads();
+}
+
+// Exclusive scan of in[0..n) into out[0..n) (n <= CAP), returns the total.
+template <int CAP>
+NNS_DEV int block_scan_array(const int* in, int* out, int n, int* wt) {
+  constexpr int IT = CAP / FIN_THREADS;
+  int v[IT];
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < IT; ++k) {
+    const int i = threadIdx.x * IT + k;
+    v[k] = i < n ? in[i] : 0;
+    s += v[k];
+  }
+  int tot;
+  int ex = block_scan_excl(s, wt, tot);
+#pragma unroll
+  for (int k = 0; k < IT; ++k) {
+    const int i = threadIdx.x * IT + k;
+    if (i < n) out[i] = ex;
+    ex += v[k];
+  }
+  return tot;
+}
+
+// Rounds of Alg. 1 until one active side is empty.  nnz, rounds and
+// pair_evals are running totals (identical in every thread on return).
+template <int CAP, class Geo>
+NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, unsigned long long& nnz,
+                        long long& rounds, long long& pair_evals, long long round_limit) {
+  const int tid = threadIdx.x;
+  const int T = blockDim.x;
+  for (;;) {
+    const int mt = S.mt, nt = S.nt;
+    if (mt == 0 || nt == 0) break;
+    if (rounds >= round_limit) {
+      if (tid == 0) atomicOr(O.err, EF_ITER);
+      break;
+    }
+    // ---- NNS: nearest active supplier of every active consumer
+    G.nns(S, mt, nt);
+    for (int p = tid; p < mt; p += T) S.cnt[p] = 0;
+    if (tid == 0) S.nflow = 0;
+    __syncthreads();
+    // ---- group the consumers by their supplier
+    for (int q = tid; q < nt; q += T) atomicAdd(&S.cnt[(int)(S.nnk[q] & 0xffffffffULL)], 1);
+    __syncthreads();
+    {
+      const int tot = block_scan_array<CAP>(S.cnt, S.off, mt, S.wt);
+      if (tid == 0) S.off[mt] = tot;
+    }
+    __syncthreads();
+    for (int q = tid; q < nt; q += T) {
+      const unsigned long long key = S.nnk[q];
+      const int p = (int)(key & 0xffffffffULL);
+      const int slot = S.off[p] + atomicSub(&S.cnt[p], 1) - 1;
+      S.mem[slot] = (key & 0xffffffff00000000ULL) | (unsigned)q;
+    }
+    __syncthreads();
+    // ---- greedy order: rank of each member inside its group
+    for (int r = tid; r < nt; r += T) {
+      const unsigned long long e = S.mem[r];
+      const int q = (int)(e & 0xffffffffULL);
+      const int p = (int)(S.nnk[q] & 0xffffffffULL);
+      const int b = S.off[p], en = S.off[p + 1];
+      int rank = 0;
+      for (int u = b; u < en; ++u) rank += S.mem[u] < e;
+      S.mem2[b + rank] = e;
+    }
+    __syncthreads();
+    // ---- flow & cost (greedy protocol), one supplier per thread
+    for (int p = tid; p < mt; p += T) {
+      const int b = S.off[p], en = S.off[p + 1];
+      if (b == en) continue;
+      double s = S.sres[p];
+      for (int r = b; r < en; ++r) {
+        if (!(s > 0.0)) break;
+        const int q = (int)(S.mem2[r] & 0xffffffffULL);
+        const double c = S.cres[q];
+        const double f = s < c ? s : c;
+        s = __dsub_rn(s, f);
+        const double cn = __dsub_rn(c, f);
+        S.cres[q] = cn;
+        const double Dij = G.dist64(S, p, q, metric);
+        const double term = __dmul_rn(f, Dij);
+        const unsigned long long slot = nnz + atomicAdd(&S.nflow, 1u);
+        if (O.terms) O.terms[slot] = term;
+        if (O.acc) xs_add(O.acc, term);
+        if (O.plan_i) {
+          if ((long long)slot < O.plan_cap) {
+            O.plan_i[slot] = S.iidx[p];
+            O.plan_j[slot] = S.jidx[q];
+            O.plan_f[slot] = f;
+          } else {
+            atomicOr(O.err, EF_CAPACITY);
+          }
+        }
+        if (O.c_glob) O.c_glob[S.jidx[q]] = cn;
+      }
+      S.sres[p] = s;
+      if (O.s_glob) O.s_glob[S.iidx[p]] = s;
+    }
+    __syncthreads();
+    nnz += S.nflow;
+    rounds += 1;
+    pair_evals += (long long)mt * nt;
+    // ---- weights update: retire spent points, compact
+    cta_compact(S, G);
+  }
+}
+
+// Load one side of a pair (raw rows, weights) into the CTA state, check it,
+// and normalise its weights by their correctly rounded total.  With DP > 0
+// the coordinates are copied (zero-padded to DP) into dst.
+template <int DP, int CAP>
+NNS_DEV bool cta_load_side(const float* pts, const double* w, int cnt, int d, float* dst, double* res, int* idx,
+                           CtaCore<CAP>& S, unsigned* err) {
+  const int tid = threadIdx.x;
+  for (int i = tid; i < XS_LIMBS; i += blockDim.x) S.acc[i] = 0ULL;
+  __syncthreads();
+  bool bad = false;
+  for (int p = tid; p < cnt; p += blockDim.x) {
+    if (DP > 0) {
+#pragma unroll
+      for (int k = 0; k < (DP > 0 ? DP : 1); ++k) {
+        const float v = k < d ? pts[(size_t)p * d + k] : 0.f;
+        if (!isfinite(v)) bad = true;
+        dst[p * DP + k] = v;
+      }
+    } else {
+      for (int k = 0; k < d; ++k)
+        if (!isfinite(pts[(size_t)p * d + k])) bad = true;
+    }
+    const double wv = w[p];
+    if (!isfinite(wv) || wv < 0.0) bad = true;
+    res[p] = wv;
+    idx[p] = p;
+    if (isfinite(wv)) xs_add(S.acc, wv);
+  }
+  bad = __syncthreads_or(bad);
+  if (tid == 0) S.total = xs_round(S.acc);
+  __syncthreads();
+  const double total = S.total;
+  if (bad || !(total > 0.0)) {
+    if (tid == 0) atomicOr(err, bad ? EF_NONFINITE : EF_ZERO_MASS);
+    __syncthreads();
+    return false;
+  }
+  for (int p = tid; p < cnt; p += blockDim.x) res[p] = __ddiv_rn(res[p], total);
+  __syncthreads();
+  return true;
+}
+
+// Whole pair in one CTA: load both sides, drop zero weights, run all rounds,
+// return R (correctly rounded) in thread 0.  Returns false on invalid input.
+template <int CAP, class Geo>
+NNS_DEV bool cta_solve_pair(CtaCore<CAP>& S, Geo& G, float* xs, float* ys, const float* x, const double* a, int m,
+                            const float* y, const double* b, int n, int d, int metric, unsigned* err, double& cost,
+                            long long& rounds, long long& pe) {
+  bool ok = cta_load_side<Geo::kDP, CAP>(x, a, m, d, xs, S.sres, S.iidx, S, err);
+  if (ok) ok = cta_load_side<Geo::kDP, CAP>(y, b, n, d, ys, S.cres, S.jidx, S, err);
+  if (!ok) return false;
+  if (threadIdx.x == 0) {
+    S.mt = m;
+    S.nt = n;
+  }
+  for (int i = threadIdx.x; i < XS_LIMBS; i += blockDim.x) S.acc[i] = 0ULL;
+  __syncthreads();
+  cta_compact(S, G);  // drop zero weights
+  CtaOut O{nullptr, S.acc, nullptr, nullptr, nullptr, 0, nullptr, nullptr, err};
+  unsigned long long nnz = 0;
+  rounds = 0;
+  pe = 0;
+  cta_rounds(S, G, metric, O, nnz, rounds, pe, (long long)m + n);
+  __syncthreads();
+  if (threadIdx.x == 0) cost = xs_round(S.acc);
+  return true;
+}
+
+}  // namespace nnsemd

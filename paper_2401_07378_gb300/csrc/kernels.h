@@ -13,8 +13,10 @@ namespace nnsemd {
 // never reads past its buffer.
 constexpr int K1_TS = 256;
 constexpr int PAD_POINTS = K1_TS;
-// Largest active set the single-CTA solver keeps in shared memory.
+// Largest active set the single-CTA solver keeps in shared memory (d <= 8:
+// with coordinates; d > 8: per-point state only, coordinates stay in L2).
 constexpr int FIN_MAX = 1024;
+constexpr int FIN_MAX_HD = 2048;
 
 __host__ __device__ inline int padded_dim(int d) { return d <= 2 ? 2 : (d <= 4 ? 4 : 8); }
 __host__ __device__ inline int64_t pad_points(int64_t n) { return (n + PAD_POINTS - 1) / PAD_POINTS * PAD_POINTS; }
@@ -83,5 +85,15 @@ struct BatchArgs {
   unsigned* err;
 };
 int launch_batched_lowd(const BatchArgs& A, int grid, cudaStream_t st);
+
+// highd.cu (d > 8) ---------------------------------------------------------
+// FP32 NNS over all active suppliers for the first `ncons` active consumers,
+// or, with `cons`, for the consumer positions listed there (count in
+// ncons_dev when given, else ncons).  Merges into B.nnkey with atomicMin.
+int launch_nns_f32(const SolveBufs& B, int mt, int ncons, const int* cons, const int* ncons_dev, cudaStream_t st);
+int launch_finish_hd(const SolveBufs& B, int64_t round_limit, cudaStream_t st);
+int launch_batched_hd(const BatchArgs& A, int grid, cudaStream_t st);
+// All d coordinates of both sides finite (else EF_NONFINITE).
+void launch_check_finite(const float* v, int64_t count, unsigned* err, cudaStream_t st);
 
 }  // namespace nnsemd

@@ -21,6 +21,7 @@
 #include <math_constants.h>
 
 #include "common.cuh"
+#include "cta.cuh"
 #include "kernels.h"
 
 namespace nnsemd {
@@ -217,236 +218,21 @@ int launch_nns_lowd(const SolveBufs& B, int mt, int nt, cudaStream_t st) {
 }
 
 // --------------------------------------------------------------------------
-// the single-CTA solver
+// one-CTA solver, d <= 8 (coordinates in shared memory)
 // --------------------------------------------------------------------------
 
-constexpr int FIN_THREADS = 1024;
-
-template <int DP>
-struct FinSmem {
-  float xs[FIN_MAX * DP];
-  float ys[FIN_MAX * DP];
-  double sres[FIN_MAX];
-  double cres[FIN_MAX];
-  int iidx[FIN_MAX];
-  int jidx[FIN_MAX];
-  unsigned long long nnk[FIN_MAX];
-  unsigned long long mem[FIN_MAX];
-  unsigned long long mem2[FIN_MAX];
-  int cnt[FIN_MAX + 1];
-  int off[FIN_MAX + 1];
-  unsigned long long acc[XS_LIMBS];
-  int wt[33];
-  int mt, nt;
-  unsigned nflow;
-  double total;
-};
-
-// Exclusive prefix sum over the block; `total` receives the block sum.
-NNS_DEV int block_scan_excl(int v, int* wt, int& total) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int t = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += t;
-  }
-  if (lane == 31) wt[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    const int nw = blockDim.x >> 5;
-    int t = lane < nw ? wt[lane] : 0;
-    int y = t;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int u = __shfl_up_sync(0xffffffffu, y, o);
-      if (lane >= o) y += u;
-    }
-    wt[lane] = y - t;
-    if (lane == 31) wt[32] = y;
-  }
-  __syncthreads();
-  total = wt[32];
-  const int r = wt[w] + x - v;
-  __syncthreads();
-  return r;
-}
-
-// Stable compaction of both active lists to the points with weight left.
-template <int DP>
-NNS_DEV void cta_compact(FinSmem<DP>& S) {
-  const int tid = threadIdx.x;
-  const int mt = S.mt, nt = S.nt;
-  const bool ks = tid < mt && S.sres[tid] > 0.0;
-  const bool kc = tid < nt && S.cres[tid] > 0.0;
-  float xv[DP], yv[DP];
-  double sv = 0.0, cv = 0.0;
-  int iv = 0, jv = 0;
-  if (ks) {
-#pragma unroll
-    for (int k = 0; k < DP; ++k) xv[k] = S.xs[tid * DP + k];
-    sv = S.sres[tid];
-    iv = S.iidx[tid];
-  }
-  if (kc) {
-#pragma unroll
-    for (int k = 0; k < DP; ++k) yv[k] = S.ys[tid * DP + k];
-    cv = S.cres[tid];
-    jv = S.jidx[tid];
-  }
-  int tot;
-  const int ex = block_scan_excl((ks ? 1 : 0) | (kc ? (1 << 16) : 0), S.wt, tot);
-  if (ks) {
-    const int p = ex & 0xffff;
-#pragma unroll
-    for (int k = 0; k < DP; ++k) S.xs[p * DP + k] = xv[k];
-    S.sres[p] = sv;
-    S.iidx[p] = iv;
-  }
-  if (kc) {
-    const int q = ex >> 16;
-#pragma unroll
-    for (int k = 0; k < DP; ++k) S.ys[q * DP + k] = yv[k];
-    S.cres[q] = cv;
-    S.jidx[q] = jv;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    S.mt = tot & 0xffff;
-    S.nt = tot >> 16;
-  }
-  __syncthreads();
-}
-
-struct CtaOut {
-  double* terms;                 // global per-flow terms (nullable)
-  unsigned long long* acc;       // exact accumulator for R (shared, nullable)
-  int32_t* plan_i;               // plan (nullable)
-  int32_t* plan_j;
-  double* plan_f;
-  long long plan_cap;
-  double* s_glob;                // residual write-back by original index (nullable)
-  double* c_glob;
-  unsigned* err;
-};
-
-// Rounds of Alg. 1 until one active side is empty.  nnz, rounds and
-// pair_evals are running totals owned by thread 0 (valid in every thread on
-// return).
 template <int D, int DP, bool L1>
-NNS_DEV void cta_rounds(FinSmem<DP>& S, int metric, const CtaOut& O, unsigned long long& nnz, long long& rounds,
-                        long long& pair_evals, long long round_limit) {
-  const int tid = threadIdx.x;
-  const int T = blockDim.x;
-  for (;;) {
-    const int mt = S.mt, nt = S.nt;
-    if (mt == 0 || nt == 0) break;
-    if (rounds >= round_limit) {
-      if (tid == 0) atomicOr(O.err, EF_ITER);
-      break;
-    }
-    // ---- NNS: nearest active supplier of every active consumer
-    int split = 1;
-    while (split < 32 && nt * split * 2 <= T) split <<= 1;
-    {
-      const int q = tid / split, part = tid & (split - 1);
-      unsigned long long bk = ~0ULL;
-      if (q < nt) {
-        float yv[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) yv[k] = S.ys[q * DP + k];
-        float best = CUDART_INF_F;
-        int bp = -1;
-        for (int p = part; p < mt; p += split) {
-          const float v = L1 ? key32<METRIC_L1>(S.xs + p * DP, yv, D) : key32<METRIC_SQL2>(S.xs + p * DP, yv, D);
-          if (bp < 0 || v < best) { best = v; bp = p; }
-        }
-        if (bp >= 0) bk = pack_key(best, (unsigned)bp);
-      }
-      for (int o = 1; o < split; o <<= 1) {
-        const unsigned long long other = __shfl_xor_sync(0xffffffffu, bk, o);
-        bk = other < bk ? other : bk;
-      }
-      if (q < nt && part == 0) S.nnk[q] = bk;
-    }
-    for (int p = tid; p < mt; p += T) S.cnt[p] = 0;
-    if (tid == 0) S.nflow = 0;
-    __syncthreads();
-    // ---- group the consumers by their supplier
-    for (int q = tid; q < nt; q += T) atomicAdd(&S.cnt[(int)(S.nnk[q] & 0xffffffffULL)], 1);
-    __syncthreads();
-    {
-      int tot;
-      const int v = tid < mt ? S.cnt[tid] : 0;
-      const int ex = block_scan_excl(v, S.wt, tot);
-      if (tid < mt) S.off[tid] = ex;
-      if (tid == 0) S.off[mt] = tot;
-    }
-    __syncthreads();
-    for (int q = tid; q < nt; q += T) {
-      const unsigned long long key = S.nnk[q];
-      const int p = (int)(key & 0xffffffffULL);
-      const int slot = S.off[p] + atomicSub(&S.cnt[p], 1) - 1;
-      S.mem[slot] = (key & 0xffffffff00000000ULL) | (unsigned)q;
-    }
-    __syncthreads();
-    // ---- greedy order: rank of each member inside its group
-    for (int r = tid; r < nt; r += T) {
-      const unsigned long long e = S.mem[r];
-      const int q = (int)(e & 0xffffffffULL);
-      const int p = (int)(S.nnk[q] & 0xffffffffULL);
-      const int b = S.off[p], en = S.off[p + 1];
-      int rank = 0;
-      for (int u = b; u < en; ++u) rank += S.mem[u] < e;
-      S.mem2[b + rank] = e;
-    }
-    __syncthreads();
-    // ---- flow & cost (greedy protocol), one supplier per thread
-    for (int p = tid; p < mt; p += T) {
-      const int b = S.off[p], en = S.off[p + 1];
-      if (b == en) continue;
-      double s = S.sres[p];
-      for (int r = b; r < en; ++r) {
-        if (!(s > 0.0)) break;
-        const int q = (int)(S.mem2[r] & 0xffffffffULL);
-        const double c = S.cres[q];
-        const double f = s < c ? s : c;
-        s = __dsub_rn(s, f);
-        const double cn = __dsub_rn(c, f);
-        S.cres[q] = cn;
-        const double Dij = cost_dist64(S.xs + p * DP, S.ys + q * DP, D, metric);
-        const double term = __dmul_rn(f, Dij);
-        const unsigned long long slot = nnz + atomicAdd(&S.nflow, 1u);
-        if (O.terms) O.terms[slot] = term;
-        if (O.acc) xs_add(O.acc, term);
-        if (O.plan_i) {
-          if ((long long)slot < O.plan_cap) {
-            O.plan_i[slot] = S.iidx[p];
-            O.plan_j[slot] = S.jidx[q];
-            O.plan_f[slot] = f;
-          } else {
-            atomicOr(O.err, EF_CAPACITY);
-          }
-        }
-        if (O.c_glob) O.c_glob[S.jidx[q]] = cn;
-      }
-      S.sres[p] = s;
-      if (O.s_glob) O.s_glob[S.iidx[p]] = s;
-    }
-    __syncthreads();
-    nnz += S.nflow;
-    rounds += 1;
-    pair_evals += (long long)mt * nt;
-    // ---- weights update: retire spent points, compact
-    cta_compact(S);
-  }
-}
+struct LowdSmem {
+  CtaCore<FIN_MAX> S;
+  GeoSmem<D, DP, L1, FIN_MAX> G;
+};
 
 // Tail of a single large solve: load the current active lists and finish.
 template <int D, int DP, bool L1>
 __global__ void __launch_bounds__(FIN_THREADS, 1) k_finish(SolveBufs B, long long round_limit) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  FinSmem<DP>& S = *reinterpret_cast<FinSmem<DP>*>(smem_raw);
+  LowdSmem<D, DP, L1>& L = *reinterpret_cast<LowdSmem<D, DP, L1>*>(smem_raw);
+  CtaCore<FIN_MAX>& S = L.S;
   const int tid = threadIdx.x;
   const int mt = B.st->mt, nt = B.st->nt;
   if (mt > FIN_MAX || nt > FIN_MAX) {
@@ -457,13 +243,13 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_finish(SolveBufs B, long lon
   const float* ya = B.ya[B.cur];
   for (int p = tid; p < mt; p += blockDim.x) {
 #pragma unroll
-    for (int k = 0; k < DP; ++k) S.xs[p * DP + k] = xa[(size_t)p * DP + k];
+    for (int k = 0; k < DP; ++k) L.G.xs[p * DP + k] = xa[(size_t)p * DP + k];
     S.iidx[p] = B.ia[B.cur][p];
     S.sres[p] = B.s[S.iidx[p]];
   }
   for (int q = tid; q < nt; q += blockDim.x) {
 #pragma unroll
-    for (int k = 0; k < DP; ++k) S.ys[q * DP + k] = ya[(size_t)q * DP + k];
+    for (int k = 0; k < DP; ++k) L.G.ys[q * DP + k] = ya[(size_t)q * DP + k];
     S.jidx[q] = B.ja[B.cur][q];
     S.cres[q] = B.c[S.jidx[q]];
   }
@@ -475,7 +261,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_finish(SolveBufs B, long lon
   CtaOut O{B.terms, nullptr, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, B.s, B.c, &B.st->err};
   unsigned long long nnz = B.st->nnz;
   long long rounds = B.st->rounds, pe = B.st->pair_evals;
-  cta_rounds<D, DP, L1>(S, B.metric, O, nnz, rounds, pe, round_limit);
+  cta_rounds(S, L.G, B.metric, O, nnz, rounds, pe, round_limit);
   if (tid == 0) {
     B.st->nnz = nnz;
     B.st->rounds = rounds;
@@ -487,7 +273,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_finish(SolveBufs B, long lon
 
 template <int D, int DP, bool L1>
 static int finish_t(const SolveBufs& B, long long round_limit, cudaStream_t st) {
-  const size_t smem = sizeof(FinSmem<DP>);
+  const size_t smem = sizeof(LowdSmem<D, DP, L1>);
   cudaError_t e = cudaFuncSetAttribute(k_finish<D, DP, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return -1;
   k_finish<D, DP, L1><<<1, FIN_THREADS, smem, st>>>(B, round_limit);
@@ -512,43 +298,10 @@ int launch_finish(const SolveBufs& B, int64_t round_limit, cudaStream_t st) {
 // pair solved start to finish by one CTA (Sec. III-D batch processing)
 // --------------------------------------------------------------------------
 
-template <int DP>
-NNS_DEV bool cta_load_side(const float* pts, const double* w, int cnt, int d, float* dst, double* res, int* idx,
-                           unsigned long long* acc, double* total_slot, unsigned* err) {
-  const int tid = threadIdx.x;
-  for (int i = tid; i < XS_LIMBS; i += blockDim.x) acc[i] = 0ULL;
-  __syncthreads();
-  bool bad = false;
-  for (int p = tid; p < cnt; p += blockDim.x) {
-#pragma unroll
-    for (int k = 0; k < DP; ++k) {
-      const float v = k < d ? pts[(size_t)p * d + k] : 0.f;
-      if (!isfinite(v)) bad = true;
-      dst[p * DP + k] = v;
-    }
-    const double wv = w[p];
-    if (!isfinite(wv) || wv < 0.0) bad = true;
-    res[p] = wv;
-    idx[p] = p;
-    if (isfinite(wv)) xs_add(acc, wv);
-  }
-  bad = __syncthreads_or(bad);
-  if (tid == 0) *total_slot = xs_round(acc);
-  __syncthreads();
-  const double total = *total_slot;
-  if (bad || !(total > 0.0)) {
-    if (tid == 0) atomicOr(err, bad ? EF_NONFINITE : EF_ZERO_MASS);
-    return false;
-  }
-  for (int p = tid; p < cnt; p += blockDim.x) res[p] = __ddiv_rn(res[p], total);
-  __syncthreads();
-  return true;
-}
-
 template <int D, int DP, bool L1>
 __global__ void __launch_bounds__(FIN_THREADS, 1) k_batched_lowd(BatchArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  FinSmem<DP>& S = *reinterpret_cast<FinSmem<DP>*>(smem_raw);
+  LowdSmem<D, DP, L1>& L = *reinterpret_cast<LowdSmem<D, DP, L1>*>(smem_raw);
   __shared__ int s_item;
   const int tid = threadIdx.x;
   for (;;) {
@@ -560,28 +313,12 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_batched_lowd(BatchArgs A) {
     const int pr = A.pair_ids[item];
     const int64_t xo = A.x_off[pr], yo = A.y_off[pr];
     const int m = (int)(A.x_off[pr + 1] - xo), n = (int)(A.y_off[pr + 1] - yo);
-    bool ok = cta_load_side<DP>(A.x + xo * A.d, A.a + xo, m, A.d, S.xs, S.sres, S.iidx, S.acc, &S.total, A.err);
-    if (ok)
-      ok = cta_load_side<DP>(A.y + yo * A.d, A.b + yo, n, A.d, S.ys, S.cres, S.jidx, S.acc, &S.total, A.err);
-    if (!ok) {
-      if (tid == 0) A.costs[pr] = CUDART_NAN;
-      __syncthreads();
-      continue;
-    }
-    if (tid == 0) {
-      S.mt = m;
-      S.nt = n;
-    }
-    for (int i = tid; i < XS_LIMBS; i += blockDim.x) S.acc[i] = 0ULL;
-    __syncthreads();
-    cta_compact(S);  // drop zero weights
-    CtaOut O{nullptr, S.acc, nullptr, nullptr, nullptr, 0, nullptr, nullptr, A.err};
-    unsigned long long nnz = 0;
+    double cost = 0.0;
     long long rounds = 0, pe = 0;
-    cta_rounds<D, DP, L1>(S, A.metric, O, nnz, rounds, pe, (long long)m + n);
-    __syncthreads();
+    const bool ok = cta_solve_pair(L.S, L.G, L.G.xs, L.G.ys, A.x + xo * A.d, A.a + xo, m, A.y + yo * A.d, A.b + yo,
+                                   n, A.d, A.metric, A.err, cost, rounds, pe);
     if (tid == 0) {
-      A.costs[pr] = xs_round(S.acc);
+      A.costs[pr] = ok ? cost : CUDART_NAN;
       if (A.rounds) A.rounds[pr] = rounds;
       if (A.pair_evals) A.pair_evals[pr] = pe;
     }
@@ -591,7 +328,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_batched_lowd(BatchArgs A) {
 
 template <int D, int DP, bool L1>
 static int batched_t(const BatchArgs& A, int grid, cudaStream_t st) {
-  const size_t smem = sizeof(FinSmem<DP>);
+  const size_t smem = sizeof(LowdSmem<D, DP, L1>);
   cudaError_t e =
       cudaFuncSetAttribute(k_batched_lowd<D, DP, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return -1;
@@ -655,7 +392,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 1)
     k_small_noalloc(const float* x, const double* a, int m, const float* y, const double* b, int n, int d,
                     int metric, double* cost_out, NoAllocScratch* scr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  FinSmem<DP>& S = *reinterpret_cast<FinSmem<DP>*>(smem_raw);
+  LowdSmem<D, DP, L1>& L = *reinterpret_cast<LowdSmem<D, DP, L1>*>(smem_raw);
   const int tid = threadIdx.x;
   if (tid == 0) {
     scr->err = 0;
@@ -663,26 +400,11 @@ __global__ void __launch_bounds__(FIN_THREADS, 1)
     scr->pair_evals = 0;
   }
   __syncthreads();
-  bool ok = cta_load_side<DP>(x, a, m, d, S.xs, S.sres, S.iidx, S.acc, &S.total, &scr->err);
-  if (ok) ok = cta_load_side<DP>(y, b, n, d, S.ys, S.cres, S.jidx, S.acc, &S.total, &scr->err);
-  if (!ok) {
-    if (tid == 0) *cost_out = CUDART_NAN;
-    return;
-  }
-  if (tid == 0) {
-    S.mt = m;
-    S.nt = n;
-  }
-  for (int i = tid; i < XS_LIMBS; i += blockDim.x) S.acc[i] = 0ULL;
-  __syncthreads();
-  cta_compact(S);
-  CtaOut O{nullptr, S.acc, nullptr, nullptr, nullptr, 0, nullptr, nullptr, &scr->err};
-  unsigned long long nnz = 0;
+  double cost = 0.0;
   long long rounds = 0, pe = 0;
-  cta_rounds<D, DP, L1>(S, metric, O, nnz, rounds, pe, (long long)m + n);
-  __syncthreads();
+  const bool ok = cta_solve_pair(L.S, L.G, L.G.xs, L.G.ys, x, a, m, y, b, n, d, metric, &scr->err, cost, rounds, pe);
   if (tid == 0) {
-    *cost_out = xs_round(S.acc);
+    *cost_out = ok ? cost : CUDART_NAN;
     scr->rounds = rounds;
     scr->pair_evals = pe;
   }
@@ -691,14 +413,13 @@ __global__ void __launch_bounds__(FIN_THREADS, 1)
 template <int D, int DP, bool L1>
 static cudaError_t small_noalloc_t(const float* x, const double* a, int m, const float* y, const double* b, int n,
                                    int metric, double* cost_out, NoAllocScratch* scr, cudaStream_t st) {
-  const size_t smem = sizeof(FinSmem<DP>);
+  const size_t smem = sizeof(LowdSmem<D, DP, L1>);
   cudaError_t e =
       cudaFuncSetAttribute(k_small_noalloc<D, DP, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_small_noalloc<D, DP, L1><<<1, FIN_THREADS, smem, st>>>(x, a, m, y, b, n, D, metric, cost_out, scr);
   return cudaGetLastError();
 }
-
 // Device address of the scratch array, looked up once per device with that
 // device current (in host code the array's name is only a stand-in).
 static std::mutex g_noalloc_mu;

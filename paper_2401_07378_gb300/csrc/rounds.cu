@@ -229,6 +229,10 @@ __global__ void __launch_bounds__(CP_THREADS) k_compact_scatter(CompactArgs A) {
   for (int k = 0; k < CP_ITEMS; ++k) {
     if (!flags[k]) continue;
     const int pos = base + k;
+    if (!S.pts_in) {  // index-only list (d > 8: coordinates stay in place)
+      S.idx_out[pos_out++] = origs[k];
+      continue;
+    }
     float v[DP];
 #pragma unroll
     for (int e = 0; e < DP; ++e) {
@@ -251,7 +255,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_compact_scatter(CompactArgs A) {
   if (lb == S.nblocks - 1) {
     const int total = s_off + wsum[CP_THREADS / 32];
     if (threadIdx.x == 0) *S.count_out = total;
-    const int padded = (int)pad_points(total);
+    const int padded = S.pts_out ? (int)pad_points(total) : 0;
     for (int p = total + threadIdx.x; p < padded; p += CP_THREADS)
 #pragma unroll
       for (int e = 0; e < DP; ++e) S.pts_out[(size_t)p * DP + e] = CUDART_NAN_F;
@@ -268,10 +272,30 @@ static void compact_launch(CompactArgs& A, int dp, cudaStream_t st) {
   else k_compact_scatter<8><<<nb, CP_THREADS, 0, st>>>(A);
 }
 
+__global__ void k_check_finite(const float* __restrict__ v, int64_t count, unsigned* err) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(v[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, EF_NONFINITE);
+}
+
+void launch_check_finite(const float* v, int64_t count, unsigned* err, cudaStream_t st) {
+  int64_t g = (count + 1023) / 1024;
+  if (g > 152 * 8) g = 152 * 8;
+  k_check_finite<<<(int)(g < 1 ? 1 : g), 256, 0, st>>>(v, count, err);
+}
+
 int launch_initial_pack(SolveBufs& B, cudaStream_t st) {
   CompactArgs A{};
-  A.side[0] = CompactSide{B.x, B.d, nullptr, B.s, B.xa[B.cur], B.ia[B.cur], (int)B.m, &B.st->mt, 0, 1};
-  A.side[1] = CompactSide{B.y, B.d, nullptr, B.c, B.ya[B.cur], B.ja[B.cur], (int)B.n, &B.st->nt, 0, 1};
+  const bool packed = B.dp > 0;  // d > 8 keeps index-only active lists
+  if (!packed) {
+    launch_check_finite(B.x, B.m * B.d, &B.st->err, st);
+    launch_check_finite(B.y, B.n * B.d, &B.st->err, st);
+  }
+  A.side[0] = CompactSide{packed ? B.x : nullptr, B.d, nullptr, B.s, packed ? B.xa[B.cur] : nullptr, B.ia[B.cur],
+                          (int)B.m, &B.st->mt, 0, 1};
+  A.side[1] = CompactSide{packed ? B.y : nullptr, B.d, nullptr, B.c, packed ? B.ya[B.cur] : nullptr, B.ja[B.cur],
+                          (int)B.n, &B.st->nt, 0, 1};
   A.blockcounts = B.blockcounts;
   A.err = &B.st->err;
   compact_launch(A, B.dp, st);
@@ -529,8 +553,11 @@ int launch_big_round(SolveBufs& B, int mt, int nt, cudaStream_t st) {
   k_flow_big<<<152, BIG_THREADS, 0, st>>>(F);
   // weights update: compact into the other buffer
   CompactArgs A{};
-  A.side[0] = CompactSide{B.xa[cur], B.dp, B.ia[cur], B.s, B.xa[cur ^ 1], B.ia[cur ^ 1], mt, &B.st->mt, 0, 0};
-  A.side[1] = CompactSide{B.ya[cur], B.dp, B.ja[cur], B.c, B.ya[cur ^ 1], B.ja[cur ^ 1], nt, &B.st->nt, 0, 0};
+  const bool packed = B.dp > 0;
+  A.side[0] = CompactSide{packed ? B.xa[cur] : nullptr, B.dp, B.ia[cur], B.s, packed ? B.xa[cur ^ 1] : nullptr,
+                          B.ia[cur ^ 1], mt, &B.st->mt, 0, 0};
+  A.side[1] = CompactSide{packed ? B.ya[cur] : nullptr, B.dp, B.ja[cur], B.c, packed ? B.ya[cur ^ 1] : nullptr,
+                          B.ja[cur ^ 1], nt, &B.st->nt, 0, 0};
   A.blockcounts = B.blockcounts;
   A.err = &B.st->err;
   compact_launch(A, B.dp, st);

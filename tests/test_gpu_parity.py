@@ -176,8 +176,14 @@ def test_errors_are_reported(ctx):
         gpu_solve(ctx, x, np.zeros(4), x, w, "l2")
     assert e.value.status == 3
     with pytest.raises(NNSEMDError) as e:
-        gpu_solve(ctx, np.zeros((4, 9), np.float32), w, np.zeros((4, 9), np.float32), w, "l2")
+        ctx.solve(dev(x, torch.float32), dev(w, torch.float64), dev(x, torch.float32), dev(w, torch.float64),
+                  metric="l2", precision="fp8")
     assert e.value.status == 8
+    bad9 = np.zeros((4, 9), np.float32)
+    bad9[2, 7] = np.inf
+    with pytest.raises(NNSEMDError) as e:
+        gpu_solve(ctx, bad9, w, np.zeros((4, 9), np.float32), w, "l2")
+    assert e.value.status == 2
     # the context stays usable after errors
     p = wl.single_pair(2)
     assert gpu_solve(ctx, p.x, p.a, p.y, p.b, "l2").cost == oracle.solve_pair(p, "l2").cost
@@ -195,3 +201,47 @@ def test_colour_transfer_full_size(ctx):
     assert np.array_equal(np.sort(gi), np.arange(65536)) and np.array_equal(np.sort(gj), np.arange(65536))
     ref = oracle.solve_pair(p, "sql2")
     assert_parity(res, ref)
+
+
+# ---------------------------------------------------------------------------
+# d > 8: tiled FP32 NNS, index-only active lists, high-d tail and batches
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d", [9, 16, 64, 130])
+@pytest.mark.parametrize("metric", ["l2", "l1"])
+def test_random_pairs_high_d(ctx, d, metric):
+    rng = np.random.default_rng(200 + d)
+    for m, n, w in ((1, 50, "dirichlet"), (70, 1, "uniform"), (257, 190, "dirichlet"), (2100, 1900, "dirichlet")):
+        p = wl.uniform_pair(m, n, d, int(rng.integers(1 << 30)), w)
+        ref = oracle.solve_pair(p, metric)
+        assert_parity(gpu_solve(ctx, p.x, p.a, p.y, p.b, metric), ref)
+
+
+def test_gmm_pair_d64(ctx):
+    p = wl.gmm_pair(seed=1, n=6000, d=64)
+    ref = oracle.solve_pair(p, "l2")
+    assert_parity(gpu_solve(ctx, p.x, p.a, p.y, p.b, "l2"), ref)
+
+
+def test_batched_documents_d300(ctx):
+    batch = wl.doc_knn(num_docs=48, seed=3, vocab_size=5000)
+    costs, stats = ctx.solve_batched(dev(batch.x, torch.float32), dev(batch.a, torch.float64), batch.x_off,
+                                     dev(batch.y, torch.float32), dev(batch.b, torch.float64), batch.y_off,
+                                     metric="l2")
+    costs = costs.cpu().numpy()
+    rounds = 0
+    for k in range(batch.num_pairs):
+        ref = oracle.solve_pair(batch.pair(k), "l2")
+        assert costs[k] == ref.cost, k
+        rounds += ref.rounds
+    assert stats["rounds"] == rounds
+
+
+def test_batched_retrieval_signatures_d128(ctx):
+    batch = wl.retrieval(num_pairs=6, seed=4, lo=256, hi=2048)
+    costs, _ = ctx.solve_batched(dev(batch.x, torch.float32), dev(batch.a, torch.float64), batch.x_off,
+                                 dev(batch.y, torch.float32), dev(batch.b, torch.float64), batch.y_off,
+                                 metric="l2")
+    costs = costs.cpu().numpy()
+    for k in range(batch.num_pairs):
+        assert costs[k] == oracle.solve_pair(batch.pair(k), "l2").cost, k
