@@ -99,9 +99,30 @@ int ensure_ws(nnsemd_ctx* ctx, size_t bytes) {
 
 // Lay out the buffers of a single-pair solve; with base == nullptr only the
 // size is computed.
-size_t layout_solve(void* base, int64_t m, int64_t n, int d, SolveBufs& B) {
+size_t layout_solve(void* base, int64_t m, int64_t n, int d, SolveBufs& B, int precision = 0) {
   Carve C(base);
   const int dp = d <= 8 ? padded_dim(d) : 0;
+  B.precision = precision;
+  if (precision != NNSEMD_FP32) {
+    const size_t kb = tc_kb(d, precision);
+    const int64_t bn = tc_bn(kb);
+    const int64_t qrows = (n + 127) / 128 * 128, srows = (m + bn - 1) / bn * bn;
+    TcBufs& T = B.tc;
+    T.A = C.take<uint8_t>(qrows * kb);
+    T.B = C.take<uint8_t>(srows * kb);
+    T.nrm_x = C.take<float>(srows);
+    T.nrm_y = C.take<float>(qrows);
+    T.scale_x = C.take<float>(srows);
+    T.scale_y = C.take<float>(qrows);
+    T.stats = C.take<unsigned>(8);
+    T.max_chunks = 152;
+    const int64_t cand = (152 + qrows / 128) * 128 * 8;
+    T.cand_v = C.take<float>(cand);
+    T.cand_p = C.take<int>(cand);
+    T.fallback = C.take<int>(n);
+    T.nfallback = C.take<int>(1);
+    T.ev0 = T.ev1 = nullptr;
+  }
   B.st = C.take<DevState>(1);
   B.xs_acc = C.take<unsigned long long>(4 * XS_LIMBS);
   B.s = C.take<double>(m);
@@ -134,12 +155,20 @@ int map_err_bits(nnsemd_ctx* ctx, unsigned bits) {
   return fail(ctx, NNSEMD_ERR_CUDA, "internal consistency check failed on the device (0x%x)", bits);
 }
 
-int check_opts(nnsemd_ctx* ctx, const nnsemd_options* opt, int d, int& metric) {
+int check_opts(nnsemd_ctx* ctx, const nnsemd_options* opt, int d, int& metric, int* precision = nullptr) {
   metric = NNSEMD_L2;
+  if (precision) *precision = NNSEMD_FP32;
   if (opt) {
     metric = opt->metric;
     if (opt->flags & ~NNSEMD_FLAG_TIME_KERNELS) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "unknown options.flags bits");
-    if (opt->precision != NNSEMD_FP32) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "reduced precision needs d > 8");
+    if (opt->precision < NNSEMD_FP32 || opt->precision > NNSEMD_FP8)
+      return fail(ctx, NNSEMD_ERR_INVALID_ARG, "unknown precision %d", opt->precision);
+    if (opt->precision != NNSEMD_FP32) {
+      if (!precision) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "reduced precision is served by nnsemd_solve only");
+      if (d <= 8) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "reduced precision serves d > 8 (d = %d)", d);
+      if (opt->metric == NNSEMD_L1) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "the L1 distance has no contraction form");
+      *precision = opt->precision;
+    }
   }
   if (metric < 0 || metric > 2) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "unknown metric %d", metric);
   if (d < 1) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "d must be >= 1");
@@ -195,10 +224,20 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
     }
     if (rounds >= round_limit) return fail(ctx, NNSEMD_ERR_ITER_LIMIT, "round limit m + n exceeded");
     CK(cudaMemsetAsync(B.nnkey, 0xff, (size_t)nt * sizeof(unsigned long long), st));
-    if (timed) CK(cudaEventRecord(ctx->ev[0], st));
-    const int nrc = lowd ? launch_nns_lowd(B, mt, nt, st) : launch_nns_f32(B, mt, nt, nullptr, nullptr, st);
-    if (nrc) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "no NNS kernel for d=%d", B.d);
-    if (timed) CK(cudaEventRecord(ctx->ev[1], st));
+    int nrc;
+    if (B.precision != NNSEMD_FP32) {
+      // tensor-core candidates + exact re-rank + certificate + FP32 rescan;
+      // the timing events bracket the tensor-core kernel alone
+      B.tc.ev0 = timed ? ctx->ev[0] : nullptr;
+      B.tc.ev1 = timed ? ctx->ev[1] : nullptr;
+      nrc = launch_nns_tc(B, B.tc, mt, nt, B.precision, st);
+      L += 5;
+    } else {
+      if (timed) CK(cudaEventRecord(ctx->ev[0], st));
+      nrc = lowd ? launch_nns_lowd(B, mt, nt, st) : launch_nns_f32(B, mt, nt, nullptr, nullptr, st);
+      if (timed) CK(cudaEventRecord(ctx->ev[1], st));
+    }
+    if (nrc) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "NNS launch failed for d=%d (%d)", B.d, nrc);
     launch_big_round(B, mt, nt, st);
     L += 10;
     CK(cudaGetLastError());
@@ -240,6 +279,8 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
     stats->pair_evals = pair_evals + ctx->hstate->pair_evals;
     stats->leftover_mass = ctx->hstate->leftover;
     stats->kernel_launches = L;
+    stats->certified = (int64_t)ctx->hstate->certified;
+    stats->fallbacks = (int64_t)ctx->hstate->fallbacks;
     stats->nns_kernel_ms = nns_ms;
     stats->nns_kernel_launches = nns_launches;
     stats->nns_kernel_pairs = nns_pairs;
@@ -309,8 +350,8 @@ int nnsemd_solve(nnsemd_ctx* ctx, const float* x, const double* a, int64_t m, co
                  nnsemd_stats* stats) {
   if (!ctx) return NNSEMD_ERR_INVALID_ARG;
   ctx->err.clear();
-  int metric;
-  int rc = check_opts(ctx, opt, d, metric);
+  int metric, precision;
+  int rc = check_opts(ctx, opt, d, metric, &precision);
   if (rc) return rc;
   if ((rc = check_sizes(ctx, m, n))) return rc;
   if (!x || !a || !y || !b || !cost_out) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "null pointer argument");
@@ -320,9 +361,9 @@ int nnsemd_solve(nnsemd_ctx* ctx, const float* x, const double* a, int64_t m, co
     return fail(ctx, NNSEMD_ERR_INVALID_ARG, "plan arrays");
   CK(cudaSetDevice(ctx->device));
   SolveBufs B{};
-  size_t bytes = layout_solve(nullptr, m, n, d, B);
+  size_t bytes = layout_solve(nullptr, m, n, d, B, precision);
   if ((rc = ensure_ws(ctx, bytes))) return rc;
-  layout_solve(ctx->ws, m, n, d, B);
+  layout_solve(ctx->ws, m, n, d, B, precision);
   B.x = x;
   B.y = y;
   B.m = m;

@@ -43,6 +43,8 @@ struct DevState {
   double total_a, total_b;       // normalisation totals (correctly rounded)
   double cost;                   // R (correctly rounded)
   double leftover;               // residual mass after the solve
+  unsigned long long certified;  // reduced precision: consumer searches settled by the certificate
+  unsigned long long fallbacks;  // reduced precision: consumer searches redone in FP32
 };
 
 // --------------------------------------------------------------------------

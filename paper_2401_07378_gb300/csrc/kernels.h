@@ -21,8 +21,27 @@ constexpr int FIN_MAX_HD = 2048;
 __host__ __device__ inline int padded_dim(int d) { return d <= 2 ? 2 : (d <= 4 ? 4 : 8); }
 __host__ __device__ inline int64_t pad_points(int64_t n) { return (n + PAD_POINTS - 1) / PAD_POINTS * PAD_POINTS; }
 
+// Buffers of the reduced-precision NNS step (tc.cu).
+struct TcBufs {
+  uint8_t* A;                  // packed consumer tiles
+  uint8_t* B;                  // packed supplier tiles
+  float* nrm_x;                // per supplier position (padded), +inf on padding
+  float* nrm_y;                // per consumer position
+  float* scale_x;
+  float* scale_y;
+  unsigned* stats;             // [8]: supplier max |x|_2, |x|_1, scale; consumer the same at +4
+  float* cand_v;               // [chunks][nt_pad][8]
+  int* cand_p;
+  int* fallback;               // consumer positions to rescan
+  int* nfallback;              // device counter (this round)
+  int max_chunks;
+  cudaEvent_t ev0, ev1;        // optional: recorded around the tensor-core kernel
+};
+
 // Buffers of one single-pair solve (device pointers inside the workspace).
 struct SolveBufs {
+  int precision;   // nnsemd_precision of the NNS step (0 = FP32)
+  TcBufs tc;       // used when precision != 0
   const float* x;  // original coordinates [m][d]
   const float* y;  // [n][d]
   int64_t m, n;
@@ -95,5 +114,12 @@ int launch_finish_hd(const SolveBufs& B, int64_t round_limit, cudaStream_t st);
 int launch_batched_hd(const BatchArgs& A, int grid, cudaStream_t st);
 // All d coordinates of both sides finite (else EF_NONFINITE).
 void launch_check_finite(const float* v, int64_t count, unsigned* err, cudaStream_t st);
+
+// tc.cu (reduced precision, d > 8, squared-Euclidean order) ----------------
+size_t tc_kb(int d, int precision);  // packed bytes per row
+int tc_bn(size_t kb);                // supplier rows per tile
+// NNS of every active consumer: tensor-core candidates, exact FP32 re-rank,
+// certificate, FP32 rescan of the rest.  Writes B.nnkey (must be all ones).
+int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int precision, cudaStream_t st);
 
 }  // namespace nnsemd

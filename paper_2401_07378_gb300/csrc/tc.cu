@@ -1,0 +1,531 @@
+// Reduced-precision NNS for d > 8 on the 5th-generation tensor cores
+// (tcgen05, sm_103a), followed by an exact FP32 re-rank with a certificate.
+//
+//   approx(i, j) = |y_j|^2 + |x_i|^2 - 2 <x~_i, y~_j>
+//
+// where x~, y~ are BF16 / FP16 / FP8-E4M3 copies of the points (FP16 and FP8
+// with a per-row power-of-two scale) and the dot products accumulate in FP32
+// in tensor memory.  For every active consumer the kernel keeps the K
+// suppliers with the smallest approximate distance.  The re-rank then
+// computes the exact FP32 key (the same definition as every other path) of
+// those candidates, takes the smallest (lowest position on ties), and
+// certifies it: every supplier that is not a candidate has an approximate
+// distance >= the K-th candidate's, so its true distance is >= that value
+// minus a rigorous bound on the quantisation and accumulation error; if the
+// best exact key is strictly below the resulting floor (shrunk by the FP32
+// key's own rounding bound) no other supplier can win, and the choice is the
+// FP32 path's choice.  Consumers that cannot be certified are scanned again
+// in FP32 (k_nns_f32_tiled).  The result is therefore identical to the FP32
+// path; only the time changes.
+//
+// K2 k_nns_tc: a CTA owns 128 consumers (the MMA's M) and streams supplier
+// tiles of BN rows.  Warp 0 issues 1-D bulk copies (TMA) of the packed tiles
+// into a ring of shared-memory stages; warp 1 allocates tensor memory and
+// one elected thread issues tcgen05.mma for each tile into one of two FP32
+// accumulators (BN columns each); warps 2..5 read each accumulator row back
+// with tcgen05.ld (one consumer per thread) and update its top-K.  Every wait
+// on an mbarrier is bounded and raises EF_TIMEOUT instead of hanging.
+#include <math_constants.h>
+
+#include <algorithm>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "common.cuh"
+#include "cta.cuh"
+#include "kernels.h"
+
+namespace nnsemd {
+
+constexpr int TC_BM = 128;         // consumers per CTA (MMA M)
+constexpr int TC_K = 8;            // candidates kept per consumer per chunk
+constexpr int TC_THREADS = 192;    // 6 warps
+constexpr int TC_SMEM_BUDGET = 220 * 1024;
+
+enum TcFmt : int { FMT_F16 = 0, FMT_BF16 = 1, FMT_E4M3 = 2 };
+
+// --------------------------------------------------------------------------
+// packing: active points -> operand tiles in the K-major, no-swizzle layout
+//
+// A tile of R rows and KB bytes per row is stored as KB/16 column blocks of
+// R rows x 16 bytes: block c holds bytes [16c, 16c+16) of every row, rows 16
+// bytes apart.  Each 8-row x 16-byte piece is one "core matrix"; neighbouring
+// core matrices are 128 bytes apart along M/N (stride byte offset) and
+// R*16 bytes apart along K (leading byte offset).
+// --------------------------------------------------------------------------
+
+NNS_DEV uint16_t to_bits16(float v, int fmt) {
+  if (fmt == FMT_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+  return __half_as_ushort(__float2half_rn(v));
+}
+
+NNS_DEV uint8_t to_e4m3(float v) {
+  return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
+
+// One thread per (point, 16-byte block).  Also writes, per point, the FP32
+// squared norm (sequential fma over the original coordinates), the
+// per-row scale and, in `stats`, the maxima of |v|_2 and |v|_1 over the
+// points (as float bits; all values are >= 0).
+__global__ void k_pack_tc(const float* __restrict__ pts, const int* __restrict__ idx, int cnt, int rows_pad, int d,
+                          int kb, int fmt, int tile_rows, uint8_t* __restrict__ out, float* __restrict__ nrm,
+                          float* __restrict__ scale, unsigned* __restrict__ stats) {
+  const int nblk = kb / 16;
+  const int64_t total = (int64_t)rows_pad * nblk;
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(w / nblk), c = (int)(w % nblk);
+    const float* row = p < cnt ? pts + (size_t)idx[p] * d : nullptr;
+    // per-row scale (power of two) for FP16 / FP8: max |v| maps to <= 2^8 / 2^8
+    float s = 1.f;
+    if (row && fmt != FMT_BF16) {
+      float mx = 0.f;
+      for (int k = 0; k < d; ++k) mx = fmaxf(mx, fabsf(row[k]));
+      if (mx > 0.f) {
+        int e;
+        frexpf(mx, &e);  // mx in [2^(e-1), 2^e)
+        s = ldexpf(1.f, e - (fmt == FMT_E4M3 ? 8 : 8));  // scaled max in [2^7, 2^8)
+      }
+    }
+    alignas(16) uint8_t bytes[16];
+    if (fmt == FMT_E4M3) {
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int k = c * 16 + e;
+        const float v = (row && k < d) ? row[k] / s : 0.f;
+        bytes[e] = to_e4m3(v);
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = c * 8 + e;
+        const float v = (row && k < d) ? row[k] / s : 0.f;
+        const uint16_t b = to_bits16(v, fmt);
+        bytes[2 * e] = (uint8_t)(b & 0xff);
+        bytes[2 * e + 1] = (uint8_t)(b >> 8);
+      }
+    }
+    const int t = p / tile_rows, r = p % tile_rows;
+    uint8_t* dst = out + (size_t)t * tile_rows * kb + (size_t)c * tile_rows * 16 + (size_t)r * 16;
+    *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(bytes);
+    if (c == 0) {
+      if (row) {
+        float acc = 0.f, l1 = 0.f;
+        for (int k = 0; k < d; ++k) {
+          acc = __fmaf_rn(row[k], row[k], acc);
+          l1 = __fadd_rn(l1, fabsf(row[k]));
+        }
+        nrm[p] = acc;
+        scale[p] = s;
+        atomicMax(stats + 0, __float_as_uint(sqrtf(acc) * (1.f + 1e-6f)));
+        atomicMax(stats + 1, __float_as_uint(l1 * (1.f + 1e-6f)));
+        atomicMax(stats + 2, __float_as_uint(s));
+      } else {
+        nrm[p] = CUDART_INF_F;
+        scale[p] = 1.f;
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// tcgen05 helpers
+// --------------------------------------------------------------------------
+
+NNS_DEV uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  // base offset 0, relative LBO, swizzle mode 0 (none)
+  return d;
+}
+
+// Instruction descriptor: D = F32, A and B of type `ab` (kind::f16: 0 = F16,
+// 1 = BF16; kind::f8f6f4: 0 = E4M3), both K-major, N = n, M = m.
+NNS_DEV uint32_t make_idesc(int ab, int m, int n) {
+  return (1u << 4) | ((uint32_t)ab << 7) | ((uint32_t)ab << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+template <int FMT>
+NNS_DEV void mma_issue(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accumulate) {
+  if (FMT == FMT_E4M3) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  }
+}
+
+NNS_DEV void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+NNS_DEV void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+NNS_DEV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+NNS_DEV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+NNS_DEV void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// --------------------------------------------------------------------------
+// K2
+// --------------------------------------------------------------------------
+
+struct TcArgs {
+  const uint8_t* A;        // packed consumer tiles (TC_BM rows each)
+  const uint8_t* B;        // packed supplier tiles (bn rows each)
+  const float* nrm_x;      // [supplier tiles * bn] squared norms (+inf on padding)
+  const float* scale_x;    // per-supplier scale
+  const float* scale_y;    // per-consumer scale
+  int nt;                  // active consumers
+  int mt;                  // active suppliers
+  int kb;                  // bytes per packed row
+  int bn;                  // suppliers per tile
+  int nstage;
+  int tiles_per_chunk;
+  int num_tiles;           // supplier tiles in total
+  int nt_pad;              // consumer count rounded up to TC_BM
+  float* cand_v;           // [chunks][nt_pad][TC_K] approximate values (v = |x|^2 - 2 <x~,y~>)
+  int* cand_p;             // [chunks][nt_pad][TC_K] supplier positions
+  unsigned* err;
+};
+
+template <int FMT, int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t bar_full[8];
+  __shared__ __align__(8) uint64_t bar_empty[8];
+  __shared__ __align__(8) uint64_t bar_acc_full[2];
+  __shared__ __align__(8) uint64_t bar_acc_empty[2];
+  __shared__ __align__(8) uint64_t bar_a;
+  __shared__ uint32_t tmem_slot;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int qtile = blockIdx.x;
+  const int t0 = blockIdx.y * P.tiles_per_chunk;
+  const int t1 = min(t0 + P.tiles_per_chunk, P.num_tiles);
+  const int ntiles = t1 - t0;
+  if (ntiles <= 0) return;
+  const int kb = P.kb;
+  const uint32_t a_bytes = TC_BM * kb;
+  const uint32_t b_bytes = BN * kb;
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + a_bytes;
+  const int NST = P.nstage;
+  constexpr uint32_t NCOLS = 2 * BN;  // two accumulators
+  constexpr uint32_t TMEM_ALLOC = NCOLS < 32 ? 32 : NCOLS;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&bar_full[s], 1);
+      mbar_init(&bar_empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bar_acc_full[b], 1);
+      mbar_init(&bar_acc_empty[b], 4 * 32);
+    }
+    mbar_init(&bar_a, 1);
+    mbar_fence_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(TMEM_ALLOC)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = tmem_slot;
+  bool ok = true;
+
+  if (warp == 0) {
+    // ---------------- producer: TMA bulk copies ----------------
+    if (lane == 0) {
+      mbar_expect_tx(&bar_a, a_bytes);
+      tma_load_1d(sA, P.A + (size_t)qtile * a_bytes, a_bytes, &bar_a);
+      for (int t = 0; t < ntiles && ok; ++t) {
+        const int s = t % NST, u = t / NST;
+        ok = mbar_wait_bounded(&bar_empty[s], (u & 1) ^ 1);
+        if (!ok) break;
+        mbar_expect_tx(&bar_full[s], b_bytes);
+        tma_load_1d(sB + (size_t)s * b_bytes, P.B + (size_t)(t0 + t) * b_bytes, b_bytes, &bar_full[s]);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      constexpr int AB = FMT == FMT_BF16 ? 1 : 0;
+      const uint32_t idesc = make_idesc(AB, TC_BM, BN);
+      const int ksteps = kb / 32;
+      ok = mbar_wait_bounded(&bar_a, 0);
+      const uint32_t a0 = smem_u32(sA);
+      for (int t = 0; t < ntiles && ok; ++t) {
+        const int s = t % NST, u = t / NST;
+        const int b = t & 1, v = t >> 1;
+        ok = mbar_wait_bounded(&bar_full[s], u & 1);
+        if (ok) ok = mbar_wait_bounded(&bar_acc_empty[b], (v & 1) ^ 1);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t b0 = smem_u32(sB + (size_t)s * b_bytes);
+        const uint32_t tmem_d = tmem_base + (uint32_t)(b * BN);
+        for (int k = 0; k < ksteps; ++k) {
+          const uint64_t ad = make_desc(a0 + k * 2 * TC_BM * 16, TC_BM * 16, 128);
+          const uint64_t bd = make_desc(b0 + k * 2 * BN * 16, BN * 16, 128);
+          mma_issue<FMT>(tmem_d, ad, bd, idesc, k > 0 ? 1u : 0u);
+        }
+        mma_commit(&bar_empty[s]);
+        mma_commit(&bar_acc_full[b]);
+      }
+    }
+  } else {
+    // ---------------- epilogue: TMEM -> top-K per consumer ----------------
+    const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+    const int row = quarter * 32 + lane;
+    const int q = qtile * TC_BM + row;
+    const float sy = (q < P.nt) ? P.scale_y[q] : 1.f;
+    float tv[TC_K];
+    int tp[TC_K];
+#pragma unroll
+    for (int k = 0; k < TC_K; ++k) { tv[k] = CUDART_INF_F; tp[k] = -1; }
+    for (int t = 0; t < ntiles; ++t) {
+      const int b = t & 1, v = t >> 1;
+      if (ok) ok = mbar_wait_bounded(&bar_acc_full[b], v & 1);
+      tc_fence_after();
+      if (ok) {
+        const int tile = t0 + t;
+        const float* nx = P.nrm_x + (size_t)tile * BN;
+        const float* sx = P.scale_x + (size_t)tile * BN;
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+          uint32_t r[16];
+          tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c0), r);
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const float acc = __uint_as_float(r[e]);
+            const float w = (FMT == FMT_BF16) ? -2.f : -2.f * sy * __ldg(sx + c0 + e);
+            const float val = __fmaf_rn(w, acc, __ldg(nx + c0 + e));
+            if (val < tv[TC_K - 1]) {
+              float nv = val;
+              int np = tile * BN + c0 + e;
+#pragma unroll
+              for (int k = 0; k < TC_K; ++k) {
+                if (nv < tv[k]) {
+                  const float fv = tv[k];
+                  const int fp = tp[k];
+                  tv[k] = nv;
+                  tp[k] = np;
+                  nv = fv;
+                  np = fp;
+                }
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&bar_acc_empty[b]);
+    }
+    if (q < P.nt) {
+      const size_t o = ((size_t)blockIdx.y * P.nt_pad + q) * TC_K;
+#pragma unroll
+      for (int k = 0; k < TC_K; ++k) {
+        P.cand_v[o + k] = tv[k];
+        P.cand_p[o + k] = tp[k];
+      }
+    }
+  }
+  if (!ok) atomicOr(P.err, EF_TIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_ALLOC)
+                              : "memory");
+}
+
+// --------------------------------------------------------------------------
+// exact re-rank + certificate
+// --------------------------------------------------------------------------
+
+struct RerankArgs {
+  const float* x;       // original coordinates
+  const float* y;
+  const int* ia;        // active supplier position -> original index
+  const int* ja;
+  int d, nt, nt_pad, chunks, metric, fmt;
+  const float* cand_v;
+  const int* cand_p;
+  const float* nrm_y;   // FP32 squared norm of each active consumer
+  const float* scale_y;
+  const unsigned* stats_x;  // max |x|_2, max |x|_1, max scale over active suppliers (float bits)
+  unsigned long long* nnkey;
+  int* fallback;        // consumer positions to rescan in FP32
+  int* nfallback;
+  unsigned long long* ncertified;
+  unsigned long long* nfallback_total;
+};
+
+// One warp per consumer.
+__global__ void k_rerank_certify(RerankArgs R) {
+  const int lane = threadIdx.x & 31;
+  const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (q >= R.nt) return;
+  const float* yrow = R.y + (size_t)R.ja[q] * R.d;
+  const int ncand = R.chunks * TC_K;
+  unsigned long long best = ~0ULL;
+  float tau = CUDART_INF_F;  // smallest chunk threshold (K-th value of each chunk)
+  for (int c = lane; c < ncand; c += 32) {
+    const size_t o = ((size_t)(c / TC_K) * R.nt_pad + q) * TC_K + (c % TC_K);
+    const int p = R.cand_p[o];
+    if ((c % TC_K) == TC_K - 1) tau = fminf(tau, R.cand_v[o]);
+    if (p < 0) continue;
+    // squared-Euclidean FP32 key (the contraction has no L1 form)
+    const float acc = key32<METRIC_SQL2>(R.x + (size_t)R.ia[p] * R.d, yrow, R.d);
+    const unsigned long long key = pack_key(acc, (unsigned)p);
+    best = key < best ? key : best;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+    best = ob < best ? ob : best;
+    tau = fminf(tau, __shfl_xor_sync(0xffffffffu, tau, o));
+  }
+  if (lane != 0) return;
+  // Error bound of approx(i, q) for any supplier i (all terms >= the truth).
+  const double d = R.d;
+  const double u32 = 0x1p-24;
+  const double uq = R.fmt == FMT_BF16 ? 0x1p-8 : (R.fmt == FMT_F16 ? 0x1p-11 : 0x1p-4);
+  const double gam = d * u32 / (1.0 - d * u32);
+  double ny = R.nrm_y[q];
+  double yl2 = 0.0, yl1 = 0.0;
+  for (int k = 0; k < R.d; ++k) {
+    yl2 += (double)yrow[k] * yrow[k];
+    yl1 += fabs((double)yrow[k]);
+  }
+  yl2 = sqrt(yl2) * (1 + 1e-12);
+  const double rx = __uint_as_float(R.stats_x[0]);
+  const double rx1 = __uint_as_float(R.stats_x[1]);
+  const double sxm = __uint_as_float(R.stats_x[2]);
+  const double sy = R.scale_y[q];
+  // smallest positive subnormal spacing / 2 of the operand format, in
+  // original units (scaled formats): absolute rounding floor per element
+  const double eta_unit = R.fmt == FMT_BF16 ? 0x1p-134 : (R.fmt == FMT_F16 ? 0x1p-25 : 0x1p-10);
+  const double eta_x = eta_unit * (R.fmt == FMT_BF16 ? 1.0 : sxm), eta_y = eta_unit * (R.fmt == FMT_BF16 ? 1.0 : sy);
+  const double dot_q = (2 * uq + uq * uq) * rx * yl2 + eta_x * (yl1 + eta_y * d) + eta_y * rx1 +
+                       eta_x * uq * yl1 + eta_y * uq * rx1;
+  const double xt = (1 + uq) * rx + eta_x * sqrt(d), yt = (1 + uq) * yl2 + eta_y * sqrt(d);
+  const double dot_acc = d * 0x1p-22 * xt * yt;
+  const double E = 2.0 * (gam * (ny + rx * rx) + 2.0 * (dot_q + dot_acc) + u32 * (rx * rx + 2.0 * xt * yt)) +
+                   1e-30;
+  const float bestk = __uint_as_float((unsigned)(best >> 32));
+  bool certified = false;
+  if (best != ~0ULL && tau < CUDART_INF_F) {
+    const double floor_true = (ny + (double)tau - E) * (1.0 - gam) * (1.0 - 0x1p-40);
+    certified = (double)bestk < floor_true;
+  } else if (best != ~0ULL) {
+    certified = true;  // fewer than K suppliers per chunk: every one was a candidate
+  }
+  if (certified) {
+    R.nnkey[q] = best;
+    atomicAdd(R.ncertified, 1ULL);
+  } else {
+    R.fallback[atomicAdd(R.nfallback, 1)] = q;
+    atomicAdd(R.nfallback_total, 1ULL);
+  }
+}
+
+// --------------------------------------------------------------------------
+// host side
+// --------------------------------------------------------------------------
+
+static int fmt_of(int precision) {
+  return precision == 1 ? FMT_BF16 : (precision == 2 ? FMT_F16 : FMT_E4M3);
+}
+
+size_t tc_kb(int d, int precision) {
+  const int esize = precision == 3 ? 1 : 2;
+  return (size_t)(((int64_t)d * esize + 31) / 32 * 32);
+}
+
+int tc_bn(size_t kb) { return kb <= 384 ? 128 : 64; }
+
+template <int FMT, int BN>
+static int launch_tc_t(const TcArgs& P, dim3 grid, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_nns_tc<FMT, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return -1;
+  k_nns_tc<FMT, BN><<<grid, TC_THREADS, smem, st>>>(P);
+  return 0;
+}
+
+int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int precision, cudaStream_t st) {
+  const int fmt = fmt_of(precision);
+  const int kb = (int)tc_kb(B.d, precision);
+  const int bn = tc_bn(kb);
+  const int qtiles = (nt + TC_BM - 1) / TC_BM;
+  const int stiles = (mt + bn - 1) / bn;
+  // pack both sides
+  if (cudaMemsetAsync(T.stats, 0, 8 * sizeof(unsigned), st) != cudaSuccess) return -1;
+  {
+    const int64_t work = (int64_t)qtiles * TC_BM * (kb / 16);
+    int g = (int)std::min<int64_t>((work + 255) / 256, 152 * 16);
+    k_pack_tc<<<g, 256, 0, st>>>(B.y, B.ja[B.cur], nt, qtiles * TC_BM, B.d, kb, fmt, TC_BM, T.A, T.nrm_y, T.scale_y,
+                                 T.stats + 4);
+  }
+  {
+    const int64_t work = (int64_t)stiles * bn * (kb / 16);
+    int g = (int)std::min<int64_t>((work + 255) / 256, 152 * 16);
+    k_pack_tc<<<g, 256, 0, st>>>(B.x, B.ia[B.cur], mt, stiles * bn, B.d, kb, fmt, bn, T.B, T.nrm_x, T.scale_x,
+                                 T.stats);
+  }
+  // chunks of supplier tiles so that the grid covers the GPU
+  int chunks = (152 + qtiles - 1) / qtiles;
+  if (chunks > stiles) chunks = stiles;
+  if (chunks > T.max_chunks) chunks = T.max_chunks;
+  const int per = (stiles + chunks - 1) / chunks;
+  chunks = (stiles + per - 1) / per;
+  const size_t a_bytes = (size_t)TC_BM * kb, b_bytes = (size_t)bn * kb;
+  int nstage = (int)((TC_SMEM_BUDGET - a_bytes) / b_bytes);
+  if (nstage > 4) nstage = 4;
+  if (nstage < 1) return -2;
+  const int nt_pad = qtiles * TC_BM;
+  TcArgs P{T.A, T.B, T.nrm_x, T.scale_x, T.scale_y, nt, mt, kb, bn, nstage, per, stiles, nt_pad,
+           T.cand_v, T.cand_p, &B.st->err};
+  const size_t smem = a_bytes + (size_t)nstage * b_bytes;
+  dim3 grid(qtiles, chunks);
+  int rc;
+  if (T.ev0) cudaEventRecord(T.ev0, st);
+  if (fmt == FMT_BF16) rc = bn == 128 ? launch_tc_t<FMT_BF16, 128>(P, grid, smem, st) : launch_tc_t<FMT_BF16, 64>(P, grid, smem, st);
+  else if (fmt == FMT_F16) rc = bn == 128 ? launch_tc_t<FMT_F16, 128>(P, grid, smem, st) : launch_tc_t<FMT_F16, 64>(P, grid, smem, st);
+  else rc = bn == 128 ? launch_tc_t<FMT_E4M3, 128>(P, grid, smem, st) : launch_tc_t<FMT_E4M3, 64>(P, grid, smem, st);
+  if (rc) return rc;
+  if (T.ev1) cudaEventRecord(T.ev1, st);
+  // exact re-rank and certificate
+  if (cudaMemsetAsync(T.nfallback, 0, sizeof(int), st) != cudaSuccess) return -1;
+  RerankArgs R{B.x,     B.y,       B.ia[B.cur], B.ja[B.cur], B.d,       nt,          nt_pad,
+               chunks,  B.metric,  fmt,         T.cand_v,    T.cand_p,  T.nrm_y,     T.scale_y,
+               T.stats, B.nnkey,   T.fallback,  T.nfallback, &B.st->certified, &B.st->fallbacks};
+  k_rerank_certify<<<(nt + 7) / 8, 256, 0, st>>>(R);
+  // FP32 scan of the consumers that were not certified
+  launch_nns_f32(B, mt, nt, T.fallback, T.nfallback, st);
+  return 0;
+}
+
+}  // namespace nnsemd

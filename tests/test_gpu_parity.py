@@ -245,3 +245,49 @@ def test_batched_retrieval_signatures_d128(ctx):
     costs = costs.cpu().numpy()
     for k in range(batch.num_pairs):
         assert costs[k] == oracle.solve_pair(batch.pair(k), "l2").cost, k
+
+
+# ---------------------------------------------------------------------------
+# reduced precision: tcgen05 contraction proposes, FP32 re-rank decides,
+# certificate or FP32 rescan -- the result must equal the FP32 path's
+# ---------------------------------------------------------------------------
+
+def gpu_solve_prec(ctx, x, a, y, b, metric, precision):
+    return ctx.solve(dev(x, torch.float32), dev(a, torch.float64), dev(y, torch.float32), dev(b, torch.float64),
+                     metric=metric, precision=precision, plan=True)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16", "fp8"])
+def test_reduced_precision_small_pair(ctx, precision):
+    p = wl.uniform_pair(300, 260, 64, 31, "dirichlet")
+    ref = oracle.solve_pair(p, "l2")
+    res = gpu_solve_prec(ctx, p.x, p.a, p.y, p.b, "l2", precision)
+    assert_parity(res, ref)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16", "fp8"])
+@pytest.mark.parametrize("shape", ["gmm64", "sift128", "words300"])
+def test_reduced_precision_equals_fp32(ctx, precision, shape):
+    if shape == "gmm64":
+        p = wl.gmm_pair(seed=2, n=5000, d=64)
+    elif shape == "sift128":
+        p = wl.retrieval(num_pairs=1, seed=5, lo=2000, hi=2048).pair(0)
+    else:
+        b = wl.doc_knn(num_docs=1, seed=6, vocab_size=3000, median=400, lo=300, hi=500)
+        p = b.pair(0)
+    for metric in ("l2", "sql2"):
+        ref = oracle.solve_pair(p, metric)
+        res = gpu_solve_prec(ctx, p.x, p.a, p.y, p.b, metric, precision)
+        assert_parity(res, ref)
+        s = res.stats
+        assert s["certified"] + s["fallbacks"] > 0
+        if precision in ("bf16", "fp16") and shape != "words300":
+            assert s["certified"] >= 0.5 * (s["certified"] + s["fallbacks"]), s
+
+
+def test_reduced_precision_rejections(ctx):
+    from paper_2401_07378_gb300.nnsemd import NNSEMDError
+    p = wl.uniform_pair(50, 40, 16, 7)
+    with pytest.raises(NNSEMDError) as e:
+        gpu_solve_prec(ctx, p.x, p.a, p.y, p.b, "l1", "bf16")
+    assert e.value.status == 8
