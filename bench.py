@@ -1,31 +1,40 @@
 #!/usr/bin/env python3
-"""NNS-EMD throughput on GB300: pairs/s on the colour-transfer workload.
+"""NNS-EMD throughput on GB300 (pairs/s), with a live roofline.
 
-A step is one full NNS-EMD solve (every round of Alg. 1, Sec. III-A) of one
-pair: two images' colour histograms, 65,536 points each in d=3 (8 Gaussian
-colour clusters, sigma 0.08, clipped to [0,1)), uniform weights, squared
-Euclidean ground distance, full sparse plan returned.  Inputs are synthetic
-(the paper's seasonal colour-transfer images are not available).
+Default workload (the one the headline metric is quoted on): one step is one
+full NNS-EMD solve (every round of Alg. 1, Sec. III-A) of a colour-transfer
+pair -- two images' colour histograms, 65,536 points each in d=3 (8 Gaussian
+colour clusters, sigma 0.08, clipped to [0,1)), uniform weights,
+squared-Euclidean ground distance, full sparse plan returned.  Inputs are
+synthetic (the paper's seasonal colour-transfer images are not available).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload colour|single|gmm|docs|retrieval] [--precision fp32|bf16|fp16|fp8]
 
-With N > 1 (launched by torchrun, one rank per GPU) every rank solves its own
-pair (seed = rank): the pairs are independent, so there is no collective on
-the data path ("weak" scaling); value = N*K pairs / max-over-ranks time.
+Other workloads (reported by hand, not by the driver):
+  single     one 256 x 256 pair in d=2, Euclidean;
+  gmm        one 262,144 x 262,144 pair in d=64 (256-component mixture), Euclidean;
+  docs       1 query document vs 4,096 documents, word vectors d=300 (batched);
+  retrieval  10,000 signature pairs, 256..2,048 descriptors of d=128 (batched).
 
-Reported on one JSON line (rank 0):
-  value / ms_per_step  device time of K solves with inputs resident in HBM
-                       (CUDA events on the launching stream; L2 flushed
-                       between steps by a 256 MiB write);
-  e2e                  the same through nnsemd_solve_host: host (pinned)
-                       inputs copied in and the plan copied out every step;
-  roofline             the NNS kernel (K1) against the FP32-pipe peak: its
-                       algorithmic work is 2d FP32 operations per
-                       supplier/consumer pair (d subtractions, d multiply-
-                       adds), timed by the library with CUDA events around
-                       every K1 launch of the timed steps;
+With N > 1 (torchrun, one rank per GPU) every rank solves its own pair(s)
+(seed = rank): the pairs are independent, so there is no collective on the
+data path ("weak" scaling); value = all ranks' pairs / max-over-ranks time.
+
+JSON line (rank 0):
+  value / ms_per_step  device time of K steps with inputs resident in HBM
+                       (CUDA events on the launching stream; L2 flushed by a
+                       256 MiB write before every step, outside the events);
+  e2e                  single-pair workloads: the same solve through
+                       nnsemd_solve_host (pinned host inputs copied in and the
+                       plan copied out every step);
+  roofline             the dominant kernel against its peak: the FP32 pipe
+                       for the CUDA-core NNS kernels (2d FP32 operations per
+                       supplier/consumer pair), the tensor pipe for the
+                       tcgen05 kernel (2d flops per pair), timed by the
+                       library with CUDA events around each launch;
   cpu_baseline         the CPU oracle (single thread) on a bounded sample of
-                       the workload, scaled to one full pair by NNS work.
+                       the workload, scaled to the metric's unit.
 """
 from __future__ import annotations
 
@@ -43,17 +52,30 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = ("colour-transfer pair: 65,536 x 65,536 points, d=3, 8 Gaussian colour clusters "
-            "(sigma 0.08, clipped to [0,1)), uniform weights, squared-Euclidean ground distance, "
-            "full sparse plan returned")
 METRIC = "NNS-EMD pairs/s at <=1e-3 rel err vs FP64 oracle; fused-kernel % of roofline"
-N_POINTS = 65536
-D = 3
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-ORACLE_SAMPLE_N = 16384        # oracle sample: the same generator at 16,384 points per side
+ORACLE_SAMPLE_N = 16384        # colour-transfer oracle sample: 16,384 points per side
 WORK_FILE = os.path.join(ROOT, "tests", "golden", "colour_transfer_oracle.json")
 COUNTERS_FILE = os.path.join(ROOT, "profiles", "k_nns_lowd_colour_transfer.json")
+
+WORKLOADS = {
+    "colour": dict(desc=("colour-transfer pair: 65,536 x 65,536 points, d=3, 8 Gaussian colour clusters "
+                         "(sigma 0.08, clipped to [0,1)), uniform weights, squared-Euclidean ground distance, "
+                         "full sparse plan returned"), metric="sql2", precision="fp32", batched=False),
+    "single": dict(desc="single pair: 256 x 256 points, d=2, Uniform[0,1), uniform weights, Euclidean, full plan",
+                   metric="l2", precision="fp32", batched=False),
+    "gmm": dict(desc=("GMM pair: 262,144 x 262,144 points, d=64, 256-component mixture (means N(0,4I), "
+                      "cov 0.25I), Dirichlet(0.5) weights, Euclidean, full plan"),
+                metric="l2", precision="bf16", batched=False),
+    "docs": dict(desc=("document kNN: 1 query vs 4,096 documents, word vectors d=300 N(0,1) L2-normalised "
+                       "(50k vocabulary), lengths LogNormal(ln 60, 0.6) clipped to [20,500], Zipf(1.1) weights, "
+                       "Euclidean, batched in one persistent launch"), metric="l2", precision="fp32",
+                 batched=True),
+    "retrieval": dict(desc=("retrieval: 10,000 signature pairs, m, n ~ U{256..2048}, d=128 |N(0,1)| "
+                            "L2-normalised x512, Dirichlet(1) weights, Euclidean, batched"),
+                      metric="l2", precision="fp32", batched=True),
+}
 
 
 # ---------------------------------------------------------------------------
@@ -145,12 +167,31 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle baseline (bounded sample, scaled to one full pair by NNS work)
+# inputs
+# ---------------------------------------------------------------------------
+
+def make_inputs(name: str, rank: int):
+    from paper_2401_07378_gb300 import workloads
+    if name == "colour":
+        return workloads.color_transfer(seed=rank)
+    if name == "single":
+        return workloads.single_pair(seed=rank)
+    if name == "gmm":
+        return workloads.gmm_pair(seed=rank)
+    if name == "docs":
+        return workloads.doc_knn(seed=rank)
+    if name == "retrieval":
+        return workloads.retrieval(seed=rank)
+    raise ValueError(name)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample, scaled to the metric's unit)
 # ---------------------------------------------------------------------------
 
 def full_pair_work() -> int | None:
-    """Sum of m_t * n_t of the full workload, as computed by the oracle
-    (tests/golden/make_oracle_values.py writes it)."""
+    """Sum of m_t * n_t of the full colour-transfer pair, as computed by the
+    oracle (tests/golden/make_oracle_values.py writes it)."""
     try:
         with open(WORK_FILE) as fh:
             return int(json.load(fh)["pair_evals"])
@@ -158,20 +199,53 @@ def full_pair_work() -> int | None:
         return None
 
 
-def oracle_sample(full_work: int | None) -> dict:
+def oracle_sample(name: str, inputs=None, full_work: int | None = None) -> dict:
+    """Time the oracle, as it stands, on a bounded sample; returns pairs/s."""
     import oracle
     from paper_2401_07378_gb300 import workloads
-    p = workloads.color_transfer(seed=0, n=ORACLE_SAMPLE_N)
+    spec = WORKLOADS[name]
     t0 = time.perf_counter()
-    r = oracle.solve_pair(p, "sql2")
-    dt = time.perf_counter() - t0
-    scale = (full_work / r.pair_evals) if full_work else (N_POINTS / ORACLE_SAMPLE_N) ** 2
-    per_pair = dt * scale
-    return {"value": 1.0 / per_pair, "unit": "pairs/s", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle (FP64 mass, FP32 decisions checked against FP64) on one {ORACLE_SAMPLE_N}-point "
-                       f"instance of the same generator: {dt:.2f} s for {r.pair_evals} pair evaluations, scaled "
-                       f"by NNS work to the full pair ({full_work or 'n^2 ratio'} evaluations)"),
-            "seconds": dt}
+    if name == "colour":
+        p = workloads.color_transfer(seed=0, n=ORACLE_SAMPLE_N)
+        r = oracle.solve_pair(p, spec["metric"])
+        dt = time.perf_counter() - t0
+        work = full_work or full_pair_work()
+        scale = (work / r.pair_evals) if work else (65536 / ORACLE_SAMPLE_N) ** 2
+        value = 1.0 / (dt * scale)
+        sample = (f"one {ORACLE_SAMPLE_N}-point instance of the same generator: {dt:.2f} s for {r.pair_evals} "
+                  f"pair evaluations, scaled by NNS work to the full pair ({work} evaluations, oracle-computed)")
+    elif name == "single":
+        p = inputs
+        done = 0
+        while True:
+            oracle.solve_pair(p, spec["metric"])
+            done += 1
+            dt = time.perf_counter() - t0
+            if dt > 5.0:
+                break
+        value = done / dt
+        sample = f"the full pair solved {done} times in {dt:.2f} s"
+    elif name == "gmm":
+        n = 8192
+        p = workloads.gmm_pair(seed=0, n=n)
+        r = oracle.solve_pair(p, spec["metric"])
+        dt = time.perf_counter() - t0
+        scale = (full_work / r.pair_evals) if full_work else (262144 / n) ** 2
+        value = 1.0 / (dt * scale)
+        sample = (f"one {n}-point instance of the same generator: {dt:.2f} s for {r.pair_evals} pair evaluations, "
+                  f"scaled by NNS work to the full pair ({full_work} evaluations as counted by the GPU run)")
+    else:
+        batch = inputs
+        done = 0
+        for k in range(batch.num_pairs):
+            oracle.solve_pair(batch.pair(k), spec["metric"])
+            done += 1
+            dt = time.perf_counter() - t0
+            if dt > 10.0:
+                break
+        value = done / dt
+        sample = f"the first {done} pairs of the batch in {dt:.2f} s"
+    return {"value": value, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": sample}
 
 
 # ---------------------------------------------------------------------------
@@ -205,26 +279,64 @@ def peaks():
         return {}
 
 
+def roofline(d: int, precision: str, pairs: int, launches: int, ms: float, total_ms: float, lowd: bool) -> dict:
+    pk = peaks()
+    per_launch_s = ms / 1e3 / max(launches, 1)
+    if precision == "fp32":
+        clk = float(pk.get("sm_max_mhz", 2070.0))
+        peak = SM_COUNT * FP32_LANES_PER_SM * clk * 1e6 / 1e12
+        ops = pairs * 2 * d / max(launches, 1)
+        basis = (f"152 SMs x 128 FP32 lanes x {clk:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json); "
+                 f"work = 2d FP32-pipe ops per supplier/consumer pair")
+        bound = "alu"
+        kernel = "k_nns_lowd (K1)" if lowd else "k_nns_f32_tiled"
+    else:
+        bf16 = float(pk.get("bf16_tflops", 1935.1))
+        peak = bf16 * (2.0 if precision == "fp8" else 1.0)
+        ops = pairs * 2 * d / max(launches, 1)
+        basis = ("measured cuBLAS bf16 burst of MEASURED_PEAKS.json" +
+                 (" x 2 (nominal fp8/bf16 ratio)" if precision == "fp8" else "") +
+                 "; work = 2d flops per supplier/consumer pair")
+        bound = "tensor"
+        kernel = f"k_nns_tc<{precision}> (tcgen05 contraction + top-8 epilogue)"
+    achieved = ops / per_launch_s / 1e12 if ms > 0 else 0.0
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if peak else None, "traffic": measured_traffic() if lowd else None,
+            "kernel": kernel, "peak_basis": basis, "launches": launches, "kernel_ms": ms,
+            "share_of_step": ms / total_ms if total_ms else None}
+
+
 def run_ours(args) -> dict | None:
     import numpy as np
     import torch
-    from paper_2401_07378_gb300 import nnsemd, workloads
+    from paper_2401_07378_gb300 import nnsemd
 
+    spec = WORKLOADS[args.workload]
+    precision = args.precision or spec["precision"]
+    metric = spec["metric"]
     rank, ws, local = world()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dist_init("nccl")
-    pair = workloads.color_transfer(seed=rank)
-    x = torch.from_numpy(pair.x).to(dev)
-    a = torch.from_numpy(pair.a).to(dev)
-    y = torch.from_numpy(pair.y).to(dev)
-    b = torch.from_numpy(pair.b).to(dev)
+    inp = make_inputs(args.workload, rank)
     ctx = nnsemd.Context(local)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     T = nnsemd.FLAG_TIME_KERNELS
+    t = lambda v: torch.from_numpy(v).to(dev)
+    x, a, y, b = t(inp.x), t(inp.a), t(inp.y), t(inp.b)
+    d = int(inp.x.shape[1])
+    if spec["batched"]:
+        P = inp.num_pairs
+        costs = torch.empty(P, dtype=torch.float64, device=dev)
+        step = lambda: ctx.solve_batched(x, a, inp.x_off, y, b, inp.y_off, metric=metric, precision=precision,
+                                         costs=costs, stats=True)[1]
+        units = P
+    else:
+        step = lambda: ctx.solve(x, a, y, b, metric=metric, precision=precision, plan=True, flags=T).stats
+        units = 1
 
     for _ in range(args.warmup):
-        ctx.solve(x, a, y, b, metric="sql2", plan=True)
+        step()
     torch.cuda.synchronize()
     dist_barrier()
     torch.cuda.synchronize()
@@ -233,96 +345,93 @@ def run_ours(args) -> dict | None:
     sampler.start()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    nns_ms = tail_ms = 0.0
-    nns_pairs = nns_launches = launches = 0
-    pair_evals = rounds = 0
-    cost = None
+    agg = {"nns_kernel_ms": 0.0, "tail_kernel_ms": 0.0, "nns_kernel_pairs": 0, "nns_kernel_launches": 0,
+           "kernel_launches": 0, "certified": 0, "fallbacks": 0}
+    last = None
     for k in range(args.steps):
         flush.zero_()
         starts[k].record()
-        res = ctx.solve(x, a, y, b, metric="sql2", plan=True, flags=T)
+        s = step()
         ends[k].record()
-        s = res.stats
-        nns_ms += s["nns_kernel_ms"]
-        tail_ms += s["tail_kernel_ms"]
-        nns_pairs += s["nns_kernel_pairs"]
-        nns_launches += s["nns_kernel_launches"]
-        launches += s["kernel_launches"]
-        pair_evals, rounds, cost = s["pair_evals"], s["rounds"], res.cost
+        for key in agg:
+            agg[key] += s.get(key, 0) or 0
+        last = s
     torch.cuda.synchronize()
     dist_barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    step_ms = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
+    total_ms = sum(step_ms)
     max_ms = dist_reduce(total_ms, "max", dev)
-    launches_all = int(dist_reduce(float(launches), "sum", dev))
+    launches_all = int(dist_reduce(float(agg["kernel_launches"]), "sum", dev))
 
-    # end to end through the host entry point (pinned buffers)
-    hx = torch.from_numpy(pair.x).pin_memory()
-    ha = torch.from_numpy(pair.a).pin_memory()
-    hy = torch.from_numpy(pair.y).pin_memory()
-    hb = torch.from_numpy(pair.b).pin_memory()
-    cap = 2 * N_POINTS - 1
-    plan_out = (torch.empty(cap, dtype=torch.int32).pin_memory(), torch.empty(cap, dtype=torch.int32).pin_memory(),
-                torch.empty(cap, dtype=torch.float64).pin_memory())
-    for _ in range(min(args.warmup, 2)):
-        ctx.solve_host(hx, ha, hy, hb, metric="sql2", plan=True, plan_out=plan_out)
-    torch.cuda.synchronize()
-    dist_barrier()
-    e2e_ms = 0.0
-    nnz = 0
-    for k in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        hres = ctx.solve_host(hx, ha, hy, hb, metric="sql2", plan=True, plan_out=plan_out)
-        e1.record()
+    e2e = None
+    if not spec["batched"]:
+        hx, ha = torch.from_numpy(inp.x).pin_memory(), torch.from_numpy(inp.a).pin_memory()
+        hy, hb = torch.from_numpy(inp.y).pin_memory(), torch.from_numpy(inp.b).pin_memory()
+        cap = inp.m + inp.n - 1
+        plan_out = (torch.empty(cap, dtype=torch.int32).pin_memory(),
+                    torch.empty(cap, dtype=torch.int32).pin_memory(),
+                    torch.empty(cap, dtype=torch.float64).pin_memory())
+        host_step = lambda: ctx.solve_host(hx, ha, hy, hb, metric=metric, precision=precision, plan=True,
+                                           plan_out=plan_out)
+        for _ in range(min(args.warmup, 2)):
+            host_step()
         torch.cuda.synchronize()
-        e2e_ms += e0.elapsed_time(e1)
-        nnz = int(hres.plan_f.numel())
-        assert hres.cost == cost
-    e2e_max = dist_reduce(e2e_ms, "max", dev)
-    h2d = sum(t.numel() * t.element_size() for t in (hx, ha, hy, hb))
-    d2h = nnz * (4 + 4 + 8) + 8
+        dist_barrier()
+        e2e_ms, nnz = 0.0, 0
+        for k in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            hres = host_step()
+            e1.record()
+            torch.cuda.synchronize()
+            e2e_ms += e0.elapsed_time(e1)
+            nnz = int(hres.plan_f.numel())
+        e2e_max = dist_reduce(e2e_ms, "max", dev)
+        e2e = {"value": ws * args.steps * units / (e2e_max / 1e3), "unit": "pairs/s",
+               "h2d_bytes_per_step": sum(v.numel() * v.element_size() for v in (hx, ha, hy, hb)),
+               "d2h_bytes_per_step": nnz * (4 + 4 + 8) + 8}
 
     if rank != 0:
         ctx.close()
         return None
 
-    pk = peaks()
-    clk_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    peak = SM_COUNT * FP32_LANES_PER_SM * clk_mhz * 1e6 / 1e12          # T FP32-pipe op/s
-    per_launch_ops = nns_pairs * 2 * D / max(nns_launches, 1)
-    per_launch_s = nns_ms / 1e3 / max(nns_launches, 1)
-    achieved = per_launch_ops / per_launch_s / 1e12 if nns_ms > 0 else 0.0
-    traffic = measured_traffic()
-    value = ws * args.steps / (max_ms / 1e3)
+    lowd = d <= 8
+    if spec["batched"]:
+        # the persistent batched kernel is the step: its NNS work against the FP32 pipe
+        rl = roofline(d, "fp32", agg.get("nns_kernel_pairs", 0) or (last or {}).get("pair_evals", 0) * args.steps,
+                      args.steps, total_ms, total_ms, lowd)
+        rl["kernel"] = "k_batched_lowd" if lowd else "k_batched_hd (persistent, one pair per CTA)"
+        rl["traffic"] = None
+    else:
+        rl = roofline(d, precision, agg["nns_kernel_pairs"], agg["nns_kernel_launches"], agg["nns_kernel_ms"],
+                      total_ms, lowd)
     line = {
-        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 distances, f64 mass/cost", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "points_per_side": N_POINTS, "d": D, "metric": "sql2",
-                   "precision": "fp32", "plan": "full", "l2": "flushed between steps (256 MiB write)",
-                   "parallelism": f"{ws} independent pairs, one per GPU" if ws > 1 else "1 GPU"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak if peak else None, "traffic": traffic,
-                     "kernel": "k_nns_lowd (K1, fused FP32 distance + argmin)",
-                     "peak_basis": (f"152 SMs x 128 FP32 lanes x {clk_mhz:.0f} MHz (sm_max_mhz of "
-                                    "MEASURED_PEAKS.json); work = 2d FP32-pipe ops per pair"),
-                     "launches": nns_launches, "kernel_ms": nns_ms,
-                     "share_of_step": nns_ms / total_ms if total_ms else None},
-        "tail_kernel_share": tail_ms / total_ms if total_ms else None,
-        "e2e": {"value": ws * args.steps / (e2e_max / 1e3), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+        "metric": METRIC, "value": ws * args.steps * units / (max_ms / 1e3), "unit": "pairs/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 distances, f64 mass/cost" if precision == "fp32" else f"{precision} contraction, f32 re-rank, f64 mass/cost",
+        "data": "synthetic",
+        "config": {"workload": spec["desc"], "name": args.workload, "d": d, "metric": metric, "precision": precision,
+                   "l2": "flushed before every step (256 MiB write)",
+                   "parallelism": f"{ws} independent problems, one per GPU" if ws > 1 else "1 GPU"},
+        "roofline": rl,
+        "tail_kernel_share": agg["tail_kernel_ms"] / total_ms if total_ms else None,
         "gpu_launches": launches_all,
-        "rounds_per_pair": rounds, "pair_evals_per_pair": pair_evals, "cost": cost,
+        "rounds_per_step": (last or {}).get("rounds"), "pair_evals_per_step": (last or {}).get("pair_evals"),
+        "certified": agg["certified"], "fallbacks": agg["fallbacks"],
         "clocks": clocks,
     }
+    if e2e:
+        line["e2e"] = e2e
+    else:
+        line["e2e"] = {"value": line["value"], "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                       "note": "batched inputs resident on the device; no host entry point for batches"}
     if ws == 1 and not args.no_cpu_baseline:
-        cb = oracle_sample(full_pair_work() or pair_evals)
-        cb.pop("seconds", None)
-        line["cpu_baseline"] = cb
+        full = (last or {}).get("pair_evals") if args.workload == "gmm" else None
+        line["cpu_baseline"] = oracle_sample(args.workload, inp, full)
     ctx.close()
     return line
 
@@ -331,22 +440,24 @@ def run_reference(args) -> dict | None:
     rank, ws, _ = world()
     if rank != 0:
         return None
-    full_work = full_pair_work()
+    name = args.workload
+    spec = WORKLOADS[name]
+    inp = make_inputs(name, 0) if name in ("single", "docs", "retrieval") else None
     for _ in range(args.warmup):
-        oracle_sample(full_work)
-    per_pair = []
+        oracle_sample(name, inp)
+    secs = []
     sample = None
     for _ in range(args.steps):
-        r = oracle_sample(full_work)
-        per_pair.append(1.0 / r["value"])
+        r = oracle_sample(name, inp)
+        secs.append(1.0 / r["value"])
         sample = r["sample"]
-    total = sum(per_pair)
+    total = sum(secs)
     value = args.steps / total
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64 (oracle; decisions also in f32)", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "points_per_side": N_POINTS, "d": D, "metric": "sql2"},
+            "config": {"workload": spec["desc"], "name": name, "metric": spec["metric"]},
             "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -354,9 +465,11 @@ def run_reference(args) -> dict | None:
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="colour")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "fp16", "fp8"], default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
     line = run_reference(args) if args.impl == "reference" else run_ours(args)

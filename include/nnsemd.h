@@ -87,6 +87,11 @@ typedef struct {
 
 /* nnsemd_options.flags bits */
 #define NNSEMD_FLAG_TIME_KERNELS 1  /* time the NNS and tail kernels with CUDA events (fills the *_ms stats) */
+#define NNSEMD_FLAG_AUTOTUNE 2      /* nnsemd_solve_batched: time the candidate tile shapes on a sample of the
+                                       batch the first time a (d, precision, size) class is seen; the winner
+                                       is kept in the context for later calls */
+#define NNSEMD_FLAG_GRAPH 4         /* nnsemd_solve_batched: capture the device work of the call in a CUDA
+                                       graph and replay it while the buffers and sizes repeat */
 
 typedef struct {
   int32_t metric;               /* nnsemd_metric */

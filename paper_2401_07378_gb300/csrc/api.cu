@@ -17,13 +17,22 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "kernels.h"
 #include "nnsemd.h"
 
 using namespace nnsemd;
+
+// A captured batched launch (NNSEMD_FLAG_GRAPH), valid while every pointer
+// and size in the key repeats.
+struct BatchGraph {
+  std::vector<uintptr_t> key;
+  cudaGraphExec_t exec = nullptr;
+};
 
 struct nnsemd_ctx {
   int device = 0;
@@ -34,6 +43,10 @@ struct nnsemd_ctx {
   std::string err;
   long long launches = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // kernel timing (NNSEMD_FLAG_TIME_KERNELS)
+  // autotuner: (d, precision, cap) -> (bn, stages) of the batched tensor-core kernel
+  std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;
+  std::vector<BatchGraph> graphs;
+  cudaStream_t capture_stream = nullptr;
 };
 
 namespace {
@@ -111,12 +124,13 @@ size_t layout_solve(void* base, int64_t m, int64_t n, int d, SolveBufs& B, int p
     T.A = C.take<uint8_t>(qrows * kb);
     T.B = C.take<uint8_t>(srows * kb);
     T.nrm_x = C.take<float>(srows);
+    T.nrm_sx = C.take<float>(srows);
     T.nrm_y = C.take<float>(qrows);
     T.scale_x = C.take<float>(srows);
     T.scale_y = C.take<float>(qrows);
     T.stats = C.take<unsigned>(8);
     T.max_chunks = 152;
-    const int64_t cand = (152 + qrows / 128) * 128 * 8;
+    const int64_t cand = (152 + qrows / 128) * 128 * 16;  // chunks x padded consumers x 16 candidates
     T.cand_v = C.take<float>(cand);
     T.cand_p = C.take<int>(cand);
     T.fallback = C.take<int>(n);
@@ -160,7 +174,8 @@ int check_opts(nnsemd_ctx* ctx, const nnsemd_options* opt, int d, int& metric, i
   if (precision) *precision = NNSEMD_FP32;
   if (opt) {
     metric = opt->metric;
-    if (opt->flags & ~NNSEMD_FLAG_TIME_KERNELS) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "unknown options.flags bits");
+    if (opt->flags & ~(NNSEMD_FLAG_TIME_KERNELS | NNSEMD_FLAG_AUTOTUNE | NNSEMD_FLAG_GRAPH))
+      return fail(ctx, NNSEMD_ERR_INVALID_ARG, "unknown options.flags bits");
     if (opt->precision < NNSEMD_FP32 || opt->precision > NNSEMD_FP8)
       return fail(ctx, NNSEMD_ERR_INVALID_ARG, "unknown precision %d", opt->precision);
     if (opt->precision != NNSEMD_FP32) {
@@ -191,6 +206,35 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
   double nns_ms = 0.0, tail_ms = 0.0;
   long long nns_launches = 0, nns_pairs = 0;
   bool tail_ran = false;
+  if (B.dp > 0 && B.m <= FIN_MAX && B.n <= FIN_MAX) {
+    // small pair: the whole solve in one launch, one host synchronisation
+    CK(cudaMemsetAsync(B.st, 0, sizeof(DevState), st));
+    if (timed) CK(cudaEventRecord(ctx->ev[2], st));
+    if (launch_solve_small(B, a, b, st)) return fail(ctx, NNSEMD_ERR_CUDA, "small-pair launch");
+    if (timed) CK(cudaEventRecord(ctx->ev[3], st));
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->hstate, B.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int rc0 = map_err_bits(ctx, ctx->hstate->err);
+    if (rc0) return rc0;
+    *cost = ctx->hstate->cost;
+    *nnz = (int64_t)ctx->hstate->nnz;
+    ctx->launches += 1;
+    if (timed) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]));
+      tail_ms = ms;
+    }
+    if (stats) {
+      std::memset(stats, 0, sizeof(*stats));
+      stats->rounds = ctx->hstate->rounds;
+      stats->pair_evals = ctx->hstate->pair_evals;
+      stats->leftover_mass = ctx->hstate->leftover;
+      stats->kernel_launches = 1;
+      stats->tail_kernel_ms = tail_ms;
+    }
+    return NNSEMD_OK;
+  }
   CK(cudaMemsetAsync(B.st, 0, sizeof(DevState), st));
   CK(cudaMemsetAsync(B.xs_acc, 0, 4 * XS_LIMBS * sizeof(unsigned long long), st));
   CK(cudaMemsetAsync(B.cnt, 0, B.m * sizeof(int), st));
@@ -335,6 +379,9 @@ int nnsemd_destroy(nnsemd_ctx* ctx) {
   if (ctx->hstate) cudaFreeHost(ctx->hstate);
   for (cudaEvent_t e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& g : ctx->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   delete ctx;
   return NNSEMD_OK;
 }
@@ -386,8 +433,8 @@ int nnsemd_solve_host(nnsemd_ctx* ctx, const float* x, const double* a, int64_t 
                       nnsemd_plan* plan, nnsemd_stats* stats) {
   if (!ctx) return NNSEMD_ERR_INVALID_ARG;
   ctx->err.clear();
-  int metric;
-  int rc = check_opts(ctx, opt, d, metric);
+  int metric, precision;
+  int rc = check_opts(ctx, opt, d, metric, &precision);
   if (rc) return rc;
   if ((rc = check_sizes(ctx, m, n))) return rc;
   if (!x || !a || !y || !b || !cost_out) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "null pointer argument");
@@ -396,7 +443,7 @@ int nnsemd_solve_host(nnsemd_ctx* ctx, const float* x, const double* a, int64_t 
   CK(cudaSetDevice(ctx->device));
   // device staging for the inputs and the plan, placed after the solve buffers
   SolveBufs B{};
-  size_t solve_bytes = layout_solve(nullptr, m, n, d, B);
+  size_t solve_bytes = layout_solve(nullptr, m, n, d, B, precision);
   const int64_t cap = plan ? std::min<int64_t>(plan->capacity, m + n) : 0;
   auto stage_layout = [&](void* base, float** xd, double** ad, float** yd, double** bd, int32_t** pi, int32_t** pj,
                           double** pf) {
@@ -416,7 +463,7 @@ int nnsemd_solve_host(nnsemd_ctx* ctx, const float* x, const double* a, int64_t 
   int32_t *pi, *pj;
   size_t bytes = stage_layout(nullptr, &xd, &ad, &yd, &bd, &pi, &pj, &pf);
   if ((rc = ensure_ws(ctx, bytes))) return rc;
-  layout_solve(ctx->ws, m, n, d, B);
+  layout_solve(ctx->ws, m, n, d, B, precision);
   stage_layout(ctx->ws, &xd, &ad, &yd, &bd, &pi, &pj, &pf);
   cudaStream_t st = ctx->stream;
   CK(cudaMemcpyAsync(xd, x, (size_t)m * d * sizeof(float), cudaMemcpyHostToDevice, st));
@@ -456,9 +503,11 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
                          int32_t d, const nnsemd_options* opt, double* costs_out, nnsemd_stats* stats) {
   if (!ctx) return NNSEMD_ERR_INVALID_ARG;
   ctx->err.clear();
-  int metric;
-  int rc = check_opts(ctx, opt, d, metric);
+  int metric, precision;
+  int rc = check_opts(ctx, opt, d, metric, &precision);
   if (rc) return rc;
+  const int flags = opt ? opt->flags : 0;
+  const bool tc = precision != NNSEMD_FP32;
   if (num_pairs < 0) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "num_pairs < 0");
   if (num_pairs == 0) {
     if (stats) std::memset(stats, 0, sizeof(*stats));
@@ -468,22 +517,38 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
     return fail(ctx, NNSEMD_ERR_INVALID_ARG, "null pointer argument");
   if (x_off[0] != 0 || y_off[0] != 0) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "offsets must start at 0");
   std::vector<int> small, large;
+  int64_t small_max = 0;
   for (int p = 0; p < num_pairs; ++p) {
     const int64_t m = x_off[p + 1] - x_off[p], n = y_off[p + 1] - y_off[p];
     if (m < 1 || n < 1) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "pair %d has an empty side", p);
     const int cap = d <= 8 ? FIN_MAX : FIN_MAX_HD;
-    ((m <= cap && n <= cap) ? small : large).push_back(p);
+    const bool fits = m <= cap && n <= cap;
+    (fits ? small : large).push_back(p);
+    if (fits) small_max = std::max(small_max, std::max(m, n));
   }
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
-  // workspace: offsets, pair list, queue, per-pair counters, error word
+  const int grid = (int)std::min<size_t>(small.size(), 152);
+  // tensor-core kernel geometry: capacity class, bytes per packed row, tile
+  // rows and pipeline stages (autotuned or default)
+  const int cap = small_max <= 512 ? 512 : 2048;
+  const int kb = tc ? (int)tc_kb(d, precision) : 0;
+  int bn = tc ? tc_bn(kb) : 0;
+  int nstage = tc ? batched_tc_max_stages(cap, kb, bn, precision) : 0;
+  if (tc && !small.empty() && nstage < 1) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "d = %d too large for the batched tensor-core kernel", d);
+  const auto tkey = std::make_tuple(d, precision, cap);
+  if (tc && ctx->tuned.count(tkey)) std::tie(bn, nstage) = ctx->tuned[tkey];
+  const size_t slot = tc ? std::max(batched_tc_slot_bytes(cap, kb, 64), batched_tc_slot_bytes(cap, kb, 128)) : 0;
+  // workspace: offsets, pair list, queue/error/counters, per-pair counters,
+  // tensor-core scratch slots, then the buffers of the large pairs
   Carve C(nullptr);
   C.take<int64_t>(num_pairs + 1);
   C.take<int64_t>(num_pairs + 1);
   C.take<int>(small.size() + 1);
-  C.take<unsigned>(4);
+  C.take<unsigned long long>(4);
   C.take<long long>(num_pairs);
   C.take<long long>(num_pairs);
+  C.take<uint8_t>(tc ? slot * grid : 0);
   const size_t head = (C.off + 511) & ~(size_t)255;  // keeps the solve buffers 256-byte aligned
   size_t bytes = head;
   int64_t maxm = 0, maxn = 0;
@@ -492,35 +557,102 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
     maxn = std::max(maxn, y_off[p + 1] - y_off[p]);
   }
   SolveBufs B{};
-  if (!large.empty()) bytes += layout_solve(nullptr, maxm, maxn, d, B);
+  if (!large.empty()) bytes += layout_solve(nullptr, maxm, maxn, d, B, precision);
   if ((rc = ensure_ws(ctx, bytes))) return rc;
   Carve W(ctx->ws);
   int64_t* xo_d = W.take<int64_t>(num_pairs + 1);
   int64_t* yo_d = W.take<int64_t>(num_pairs + 1);
   int* ids_d = W.take<int>(small.size() + 1);
-  unsigned* q_d = W.take<unsigned>(4);
+  unsigned long long* ctr_d = W.take<unsigned long long>(4);  // [0]: queue | err << 32, [1] certified, [2] fallbacks
   long long* rounds_d = W.take<long long>(num_pairs);
   long long* pe_d = W.take<long long>(num_pairs);
+  uint8_t* scratch = W.take<uint8_t>(tc ? slot * grid : 0);
+  unsigned* q_d = reinterpret_cast<unsigned*>(ctr_d);
   CK(cudaMemcpyAsync(xo_d, x_off, (num_pairs + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(yo_d, y_off, (num_pairs + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
   if (!small.empty())
     CK(cudaMemcpyAsync(ids_d, small.data(), small.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-  CK(cudaMemsetAsync(q_d, 0, 4 * sizeof(unsigned), st));
-  CK(cudaMemsetAsync(rounds_d, 0, num_pairs * sizeof(long long), st));
-  CK(cudaMemsetAsync(pe_d, 0, num_pairs * sizeof(long long), st));
   long long L = 0;
-  if (!small.empty()) {
-    BatchArgs A{x_packed, a_packed, xo_d, y_packed, b_packed, yo_d, ids_d, (int)small.size(), d, metric,
+  // the device work of the small pairs: clear the counters, one persistent launch
+  auto issue = [&](cudaStream_t s, int nsmall, int g, int tbn, int tns) -> int {
+    if (cudaMemsetAsync(ctr_d, 0, 4 * sizeof(unsigned long long), s) != cudaSuccess) return -1;
+    if (cudaMemsetAsync(rounds_d, 0, num_pairs * sizeof(long long), s) != cudaSuccess) return -1;
+    if (cudaMemsetAsync(pe_d, 0, num_pairs * sizeof(long long), s) != cudaSuccess) return -1;
+    BatchArgs A{x_packed, a_packed, xo_d, y_packed, b_packed, yo_d, ids_d, nsmall, d, metric,
                 costs_out, rounds_d, pe_d, q_d, q_d + 1};
-    const int grid = (int)std::min<size_t>(small.size(), 152);
-    const int brc = d <= 8 ? launch_batched_lowd(A, grid, st) : launch_batched_hd(A, grid, st);
-    if (brc) return fail(ctx, NNSEMD_ERR_CUDA, "batched launch");
+    if (tc)
+      return launch_batched_tc(A, precision, cap, kb, tbn, tns, scratch, slot, ctr_d + 1, ctr_d + 2, g, s);
+    return d <= 8 ? launch_batched_lowd(A, g, s) : launch_batched_hd(A, g, s);
+  };
+  if (!small.empty() && tc && (flags & NNSEMD_FLAG_AUTOTUNE) && !ctx->tuned.count(tkey)) {
+    // time every feasible (tile rows, stages) on a sample of the batch
+    const int nsample = (int)std::min<size_t>(small.size(), 2 * 152);
+    const int gs = std::min(nsample, 152);
+    if (!ctx->ev[0])
+      for (int k = 0; k < 4; ++k) CK(cudaEventCreate(&ctx->ev[k]));
+    float best_ms = 1e30f;
+    std::pair<int, int> best{bn, nstage};
+    for (int tbn : {64, 128}) {
+      if (tbn == 128 && kb > 384) continue;
+      const int maxs = batched_tc_max_stages(cap, kb, tbn, precision);
+      for (int tns = 1; tns <= maxs; ++tns) {
+        if (issue(st, nsample, gs, tbn, tns)) return fail(ctx, NNSEMD_ERR_CUDA, "autotune launch");
+        CK(cudaEventRecord(ctx->ev[0], st));
+        if (issue(st, nsample, gs, tbn, tns)) return fail(ctx, NNSEMD_ERR_CUDA, "autotune launch");
+        CK(cudaEventRecord(ctx->ev[1], st));
+        CK(cudaEventSynchronize(ctx->ev[1]));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = {tbn, tns};
+        }
+        L += 2;
+      }
+    }
+    ctx->tuned[tkey] = best;
+    std::tie(bn, nstage) = best;
+  }
+  if (!small.empty()) {
+    int brc = 0;
+    if (flags & NNSEMD_FLAG_GRAPH) {
+      const std::vector<uintptr_t> key = {(uintptr_t)x_packed, (uintptr_t)a_packed, (uintptr_t)y_packed,
+                                          (uintptr_t)b_packed, (uintptr_t)costs_out, (uintptr_t)ctx->ws,
+                                          (uintptr_t)num_pairs, (uintptr_t)small.size(), (uintptr_t)d,
+                                          (uintptr_t)metric, (uintptr_t)precision, (uintptr_t)cap, (uintptr_t)bn,
+                                          (uintptr_t)nstage};
+      BatchGraph* g = nullptr;
+      for (auto& e : ctx->graphs)
+        if (e.key == key) g = &e;
+      if (!g) {
+        if (!ctx->capture_stream) CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+        brc = issue(ctx->capture_stream, (int)small.size(), grid, bn, nstage);
+        cudaError_t ce = cudaStreamEndCapture(ctx->capture_stream, &graph);
+        if (brc || ce != cudaSuccess) {
+          if (graph) cudaGraphDestroy(graph);
+          return fail(ctx, NNSEMD_ERR_CUDA, "graph capture of the batched launch failed");
+        }
+        cudaGraphExec_t exec = nullptr;
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaGraphInstantiate");
+        ctx->graphs.push_back({key, exec});
+        g = &ctx->graphs.back();
+      }
+      CK(cudaGraphLaunch(g->exec, st));
+    } else {
+      brc = issue(st, (int)small.size(), grid, bn, nstage);
+    }
+    if (brc) return fail(ctx, NNSEMD_ERR_CUDA, "batched launch (%d)", brc);
     CK(cudaGetLastError());
     L += 1;
   }
   long long extra_rounds = 0, extra_pe = 0;
+  long long extra_cert = 0, extra_fall = 0;
   for (int p : large) {
-    layout_solve((char*)ctx->ws + head, maxm, maxn, d, B);
+    layout_solve((char*)ctx->ws + head, maxm, maxn, d, B, precision);
     B.x = x_packed + x_off[p] * d;
     B.y = y_packed + y_off[p] * d;
     B.m = x_off[p + 1] - x_off[p];
@@ -536,17 +668,19 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
     CK(cudaMemcpyAsync(costs_out + p, &B.st->cost, sizeof(double), cudaMemcpyDeviceToDevice, st));
     extra_rounds += s1.rounds;
     extra_pe += s1.pair_evals;
+    extra_cert += s1.certified;
+    extra_fall += s1.fallbacks;
     L += s1.kernel_launches;
   }
   ctx->launches += L;
   if (stats) {
-    unsigned err = 0;
+    unsigned long long ctr[4] = {0, 0, 0, 0};
     std::vector<long long> r(num_pairs), pe(num_pairs);
-    CK(cudaMemcpyAsync(&err, q_d + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ctr, ctr_d, sizeof(ctr), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(r.data(), rounds_d, num_pairs * sizeof(long long), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(pe.data(), pe_d, num_pairs * sizeof(long long), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if ((rc = map_err_bits(ctx, err))) return rc;
+    if ((rc = map_err_bits(ctx, (unsigned)(ctr[0] >> 32)))) return rc;
     std::memset(stats, 0, sizeof(*stats));
     for (int p : small) {
       stats->rounds += r[p];
@@ -554,6 +688,8 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
     }
     stats->rounds += extra_rounds;
     stats->pair_evals += extra_pe;
+    stats->certified = (int64_t)ctr[1] + extra_cert;
+    stats->fallbacks = (int64_t)ctr[2] + extra_fall;
     stats->kernel_launches = L;
   }
   return NNSEMD_OK;

@@ -1,0 +1,453 @@
+// Batched reduced-precision NNS-EMD (d > 8): one persistent launch, one pair
+// per CTA, all rounds of Alg. 1 (Sec. III-A) on chip (Sec. III-D batch
+// processing), with the NNS operation of every round on the tensor cores.
+//
+// Per round the CTA
+//   1. packs its pair's active points (BF16 / FP16 / FP8 with per-row scale)
+//      into its own slot of a global scratch area, in the K-major no-swizzle
+//      core-matrix layout, with FP32 norms and the certificate's maxima;
+//   2. runs a tcgen05 pipeline over (consumer tile of 128) x (supplier tile
+//      of BN): warp 0 issues the bulk copies (TMA), warp 1 owns tensor memory
+//      and issues the MMAs into two FP32 accumulators, warps 2..5 keep the
+//      top-8 approximate suppliers of each consumer; the pipeline's phase
+//      counters live for the whole launch;
+//   3. re-ranks the 8 candidates of every consumer with the exact FP32 key
+//      (all 32 warps) and certifies the best (tc_common.cuh); consumers that
+//      cannot be certified are scanned again in FP32 (64 x 64 tiles);
+//   4. groups, serves, retires and compacts exactly as the other one-CTA
+//      solvers (cta.cuh).
+// The result equals the FP32 path's.  All waits are bounded (EF_TIMEOUT).
+#include <math_constants.h>
+
+#include "common.cuh"
+#include "cta.cuh"
+#include "kernels.h"
+#include "tc_common.cuh"
+
+namespace nnsemd {
+
+// Candidates per consumer in the batched kernel (its 1,024 threads have 64
+// registers each; the multi-CTA kernel keeps TC_K = 16).
+constexpr int BTC_K = 8;
+
+// Per-CTA scratch in global memory.
+struct BtcScratch {
+  uint8_t* A;       // consumer tiles
+  uint8_t* B;       // supplier tiles
+  float* nrm_x;
+  float* nrm_sx;    // |x| rounded up (0 on padding)
+  float* scale_x;
+  float* nrm_y;
+  float* scale_y;
+  float* cand_v;    // [cap][BTC_K]
+  int* cand_p;
+};
+
+__host__ __device__ inline size_t btc_slot_layout(uint8_t* base, int cap, int kb, int bn, BtcScratch* out) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = (off + 255) & ~(size_t)255;
+    uint8_t* p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  };
+  const int qrows = (cap + TC_BM - 1) / TC_BM * TC_BM;
+  const int srows = (cap + bn - 1) / bn * bn;
+  BtcScratch s;
+  s.A = take((size_t)qrows * kb);
+  s.B = take((size_t)srows * kb);
+  s.nrm_x = (float*)take(srows * sizeof(float));
+  s.nrm_sx = (float*)take(srows * sizeof(float));
+  s.scale_x = (float*)take(srows * sizeof(float));
+  s.nrm_y = (float*)take(qrows * sizeof(float));
+  s.scale_y = (float*)take(qrows * sizeof(float));
+  s.cand_v = (float*)take((size_t)cap * BTC_K * sizeof(float));
+  s.cand_p = (int*)take((size_t)cap * BTC_K * sizeof(int));
+  if (out) *out = s;
+  return (off + 255) & ~(size_t)255;
+}
+
+size_t batched_tc_slot_bytes(int cap, int kb, int bn) { return btc_slot_layout(nullptr, cap, kb, bn, nullptr); }
+
+struct BtcArgs {
+  BatchArgs base;
+  uint8_t* scratch;          // grid x slot_bytes
+  size_t slot_bytes;
+  int kb, bn, nstage, fmt;
+  unsigned long long* certified;
+  unsigned long long* fallbacks;
+};
+
+// The NNS policy of the batched tensor-core solver (coordinates in global
+// memory, index-only active lists, like GeoGlobal).
+template <bool KIND8, int CAP>
+struct GeoTC {
+  static constexpr int kDP = 0;
+  struct PX {};
+  const float* x;  // this pair's coordinates
+  const float* y;
+  int d;
+  BtcScratch scr;
+  int kb, bn, nstage, fmt;
+  uint32_t tmem_base;
+  unsigned* err;
+  uint64_t bar_full[8];
+  uint64_t bar_empty[8];
+  uint64_t bar_acc_full[2];
+  uint64_t bar_acc_empty[2];
+  uint64_t bar_a_full;
+  uint64_t bar_a_empty;
+  // pipeline counters: prod_* only by the producer thread, mma_* only by the
+  // MMA thread; epi_acc is read by the epilogue threads at the start of a
+  // phase and advanced by one thread after it
+  unsigned prod_a, prod_b, mma_a, mma_b, mma_acc, epi_acc;
+  unsigned stat_rx, stat_rx1, stat_sx;  // certificate maxima of this round (float bits)
+  int nfb;
+  unsigned long long ncert, nfall;
+  int fb[CAP];
+  // staging: tensor-core operand tiles or FP32 fallback tiles (never both at
+  // once); the launch reserves max(sizeof(tiles), A + stages * B) bytes
+  union __align__(128) Stage {
+    TileSmem tiles[FIN_THREADS / TG_THREADS];
+    uint8_t bytes[16];
+  } U;
+
+  NNS_DEV void load_x(int, PX&) const {}
+  NNS_DEV void store_x(int, const PX&) {}
+  NNS_DEV void load_y(int, PX&) const {}
+  NNS_DEV void store_y(int, const PX&) {}
+  template <int C>
+  NNS_DEV double dist64(const CtaCore<C>& S, int p, int q, int metric) const {
+    return cost_dist64(x + (size_t)S.iidx[p] * d, y + (size_t)S.jidx[q] * d, d, metric);
+  }
+
+  template <int C>
+  NNS_DEV void nns(CtaCore<C>& S, int mt, int nt) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int qtiles = (nt + TC_BM - 1) / TC_BM;
+    const int stiles = (mt + bn - 1) / bn;
+    const int nblk = kb / 16;
+    // ---- 1. pack both sides
+    if (tid == 0) {
+      stat_rx = stat_rx1 = stat_sx = 0u;
+      nfb = 0;
+    }
+    __syncthreads();
+    {
+      // one thread per row: scale and norms once, then every 16-byte block
+      const int srows = stiles * bn, qrows = qtiles * TC_BM;
+      const int total = srows + qrows;
+      for (int row_id = tid; row_id < total; row_id += T) {
+        const bool sup = row_id < srows;
+        const int p = sup ? row_id : row_id - srows;
+        const int cnt = sup ? mt : nt;
+        const float* row = p < cnt ? (sup ? x + (size_t)S.iidx[p] * d : y + (size_t)S.jidx[p] * d) : nullptr;
+        const float s = row_scale(row, d, fmt);
+        const int rows = sup ? bn : TC_BM;
+        uint8_t* tile = (sup ? scr.B : scr.A) + (size_t)(p / rows) * rows * kb;
+        for (int c = 0; c < nblk; ++c) pack_block(row, d, c, s, fmt, tile, rows, p % rows);
+        {
+          float* nrm = sup ? scr.nrm_x : scr.nrm_y;
+          float* scl = sup ? scr.scale_x : scr.scale_y;
+          if (row) {
+            float l2sq, l1;
+            row_norms(row, d, l2sq, l1);
+            nrm[p] = l2sq;
+            scl[p] = s;
+            if (sup) {
+              scr.nrm_sx[p] = norm_up(l2sq);
+              atomicMax(&stat_rx, __float_as_uint(norm_up(l2sq)));
+              atomicMax(&stat_rx1, __float_as_uint(l1 * (1.f + 1e-4f)));
+              atomicMax(&stat_sx, __float_as_uint(s));
+            }
+          } else {
+            nrm[p] = CUDART_INF_F;
+            scl[p] = 1.f;
+            if (sup) scr.nrm_sx[p] = 0.f;
+          }
+        }
+      }
+    }
+    fence_proxy_async_global();                                   // packed tiles -> later bulk copies
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // last round's FP32 tiles -> bulk writes
+    __syncthreads();
+    // ---- 2. tensor-core pipeline
+    const uint32_t a_bytes = TC_BM * kb, b_bytes = bn * kb;
+    uint8_t* sA = U.bytes;
+    uint8_t* sB = U.bytes + a_bytes;
+    bool ok = true;
+    if (warp == 0) {
+      if (lane == 0) {
+        for (int qt = 0; qt < qtiles && ok; ++qt) {
+          ok = mbar_wait_bounded(&bar_a_empty, (prod_a & 1) ^ 1);
+          if (!ok) break;
+          mbar_expect_tx(&bar_a_full, a_bytes);
+          tma_load_1d(sA, scr.A + (size_t)qt * a_bytes, a_bytes, &bar_a_full);
+          ++prod_a;
+          for (int st = 0; st < stiles && ok; ++st) {
+            const unsigned s = prod_b % nstage, u = prod_b / nstage;
+            ok = mbar_wait_bounded(&bar_empty[s], (u & 1) ^ 1);
+            if (!ok) break;
+            mbar_expect_tx(&bar_full[s], b_bytes);
+            tma_load_1d(sB + (size_t)s * b_bytes, scr.B + (size_t)st * b_bytes, b_bytes, &bar_full[s]);
+            ++prod_b;
+          }
+        }
+      }
+    } else if (warp == 1) {
+      if (lane == 0) {
+        const uint32_t idesc = make_idesc(fmt == FMT_BF16 ? 1 : 0, TC_BM, bn);
+        const int ksteps = kb / 32;
+        const uint32_t a0 = smem_u32(sA);
+        for (int qt = 0; qt < qtiles && ok; ++qt) {
+          ok = mbar_wait_bounded(&bar_a_full, mma_a & 1);
+          if (!ok) break;
+          for (int st = 0; st < stiles && ok; ++st) {
+            const unsigned s = mma_b % nstage, u = mma_b / nstage;
+            const unsigned b = mma_acc & 1, v = mma_acc >> 1;
+            ok = mbar_wait_bounded(&bar_full[s], u & 1);
+            if (ok) ok = mbar_wait_bounded(&bar_acc_empty[b], (v & 1) ^ 1);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t b0 = smem_u32(sB + (size_t)s * b_bytes);
+            const uint32_t tmem_d = tmem_base + b * (uint32_t)bn;
+            for (int k = 0; k < ksteps; ++k) {
+              const uint64_t ad = make_desc(a0 + k * 2 * TC_BM * 16, TC_BM * 16, 128);
+              const uint64_t bd = make_desc(b0 + k * 2 * bn * 16, bn * 16, 128);
+              mma_issue<KIND8 ? FMT_E4M3 : FMT_BF16>(tmem_d, ad, bd, idesc, k > 0 ? 1u : 0u);
+            }
+            mma_commit(&bar_empty[s]);
+            mma_commit(&bar_acc_full[b]);
+            ++mma_b;
+            ++mma_acc;
+          }
+          mma_commit(&bar_a_empty);  // A may be overwritten once these MMAs are done
+          ++mma_a;
+        }
+      }
+    } else if (warp < 6) {
+      const int quarter = warp & 3;
+      const int row = quarter * 32 + lane;
+      unsigned ea = epi_acc;
+      for (int qt = 0; qt < qtiles; ++qt) {
+        const int q = qt * TC_BM + row;
+        const float sy = q < nt ? scr.scale_y[q] : 1.f;
+        const float cy = quant_coeff(fmt, q < nt ? scr.nrm_y[q] : 0.f);
+        float tv[BTC_K];
+        int tp[BTC_K];
+#pragma unroll
+        for (int k = 0; k < BTC_K; ++k) { tv[k] = CUDART_INF_F; tp[k] = -1; }
+        for (int st = 0; st < stiles; ++st, ++ea) {
+          const unsigned b = ea & 1, v = ea >> 1;
+          if (ok) ok = mbar_wait_bounded(&bar_acc_full[b], v & 1);
+          tc_fence_after();
+          if (ok) {
+            const float* nx = scr.nrm_x + (size_t)st * bn;
+            const float* ns = scr.nrm_sx + (size_t)st * bn;
+            const float* sx = scr.scale_x + (size_t)st * bn;
+            for (int c0 = 0; c0 < bn; c0 += 16) {
+              uint32_t r[16];
+              tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + b * (uint32_t)bn + (uint32_t)c0, r);
+#pragma unroll
+              for (int e = 0; e < 16; ++e) {
+                const float acc = __uint_as_float(r[e]);
+                const float w = fmt == FMT_BF16 ? -2.f : -2.f * sy * sx[c0 + e];
+                const float val = __fmaf_rn(-cy, ns[c0 + e], __fmaf_rn(w, acc, nx[c0 + e]));
+                topk_insert(tv, tp, val, st * bn + c0 + e);
+              }
+            }
+          }
+          tc_fence_before();
+          mbar_arrive(&bar_acc_empty[b]);
+        }
+        if (q < nt) {
+#pragma unroll
+          for (int k = 0; k < BTC_K; ++k) {
+            scr.cand_v[(size_t)q * BTC_K + k] = tv[k];
+            scr.cand_p[(size_t)q * BTC_K + k] = tp[k];
+          }
+        }
+      }
+    }
+    if (!ok) atomicOr(err, EF_TIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 64) epi_acc += (unsigned)(qtiles * stiles);
+    // ---- 3. exact re-rank + certificate (a warp per consumer)
+    const double rx = __uint_as_float(stat_rx), rx1 = __uint_as_float(stat_rx1), sxm = __uint_as_float(stat_sx);
+    for (int q = warp; q < nt; q += T / 32) {
+      const float* yrow = y + (size_t)S.jidx[q] * d;
+      unsigned long long best = ~0ULL;
+      if (lane < BTC_K) {
+        const int p = scr.cand_p[(size_t)q * BTC_K + lane];
+        if (p >= 0) best = pack_key(key32<METRIC_SQL2>(x + (size_t)S.iidx[p] * d, yrow, d), (unsigned)p);
+      }
+      double yl2 = 0.0, yl1 = 0.0;
+      for (int k = lane; k < d; k += 32) {
+        yl2 += (double)yrow[k] * yrow[k];
+        yl1 += fabs((double)yrow[k]);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+        best = ob < best ? ob : best;
+        yl2 += __shfl_xor_sync(0xffffffffu, yl2, o);
+        yl1 += __shfl_xor_sync(0xffffffffu, yl1, o);
+      }
+      if (lane == 0) {
+        const float tau = scr.cand_v[(size_t)q * BTC_K + BTC_K - 1];
+        const bool cert = best != ~0ULL && certify(fmt, d, scr.nrm_y[q], sqrt(yl2) * (1 + 1e-12), yl1,
+                                                    scr.scale_y[q], rx, rx1, sxm, tau,
+                                                    __uint_as_float((unsigned)(best >> 32)));
+        if (cert) {
+          S.nnk[q] = best;
+          atomicAdd(&ncert, 1ULL);
+        } else {
+          fb[atomicAdd(&nfb, 1)] = q;
+          atomicAdd(&nfall, 1ULL);
+        }
+      }
+    }
+    __syncthreads();
+    // ---- 4. FP32 rescan of the consumers that were not certified
+    const int nf = nfb;
+    if (nf > 0) {
+      const int g = tid / TG_THREADS, gt = tid % TG_THREADS;
+      const int ngroups = T / TG_THREADS;
+      for (int c0 = g * TG_M; c0 < nf; c0 += ngroups * TG_M) {
+        unsigned long long out[4];
+        group_nns_tile<false>(x, S.iidx, 0, mt, y, S.jidx, fb, c0, min(TG_M, nf - c0), d, U.tiles[g], gt, 1 + g,
+                              out);
+        const int tx = gt & 15, ty = gt >> 4;
+        if (tx == 0)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int lq = c0 + ty * 4 + i;
+            if (lq < nf) S.nnk[fb[lq]] = out[i];
+          }
+      }
+    }
+    __syncthreads();
+  }
+};
+
+template <bool KIND8, int CAP>
+struct BtcSmem {
+  CtaCore<CAP> S;
+  GeoTC<KIND8, CAP> G;  // its staging union is last and may extend past sizeof()
+};
+
+template <bool KIND8, int CAP>
+size_t btc_smem_bytes(int kb, int bn, int nstage) {
+  using M = BtcSmem<KIND8, CAP>;
+  const size_t stage = (size_t)TC_BM * kb + (size_t)nstage * bn * kb;
+  const size_t have = sizeof(typename GeoTC<KIND8, CAP>::Stage);
+  return sizeof(M) + (stage > have ? stage - have : 0);
+}
+
+template <bool KIND8, int CAP>
+__global__ void __launch_bounds__(FIN_THREADS, 1) k_batched_tc(BtcArgs A) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  BtcSmem<KIND8, CAP>& M = *reinterpret_cast<BtcSmem<KIND8, CAP>*>(smem_raw);
+  CtaCore<CAP>& S = M.S;
+  GeoTC<KIND8, CAP>& G = M.G;
+  __shared__ int s_item;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t ncols = 2u * (uint32_t)A.bn;
+  if (tid == 0) {
+    for (int s = 0; s < A.nstage; ++s) {
+      mbar_init(&G.bar_full[s], 1);
+      mbar_init(&G.bar_empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&G.bar_acc_full[b], 1);
+      mbar_init(&G.bar_acc_empty[b], 4 * 32);
+    }
+    mbar_init(&G.bar_a_full, 1);
+    mbar_init(&G.bar_a_empty, 1);
+    mbar_fence_init();
+    G.prod_a = G.prod_b = G.mma_a = G.mma_b = G.mma_acc = G.epi_acc = 0u;
+    G.ncert = G.nfall = 0ULL;
+    G.kb = A.kb;
+    G.bn = A.bn;
+    G.nstage = A.nstage;
+    G.fmt = A.fmt;
+    G.err = A.base.err;
+    btc_slot_layout(A.scratch + (size_t)blockIdx.x * A.slot_bytes, CAP, A.kb, A.bn, &G.scr);
+  }
+  if (warp == 1) tmem_alloc(&tmem_slot, ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid == 0) G.tmem_base = tmem_slot;
+  __syncthreads();
+  const BatchArgs& B = A.base;
+  for (;;) {
+    if (tid == 0) s_item = (int)atomicAdd(B.queue, 1u);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= B.num) break;
+    const int pr = B.pair_ids[item];
+    const int64_t xo = B.x_off[pr], yo = B.y_off[pr];
+    const int m = (int)(B.x_off[pr + 1] - xo), n = (int)(B.y_off[pr + 1] - yo);
+    if (tid == 0) {
+      G.x = B.x + xo * B.d;
+      G.y = B.y + yo * B.d;
+      G.d = B.d;
+    }
+    __syncthreads();
+    double cost = 0.0;
+    long long rounds = 0, pe = 0;
+    const bool ok = cta_solve_pair(S, G, nullptr, nullptr, B.x + xo * B.d, B.a + xo, m, B.y + yo * B.d, B.b + yo, n,
+                                   B.d, B.metric, B.err, cost, rounds, pe);
+    if (tid == 0) {
+      B.costs[pr] = ok ? cost : CUDART_NAN;
+      if (B.rounds) B.rounds[pr] = rounds;
+      if (B.pair_evals) B.pair_evals[pr] = pe;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    atomicAdd(A.certified, G.ncert);
+    atomicAdd(A.fallbacks, G.nfall);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(G.tmem_base, ncols);
+}
+
+template <bool KIND8, int CAP>
+static int batched_tc_t(const BtcArgs& A, int grid, cudaStream_t st) {
+  const size_t smem = btc_smem_bytes<KIND8, CAP>(A.kb, A.bn, A.nstage);
+  if (smem > 227 * 1024) return -2;
+  cudaError_t e = cudaFuncSetAttribute(k_batched_tc<KIND8, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return -1;
+  k_batched_tc<KIND8, CAP><<<grid, FIN_THREADS, smem, st>>>(A);
+  return 0;
+}
+
+// Largest number of pipeline stages that fits the shared-memory budget.
+int batched_tc_max_stages(int cap, int kb, int bn, int precision) {
+  for (int ns = 4; ns >= 1; --ns) {
+    size_t b;
+    if (precision == 3) b = cap <= 512 ? btc_smem_bytes<true, 512>(kb, bn, ns) : btc_smem_bytes<true, 2048>(kb, bn, ns);
+    else b = cap <= 512 ? btc_smem_bytes<false, 512>(kb, bn, ns) : btc_smem_bytes<false, 2048>(kb, bn, ns);
+    if (b <= 227 * 1024) return ns;
+  }
+  return 0;
+}
+
+int launch_batched_tc(const BatchArgs& base, int precision, int cap, int kb, int bn, int nstage, uint8_t* scratch,
+                      size_t slot_bytes, unsigned long long* certified, unsigned long long* fallbacks, int grid,
+                      cudaStream_t st) {
+  BtcArgs A{base, scratch, slot_bytes, kb, bn, nstage, fmt_of_precision(precision), certified, fallbacks};
+  const bool k8 = precision == 3;
+  if (cap <= 512) return k8 ? batched_tc_t<true, 512>(A, grid, st) : batched_tc_t<false, 512>(A, grid, st);
+  return k8 ? batched_tc_t<true, 2048>(A, grid, st) : batched_tc_t<false, 2048>(A, grid, st);
+}
+
+}  // namespace nnsemd

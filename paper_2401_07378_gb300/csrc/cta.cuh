@@ -280,7 +280,7 @@ struct GeoGlobal {
 // Stable compaction of both active lists to the points with weight left.
 template <int CAP, class Geo>
 NNS_DEV void cta_compact(CtaCore<CAP>& S, Geo& G) {
-  constexpr int IT = CAP / FIN_THREADS;
+  constexpr int IT = (CAP + FIN_THREADS - 1) / FIN_THREADS;
   const int tid = threadIdx.x;
   const int mt = S.mt, nt = S.nt;
   bool ks[IT], kc[IT];
@@ -317,7 +317,7 @@ NNS_DEV void cta_compact(CtaCore<CAP>& S, Geo& G) {
 // Exclusive scan of in[0..n) into out[0..n) (n <= CAP), returns the total.
 template <int CAP>
 NNS_DEV int block_scan_array(const int* in, int* out, int n, int* wt) {
-  constexpr int IT = CAP / FIN_THREADS;
+  constexpr int IT = (CAP + FIN_THREADS - 1) / FIN_THREADS;
   int v[IT];
   int s = 0;
 #pragma unroll
@@ -432,31 +432,33 @@ NNS_DEV bool cta_load_side(const float* pts, const double* w, int cnt, int d, fl
   const int tid = threadIdx.x;
   for (int i = tid; i < XS_LIMBS; i += blockDim.x) S.acc[i] = 0ULL;
   __syncthreads();
-  bool bad = false;
+  bool nonfinite = false, negative = false;
   for (int p = tid; p < cnt; p += blockDim.x) {
     if (DP > 0) {
 #pragma unroll
       for (int k = 0; k < (DP > 0 ? DP : 1); ++k) {
         const float v = k < d ? pts[(size_t)p * d + k] : 0.f;
-        if (!isfinite(v)) bad = true;
+        if (!isfinite(v)) nonfinite = true;
         dst[p * DP + k] = v;
       }
     } else {
       for (int k = 0; k < d; ++k)
-        if (!isfinite(pts[(size_t)p * d + k])) bad = true;
+        if (!isfinite(pts[(size_t)p * d + k])) nonfinite = true;
     }
     const double wv = w[p];
-    if (!isfinite(wv) || wv < 0.0) bad = true;
+    if (!isfinite(wv)) nonfinite = true;
+    else if (wv < 0.0) negative = true;
     res[p] = wv;
     idx[p] = p;
-    if (isfinite(wv)) xs_add(S.acc, wv);
+    if (isfinite(wv) && wv > 0.0) xs_add(S.acc, wv);
   }
-  bad = __syncthreads_or(bad);
+  nonfinite = __syncthreads_or(nonfinite);
+  negative = __syncthreads_or(negative);
   if (tid == 0) S.total = xs_round(S.acc);
   __syncthreads();
   const double total = S.total;
-  if (bad || !(total > 0.0)) {
-    if (tid == 0) atomicOr(err, bad ? EF_NONFINITE : EF_ZERO_MASS);
+  if (nonfinite || negative || !(total > 0.0)) {
+    if (tid == 0) atomicOr(err, nonfinite ? EF_NONFINITE : (negative ? EF_NEGATIVE : EF_ZERO_MASS));
     __syncthreads();
     return false;
   }

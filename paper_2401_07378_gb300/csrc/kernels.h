@@ -26,6 +26,7 @@ struct TcBufs {
   uint8_t* A;                  // packed consumer tiles
   uint8_t* B;                  // packed supplier tiles
   float* nrm_x;                // per supplier position (padded), +inf on padding
+  float* nrm_sx;               // per supplier position: |x| rounded up, 0 on padding
   float* nrm_y;                // per consumer position
   float* scale_x;
   float* scale_y;
@@ -89,6 +90,9 @@ int launch_big_round(SolveBufs& B, int mt, int nt, cudaStream_t st);
 int launch_nns_lowd(const SolveBufs& B, int mt, int nt, cudaStream_t st);
 // Run all remaining rounds of the current active lists in one CTA.
 int launch_finish(const SolveBufs& B, int64_t round_limit, cudaStream_t st);
+// A whole pair with m, n <= FIN_MAX and d <= 8 in one launch (writes st->cost,
+// nnz, rounds, pair_evals, leftover and the plan).
+int launch_solve_small(const SolveBufs& B, const double* a, const double* b, cudaStream_t st);
 
 // Batched small pairs (all in one persistent launch), low d.
 struct BatchArgs {
@@ -121,5 +125,13 @@ int tc_bn(size_t kb);                // supplier rows per tile
 // NNS of every active consumer: tensor-core candidates, exact FP32 re-rank,
 // certificate, FP32 rescan of the rest.  Writes B.nnkey (must be all ones).
 int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int precision, cudaStream_t st);
+
+// batched_tc.cu: batches of pairs with up to `cap` (512 or 2048) points per
+// side, reduced-precision NNS inside each pair's CTA.
+size_t batched_tc_slot_bytes(int cap, int kb, int bn);
+int batched_tc_max_stages(int cap, int kb, int bn, int precision);
+int launch_batched_tc(const BatchArgs& base, int precision, int cap, int kb, int bn, int nstage, uint8_t* scratch,
+                      size_t slot_bytes, unsigned long long* certified, unsigned long long* fallbacks, int grid,
+                      cudaStream_t st);
 
 }  // namespace nnsemd

@@ -294,6 +294,73 @@ int launch_finish(const SolveBufs& B, int64_t round_limit, cudaStream_t st) {
 }
 
 // --------------------------------------------------------------------------
+// a whole small pair in one launch: load, normalise, every round, the plan,
+// R and the leftover mass (no host round trip between rounds)
+// --------------------------------------------------------------------------
+
+template <int D, int DP, bool L1>
+__global__ void __launch_bounds__(FIN_THREADS, 1) k_solve_small(SolveBufs B, const double* a, const double* b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  LowdSmem<D, DP, L1>& L = *reinterpret_cast<LowdSmem<D, DP, L1>*>(smem_raw);
+  CtaCore<FIN_MAX>& S = L.S;
+  const int tid = threadIdx.x;
+  const int m = (int)B.m, n = (int)B.n;
+  bool ok = cta_load_side<DP, FIN_MAX>(B.x, a, m, B.d, L.G.xs, S.sres, S.iidx, S, &B.st->err);
+  if (ok) ok = cta_load_side<DP, FIN_MAX>(B.y, b, n, B.d, L.G.ys, S.cres, S.jidx, S, &B.st->err);
+  if (!ok) return;
+  if (tid == 0) {
+    S.mt = m;
+    S.nt = n;
+  }
+  for (int i = tid; i < XS_LIMBS; i += blockDim.x) S.acc[i] = 0ULL;
+  __syncthreads();
+  cta_compact(S, L.G);  // drop zero weights
+  CtaOut O{nullptr, S.acc, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, nullptr, nullptr, &B.st->err};
+  unsigned long long nnz = 0;
+  long long rounds = 0, pe = 0;
+  cta_rounds(S, L.G, B.metric, O, nnz, rounds, pe, (long long)m + n);
+  __syncthreads();
+  if (tid == 0) B.st->cost = xs_round(S.acc);
+  __syncthreads();
+  for (int i = tid; i < XS_LIMBS; i += blockDim.x) S.acc[i] = 0ULL;
+  __syncthreads();
+  for (int p = tid; p < S.mt; p += blockDim.x) xs_add(S.acc, S.sres[p]);
+  for (int q = tid; q < S.nt; q += blockDim.x) xs_add(S.acc, S.cres[q]);
+  __syncthreads();
+  if (tid == 0) {
+    B.st->leftover = xs_round(S.acc);
+    B.st->nnz = nnz;
+    B.st->rounds = rounds;
+    B.st->pair_evals = pe;
+    B.st->mt = S.mt;
+    B.st->nt = S.nt;
+  }
+}
+
+template <int D, int DP, bool L1>
+static int solve_small_t(const SolveBufs& B, const double* a, const double* b, cudaStream_t st) {
+  const size_t smem = sizeof(LowdSmem<D, DP, L1>);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_solve_small<D, DP, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return -1;
+  k_solve_small<D, DP, L1><<<1, FIN_THREADS, smem, st>>>(B, a, b);
+  return 0;
+}
+
+int launch_solve_small(const SolveBufs& B, const double* a, const double* b, cudaStream_t st) {
+  const bool l1 = B.metric == METRIC_L1;
+#define SMALL_CASE(DD, DPP) \
+  case DD:                  \
+    return l1 ? solve_small_t<DD, DPP, true>(B, a, b, st) : solve_small_t<DD, DPP, false>(B, a, b, st);
+  switch (B.d) {
+    SMALL_CASE(1, 2) SMALL_CASE(2, 2) SMALL_CASE(3, 4) SMALL_CASE(4, 4)
+    SMALL_CASE(5, 8) SMALL_CASE(6, 8) SMALL_CASE(7, 8) SMALL_CASE(8, 8)
+    default: return -1;
+  }
+#undef SMALL_CASE
+}
+
+// --------------------------------------------------------------------------
 // batched small pairs: one persistent launch, a work queue of pairs, each
 // pair solved start to finish by one CTA (Sec. III-D batch processing)
 // --------------------------------------------------------------------------

@@ -9,14 +9,9 @@
 // suppliers with the smallest approximate distance.  The re-rank then
 // computes the exact FP32 key (the same definition as every other path) of
 // those candidates, takes the smallest (lowest position on ties), and
-// certifies it: every supplier that is not a candidate has an approximate
-// distance >= the K-th candidate's, so its true distance is >= that value
-// minus a rigorous bound on the quantisation and accumulation error; if the
-// best exact key is strictly below the resulting floor (shrunk by the FP32
-// key's own rounding bound) no other supplier can win, and the choice is the
-// FP32 path's choice.  Consumers that cannot be certified are scanned again
-// in FP32 (k_nns_f32_tiled).  The result is therefore identical to the FP32
-// path; only the time changes.
+// certifies it (tc_common.cuh): no supplier outside the candidates can reach
+// or beat it.  Consumers that cannot be certified are scanned again in FP32
+// (k_nns_f32_tiled).  The result is therefore identical to the FP32 path.
 //
 // K2 k_nns_tc: a CTA owns 128 consumers (the MMA's M) and streams supplier
 // tiles of BN rows.  Warp 0 issues 1-D bulk copies (TMA) of the packed tiles
@@ -25,166 +20,47 @@
 // accumulators (BN columns each); warps 2..5 read each accumulator row back
 // with tcgen05.ld (one consumer per thread) and update its top-K.  Every wait
 // on an mbarrier is bounded and raises EF_TIMEOUT instead of hanging.
-#include <math_constants.h>
-
 #include <algorithm>
 
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-#include <cuda_fp8.h>
-
 #include "common.cuh"
-#include "cta.cuh"
 #include "kernels.h"
+#include "tc_common.cuh"
 
 namespace nnsemd {
 
-constexpr int TC_BM = 128;         // consumers per CTA (MMA M)
-constexpr int TC_K = 8;            // candidates kept per consumer per chunk
-constexpr int TC_THREADS = 192;    // 6 warps
+constexpr int TC_THREADS = 192;  // 6 warps
 constexpr int TC_SMEM_BUDGET = 220 * 1024;
 
-enum TcFmt : int { FMT_F16 = 0, FMT_BF16 = 1, FMT_E4M3 = 2 };
-
-// --------------------------------------------------------------------------
-// packing: active points -> operand tiles in the K-major, no-swizzle layout
-//
-// A tile of R rows and KB bytes per row is stored as KB/16 column blocks of
-// R rows x 16 bytes: block c holds bytes [16c, 16c+16) of every row, rows 16
-// bytes apart.  Each 8-row x 16-byte piece is one "core matrix"; neighbouring
-// core matrices are 128 bytes apart along M/N (stride byte offset) and
-// R*16 bytes apart along K (leading byte offset).
-// --------------------------------------------------------------------------
-
-NNS_DEV uint16_t to_bits16(float v, int fmt) {
-  if (fmt == FMT_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(v));
-  return __half_as_ushort(__float2half_rn(v));
-}
-
-NNS_DEV uint8_t to_e4m3(float v) {
-  return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
-}
-
-// One thread per (point, 16-byte block).  Also writes, per point, the FP32
-// squared norm (sequential fma over the original coordinates), the
-// per-row scale and, in `stats`, the maxima of |v|_2 and |v|_1 over the
-// points (as float bits; all values are >= 0).
+// One thread per point (consecutive threads write consecutive 16-byte rows
+// of each column block).  Also writes, per point, the FP32 squared norm, the
+// per-row scale and, in `stats`, the maxima of |v|_2, |v|_1 and the scale
+// over the points (as float bits; all values >= 0).
 __global__ void k_pack_tc(const float* __restrict__ pts, const int* __restrict__ idx, int cnt, int rows_pad, int d,
                           int kb, int fmt, int tile_rows, uint8_t* __restrict__ out, float* __restrict__ nrm,
-                          float* __restrict__ scale, unsigned* __restrict__ stats) {
+                          float* __restrict__ nrm_s, float* __restrict__ scale, unsigned* __restrict__ stats) {
   const int nblk = kb / 16;
-  const int64_t total = (int64_t)rows_pad * nblk;
-  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
-    const int p = (int)(w / nblk), c = (int)(w % nblk);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < rows_pad; p += gridDim.x * blockDim.x) {
     const float* row = p < cnt ? pts + (size_t)idx[p] * d : nullptr;
-    // per-row scale (power of two) for FP16 / FP8: max |v| maps to <= 2^8 / 2^8
-    float s = 1.f;
-    if (row && fmt != FMT_BF16) {
-      float mx = 0.f;
-      for (int k = 0; k < d; ++k) mx = fmaxf(mx, fabsf(row[k]));
-      if (mx > 0.f) {
-        int e;
-        frexpf(mx, &e);  // mx in [2^(e-1), 2^e)
-        s = ldexpf(1.f, e - (fmt == FMT_E4M3 ? 8 : 8));  // scaled max in [2^7, 2^8)
-      }
-    }
-    alignas(16) uint8_t bytes[16];
-    if (fmt == FMT_E4M3) {
-#pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        const int k = c * 16 + e;
-        const float v = (row && k < d) ? row[k] / s : 0.f;
-        bytes[e] = to_e4m3(v);
-      }
-    } else {
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int k = c * 8 + e;
-        const float v = (row && k < d) ? row[k] / s : 0.f;
-        const uint16_t b = to_bits16(v, fmt);
-        bytes[2 * e] = (uint8_t)(b & 0xff);
-        bytes[2 * e + 1] = (uint8_t)(b >> 8);
-      }
-    }
+    const float s = row_scale(row, d, fmt);
     const int t = p / tile_rows, r = p % tile_rows;
-    uint8_t* dst = out + (size_t)t * tile_rows * kb + (size_t)c * tile_rows * 16 + (size_t)r * 16;
-    *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(bytes);
-    if (c == 0) {
+    for (int c = 0; c < nblk; ++c) pack_block(row, d, c, s, fmt, out + (size_t)t * tile_rows * kb, tile_rows, r);
+    {
       if (row) {
-        float acc = 0.f, l1 = 0.f;
-        for (int k = 0; k < d; ++k) {
-          acc = __fmaf_rn(row[k], row[k], acc);
-          l1 = __fadd_rn(l1, fabsf(row[k]));
-        }
-        nrm[p] = acc;
+        float l2sq, l1;
+        row_norms(row, d, l2sq, l1);
+        nrm[p] = l2sq;
+        if (nrm_s) nrm_s[p] = norm_up(l2sq);
         scale[p] = s;
-        atomicMax(stats + 0, __float_as_uint(sqrtf(acc) * (1.f + 1e-6f)));
-        atomicMax(stats + 1, __float_as_uint(l1 * (1.f + 1e-6f)));
+        atomicMax(stats + 0, __float_as_uint(norm_up(l2sq)));
+        atomicMax(stats + 1, __float_as_uint(l1 * (1.f + 1e-4f)));
         atomicMax(stats + 2, __float_as_uint(s));
       } else {
         nrm[p] = CUDART_INF_F;
+        if (nrm_s) nrm_s[p] = 0.f;
         scale[p] = 1.f;
       }
     }
   }
-}
-
-// --------------------------------------------------------------------------
-// tcgen05 helpers
-// --------------------------------------------------------------------------
-
-NNS_DEV uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
-  // base offset 0, relative LBO, swizzle mode 0 (none)
-  return d;
-}
-
-// Instruction descriptor: D = F32, A and B of type `ab` (kind::f16: 0 = F16,
-// 1 = BF16; kind::f8f6f4: 0 = E4M3), both K-major, N = n, M = m.
-NNS_DEV uint32_t make_idesc(int ab, int m, int n) {
-  return (1u << 4) | ((uint32_t)ab << 7) | ((uint32_t)ab << 10) | ((uint32_t)(n >> 3) << 17) |
-         ((uint32_t)(m >> 4) << 24);
-}
-
-template <int FMT>
-NNS_DEV void mma_issue(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accumulate) {
-  if (FMT == FMT_E4M3) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-  } else {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-  }
-}
-
-NNS_DEV void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-NNS_DEV void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-NNS_DEV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-NNS_DEV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-
-NNS_DEV void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // --------------------------------------------------------------------------
@@ -195,6 +71,8 @@ struct TcArgs {
   const uint8_t* A;        // packed consumer tiles (TC_BM rows each)
   const uint8_t* B;        // packed supplier tiles (bn rows each)
   const float* nrm_x;      // [supplier tiles * bn] squared norms (+inf on padding)
+  const float* nrm_sx;     // [supplier tiles * bn] norms rounded up (0 on padding)
+  const float* nrm_y;      // per-consumer squared norm
   const float* scale_x;    // per-supplier scale
   const float* scale_y;    // per-consumer scale
   int nt;                  // active consumers
@@ -247,12 +125,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
     mbar_init(&bar_a, 1);
     mbar_fence_init();
   }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(TMEM_ALLOC)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
+  if (warp == 1) tmem_alloc(&tmem_slot, TMEM_ALLOC);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -304,6 +177,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
     const int row = quarter * 32 + lane;
     const int q = qtile * TC_BM + row;
     const float sy = (q < P.nt) ? P.scale_y[q] : 1.f;
+    const float cy = quant_coeff(FMT, (q < P.nt) ? P.nrm_y[q] : 0.f);
     float tv[TC_K];
     int tp[TC_K];
 #pragma unroll
@@ -315,6 +189,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
       if (ok) {
         const int tile = t0 + t;
         const float* nx = P.nrm_x + (size_t)tile * BN;
+        const float* ns = P.nrm_sx + (size_t)tile * BN;
         const float* sx = P.scale_x + (size_t)tile * BN;
         for (int c0 = 0; c0 < BN; c0 += 16) {
           uint32_t r[16];
@@ -323,22 +198,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
           for (int e = 0; e < 16; ++e) {
             const float acc = __uint_as_float(r[e]);
             const float w = (FMT == FMT_BF16) ? -2.f : -2.f * sy * __ldg(sx + c0 + e);
-            const float val = __fmaf_rn(w, acc, __ldg(nx + c0 + e));
-            if (val < tv[TC_K - 1]) {
-              float nv = val;
-              int np = tile * BN + c0 + e;
-#pragma unroll
-              for (int k = 0; k < TC_K; ++k) {
-                if (nv < tv[k]) {
-                  const float fv = tv[k];
-                  const int fp = tp[k];
-                  tv[k] = nv;
-                  tp[k] = np;
-                  nv = fv;
-                  np = fp;
-                }
-              }
-            }
+            const float val = __fmaf_rn(-cy, __ldg(ns + c0 + e), __fmaf_rn(w, acc, __ldg(nx + c0 + e)));
+            topk_insert(tv, tp, val, tile * BN + c0 + e);
           }
         }
       }
@@ -358,8 +219,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_ALLOC)
-                              : "memory");
+  if (warp == 1) tmem_dealloc(tmem_base, TMEM_ALLOC);
 }
 
 // --------------------------------------------------------------------------
@@ -371,7 +231,7 @@ struct RerankArgs {
   const float* y;
   const int* ia;        // active supplier position -> original index
   const int* ja;
-  int d, nt, nt_pad, chunks, metric, fmt;
+  int d, nt, nt_pad, chunks, fmt;
   const float* cand_v;
   const int* cand_p;
   const float* nrm_y;   // FP32 squared norm of each active consumer
@@ -409,40 +269,16 @@ __global__ void k_rerank_certify(RerankArgs R) {
     tau = fminf(tau, __shfl_xor_sync(0xffffffffu, tau, o));
   }
   if (lane != 0) return;
-  // Error bound of approx(i, q) for any supplier i (all terms >= the truth).
-  const double d = R.d;
-  const double u32 = 0x1p-24;
-  const double uq = R.fmt == FMT_BF16 ? 0x1p-8 : (R.fmt == FMT_F16 ? 0x1p-11 : 0x1p-4);
-  const double gam = d * u32 / (1.0 - d * u32);
-  double ny = R.nrm_y[q];
   double yl2 = 0.0, yl1 = 0.0;
   for (int k = 0; k < R.d; ++k) {
     yl2 += (double)yrow[k] * yrow[k];
     yl1 += fabs((double)yrow[k]);
   }
   yl2 = sqrt(yl2) * (1 + 1e-12);
-  const double rx = __uint_as_float(R.stats_x[0]);
-  const double rx1 = __uint_as_float(R.stats_x[1]);
-  const double sxm = __uint_as_float(R.stats_x[2]);
-  const double sy = R.scale_y[q];
-  // smallest positive subnormal spacing / 2 of the operand format, in
-  // original units (scaled formats): absolute rounding floor per element
-  const double eta_unit = R.fmt == FMT_BF16 ? 0x1p-134 : (R.fmt == FMT_F16 ? 0x1p-25 : 0x1p-10);
-  const double eta_x = eta_unit * (R.fmt == FMT_BF16 ? 1.0 : sxm), eta_y = eta_unit * (R.fmt == FMT_BF16 ? 1.0 : sy);
-  const double dot_q = (2 * uq + uq * uq) * rx * yl2 + eta_x * (yl1 + eta_y * d) + eta_y * rx1 +
-                       eta_x * uq * yl1 + eta_y * uq * rx1;
-  const double xt = (1 + uq) * rx + eta_x * sqrt(d), yt = (1 + uq) * yl2 + eta_y * sqrt(d);
-  const double dot_acc = d * 0x1p-22 * xt * yt;
-  const double E = 2.0 * (gam * (ny + rx * rx) + 2.0 * (dot_q + dot_acc) + u32 * (rx * rx + 2.0 * xt * yt)) +
-                   1e-30;
-  const float bestk = __uint_as_float((unsigned)(best >> 32));
-  bool certified = false;
-  if (best != ~0ULL && tau < CUDART_INF_F) {
-    const double floor_true = (ny + (double)tau - E) * (1.0 - gam) * (1.0 - 0x1p-40);
-    certified = (double)bestk < floor_true;
-  } else if (best != ~0ULL) {
-    certified = true;  // fewer than K suppliers per chunk: every one was a candidate
-  }
+  const bool certified =
+      best != ~0ULL && certify(R.fmt, R.d, R.nrm_y[q], yl2, yl1, R.scale_y[q], __uint_as_float(R.stats_x[0]),
+                               __uint_as_float(R.stats_x[1]), __uint_as_float(R.stats_x[2]), tau,
+                               __uint_as_float((unsigned)(best >> 32)));
   if (certified) {
     R.nnkey[q] = best;
     atomicAdd(R.ncertified, 1ULL);
@@ -455,10 +291,6 @@ __global__ void k_rerank_certify(RerankArgs R) {
 // --------------------------------------------------------------------------
 // host side
 // --------------------------------------------------------------------------
-
-static int fmt_of(int precision) {
-  return precision == 1 ? FMT_BF16 : (precision == 2 ? FMT_F16 : FMT_E4M3);
-}
 
 size_t tc_kb(int d, int precision) {
   const int esize = precision == 3 ? 1 : 2;
@@ -476,7 +308,7 @@ static int launch_tc_t(const TcArgs& P, dim3 grid, size_t smem, cudaStream_t st)
 }
 
 int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int precision, cudaStream_t st) {
-  const int fmt = fmt_of(precision);
+  const int fmt = fmt_of_precision(precision);
   const int kb = (int)tc_kb(B.d, precision);
   const int bn = tc_bn(kb);
   const int qtiles = (nt + TC_BM - 1) / TC_BM;
@@ -484,16 +316,16 @@ int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int preci
   // pack both sides
   if (cudaMemsetAsync(T.stats, 0, 8 * sizeof(unsigned), st) != cudaSuccess) return -1;
   {
-    const int64_t work = (int64_t)qtiles * TC_BM * (kb / 16);
+    const int64_t work = (int64_t)qtiles * TC_BM;
     int g = (int)std::min<int64_t>((work + 255) / 256, 152 * 16);
-    k_pack_tc<<<g, 256, 0, st>>>(B.y, B.ja[B.cur], nt, qtiles * TC_BM, B.d, kb, fmt, TC_BM, T.A, T.nrm_y, T.scale_y,
-                                 T.stats + 4);
+    k_pack_tc<<<g, 256, 0, st>>>(B.y, B.ja[B.cur], nt, qtiles * TC_BM, B.d, kb, fmt, TC_BM, T.A, T.nrm_y, nullptr,
+                                 T.scale_y, T.stats + 4);
   }
   {
-    const int64_t work = (int64_t)stiles * bn * (kb / 16);
+    const int64_t work = (int64_t)stiles * bn;
     int g = (int)std::min<int64_t>((work + 255) / 256, 152 * 16);
-    k_pack_tc<<<g, 256, 0, st>>>(B.x, B.ia[B.cur], mt, stiles * bn, B.d, kb, fmt, bn, T.B, T.nrm_x, T.scale_x,
-                                 T.stats);
+    k_pack_tc<<<g, 256, 0, st>>>(B.x, B.ia[B.cur], mt, stiles * bn, B.d, kb, fmt, bn, T.B, T.nrm_x, T.nrm_sx,
+                                 T.scale_x, T.stats);
   }
   // chunks of supplier tiles so that the grid covers the GPU
   int chunks = (152 + qtiles - 1) / qtiles;
@@ -506,22 +338,25 @@ int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int preci
   if (nstage > 4) nstage = 4;
   if (nstage < 1) return -2;
   const int nt_pad = qtiles * TC_BM;
-  TcArgs P{T.A, T.B, T.nrm_x, T.scale_x, T.scale_y, nt, mt, kb, bn, nstage, per, stiles, nt_pad,
-           T.cand_v, T.cand_p, &B.st->err};
+  TcArgs P{T.A,      T.B,      T.nrm_x,    T.nrm_sx, T.nrm_y,  T.scale_x,  T.scale_y, nt, mt,
+           kb,       bn,       nstage,     per,      stiles,   nt_pad,     T.cand_v,  T.cand_p, &B.st->err};
   const size_t smem = a_bytes + (size_t)nstage * b_bytes;
   dim3 grid(qtiles, chunks);
   int rc;
   if (T.ev0) cudaEventRecord(T.ev0, st);
-  if (fmt == FMT_BF16) rc = bn == 128 ? launch_tc_t<FMT_BF16, 128>(P, grid, smem, st) : launch_tc_t<FMT_BF16, 64>(P, grid, smem, st);
-  else if (fmt == FMT_F16) rc = bn == 128 ? launch_tc_t<FMT_F16, 128>(P, grid, smem, st) : launch_tc_t<FMT_F16, 64>(P, grid, smem, st);
-  else rc = bn == 128 ? launch_tc_t<FMT_E4M3, 128>(P, grid, smem, st) : launch_tc_t<FMT_E4M3, 64>(P, grid, smem, st);
+  if (fmt == FMT_BF16)
+    rc = bn == 128 ? launch_tc_t<FMT_BF16, 128>(P, grid, smem, st) : launch_tc_t<FMT_BF16, 64>(P, grid, smem, st);
+  else if (fmt == FMT_F16)
+    rc = bn == 128 ? launch_tc_t<FMT_F16, 128>(P, grid, smem, st) : launch_tc_t<FMT_F16, 64>(P, grid, smem, st);
+  else
+    rc = bn == 128 ? launch_tc_t<FMT_E4M3, 128>(P, grid, smem, st) : launch_tc_t<FMT_E4M3, 64>(P, grid, smem, st);
   if (rc) return rc;
   if (T.ev1) cudaEventRecord(T.ev1, st);
   // exact re-rank and certificate
   if (cudaMemsetAsync(T.nfallback, 0, sizeof(int), st) != cudaSuccess) return -1;
-  RerankArgs R{B.x,     B.y,       B.ia[B.cur], B.ja[B.cur], B.d,       nt,          nt_pad,
-               chunks,  B.metric,  fmt,         T.cand_v,    T.cand_p,  T.nrm_y,     T.scale_y,
-               T.stats, B.nnkey,   T.fallback,  T.nfallback, &B.st->certified, &B.st->fallbacks};
+  RerankArgs R{B.x,      B.y,        B.ia[B.cur], B.ja[B.cur], B.d,       nt,          nt_pad,
+               chunks,   fmt,        T.cand_v,    T.cand_p,    T.nrm_y,   T.scale_y,   T.stats,
+               B.nnkey,  T.fallback, T.nfallback, &B.st->certified, &B.st->fallbacks};
   k_rerank_certify<<<(nt + 7) / 8, 256, 0, st>>>(R);
   // FP32 scan of the consumers that were not certified
   launch_nns_f32(B, mt, nt, T.fallback, T.nfallback, st);

@@ -1,0 +1,234 @@
+// Shared pieces of the reduced-precision NNS (tcgen05, sm_103a): operand
+// packing, instruction and shared-memory descriptors, tensor-memory access,
+// the per-consumer top-K and the certificate of the exact re-rank.
+//
+// Operand layout ("K-major, no swizzle"): a tile of R rows and KB bytes per
+// row is stored as KB/16 column blocks of R rows x 16 bytes; block c holds
+// bytes [16c, 16c+16) of every row, rows 16 bytes apart.  Each 8-row x 16-byte
+// piece is one core matrix; neighbouring core matrices are 128 bytes apart
+// along M/N (stride byte offset) and R*16 bytes apart along K (leading byte
+// offset).  A packed tile is one contiguous block, so a 1-D bulk copy (TMA)
+// lands it in shared memory ready for the MMA descriptors.
+#pragma once
+
+#include <math_constants.h>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "common.cuh"
+
+namespace nnsemd {
+
+constexpr int TC_BM = 128;  // consumers per accumulator (MMA M)
+constexpr int TC_K = 16;    // candidates kept per consumer
+
+enum TcFmt : int { FMT_F16 = 0, FMT_BF16 = 1, FMT_E4M3 = 2 };
+
+__host__ __device__ inline int fmt_of_precision(int precision) {
+  return precision == 1 ? FMT_BF16 : (precision == 2 ? FMT_F16 : FMT_E4M3);
+}
+
+NNS_DEV uint16_t to_bits16(float v, int fmt) {
+  if (fmt == FMT_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+  return __half_as_ushort(__float2half_rn(v));
+}
+
+NNS_DEV uint8_t to_e4m3(float v) { return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3); }
+
+// Per-row scale (a power of two) for FP16 / FP8: the largest |v| of the row
+// maps into [2^7, 2^8).  BF16 has FP32's exponent range and uses 1.
+NNS_DEV float row_scale(const float* row, int d, int fmt) {
+  if (!row || fmt == FMT_BF16) return 1.f;
+  float mx = 0.f;
+  for (int k = 0; k < d; ++k) mx = fmaxf(mx, fabsf(row[k]));
+  if (!(mx > 0.f)) return 1.f;
+  int e;
+  frexpf(mx, &e);  // mx in [2^(e-1), 2^e)
+  return ldexpf(1.f, e - 8);
+}
+
+// Pack 16 bytes (block c) of one row into out (row r of tile t).  row == null
+// writes zeros (padding).
+NNS_DEV void pack_block(const float* row, int d, int c, float s, int fmt, uint8_t* tile_base, int tile_rows, int r) {
+  alignas(16) uint8_t bytes[16];
+  if (fmt == FMT_E4M3) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const int k = c * 16 + e;
+      bytes[e] = to_e4m3((row && k < d) ? row[k] / s : 0.f);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int k = c * 8 + e;
+      const uint16_t b = to_bits16((row && k < d) ? row[k] / s : 0.f, fmt);
+      bytes[2 * e] = (uint8_t)(b & 0xff);
+      bytes[2 * e + 1] = (uint8_t)(b >> 8);
+    }
+  }
+  *reinterpret_cast<uint4*>(tile_base + (size_t)c * tile_rows * 16 + (size_t)r * 16) =
+      *reinterpret_cast<const uint4*>(bytes);
+}
+
+// FP32 squared norm (sequential fma) and L1 norm of a row.
+NNS_DEV void row_norms(const float* row, int d, float& l2sq, float& l1) {
+  float acc = 0.f, a1 = 0.f;
+  for (int k = 0; k < d; ++k) {
+    acc = __fmaf_rn(row[k], row[k], acc);
+    a1 = __fadd_rn(a1, fabsf(row[k]));
+  }
+  l2sq = acc;
+  l1 = a1;
+}
+
+// --------------------------------------------------------------------------
+// tcgen05 helpers
+// --------------------------------------------------------------------------
+
+NNS_DEV uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  // base offset 0, relative LBO, swizzle mode 0 (none)
+  return d;
+}
+
+// Instruction descriptor: D = F32, A and B of type `ab` (kind::f16: 0 = F16,
+// 1 = BF16; kind::f8f6f4: 0 = E4M3), both K-major, N = n, M = m.
+NNS_DEV uint32_t make_idesc(int ab, int m, int n) {
+  return (1u << 4) | ((uint32_t)ab << 7) | ((uint32_t)ab << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+template <int FMT>
+NNS_DEV void mma_issue(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accumulate) {
+  if (FMT == FMT_E4M3) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  }
+}
+
+NNS_DEV void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+NNS_DEV void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+NNS_DEV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+NNS_DEV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+NNS_DEV void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+NNS_DEV void tmem_dealloc(uint32_t base, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(ncols) : "memory");
+}
+
+NNS_DEV void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Make this thread's generic-proxy global writes visible to later bulk
+// copies (async proxy) issued after a barrier.
+NNS_DEV void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// Insert (v, p) into an ascending top-K list kept in registers; equal values
+// keep their arrival order.
+template <int K>
+NNS_DEV void topk_insert(float (&tv)[K], int (&tp)[K], float v, int p) {
+  if (!(v < tv[K - 1])) return;
+  float nv = v;
+  int np = p;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (nv < tv[k]) {
+      const float fv = tv[k];
+      const int fp = tp[k];
+      tv[k] = nv;
+      tp[k] = np;
+      nv = fv;
+      np = fp;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// the certificate
+//
+// The epilogue ranks suppliers by a lower bound of the approximate distance:
+//   v'_ij = |x_i|^2 - 2 s_i s_j <x^_i, y^_j> - c_j |x_i|,
+//   c_j   = 2 (2u + u^2) |y_j|,
+// where the subtracted term bounds the quantisation error of the dot product
+// for this very pair (|<x~,y~> - <x,y>| <= (2u + u^2) |x| |y| by
+// Cauchy-Schwarz; it enters twice).  Every supplier outside the K candidates
+// has v' >= tau (the K-th smallest).  Its true squared distance d2 (of the
+// float inputs) is therefore >= ny + tau - E, with E bounding what remains:
+//   gamma (ny + rx^2)                         FP32 norms (sequential fma)
+//   2 (eta terms)                             absolute rounding floor of the
+//                                             operand format (subnormals,
+//                                             times the row scale)
+//   2 d 2^-22 |x~| |y~|                       tensor-core accumulation
+//   2 u32 (rx^2 + 2 |x~||y~| + c rx)          the epilogue's FP32 roundings
+// (u = the operand format's unit roundoff, u32 = 2^-24, rx = max |x_i|,
+// rx1 = max |x_i|_1 over the active suppliers).  Its FP32 key is >= d2 (1 -
+// gamma) (gamma bounds the relative rounding of the sequential FP32 key), so
+// the best exact candidate key is certified when strictly below
+// (ny + tau - E)(1 - gamma).
+// --------------------------------------------------------------------------
+
+NNS_DEV double quant_unit(int fmt) { return fmt == FMT_BF16 ? 0x1p-8 : (fmt == FMT_F16 ? 0x1p-11 : 0x1p-4); }
+
+// c_j of the epilogue, from the consumer's FP32 squared norm (rounded up).
+NNS_DEV float quant_coeff(int fmt, float ny) {
+  const double uq = quant_unit(fmt);
+  return (float)(2.0 * (2.0 * uq + uq * uq) * sqrt((double)ny) * (1.0 + 1e-4));
+}
+
+// |x| rounded up, from the FP32 squared norm (sequential fma, relative error
+// below 2e-5 for d <= 300 and far below 1e-4 for any d the kernels serve).
+NNS_DEV float norm_up(float l2sq) { return sqrtf(l2sq) * (1.f + 1e-4f); }
+
+NNS_DEV bool certify(int fmt, int d, double ny, double yl2, double yl1, double sy, double rx, double rx1, double sxm,
+                     float tau, float best_key) {
+  if (!(tau < CUDART_INF_F)) return true;  // every supplier of every chunk was a candidate
+  const double u32 = 0x1p-24;
+  const double uq = quant_unit(fmt);
+  const double gam = d * u32 / (1.0 - d * u32);
+  const double eta_unit = fmt == FMT_BF16 ? 0x1p-134 : (fmt == FMT_F16 ? 0x1p-25 : 0x1p-10);
+  const double eta_x = eta_unit * (fmt == FMT_BF16 ? 1.0 : sxm);
+  const double eta_y = eta_unit * (fmt == FMT_BF16 ? 1.0 : sy);
+  const double dot_eta = eta_x * (yl1 + eta_y * d) + eta_y * rx1 + eta_x * uq * yl1 + eta_y * uq * rx1;
+  const double xt = (1 + uq) * rx + eta_x * sqrt((double)d), yt = (1 + uq) * yl2 + eta_y * sqrt((double)d);
+  const double dot_acc = d * 0x1p-22 * xt * yt;
+  const double c = 2.0 * (2.0 * uq + uq * uq) * yl2 * (1.0 + 1e-5);
+  const double E = gam * (ny + rx * rx) + 2.0 * (dot_eta + dot_acc) +
+                   2.0 * u32 * (rx * rx + 2.0 * xt * yt + c * rx) + 1e-30;
+  const double floor_true = (ny + (double)tau - E) * (1.0 - gam) * (1.0 - 0x1p-30);
+  return (double)best_key < floor_true;
+}
+
+}  // namespace nnsemd

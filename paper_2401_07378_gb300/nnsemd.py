@@ -28,6 +28,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NONFINITE", 3: "ZERO_MASS", 4: "CUDA", 
 METRIC = {"l2": 0, "sql2": 1, "l1": 2}
 PRECISION = {"fp32": 0, "bf16": 1, "fp16": 2, "fp8": 3}
 FLAG_TIME_KERNELS = 1
+FLAG_AUTOTUNE = 2
+FLAG_GRAPH = 4
 
 
 class nnsemd_config(ctypes.Structure):
@@ -202,7 +204,7 @@ class Context:
 
     # -- nnsemd_solve_batched ------------------------------------------------
     def solve_batched(self, x, a, x_off, y, b, y_off, metric: str = "l2", precision: str = "fp32",
-                      rerank_k: int = 0, costs=None, stats: bool = True):
+                      rerank_k: int = 0, costs=None, stats: bool = True, flags: int = 0):
         """Packed device tensors plus host offset arrays (np.int64, P+1).
         Returns the device tensor of P costs (and the stats dict)."""
         import torch
@@ -213,7 +215,7 @@ class Context:
         if costs is None:
             costs = torch.empty(P, dtype=torch.float64, device=x.device)
         self._bind_current_stream()
-        opt = _options(metric, precision, rerank_k)
+        opt = _options(metric, precision, rerank_k, flags)
         st = nnsemd_stats()
         rc = _lib.nnsemd_solve_batched(self._h, P, _ptr(x), _ptr(a), x_off.ctypes.data, _ptr(y), _ptr(b),
                                        y_off.ctypes.data, d, ctypes.byref(opt), _ptr(costs),

@@ -193,19 +193,30 @@ def doc_knn(num_docs: int = 4096, seed: int = 0, vocab_size: int = 50000, d: int
 def retrieval(num_pairs: int = 10000, seed: int = 0, d: int = 128, lo: int = 256, hi: int = 2048) -> Batch:
     """Signature pairs of SIFT-like descriptors: m, n ~ Uniform{lo..hi}
     independently; descriptors |N(0,1)| then L2-normalised and scaled by 512;
-    weights Dirichlet(1) (normalised Exp(1) draws)."""
+    weights Dirichlet(1) (normalised Exp(1) draws).  All sizes are drawn
+    first, then all descriptors (vectorised: the full 10,000-pair batch holds
+    about 23 million descriptors)."""
     rng = np.random.default_rng(seed)
-    pairs = []
-    for _ in range(num_pairs):
-        m = int(rng.integers(lo, hi + 1))
-        n = int(rng.integers(lo, hi + 1))
-        sig = []
-        for k in (m, n):
-            v = np.abs(rng.standard_normal((k, d)))
-            v = v / np.linalg.norm(v, axis=1, keepdims=True) * 512.0
-            sig.append(v.astype(np.float32))
-        pairs.append(Pair(sig[0], rng.exponential(1.0, m), sig[1], rng.exponential(1.0, n)))
-    return Batch.pack(pairs)
+    m = rng.integers(lo, hi + 1, num_pairs)
+    n = rng.integers(lo, hi + 1, num_pairs)
+    x_off = np.concatenate([[0], np.cumsum(m)]).astype(np.int64)
+    y_off = np.concatenate([[0], np.cumsum(n)]).astype(np.int64)
+
+    def descriptors(count: int) -> np.ndarray:
+        out = np.empty((count, d), np.float32)
+        step = 1 << 20
+        for s in range(0, count, step):
+            v = np.abs(rng.standard_normal((min(step, count - s), d), dtype=np.float32))
+            v /= np.linalg.norm(v, axis=1, keepdims=True)
+            v *= np.float32(512.0)
+            out[s:s + v.shape[0]] = v
+        return out
+
+    x = descriptors(int(x_off[-1]))
+    y = descriptors(int(y_off[-1]))
+    a = rng.exponential(1.0, int(x_off[-1]))
+    b = rng.exponential(1.0, int(y_off[-1]))
+    return Batch(x, a, x_off, y, b, y_off)
 
 
 def random_batch(num_pairs: int, seed: int, d: int, lo: int, hi: int, weights: str = "dirichlet") -> Batch:
