@@ -168,6 +168,59 @@ int nnsemd_solve_batched(nnsemd_ctx *ctx, int32_t num_pairs,
                          int32_t d, const nnsemd_options *opt,
                          double *costs_out, nnsemd_stats *stats);
 
+/* ---- the NNS operation alone --------------------------------------------
+ * Round one of Alg. 1 (Sec. III-A, NNS step): for every consumer j, the
+ * nearest supplier nn_out[j] (device int32 [n]), ties to the lowest index,
+ * decided on the FP32 key of this header's conventions.  x [m][d], y [n][d]
+ * device.  Used to build the training traces of the learned proposal. */
+int nnsemd_nearest(nnsemd_ctx *ctx, const float *x, int64_t m, const float *y, int64_t n,
+                   int32_t d, int32_t metric, int32_t *nn_out);
+
+/* ---- learned candidate proposal ------------------------------------------
+ * Not in the paper.  A fixed codebook of `cells` centroids (k-means) and an
+ * MLP d -> hidden -> hidden -> cells (ReLU) that scores the cells most likely
+ * to hold a consumer's nearest supplier.  Passed as nnsemd_options.proposal
+ * to nnsemd_solve or nnsemd_solve_host (d > 8, metric L2 or SQL2, FP32
+ * precision), it replaces the full NNS scan
+ * of every round by an exact FP32 scan of the suppliers in each consumer's
+ * first 32 proposed non-empty cells, certified by a triangle-inequality
+ * bound on every other non-empty cell; consumers that cannot be certified
+ * are scanned in full.  Results equal the FP32 path's; stats report
+ * certified and fallback counts.  Training runs on the GPU (Adam over
+ * minibatches of the softmax cross-entropy, the label being the cell of the
+ * consumer's nearest supplier).  All pointers are device pointers unless
+ * stated.  Errors: INVALID_ARG, OOM, CUDA. */
+typedef struct nnsemd_proposal nnsemd_proposal;
+
+/* New proposal with seeded He-uniform weights (cells >= 64). */
+int nnsemd_proposal_create(nnsemd_ctx *ctx, int32_t d, int32_t cells, int32_t hidden, uint64_t seed,
+                           nnsemd_proposal **out);
+int nnsemd_proposal_destroy(nnsemd_proposal *p);
+/* k-means (seeded picks, `iters` Lloyd steps) of pts [N][d] into the
+ * codebook; also sets the network's input standardisation from pts. */
+int nnsemd_proposal_fit(nnsemd_ctx *ctx, nnsemd_proposal *p, const float *pts, int64_t N, int32_t iters,
+                        uint64_t seed);
+/* Train on N consumer points y [N][d] whose nearest suppliers are x_nn
+ * [N][d]; `epochs` passes of shuffled minibatches of `batch`, Adam with
+ * learning rate lr.  *loss_out (host, nullable): mean loss of the last epoch. */
+int nnsemd_proposal_train(nnsemd_ctx *ctx, nnsemd_proposal *p, const float *y, const float *x_nn, int64_t N,
+                          int32_t epochs, int32_t batch, float lr, uint64_t seed, double *loss_out);
+/* Mean softmax cross-entropy of N samples (y [N][d], labels [N] cell ids)
+ * into *loss_out (host) and its gradient with respect to every parameter
+ * into grad_out (device float [nparams], the layout of nnsemd_proposal_params). */
+int nnsemd_proposal_loss_grad(nnsemd_ctx *ctx, const nnsemd_proposal *p, const float *y, const int32_t *labels,
+                              int64_t N, double *loss_out, float *grad_out);
+/* Shape of a proposal (host outputs, each nullable). */
+int nnsemd_proposal_info(const nnsemd_proposal *p, int32_t *d, int32_t *cells, int32_t *hidden, int64_t *nparams);
+/* Copy the parameters to (set = 0) or from (set = 1) the HOST buffer, laid
+ * out as W1 [hidden][d], b1 [hidden], W2 [hidden][hidden], b2 [hidden],
+ * W3 [cells][hidden], b3 [cells]. */
+int nnsemd_proposal_params(nnsemd_ctx *ctx, nnsemd_proposal *p, float *host, int32_t set);
+/* Checkpoint: a flat binary file (header, centroids, standardisation,
+ * parameters). */
+int nnsemd_proposal_save(nnsemd_ctx *ctx, const nnsemd_proposal *p, const char *path);
+int nnsemd_proposal_load(nnsemd_ctx *ctx, const char *path, nnsemd_proposal **out);
+
 /* Solve one small pair without allocating any memory.  The paper has no
  * counterpart: this exists for callers that cannot call cudaMalloc (a plugin
  * running inside another framework's launch callback, a process whose device

@@ -22,32 +22,12 @@
 #include <tuple>
 #include <vector>
 
+#include "ctx.h"
 #include "kernels.h"
 #include "nnsemd.h"
+#include "proposal.h"
 
 using namespace nnsemd;
-
-// A captured batched launch (NNSEMD_FLAG_GRAPH), valid while every pointer
-// and size in the key repeats.
-struct BatchGraph {
-  std::vector<uintptr_t> key;
-  cudaGraphExec_t exec = nullptr;
-};
-
-struct nnsemd_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  void* ws = nullptr;
-  size_t ws_bytes = 0;
-  DevState* hstate = nullptr;  // pinned mirror of the device state
-  std::string err;
-  long long launches = 0;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // kernel timing (NNSEMD_FLAG_TIME_KERNELS)
-  // autotuner: (d, precision, cap) -> (bn, stages) of the batched tensor-core kernel
-  std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;
-  std::vector<BatchGraph> graphs;
-  cudaStream_t capture_stream = nullptr;
-};
 
 namespace {
 
@@ -66,6 +46,21 @@ int fail(nnsemd_ctx* ctx, int status, const char* fmt, ...) {
   else g_create_err = buf;
   return status;
 }
+
+}  // namespace
+
+int nnsemd::ctx_fail(nnsemd_ctx* ctx, int status, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  else g_create_err = buf;
+  return status;
+}
+
+namespace {
 
 int cuda_fail(nnsemd_ctx* ctx, cudaError_t e, const char* where) {
   return fail(ctx, NNSEMD_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
@@ -112,10 +107,30 @@ int ensure_ws(nnsemd_ctx* ctx, size_t bytes) {
 
 // Lay out the buffers of a single-pair solve; with base == nullptr only the
 // size is computed.
-size_t layout_solve(void* base, int64_t m, int64_t n, int d, SolveBufs& B, int precision = 0) {
+size_t layout_solve(void* base, int64_t m, int64_t n, int d, SolveBufs& B, int precision = 0,
+                    const nnsemd_proposal* P = nullptr, LearnedBufs* L = nullptr) {
   Carve C(base);
   const int dp = d <= 8 ? padded_dim(d) : 0;
   B.precision = precision;
+  if (P && L) {
+    const int K = P->cells, h = P->hidden;
+    L->P = P;
+    L->chunk = 4096;
+    L->cell_of_x = C.take<int>(m);
+    L->radius = C.take<float>(K);
+    L->prop_cells = C.take<int>((size_t)n * PROP_LIST);
+    L->bound_cells = C.take<int>((size_t)n * PROP_LIST);
+    L->bound_vals = C.take<float>((size_t)n * PROP_LIST);
+    L->cell_cnt = C.take<int>(K + 1);
+    L->cell_off = C.take<int>(K + 1);
+    L->cell_fill = C.take<int>(K);
+    L->cell_members = C.take<int>(m);
+    L->fallback = C.take<int>(n);
+    L->nfallback = C.take<int>(1);
+    L->tmp = C.take<float>((size_t)2 * L->chunk * h);
+    L->tmp2 = C.take<float>((size_t)L->chunk * K);
+    L->tmp3 = C.take<float>((size_t)L->chunk * d);
+  }
   if (precision != NNSEMD_FP32) {
     const size_t kb = tc_kb(d, precision);
     const int64_t bn = tc_bn(kb);
@@ -197,7 +212,7 @@ int packed_dim(int d) { return d <= 8 ? padded_dim(d) : 0; }
 // The device part of a single-pair solve on buffers that are already laid
 // out; writes R to *cost and fills the counters.
 int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, double* cost, int64_t* nnz,
-              nnsemd_stats* stats, int flags = 0) {
+              nnsemd_stats* stats, int flags = 0, const LearnedBufs* learned = nullptr) {
   cudaStream_t st = ctx->stream;
   long long L = 0;
   const bool timed = (flags & NNSEMD_FLAG_TIME_KERNELS) != 0;
@@ -254,6 +269,11 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
   long long rounds = 0, pair_evals = 0;
   const long long round_limit = B.m + B.n;
   const bool lowd = B.dp > 0;
+  if (learned) {
+    // once per solve: supplier cells and radii, consumer proposals and bounds
+    if (learned_prepare(*learned, B.x, B.m, B.y, B.n, B.d, st)) return fail(ctx, NNSEMD_ERR_CUDA, "proposal preparation");
+    L += 8 + 8 * ((B.n + learned->chunk - 1) / learned->chunk);
+  }
   while (mt > 0 && nt > 0) {
     const bool tail = lowd ? (mt <= FIN_MAX && nt <= FIN_MAX && (int64_t)mt * nt <= FIN_PAIRS)
                            : (mt <= FIN_MAX_HD && nt <= FIN_MAX_HD && (int64_t)mt * nt * B.d <= FIN_HD_WORK);
@@ -269,7 +289,12 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
     if (rounds >= round_limit) return fail(ctx, NNSEMD_ERR_ITER_LIMIT, "round limit m + n exceeded");
     CK(cudaMemsetAsync(B.nnkey, 0xff, (size_t)nt * sizeof(unsigned long long), st));
     int nrc;
-    if (B.precision != NNSEMD_FP32) {
+    if (learned) {
+      if (timed) CK(cudaEventRecord(ctx->ev[0], st));
+      nrc = launch_nns_learned(B, *learned, mt, nt, st);
+      if (timed) CK(cudaEventRecord(ctx->ev[1], st));
+      L += 6;
+    } else if (B.precision != NNSEMD_FP32) {
       // tensor-core candidates + exact re-rank + certificate + FP32 rescan;
       // the timing events bracket the tensor-core kernel alone
       B.tc.ev0 = timed ? ctx->ev[0] : nullptr;
@@ -340,6 +365,18 @@ int check_sizes(nnsemd_ctx* ctx, int64_t m, int64_t n) {
   return NNSEMD_OK;
 }
 
+// A learned proposal replaces the full NNS scan only where its candidate
+// search applies: d > 8, L2 or SQL2, FP32 decisions, the proposal's own d.
+int check_proposal(nnsemd_ctx* ctx, const nnsemd_options* opt, int d, int metric, int precision,
+                   const nnsemd_proposal** out) {
+  const nnsemd_proposal* P = opt ? static_cast<const nnsemd_proposal*>(opt->proposal) : nullptr;
+  *out = P;
+  if (P && (d <= 8 || metric == NNSEMD_L1 || precision != NNSEMD_FP32 || P->d != d || !P->codebook_ready))
+    return fail(ctx, NNSEMD_ERR_UNSUPPORTED,
+                "a proposal needs d > 8, metric L2 or SQL2, FP32 precision, its own d and a fitted codebook");
+  return NNSEMD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -406,11 +443,14 @@ int nnsemd_solve(nnsemd_ctx* ctx, const float* x, const double* a, int64_t m, co
     return fail(ctx, NNSEMD_ERR_INVALID_ARG, "misaligned input pointer");
   if (plan && (!plan->i || !plan->j || !plan->f || plan->capacity < 0))
     return fail(ctx, NNSEMD_ERR_INVALID_ARG, "plan arrays");
+  const nnsemd_proposal* P = nullptr;
+  if ((rc = check_proposal(ctx, opt, d, metric, precision, &P))) return rc;
   CK(cudaSetDevice(ctx->device));
   SolveBufs B{};
-  size_t bytes = layout_solve(nullptr, m, n, d, B, precision);
+  LearnedBufs Lb{};
+  size_t bytes = layout_solve(nullptr, m, n, d, B, precision, P, P ? &Lb : nullptr);
   if ((rc = ensure_ws(ctx, bytes))) return rc;
-  layout_solve(ctx->ws, m, n, d, B, precision);
+  layout_solve(ctx->ws, m, n, d, B, precision, P, P ? &Lb : nullptr);
   B.x = x;
   B.y = y;
   B.m = m;
@@ -423,7 +463,7 @@ int nnsemd_solve(nnsemd_ctx* ctx, const float* x, const double* a, int64_t m, co
   B.plan_f = plan ? plan->f : nullptr;
   B.plan_cap = plan ? plan->capacity : 0;
   int64_t nnz = 0;
-  rc = run_solve(ctx, B, a, b, cost_out, &nnz, stats, opt ? opt->flags : 0);
+  rc = run_solve(ctx, B, a, b, cost_out, &nnz, stats, opt ? opt->flags : 0, P ? &Lb : nullptr);
   if (plan) plan->nnz = rc ? 0 : nnz;
   return rc;
 }
@@ -440,10 +480,13 @@ int nnsemd_solve_host(nnsemd_ctx* ctx, const float* x, const double* a, int64_t 
   if (!x || !a || !y || !b || !cost_out) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "null pointer argument");
   if (plan && (!plan->i || !plan->j || !plan->f || plan->capacity < 0))
     return fail(ctx, NNSEMD_ERR_INVALID_ARG, "plan arrays");
+  const nnsemd_proposal* P = nullptr;
+  if ((rc = check_proposal(ctx, opt, d, metric, precision, &P))) return rc;
   CK(cudaSetDevice(ctx->device));
   // device staging for the inputs and the plan, placed after the solve buffers
   SolveBufs B{};
-  size_t solve_bytes = layout_solve(nullptr, m, n, d, B, precision);
+  LearnedBufs Lb{};
+  size_t solve_bytes = layout_solve(nullptr, m, n, d, B, precision, P, P ? &Lb : nullptr);
   const int64_t cap = plan ? std::min<int64_t>(plan->capacity, m + n) : 0;
   auto stage_layout = [&](void* base, float** xd, double** ad, float** yd, double** bd, int32_t** pi, int32_t** pj,
                           double** pf) {
@@ -463,7 +506,7 @@ int nnsemd_solve_host(nnsemd_ctx* ctx, const float* x, const double* a, int64_t 
   int32_t *pi, *pj;
   size_t bytes = stage_layout(nullptr, &xd, &ad, &yd, &bd, &pi, &pj, &pf);
   if ((rc = ensure_ws(ctx, bytes))) return rc;
-  layout_solve(ctx->ws, m, n, d, B, precision);
+  layout_solve(ctx->ws, m, n, d, B, precision, P, P ? &Lb : nullptr);
   stage_layout(ctx->ws, &xd, &ad, &yd, &bd, &pi, &pj, &pf);
   cudaStream_t st = ctx->stream;
   CK(cudaMemcpyAsync(xd, x, (size_t)m * d * sizeof(float), cudaMemcpyHostToDevice, st));
@@ -482,7 +525,7 @@ int nnsemd_solve_host(nnsemd_ctx* ctx, const float* x, const double* a, int64_t 
   B.plan_f = plan ? pf : nullptr;
   B.plan_cap = cap;
   int64_t nnz = 0;
-  rc = run_solve(ctx, B, ad, bd, cost_out, &nnz, stats, opt ? opt->flags : 0);
+  rc = run_solve(ctx, B, ad, bd, cost_out, &nnz, stats, opt ? opt->flags : 0, P ? &Lb : nullptr);
   if (rc) {
     if (plan) plan->nnz = 0;
     return rc;
@@ -516,6 +559,7 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
   if (!x_packed || !a_packed || !x_off || !y_packed || !b_packed || !y_off || !costs_out)
     return fail(ctx, NNSEMD_ERR_INVALID_ARG, "null pointer argument");
   if (x_off[0] != 0 || y_off[0] != 0) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "offsets must start at 0");
+  if (opt && opt->proposal) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "proposals serve nnsemd_solve only");
   std::vector<int> small, large;
   int64_t small_max = 0;
   for (int p = 0; p < num_pairs; ++p) {

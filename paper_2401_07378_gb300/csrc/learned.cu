@@ -1,0 +1,663 @@
+// The learned candidate proposal (not in the paper; see proposal.h).
+//
+// Training and inference of the proposal network run in the kernels below:
+// a tiled FP32 GEMM with fused bias / ReLU / ReLU-mask epilogues for the
+// forward and backward passes of a 3-layer MLP, a row-wise softmax
+// cross-entropy, column sums for the bias gradients and an Adam step.  The
+// codebook is fitted by Lloyd's k-means (assignment = a nearest-centroid
+// search with the same tiled FP32 distance routine as the NNS operation).
+//
+// Per solve the network's scores give each consumer its 64 best cells, and a
+// pass over the centroids gives it the 64 cells with the smallest lower
+// bound max(0, |y - mu_c| - r_c)^2 on the squared distance to any supplier
+// of the cell (r_c = the largest |x - mu_c| over the instance's suppliers in
+// c; the triangle inequality makes it a bound).  Per round every active
+// consumer scans, with the exact FP32 key, the active suppliers of its first
+// 32 proposed cells that still hold any; the best key is certified when it
+// is strictly below the bound of every other cell that still holds an active
+// supplier (scaled by the key's own rounding bound), so no supplier outside
+// the candidates can win or tie.  Uncertified consumers are scanned in full.
+#include <math_constants.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "cta.cuh"
+#include "kernels.h"
+#include "proposal.h"
+
+namespace nnsemd {
+
+// --------------------------------------------------------------------------
+// tiled FP32 GEMM: C[M][N] = sum_k A(m,k) B(k,n), with
+//   A(m,k) = TA ? A[k*lda + m] : A[m*lda + k]
+//   B(k,n) = TB ? B[n*ldb + k] : B[k*ldb + n]
+// and an epilogue: none, +bias[n], relu(+bias[n]), or * (mask[m][n] > 0).
+// --------------------------------------------------------------------------
+
+enum Epi : int { EPI_NONE = 0, EPI_BIAS = 1, EPI_BIAS_RELU = 2, EPI_MASK = 3 };
+
+constexpr int GM = 64, GN = 64, GK = 16, GT = 256;
+
+template <bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(GT) k_gemm(const float* __restrict__ A, int lda, const float* __restrict__ B,
+                                             int ldb, float* __restrict__ C, int ldc, int M, int N, int K,
+                                             const float* __restrict__ aux) {
+  __shared__ float As[GK][GM + 4];
+  __shared__ float Bs[GK][GN + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += GK) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int idx = tid + i * GT;
+      int mm, kk;
+      if (TA) { kk = idx / GM; mm = idx % GM; } else { mm = idx / GK; kk = idx % GK; }
+      const int m = m0 + mm, k = k0 + kk;
+      As[kk][mm] = (m < M && k < K) ? (TA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k]) : 0.f;
+      int nn, kb;
+      if (TB) { nn = idx / GK; kb = idx % GK; } else { kb = idx / GN; nn = idx % GN; }
+      const int n = n0 + nn, k2 = k0 + kb;
+      Bs[kb][nn] = (n < N && k2 < K) ? (TB ? B[(size_t)n * ldb + k2] : B[(size_t)k2 * ldb + n]) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty * 4 + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx * 4 + j;
+      if (n >= N) continue;
+      float v = acc[i][j];
+      if (EPI == EPI_BIAS) v += aux[n];
+      if (EPI == EPI_BIAS_RELU) v = fmaxf(v + aux[n], 0.f);
+      if (EPI == EPI_MASK) v = aux[(size_t)m * ldc + n] > 0.f ? v : 0.f;
+      C[(size_t)m * ldc + n] = v;
+    }
+  }
+}
+
+template <bool TA, bool TB, int EPI>
+static void gemm(const float* A, int lda, const float* B, int ldb, float* C, int ldc, int M, int N, int K,
+                 const float* aux, cudaStream_t st) {
+  dim3 grid((N + GN - 1) / GN, (M + GM - 1) / GM);
+  k_gemm<TA, TB, EPI><<<grid, GT, 0, st>>>(A, lda, B, ldb, C, ldc, M, N, K, aux);
+}
+
+// standardise rows: out = (x - mean) * scale
+__global__ void k_standardise(const float* __restrict__ x, int rows, int d, const float* __restrict__ mean,
+                              const float* __restrict__ scale, float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)rows * d;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i % d);
+    out[i] = (x[i] - mean[k]) * scale[k];
+  }
+}
+
+int mlp_forward(const nnsemd_proposal* P, const float* Xs, int rows, float* H1, float* H2, float* Z, cudaStream_t st) {
+  const float* p = P->params;
+  const int d = P->d, h = P->hidden, c = P->cells;
+  gemm<false, true, EPI_BIAS_RELU>(Xs, d, p + P->off_W1(), d, H1, h, rows, h, d, p + P->off_b1(), st);
+  gemm<false, true, EPI_BIAS_RELU>(H1, h, p + P->off_W2(), h, H2, h, rows, h, h, p + P->off_b2(), st);
+  gemm<false, true, EPI_BIAS>(H2, h, p + P->off_W3(), h, Z, c, rows, c, h, p + P->off_b3(), st);
+  return 0;
+}
+
+// Softmax cross-entropy per row; dZ = (softmax - onehot) / rows; the mean
+// loss is added to *loss.
+__global__ void k_softmax_xent(const float* __restrict__ Z, const int* __restrict__ labels, int rows, int cols,
+                               float* __restrict__ dZ, double* loss) {
+  __shared__ float red[32];
+  const int r = blockIdx.x;
+  const float* z = Z + (size_t)r * cols;
+  float mx = -CUDART_INF_F;
+  for (int c = threadIdx.x; c < cols; c += blockDim.x) mx = fmaxf(mx, z[c]);
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  mx = red[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
+  __syncthreads();
+  float s = 0.f;
+  for (int c = threadIdx.x; c < cols; c += blockDim.x) s += expf(z[c] - mx);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  float sum = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+  const int lab = labels[r];
+  const float zl = z[lab];  // read before dZ (which may alias Z) is written
+  __syncthreads();
+  const float inv = 1.f / (float)rows;
+  for (int c = threadIdx.x; c < cols; c += blockDim.x)
+    dZ[(size_t)r * cols + c] = (expf(z[c] - mx) / sum - (c == lab ? 1.f : 0.f)) * inv;
+  if (threadIdx.x == 0) atomicAdd(loss, ((double)logf(sum) + mx - zl) / rows);
+}
+
+// out[c] = sum over rows of M[row][c]
+__global__ void k_colsum(const float* __restrict__ M, int rows, int cols, float* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  float s = 0.f;
+  for (int r = 0; r < rows; ++r) s += M[(size_t)r * cols + c];
+  out[c] = s;
+}
+
+int mlp_loss_grad(const nnsemd_proposal* P, const float* Xs, const int* labels, int rows, float* H1, float* H2,
+                  float* Z, float* dbuf1, float* dbuf2, float* grad, double* loss_dev, cudaStream_t st) {
+  const float* p = P->params;
+  const int d = P->d, h = P->hidden, c = P->cells;
+  mlp_forward(P, Xs, rows, H1, H2, Z, st);
+  // dZ in place of Z
+  k_softmax_xent<<<rows, 256, 0, st>>>(Z, labels, rows, c, Z, loss_dev);
+  float* g = grad;
+  // layer 3: dW3 = dZ^T H2, db3 = colsum dZ, dH2 = (dZ W3) masked by H2
+  gemm<true, false, EPI_NONE>(Z, c, H2, h, g + P->off_W3(), h, c, h, rows, nullptr, st);
+  k_colsum<<<(c + 255) / 256, 256, 0, st>>>(Z, rows, c, g + P->off_b3());
+  gemm<false, false, EPI_MASK>(Z, c, p + P->off_W3(), h, dbuf2, h, rows, h, c, H2, st);
+  // layer 2
+  gemm<true, false, EPI_NONE>(dbuf2, h, H1, h, g + P->off_W2(), h, h, h, rows, nullptr, st);
+  k_colsum<<<(h + 255) / 256, 256, 0, st>>>(dbuf2, rows, h, g + P->off_b2());
+  gemm<false, false, EPI_MASK>(dbuf2, h, p + P->off_W2(), h, dbuf1, h, rows, h, h, H1, st);
+  // layer 1
+  gemm<true, false, EPI_NONE>(dbuf1, h, Xs, d, g + P->off_W1(), d, h, d, rows, nullptr, st);
+  k_colsum<<<(h + 255) / 256, 256, 0, st>>>(dbuf1, rows, h, g + P->off_b1());
+  return 0;
+}
+
+__global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ g, long long n, float lr, float b1, float b2, float c1, float c2,
+                       float eps) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+void adam_update(nnsemd_proposal* P, const float* grad, float lr, cudaStream_t st) {
+  P->adam_step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)P->adam_step), c2 = 1.f - powf(b2, (float)P->adam_step);
+  k_adam<<<152 * 8, 256, 0, st>>>(P->params, P->adam_m, P->adam_v, grad, P->nparams, lr, b1, b2, c1, c2, 1e-8f);
+}
+
+// --------------------------------------------------------------------------
+// nearest neighbour over a whole set (k-means assignment, round one of
+// Alg. 1 for training traces)
+// --------------------------------------------------------------------------
+
+template <bool L1>
+__global__ void __launch_bounds__(TG_THREADS)
+    k_nearest(const float* __restrict__ x, const int* __restrict__ iota, int m, int chunk,
+              const float* __restrict__ y, int n, int d, unsigned long long* __restrict__ keys) {
+  __shared__ TileSmem T;
+  const int c0 = blockIdx.x * TG_M;
+  const int p0 = blockIdx.y * chunk;
+  const int p1 = min(p0 + chunk, m);
+  if (c0 >= n || p0 >= p1) return;
+  unsigned long long out[4];
+  group_nns_tile<L1>(x, iota, p0, p1, y, iota, nullptr, c0, min(TG_M, n - c0), d, T, threadIdx.x, 0, out);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  if (tx == 0)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int q = c0 + ty * 4 + i;
+      if (q < n) atomicMin(keys + q, out[i]);
+    }
+}
+
+__global__ void k_iota(int* v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = (int)i;
+}
+
+__global__ void k_keys_to_index(const unsigned long long* keys, int64_t n, int* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int)(keys[i] & 0xffffffffULL);
+}
+
+// `iota_m` must hold 0..max(m, n)-1.
+int nearest_all(const float* x, int64_t m, const float* y, int64_t n, int d, int metric, int* iota_m,
+                unsigned long long* keys, int* out, cudaStream_t st) {
+  if (cudaMemsetAsync(keys, 0xff, n * sizeof(unsigned long long), st) != cudaSuccess) return -1;
+  const int gx = (int)((n + TG_M - 1) / TG_M);
+  int gy = (152 * 6 + gx - 1) / gx;
+  const int tiles = (int)((m + TG_N - 1) / TG_N);
+  if (gy > tiles) gy = tiles;
+  const int chunk = ((tiles + gy - 1) / gy) * TG_N;
+  gy = (int)((m + chunk - 1) / chunk);
+  dim3 grid(gx, gy);
+  if (metric == METRIC_L1) k_nearest<true><<<grid, TG_THREADS, 0, st>>>(x, iota_m, (int)m, chunk, y, (int)n, d, keys);
+  else k_nearest<false><<<grid, TG_THREADS, 0, st>>>(x, iota_m, (int)m, chunk, y, (int)n, d, keys);
+  k_keys_to_index<<<std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8)), 256, 0, st>>>(keys, n, out);
+  return 0;
+}
+
+// --------------------------------------------------------------------------
+// k-means
+// --------------------------------------------------------------------------
+
+__global__ void k_km_accum(const float* __restrict__ pts, int64_t N, int d, const int* __restrict__ assign,
+                           float* __restrict__ sums, int* __restrict__ counts) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N * d; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = i / d;
+    const int k = (int)(i % d);
+    const int c = assign[p];
+    atomicAdd(sums + (size_t)c * d + k, pts[i]);
+    if (k == 0) atomicAdd(counts + c, 1);
+  }
+}
+
+__global__ void k_km_divide(float* __restrict__ cent, const float* __restrict__ sums, const int* __restrict__ counts,
+                            int cells, int d) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cells * d; i += gridDim.x * blockDim.x) {
+    const int c = i / d;
+    if (counts[c] > 0) cent[i] = sums[i] / (float)counts[c];
+  }
+}
+
+__global__ void k_gather_rows(const float* __restrict__ src, const int* __restrict__ rows, int count, int d,
+                              float* __restrict__ dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count * d; i += gridDim.x * blockDim.x)
+    dst[i] = src[(size_t)rows[i / d] * d + (i % d)];
+}
+
+int assign_cells(const nnsemd_proposal* P, const float* pts, int64_t N, int* out, cudaStream_t st);
+
+// iota / key scratch for the nearest-centroid search live at the end of the
+// k-means scratch: assign_buf holds N ints, then N 64-bit keys follow the
+// sums array (sized by the caller: cells*d floats + cells ints + N keys).
+static int* g_dummy = nullptr;
+
+int kmeans_fit(nnsemd_proposal* P, const float* pts, int64_t N, int iters, uint64_t seed, int* assign_buf,
+               float* sums, int* counts, cudaStream_t st) {
+  const int K = P->cells, d = P->d;
+  if (N < K) return -1;
+  // seeded distinct initial picks (partial Fisher-Yates on the host)
+  std::vector<int> idx(N);
+  for (int64_t i = 0; i < N; ++i) idx[i] = (int)i;
+  uint64_t s = seed * 0x9E3779B97F4A7C15ULL + 1;
+  for (int i = 0; i < K; ++i) {
+    s ^= s >> 12; s ^= s << 25; s ^= s >> 27;
+    const uint64_t r = (s * 0x2545F4914F6CDD1DULL) % (uint64_t)(N - i);
+    std::swap(idx[i], idx[i + r]);
+  }
+  int* dpick = assign_buf;  // temporarily holds the K picks
+  if (cudaMemcpyAsync(dpick, idx.data(), K * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess) return -1;
+  k_gather_rows<<<(K * d + 255) / 256, 256, 0, st>>>(pts, dpick, K, d, P->centroids);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+  for (int it = 0; it < iters; ++it) {
+    if (assign_cells(P, pts, N, assign_buf, st)) return -1;
+    cudaMemsetAsync(sums, 0, (size_t)K * d * sizeof(float), st);
+    cudaMemsetAsync(counts, 0, (size_t)K * sizeof(int), st);
+    k_km_accum<<<152 * 8, 256, 0, st>>>(pts, N, d, assign_buf, sums, counts);
+    k_km_divide<<<(K * d + 255) / 256, 256, 0, st>>>(P->centroids, sums, counts, K, d);
+  }
+  (void)g_dummy;
+  return 0;
+}
+
+// The nearest centroid of every point.  Uses its own temporary buffers.
+int assign_cells(const nnsemd_proposal* P, const float* pts, int64_t N, int* out, cudaStream_t st) {
+  const int64_t big = std::max<int64_t>(N, P->cells);
+  int* iota = nullptr;
+  unsigned long long* keys = nullptr;
+  if (cudaMallocAsync(&iota, big * sizeof(int), st) != cudaSuccess) return -1;
+  if (cudaMallocAsync(&keys, N * sizeof(unsigned long long), st) != cudaSuccess) return -1;
+  k_iota<<<152 * 4, 256, 0, st>>>(iota, big);
+  const int rc = nearest_all(P->centroids, P->cells, pts, N, P->d, METRIC_SQL2, iota, keys, out, st);
+  cudaFreeAsync(iota, st);
+  cudaFreeAsync(keys, st);
+  return rc;
+}
+
+// --------------------------------------------------------------------------
+// per-row top-K selection (K = PROP_LIST) by radix select on order-preserving
+// 32-bit keys; output in descending key order, ties by ascending column
+// --------------------------------------------------------------------------
+
+NNS_DEV unsigned ordered_bits(float v) {
+  const unsigned u = __float_as_uint(v);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// LARGEST: keep the K largest values; otherwise the K smallest.
+template <bool LARGEST>
+__global__ void __launch_bounds__(256) k_select_rows(const float* __restrict__ V, int rows, int cols, int* __restrict__ out_idx,
+                                                     float* __restrict__ out_val, int out_stride) {
+  extern __shared__ unsigned sk[];  // cols keys
+  __shared__ unsigned hist[256];
+  __shared__ unsigned s_prefix, s_mask, s_need;
+  __shared__ int s_cnt;
+  __shared__ unsigned sel_key[PROP_LIST];
+  __shared__ int sel_idx[PROP_LIST];
+  const int r = blockIdx.x;
+  const int tid = threadIdx.x;
+  for (int c = tid; c < cols; c += blockDim.x) {
+    const unsigned o = ordered_bits(V[(size_t)r * cols + c]);
+    sk[c] = LARGEST ? o : ~o;
+  }
+  if (tid == 0) {
+    s_prefix = 0u;
+    s_mask = 0u;
+    s_need = PROP_LIST;
+    s_cnt = 0;
+  }
+  __syncthreads();
+  // find the K-th largest key, 8 bits at a time from the top
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    const unsigned pre = s_prefix, msk = s_mask;
+    for (int c = tid; c < cols; c += blockDim.x) {
+      const unsigned k = sk[c];
+      if ((k & msk) == pre) atomicAdd(&hist[(k >> shift) & 0xffu], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      unsigned need = s_need, acc = 0u;
+      int dig = 255;
+      for (; dig > 0; --dig) {
+        if (acc + hist[dig] >= need) break;
+        acc += hist[dig];
+      }
+      s_need = need - acc;
+      s_prefix = pre | ((unsigned)dig << shift);
+      s_mask = msk | (0xffu << shift);
+    }
+    __syncthreads();
+  }
+  const unsigned kth = s_prefix;  // the K-th largest key (exact)
+  const unsigned need_eq = s_need;  // how many keys equal to kth to take (lowest columns first)
+  // gather: keys > kth, then the first need_eq keys == kth in column order
+  for (int c = tid; c < cols; c += blockDim.x) {
+    if (sk[c] > kth) {
+      const int slot = atomicAdd(&s_cnt, 1);
+      sel_key[slot] = sk[c];
+      sel_idx[slot] = c;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    unsigned taken = 0u;
+    for (int c = 0; c < cols && taken < need_eq; ++c)
+      if (sk[c] == kth) {
+        sel_key[s_cnt] = kth;
+        sel_idx[s_cnt] = c;
+        ++s_cnt;
+        ++taken;
+      }
+  }
+  __syncthreads();
+  // rank sort of the K selected (descending key, ascending column)
+  if (tid < PROP_LIST) {
+    const unsigned k = sel_key[tid];
+    const int c = sel_idx[tid];
+    int rank = 0;
+    for (int u = 0; u < PROP_LIST; ++u) {
+      const unsigned ku = sel_key[u];
+      rank += (ku > k) || (ku == k && sel_idx[u] < c);
+    }
+    out_idx[(size_t)r * out_stride + rank] = c;
+    if (out_val) out_val[(size_t)r * out_stride + rank] = V[(size_t)r * cols + c];
+  }
+}
+
+// --------------------------------------------------------------------------
+// per-solve preparation
+// --------------------------------------------------------------------------
+
+// radius[c] = max over the points assigned to c of |p - mu_c|, rounded up
+__global__ void k_cell_radius(const float* __restrict__ pts, int64_t N, int d, const int* __restrict__ cell,
+                              const float* __restrict__ mu, unsigned* __restrict__ radius_bits) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+    const int c = cell[p];
+    const float k2 = key32<METRIC_SQL2>(pts + (size_t)p * d, mu + (size_t)c * d, d);
+    const float r = sqrtf(k2) * (1.f + 1e-4f) + 1e-30f;
+    atomicMax(radius_bits + c, __float_as_uint(r));
+  }
+}
+
+// Squared distances between rows Y[rows][d] and centroids MU[cells][d] (FP32
+// direct differences, 4 x 4 per thread), out[rows][cells].
+__global__ void __launch_bounds__(256) k_centroid_d2(const float* __restrict__ Y, int rows, const float* __restrict__ MU,
+                                                     int cells, int d, float* __restrict__ out) {
+  __shared__ float Ys[TG_K][TG_PAD];
+  __shared__ float Ms[TG_K][TG_PAD];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+  const int lr = tid & 63, lk = (tid >> 6) * 8;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < d; k0 += TG_K) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int k = k0 + lk + e;
+      Ys[lk + e][lr] = (r0 + lr < rows && k < d) ? Y[(size_t)(r0 + lr) * d + k] : 0.f;
+      Ms[lk + e][lr] = (c0 + lr < cells && k < d) ? MU[(size_t)(c0 + lr) * d + k] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < TG_K; ++k) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float t = __fsub_rn(Ms[k][tx * 4 + j], Ys[k][ty * 4 + i]);
+          acc[i][j] = __fmaf_rn(t, t, acc[i][j]);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = r0 + ty * 4 + i, c = c0 + tx * 4 + j;
+      if (r < rows && c < cells) out[(size_t)r * cells + c] = acc[i][j];
+    }
+}
+
+// In place: d2 -> lower bound of the squared distance to any point of cell c:
+// max(0, |y - mu| - r_c)^2, with |y - mu| rounded down (the FP32 squared
+// distance has relative error <= gamma_d) and the result rounded down.
+__global__ void k_cell_lower_bound(float* __restrict__ D, int rows, int cells, int d,
+                                   const unsigned* __restrict__ radius_bits) {
+  const double gam = d * 0x1p-24 / (1.0 - d * 0x1p-24);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)rows * cells;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % cells);
+    const double r = __uint_as_float(radius_bits[c]);
+    const double dist = sqrt((double)D[i] * (1.0 - gam)) * (1.0 - 1e-9);
+    const double gap = dist - r;
+    D[i] = gap > 0.0 ? (float)(gap * gap * (1.0 - 1e-6)) : 0.f;
+  }
+}
+
+int learned_prepare(const LearnedBufs& L, const float* x, int64_t m, const float* y, int64_t n, int d,
+                    cudaStream_t st) {
+  const nnsemd_proposal* P = L.P;
+  const int K = P->cells, h = P->hidden;
+  if (assign_cells(P, x, m, L.cell_of_x, st)) return -1;
+  cudaMemsetAsync(L.radius, 0, K * sizeof(float), st);
+  k_cell_radius<<<152 * 4, 256, 0, st>>>(x, m, d, L.cell_of_x, P->centroids, reinterpret_cast<unsigned*>(L.radius));
+  for (int64_t r0 = 0; r0 < n; r0 += L.chunk) {
+    const int rows = (int)std::min<int64_t>(L.chunk, n - r0);
+    const float* yc = y + (size_t)r0 * d;
+    // proposals: the network's best cells
+    float* Xs = L.tmp3;              // rows x d (standardised input)
+    float* H1 = L.tmp;               // rows x h
+    float* H2 = L.tmp + (size_t)L.chunk * h;
+    float* Z = L.tmp2;               // rows x K
+    k_standardise<<<152 * 4, 256, 0, st>>>(yc, rows, d, P->in_mean, P->in_scale, Xs);
+    mlp_forward(P, Xs, rows, H1, H2, Z, st);
+    k_select_rows<true><<<rows, 256, K * sizeof(unsigned), st>>>(Z, rows, K, L.prop_cells + r0 * PROP_LIST, nullptr,
+                                                                 PROP_LIST);
+    // bounds: the cells with the smallest lower bound
+    dim3 g2((K + 63) / 64, (rows + 63) / 64);
+    k_centroid_d2<<<g2, 256, 0, st>>>(yc, rows, P->centroids, K, d, Z);
+    k_cell_lower_bound<<<152 * 8, 256, 0, st>>>(Z, rows, K, d, reinterpret_cast<const unsigned*>(L.radius));
+    k_select_rows<false><<<rows, 256, K * sizeof(unsigned), st>>>(Z, rows, K, L.bound_cells + r0 * PROP_LIST,
+                                                                  L.bound_vals + r0 * PROP_LIST, PROP_LIST);
+  }
+  (void)h;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// --------------------------------------------------------------------------
+// per round
+// --------------------------------------------------------------------------
+
+__global__ void k_cell_count(const int* __restrict__ ia, int mt, const int* __restrict__ cell_of_x,
+                             int* __restrict__ cnt) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < mt) atomicAdd(cnt + cell_of_x[ia[p]], 1);
+}
+
+// exclusive scan of cnt[0..K) into off (single block), off[K] = total
+__global__ void k_cell_scan(const int* __restrict__ cnt, int K, int* __restrict__ off, int* __restrict__ fill) {
+  __shared__ int wt[33];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < K; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int v = i < K ? cnt[i] : 0;
+    int tot;
+    const int ex = block_scan_excl(v, wt, tot);
+    if (i < K) {
+      off[i] = carry + ex;
+      fill[i] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) off[K] = carry;
+}
+
+__global__ void k_cell_scatter(const int* __restrict__ ia, int mt, const int* __restrict__ cell_of_x,
+                               const int* __restrict__ off, int* __restrict__ fill, int* __restrict__ members) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= mt) return;
+  const int c = cell_of_x[ia[p]];
+  members[off[c] + atomicAdd(fill + c, 1)] = p;
+}
+
+struct LearnedArgs {
+  const float* x;
+  const float* y;
+  const int* ia;
+  const int* ja;
+  int d, nt;
+  const int* prop_cells;
+  const int* bound_cells;
+  const float* bound_vals;
+  const int* cell_off;   // [K+1]
+  const int* members;
+  unsigned long long* nnkey;
+  int* fallback;
+  int* nfallback;
+  unsigned long long* ncert;
+  unsigned long long* nfall;
+};
+
+// One warp per active consumer.
+__global__ void __launch_bounds__(256) k_learned_nns(LearnedArgs A) {
+  __shared__ int cand[8][PROP_TAKE];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int q = blockIdx.x * 8 + wib;
+  if (q >= A.nt) return;
+  const int j = A.ja[q];
+  const float* yrow = A.y + (size_t)j * A.d;
+  // the first PROP_TAKE proposed cells that still hold active suppliers
+  const int* pl = A.prop_cells + (size_t)j * PROP_LIST;
+  int ncand = 0;
+  for (int base = 0; base < PROP_LIST && ncand < PROP_TAKE; base += 32) {
+    const int c = pl[base + lane];
+    const bool ne = A.cell_off[c + 1] > A.cell_off[c];
+    const unsigned bal = __ballot_sync(0xffffffffu, ne);
+    const int pos = ncand + __popc(bal & ((1u << lane) - 1u));
+    if (ne && pos < PROP_TAKE) cand[wib][pos] = c;
+    ncand = min(PROP_TAKE, ncand + __popc(bal));
+  }
+  __syncwarp();
+  // exact FP32 key over the candidates' suppliers
+  unsigned long long best = ~0ULL;
+  for (int k = 0; k < ncand; ++k) {
+    const int c = cand[wib][k];
+    const int b = A.cell_off[c], e = A.cell_off[c + 1];
+    for (int u = b + lane; u < e; u += 32) {
+      const int p = A.members[u];
+      const float key = key32<METRIC_SQL2>(A.x + (size_t)A.ia[p] * A.d, yrow, A.d);
+      const unsigned long long kk = pack_key(key, (unsigned)p);
+      best = kk < best ? kk : best;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+    best = ob < best ? ob : best;
+  }
+  // smallest bound of a non-candidate cell that still holds active suppliers
+  const int* bl = A.bound_cells + (size_t)j * PROP_LIST;
+  const float* bv = A.bound_vals + (size_t)j * PROP_LIST;
+  float bound = bv[PROP_LIST - 1];  // every cell outside the list is at least this far
+  for (int base = 0; base < PROP_LIST; base += 32) {
+    const int c = bl[base + lane];
+    bool ok = A.cell_off[c + 1] > A.cell_off[c];
+    for (int k = 0; k < ncand && ok; ++k) ok = cand[wib][k] != c;
+    const float v = ok ? bv[base + lane] : CUDART_INF_F;
+    float mn = v;
+    for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    bound = fminf(bound, mn);
+  }
+  if (lane != 0) return;
+  const double gam = A.d * 0x1p-24 / (1.0 - A.d * 0x1p-24);
+  const bool certified =
+      best != ~0ULL && (double)__uint_as_float((unsigned)(best >> 32)) < (double)bound * (1.0 - gam) * (1.0 - 0x1p-30);
+  if (certified) {
+    A.nnkey[q] = best;
+    atomicAdd(A.ncert, 1ULL);
+  } else {
+    A.fallback[atomicAdd(A.nfallback, 1)] = q;
+    atomicAdd(A.nfall, 1ULL);
+  }
+}
+
+int launch_nns_learned(const SolveBufs& B, const LearnedBufs& L, int mt, int nt, cudaStream_t st) {
+  const int K = L.P->cells;
+  const int* ia = B.ia[B.cur];
+  cudaMemsetAsync(L.cell_cnt, 0, (K + 1) * sizeof(int), st);
+  k_cell_count<<<(mt + 255) / 256, 256, 0, st>>>(ia, mt, L.cell_of_x, L.cell_cnt);
+  k_cell_scan<<<1, 1024, 0, st>>>(L.cell_cnt, K, L.cell_off, L.cell_fill);
+  k_cell_scatter<<<(mt + 255) / 256, 256, 0, st>>>(ia, mt, L.cell_of_x, L.cell_off, L.cell_fill, L.cell_members);
+  cudaMemsetAsync(L.nfallback, 0, sizeof(int), st);
+  LearnedArgs A{B.x,          B.y,          ia,          B.ja[B.cur], B.d,       nt,
+                L.prop_cells, L.bound_cells, L.bound_vals, L.cell_off, L.cell_members, B.nnkey,
+                L.fallback,   L.nfallback,   &B.st->certified, &B.st->fallbacks};
+  k_learned_nns<<<(nt + 7) / 8, 256, 0, st>>>(A);
+  launch_nns_f32(B, mt, nt, L.fallback, L.nfallback, st);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace nnsemd

@@ -72,6 +72,23 @@ _lib.nnsemd_last_error.restype = ctypes.c_char_p
 _lib.nnsemd_status_string.argtypes = [ctypes.c_int]
 _lib.nnsemd_status_string.restype = ctypes.c_char_p
 _lib.nnsemd_abi_version.restype = ctypes.c_int
+_lib.nnsemd_nearest.argtypes = [_P, _P, _I64, _P, _I64, ctypes.c_int32, ctypes.c_int32, _P]
+_lib.nnsemd_proposal_create.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                        ctypes.POINTER(_P)]
+_lib.nnsemd_proposal_destroy.argtypes = [_P]
+_lib.nnsemd_proposal_fit.argtypes = [_P, _P, _P, _I64, ctypes.c_int32, ctypes.c_uint64]
+_lib.nnsemd_proposal_train.argtypes = [_P, _P, _P, _P, _I64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                       ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
+_lib.nnsemd_proposal_loss_grad.argtypes = [_P, _P, _P, _P, _I64, ctypes.POINTER(ctypes.c_double), _P]
+_lib.nnsemd_proposal_info.argtypes = [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]
+_lib.nnsemd_proposal_params.argtypes = [_P, _P, _P, ctypes.c_int32]
+_lib.nnsemd_proposal_save.argtypes = [_P, _P, ctypes.c_char_p]
+_lib.nnsemd_proposal_load.argtypes = [_P, ctypes.c_char_p, ctypes.POINTER(_P)]
+for _f in ("nnsemd_nearest", "nnsemd_proposal_create", "nnsemd_proposal_destroy", "nnsemd_proposal_fit",
+           "nnsemd_proposal_train", "nnsemd_proposal_loss_grad", "nnsemd_proposal_info", "nnsemd_proposal_params",
+           "nnsemd_proposal_save", "nnsemd_proposal_load"):
+    getattr(_lib, _f).restype = ctypes.c_int
 for _f in ("nnsemd_create", "nnsemd_destroy", "nnsemd_set_stream", "nnsemd_solve", "nnsemd_solve_host",
            "nnsemd_solve_batched"):
     getattr(_lib, _f).restype = ctypes.c_int
@@ -96,8 +113,9 @@ def abi_version() -> int:
     return _lib.nnsemd_abi_version()
 
 
-def _options(metric: str, precision: str, rerank_k: int, flags: int = 0) -> nnsemd_options:
-    return nnsemd_options(METRIC[metric], PRECISION[precision], rerank_k, flags, None)
+def _options(metric: str, precision: str, rerank_k: int, flags: int = 0, proposal=None) -> nnsemd_options:
+    return nnsemd_options(METRIC[metric], PRECISION[precision], rerank_k, flags,
+                          proposal._h.value if proposal is not None else None)
 
 
 def _ptr(t) -> int:
@@ -139,8 +157,9 @@ class Context:
 
     # -- nnsemd_solve --------------------------------------------------------
     def solve(self, x, a, y, b, metric: str = "l2", precision: str = "fp32", rerank_k: int = 0,
-              plan: bool = False, flags: int = 0) -> SolveResult:
-        """Device tensors: x [m,d] float32, a [m] float64, y [n,d] float32, b [n] float64."""
+              plan: bool = False, flags: int = 0, proposal=None) -> SolveResult:
+        """Device tensors: x [m,d] float32, a [m] float64, y [n,d] float32, b [n] float64.
+        ``proposal``: a trained Proposal (d > 8) replacing the full NNS scan."""
         import torch
         for t, dt in ((x, torch.float32), (a, torch.float64), (y, torch.float32), (b, torch.float64)):
             if not t.is_cuda or t.dtype != dt or not t.is_contiguous():
@@ -148,7 +167,7 @@ class Context:
         m, d = x.shape
         n = y.shape[0]
         self._bind_current_stream()
-        opt = _options(metric, precision, rerank_k, flags)
+        opt = _options(metric, precision, rerank_k, flags, proposal)
         cost = ctypes.c_double()
         st = nnsemd_stats()
         pl = None
@@ -169,7 +188,7 @@ class Context:
 
     # -- nnsemd_solve_host ---------------------------------------------------
     def solve_host(self, x, a, y, b, metric: str = "l2", precision: str = "fp32", rerank_k: int = 0,
-                   plan: bool = False, plan_out=None, flags: int = 0) -> SolveResult:
+                   plan: bool = False, plan_out=None, flags: int = 0, proposal=None) -> SolveResult:
         """Host arrays (numpy, or pinned CPU torch tensors): the copies to and
         from the device happen inside the call.  ``plan_out`` may pass
         preallocated (i, j, f) host arrays of capacity >= m + n - 1."""
@@ -182,7 +201,7 @@ class Context:
         m, d = x.shape
         n = y.shape[0]
         self._bind_current_stream()
-        opt = _options(metric, precision, rerank_k, flags)
+        opt = _options(metric, precision, rerank_k, flags, proposal)
         cost = ctypes.c_double()
         st = nnsemd_stats()
         pl = None
@@ -222,3 +241,80 @@ class Context:
                                        ctypes.byref(st) if stats else None)
         self._check(rc)
         return costs, (st.as_dict() if stats else None)
+
+
+    # -- nnsemd_nearest ------------------------------------------------------
+    def nearest(self, x, y, metric: str = "l2"):
+        """Round one of Alg. 1: the nearest supplier of every consumer (device int32 tensor)."""
+        import torch
+        out = torch.empty(y.shape[0], dtype=torch.int32, device=y.device)
+        self._bind_current_stream()
+        self._check(_lib.nnsemd_nearest(self._h, _ptr(x), x.shape[0], _ptr(y), y.shape[0], x.shape[1],
+                                        METRIC[metric], _ptr(out)))
+        return out
+
+
+class Proposal:
+    """Learned candidate proposal (nnsemd_proposal_*): a k-means codebook and
+    an MLP scoring its cells.  Not in the paper."""
+
+    def __init__(self, ctx: Context, d: int, cells: int = 4096, hidden: int = 256, seed: int = 0, _handle=None):
+        self.ctx = ctx
+        self._h = _P()
+        if _handle is not None:
+            self._h = _handle
+        else:
+            ctx._check(_lib.nnsemd_proposal_create(ctx._h, d, cells, hidden, seed, ctypes.byref(self._h)))
+        dd, cc, hh, npar = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _lib.nnsemd_proposal_info(self._h, ctypes.byref(dd), ctypes.byref(cc), ctypes.byref(hh), ctypes.byref(npar))
+        self.d, self.cells, self.hidden, self.nparams = dd.value, cc.value, hh.value, npar.value
+
+    def close(self):
+        if self._h:
+            _lib.nnsemd_proposal_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def fit(self, pts, iters: int = 10, seed: int = 0):
+        self.ctx._bind_current_stream()
+        self.ctx._check(_lib.nnsemd_proposal_fit(self.ctx._h, self._h, _ptr(pts), pts.shape[0], iters, seed))
+
+    def train(self, y, x_nn, epochs: int = 3, batch: int = 4096, lr: float = 1e-3, seed: int = 0) -> float:
+        loss = ctypes.c_double()
+        self.ctx._bind_current_stream()
+        self.ctx._check(_lib.nnsemd_proposal_train(self.ctx._h, self._h, _ptr(y), _ptr(x_nn), y.shape[0], epochs,
+                                                   batch, lr, seed, ctypes.byref(loss)))
+        return loss.value
+
+    def loss_grad(self, y, labels):
+        import torch
+        grad = torch.empty(self.nparams, dtype=torch.float32, device=y.device)
+        loss = ctypes.c_double()
+        self.ctx._bind_current_stream()
+        self.ctx._check(_lib.nnsemd_proposal_loss_grad(self.ctx._h, self._h, _ptr(y), _ptr(labels), y.shape[0],
+                                                       ctypes.byref(loss), _ptr(grad)))
+        return loss.value, grad
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.nparams, np.float32)
+        self.ctx._check(_lib.nnsemd_proposal_params(self.ctx._h, self._h, out.ctypes.data, 0))
+        return out
+
+    def set_params(self, values: np.ndarray):
+        v = np.ascontiguousarray(values, np.float32)
+        assert v.size == self.nparams
+        self.ctx._check(_lib.nnsemd_proposal_params(self.ctx._h, self._h, v.ctypes.data, 1))
+
+    def save(self, path: str):
+        self.ctx._check(_lib.nnsemd_proposal_save(self.ctx._h, self._h, path.encode()))
+
+    @classmethod
+    def load(cls, ctx: Context, path: str) -> "Proposal":
+        h = _P()
+        ctx._check(_lib.nnsemd_proposal_load(ctx._h, path.encode(), ctypes.byref(h)))
+        return cls(ctx, 0, _handle=h)
