@@ -192,7 +192,7 @@ int nnsemd_nearest(nnsemd_ctx *ctx, const float *x, int64_t m, const float *y, i
  * stated.  Errors: INVALID_ARG, OOM, CUDA. */
 typedef struct nnsemd_proposal nnsemd_proposal;
 
-/* New proposal with seeded He-uniform weights (cells >= 64). */
+/* New proposal with seeded He-uniform weights (64 <= cells <= 8192). */
 int nnsemd_proposal_create(nnsemd_ctx *ctx, int32_t d, int32_t cells, int32_t hidden, uint64_t seed,
                            nnsemd_proposal **out);
 int nnsemd_proposal_destroy(nnsemd_proposal *p);

@@ -86,7 +86,7 @@ int nnsemd_proposal_create(nnsemd_ctx* ctx, int32_t d, int32_t cells, int32_t hi
   if (!ctx || !out) return NNSEMD_ERR_INVALID_ARG;
   ctx->err.clear();
   *out = nullptr;
-  if (d < 1 || cells < PROP_LIST || cells > 65536 || hidden < 1 || hidden > 8192)
+  if (d < 1 || cells < PROP_LIST || cells > PROP_MAX_CELLS || hidden < 1 || hidden > 8192)
     return ctx_fail(ctx, NNSEMD_ERR_INVALID_ARG, "bad proposal shape d=%d cells=%d hidden=%d", d, cells, hidden);
   PCK(cudaSetDevice(ctx->device));
   nnsemd_proposal* P = new nnsemd_proposal();

@@ -39,6 +39,7 @@ namespace nnsemd {
 
 constexpr int PROP_LIST = 64;  // cells kept per consumer (by score and by bound)
 constexpr int PROP_TAKE = 32;  // non-empty proposed cells scanned per round
+constexpr int PROP_MAX_CELLS = 8192;  // per-row selection keeps every cell's key in shared memory
 
 // Per-solve buffers of the learned NNS step.
 struct LearnedBufs {
