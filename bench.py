@@ -170,18 +170,20 @@ class ClockSampler:
 # inputs
 # ---------------------------------------------------------------------------
 
-def make_inputs(name: str, rank: int):
+def make_inputs(name: str, rank: int, points: int | None = None, pairs: int | None = None):
+    """The workload's synthetic input (seed = rank).  ``points`` / ``pairs``
+    shrink it for profiling captures (not for bench lines)."""
     from paper_2401_07378_gb300 import workloads
     if name == "colour":
-        return workloads.color_transfer(seed=rank)
+        return workloads.color_transfer(seed=rank, n=points or 65536)
     if name == "single":
         return workloads.single_pair(seed=rank)
     if name == "gmm":
-        return workloads.gmm_pair(seed=rank)
+        return workloads.gmm_pair(seed=rank, n=points or 262144)
     if name == "docs":
-        return workloads.doc_knn(seed=rank)
+        return workloads.doc_knn(seed=rank, num_docs=pairs or 4096)
     if name == "retrieval":
-        return workloads.retrieval(seed=rank)
+        return workloads.retrieval(seed=rank, num_pairs=pairs or 10000)
     raise ValueError(name)
 
 
@@ -318,7 +320,7 @@ def run_ours(args) -> dict | None:
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dist_init("nccl")
-    inp = make_inputs(args.workload, rank)
+    inp = make_inputs(args.workload, rank, args.points, args.pairs)
     ctx = nnsemd.Context(local)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     T = nnsemd.FLAG_TIME_KERNELS
@@ -442,11 +444,14 @@ def run_ours(args) -> dict | None:
     else:
         line["e2e"] = {"value": line["value"], "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                        "note": "batched inputs resident on the device; no host entry point for batches"}
+    if args.points or args.pairs:
+        line["config"]["reduced_size"] = {"points": args.points, "pairs": args.pairs}
+        line["config"]["workload"] += " [REDUCED SIZE: profiling case, not the workload]"
     if prop is not None:
         line["config"]["proposal"] = "learned (trained before timing; training not in the timed region)"
         line["dtype"] = "f32 distances, f64 mass/cost"
         prop.close()
-    if ws == 1 and not args.no_cpu_baseline:
+    if ws == 1 and not args.no_cpu_baseline and not (args.points or args.pairs):
         full = (last or {}).get("pair_evals") if args.workload == "gmm" else None
         line["cpu_baseline"] = oracle_sample(args.workload, inp, full)
     ctx.close()
@@ -489,6 +494,10 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["fp32", "bf16", "fp16", "fp8"], default=None)
     ap.add_argument("--proposal", choices=["none", "learned"], default="none",
                     help="gmm only: train a learned candidate proposal before timing and solve with it")
+    ap.add_argument("--points", type=int, default=None,
+                    help="colour/gmm: points per side (default the full workload; smaller sizes are for profiling)")
+    ap.add_argument("--pairs", type=int, default=None,
+                    help="docs/retrieval: number of pairs (default the full workload; smaller is for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
     line = run_reference(args) if args.impl == "reference" else run_ours(args)

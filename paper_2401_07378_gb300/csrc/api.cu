@@ -167,6 +167,7 @@ size_t layout_solve(void* base, int64_t m, int64_t n, int d, SolveBufs& B, int p
   B.seg = C.take<int2>(m);
   B.seglist = C.take<int>(m);
   B.biglist = C.take<int>(m);
+  B.medlist = C.take<int>(m);
   B.member = C.take<unsigned long long>(n);
   B.terms = C.take<double>(m + n);
   B.blockcounts = C.take<int>((m + n) / 1024 + 8);

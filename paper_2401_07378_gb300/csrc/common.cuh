@@ -37,6 +37,7 @@ struct DevState {
   unsigned err;                  // ErrFlag bits
   int nseg;                      // non-empty supplier groups this round
   int nbig;                      // groups longer than a warp this round
+  int nmed;                      // groups of 9..32 consumers this round
   unsigned seg_cursor;           // member slots handed out this round
   long long rounds;              // rounds run on the device (finisher)
   long long pair_evals;          // sum of m_t * n_t over device-run rounds
@@ -91,6 +92,24 @@ NNS_DEV double cost_dist64(const float* x, const float* y, int d, int metric) {
 // minimum picks the smallest distance and then the smallest index.
 NNS_DEV unsigned long long pack_key(float k, unsigned idx) {
   return ((unsigned long long)__float_as_uint(k) << 32) | idx;
+}
+
+// One step of the greedy protocol (Alg. 1): f = min(s, c); s -= f; c -= f.
+// Residuals are finite and never negative (they start positive and every
+// step leaves x - x = +0 or the difference of the larger and the smaller),
+// so their order is the order of their bit patterns, and the side that gave
+// f becomes exactly +0: one FP64 subtraction, bit-identical to the two of
+// the plain statement.  Returns f.
+NNS_DEV bool residual_positive(double v) { return __double_as_longlong(v) > 0; }
+
+NNS_DEV double greedy_step(double& s, double& c) {
+  const long long sb = __double_as_longlong(s), cb = __double_as_longlong(c);
+  const bool take_s = sb < cb;  // s < c: f = s
+  const double f = take_s ? s : c;
+  const double d = __dsub_rn(take_s ? c : s, f);
+  s = take_s ? 0.0 : d;
+  c = take_s ? d : 0.0;
+  return f;
 }
 
 // --------------------------------------------------------------------------

@@ -291,8 +291,8 @@ NNS_DEV void cta_compact(CtaCore<CAP>& S, Geo& G) {
 #pragma unroll
   for (int k = 0; k < IT; ++k) {
     const int p = tid * IT + k;
-    ks[k] = p < mt && S.sres[p] > 0.0;
-    kc[k] = p < nt && S.cres[p] > 0.0;
+    ks[k] = p < mt && residual_positive(S.sres[p]);
+    kc[k] = p < nt && residual_positive(S.cres[p]);
     if (ks[k]) { sv[k] = S.sres[p]; iv[k] = S.iidx[p]; G.load_x(p, px[k]); }
     if (kc[k]) { cv[k] = S.cres[p]; jv[k] = S.jidx[p]; G.load_y(p, py[k]); }
     ns += ks[k];
@@ -382,40 +382,50 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
       S.mem2[b + rank] = e;
     }
     __syncthreads();
-    // ---- flow & cost (greedy protocol), one supplier per thread
+    // ---- flow (greedy protocol), one supplier per thread: the residual
+    // chain only; each flow (p, q) and f is recorded in mem / nnk, which are
+    // free after the ordering step (every consumer flows at most once)
     for (int p = tid; p < mt; p += T) {
       const int b = S.off[p], en = S.off[p + 1];
       if (b == en) continue;
       double s = S.sres[p];
       for (int r = b; r < en; ++r) {
-        if (!(s > 0.0)) break;
+        if (!residual_positive(s)) break;
         const int q = (int)(S.mem2[r] & 0xffffffffULL);
-        const double c = S.cres[q];
-        const double f = s < c ? s : c;
-        s = __dsub_rn(s, f);
-        const double cn = __dsub_rn(c, f);
-        S.cres[q] = cn;
-        const double Dij = G.dist64(S, p, q, metric);
-        const double term = __dmul_rn(f, Dij);
-        const unsigned long long slot = nnz + atomicAdd(&S.nflow, 1u);
-        if (O.terms) O.terms[slot] = term;
-        if (O.acc) xs_add(O.acc, term);
-        if (O.plan_i) {
-          if ((long long)slot < O.plan_cap) {
-            O.plan_i[slot] = S.iidx[p];
-            O.plan_j[slot] = S.jidx[q];
-            O.plan_f[slot] = f;
-          } else {
-            atomicOr(O.err, EF_CAPACITY);
-          }
-        }
-        if (O.c_glob) O.c_glob[S.jidx[q]] = cn;
+        double c = S.cres[q];
+        const double f = greedy_step(s, c);
+        S.cres[q] = c;
+        const unsigned k = atomicAdd(&S.nflow, 1u);
+        S.mem[k] = ((unsigned long long)p << 32) | (unsigned)q;
+        S.nnk[k] = (unsigned long long)__double_as_longlong(f);
       }
       S.sres[p] = s;
       if (O.s_glob) O.s_glob[S.iidx[p]] = s;
     }
     __syncthreads();
-    nnz += S.nflow;
+    // ---- cost terms and plan entries of the round's flows, one per thread
+    const unsigned nflow = S.nflow;
+    for (unsigned k = tid; k < nflow; k += T) {
+      const unsigned long long pq = S.mem[k];
+      const int p = (int)(pq >> 32), q = (int)(pq & 0xffffffffULL);
+      const double f = __longlong_as_double((long long)S.nnk[k]);
+      const double term = __dmul_rn(f, G.dist64(S, p, q, metric));
+      const unsigned long long slot = nnz + k;
+      if (O.terms) O.terms[slot] = term;
+      if (O.acc) xs_add(O.acc, term);
+      if (O.plan_i) {
+        if ((long long)slot < O.plan_cap) {
+          O.plan_i[slot] = S.iidx[p];
+          O.plan_j[slot] = S.jidx[q];
+          O.plan_f[slot] = f;
+        } else {
+          atomicOr(O.err, EF_CAPACITY);
+        }
+      }
+      if (O.c_glob) O.c_glob[S.jidx[q]] = S.cres[q];
+    }
+    __syncthreads();
+    nnz += nflow;
     rounds += 1;
     pair_evals += (long long)mt * nt;
     // ---- weights update: retire spent points, compact

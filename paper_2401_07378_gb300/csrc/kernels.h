@@ -59,6 +59,7 @@ struct SolveBufs {
   int2* seg;       // [m] (offset, length) of each supplier's group
   int* seglist;    // [m] non-empty groups
   int* biglist;    // [m] groups longer than a warp
+  int* medlist;    // [m] groups of 9..32 consumers
   unsigned long long* member;  // [n] group members: key32 bits << 32 | consumer position
   double* terms;   // [m+n] per-flow cost terms f * D_ij
   int* blockcounts;            // compaction scratch

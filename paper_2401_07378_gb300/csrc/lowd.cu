@@ -33,14 +33,20 @@ namespace nnsemd {
 constexpr int K1_THREADS = 256;
 // consumers per thread (two per packed register): fewer at larger d so that
 // the consumer coordinates stay in registers
-__host__ __device__ constexpr int k1_p(int D) { return D <= 3 ? 8 : 4; }
+__host__ __device__ constexpr int k1_p(int D) { return D <= 3 ? 8 : (D <= 6 ? 4 : 2); }
+// resident CTAs per SM the register budget allows (128 or 64 registers)
+__host__ __device__ constexpr int k1_min_blocks(int D, int P) { return (P == 2 && D <= 6) ? 4 : 2; }
 
-template <int D, int DP, bool L1>
-__global__ void __launch_bounds__(K1_THREADS, 2)
+// K1_P consumers per thread: k1_p(D) for large rounds, 2 for small ones
+// (more CTAs, shorter per-thread loops).  A chunk is a multiple of 64
+// suppliers; each tile copy stops at the chunk's end rounded up to a whole
+// group of 8 (inside the NaN padding of the active list).
+template <int D, int DP, bool L1, int K1_P>
+__global__ void __launch_bounds__(K1_THREADS, k1_min_blocks(D, K1_P))
     k_nns_lowd(const float* __restrict__ xa, int mt, int chunk, const float* __restrict__ ya, int nt,
                unsigned long long* __restrict__ nnkey, unsigned* __restrict__ err) {
   static_assert(K1_TS % 8 == 0, "tile must hold whole groups");
-  constexpr int K1_P = k1_p(D);
+  static_assert(K1_P % 2 == 0, "consumers are packed in pairs");
   __shared__ __align__(128) float tile[2][K1_TS * DP];
   __shared__ __align__(8) uint64_t bar[2];
 
@@ -69,7 +75,11 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
   for (int c = 0; c < K1_P; ++c) { best[c] = CUDART_INF_F; bestg[c] = -1; }
 
   const int ntile = (p1 - p0 + K1_TS - 1) / K1_TS;
-  const unsigned bytes = K1_TS * DP * sizeof(float);
+  // bytes of tile t: its points up to p1 rounded up to 8 (a multiple of 64 B)
+  auto tile_bytes = [&](int t) -> unsigned {
+    const int base = p0 + t * K1_TS;
+    return (unsigned)(min(K1_TS, (p1 - base + 7) & ~7) * DP * sizeof(float));
+  };
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -77,15 +87,17 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
   }
   __syncthreads();
   if (tid == 0) {
-    mbar_expect_tx(&bar[0], bytes);
-    tma_load_1d(tile[0], xa + (size_t)p0 * DP, bytes, &bar[0]);
+    const unsigned b0 = tile_bytes(0);
+    mbar_expect_tx(&bar[0], b0);
+    tma_load_1d(tile[0], xa + (size_t)p0 * DP, b0, &bar[0]);
   }
   bool ok = true;
   for (int t = 0; t < ntile; ++t) {
     const int buf = t & 1;
     if (tid == 0 && t + 1 < ntile) {
-      mbar_expect_tx(&bar[buf ^ 1], bytes);
-      tma_load_1d(tile[buf ^ 1], xa + (size_t)(p0 + (t + 1) * K1_TS) * DP, bytes, &bar[buf ^ 1]);
+      const unsigned bn = tile_bytes(t + 1);
+      mbar_expect_tx(&bar[buf ^ 1], bn);
+      tma_load_1d(tile[buf ^ 1], xa + (size_t)(p0 + (t + 1) * K1_TS) * DP, bn, &bar[buf ^ 1]);
     }
     if (ok) ok = mbar_wait_bounded(&bar[buf], (t >> 1) & 1);
     if (ok) {
@@ -184,21 +196,62 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
   }
 }
 
+// Launch shape of K1 for one round: consumers per thread P and the supplier
+// chunk of a CTA, from a cost model of the kernel.  A wave of CTAs costs a
+// fixed amount plus P x chunk pairs per thread at a per-pair time that grows
+// with the CTAs sharing an SM (the FP32 pipe is shared): at d = 3, 7.9 ns
+// per pair per thread alone on an SM for P = k1_p (15.8 ns with the 2
+// resident CTAs of the full-size rounds), about 30 % more for P = 2 (the
+// supplier loads are shared by fewer consumers), which fits 4 CTAs per SM
+// for d <= 6; scaled by (d + 1) / 4 for other d.
+struct K1Shape {
+  int P, chunk, gx, gy;
+};
+
+static K1Shape k1_shape(int D, int mt, int nt) {
+  const int PB = k1_p(D);
+  constexpr double kWaveNs = 2000.0;
+  K1Shape best{PB, 64, 1, 1};
+  double best_t = 1e30;
+  const int Ps[2] = {PB, 2};
+  for (int k = 0; k < 2; ++k) {
+    const int P = Ps[k];
+    const int per_sm = k1_min_blocks(D, P);
+    const double pair_ns = (P == 2 ? 10.2 : 7.9) * (D + 1) / 4.0;  // measured at d = 3
+    const long long resident = 152LL * per_sm;
+    const int gx = (nt + K1_THREADS * P - 1) / (K1_THREADS * P);
+    const int max_gy = (mt + 63) / 64;
+    int last_chunk = -1;
+    for (int gy0 = 1; gy0 <= max_gy; gy0 += (gy0 < 64 ? 1 : gy0 / 16)) {
+      const int chunk = ((mt + gy0 - 1) / gy0 + 63) / 64 * 64;
+      if (chunk == last_chunk) continue;
+      last_chunk = chunk;
+      const int gy = (mt + chunk - 1) / chunk;
+      const long long ctas = (long long)gx * gy;
+      if (gy > 65535) continue;
+      const double per_cta_ns = (double)P * chunk * pair_ns;
+      const long long full = ctas / resident, rem = ctas % resident;
+      double t = (double)full * (kWaveNs + per_cta_ns * per_sm);
+      if (rem) t += kWaveNs + per_cta_ns * (double)((rem + 151) / 152);
+      if (t < best_t) {
+        best_t = t;
+        best = K1Shape{P, chunk, gx, gy};
+      }
+    }
+  }
+  return best;
+}
+
 template <int D, int DP, bool L1>
 static void nns_lowd_t(const SolveBufs& B, int mt, int nt, cudaStream_t st) {
-  const int per_cta = K1_THREADS * k1_p(D);
-  const int gx = (nt + per_cta - 1) / per_cta;
-  // enough CTAs for several waves over the 152 SMs; chunks stay whole tiles
-  const int target = 152 * 8;
-  int gy = (target + gx - 1) / gx;
-  int tiles = (mt + K1_TS - 1) / K1_TS;
-  if (gy > tiles) gy = tiles;
-  int chunk_tiles = (tiles + gy - 1) / gy;
-  int chunk = chunk_tiles * K1_TS;
-  gy = (mt + chunk - 1) / chunk;
-  dim3 grid(gx, gy);
-  k_nns_lowd<D, DP, L1><<<grid, K1_THREADS, 0, st>>>(B.xa[B.cur], mt, chunk, B.ya[B.cur], nt, B.nnkey,
-                                                     &B.st->err);
+  const K1Shape sh = k1_shape(D, mt, nt);
+  dim3 grid(sh.gx, sh.gy);
+  if (sh.P == 2)
+    k_nns_lowd<D, DP, L1, 2><<<grid, K1_THREADS, 0, st>>>(B.xa[B.cur], mt, sh.chunk, B.ya[B.cur], nt, B.nnkey,
+                                                          &B.st->err);
+  else
+    k_nns_lowd<D, DP, L1, k1_p(D)><<<grid, K1_THREADS, 0, st>>>(B.xa[B.cur], mt, sh.chunk, B.ya[B.cur], nt,
+                                                                B.nnkey, &B.st->err);
 }
 
 int launch_nns_lowd(const SolveBufs& B, int mt, int nt, cudaStream_t st) {

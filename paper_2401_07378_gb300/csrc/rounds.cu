@@ -7,9 +7,10 @@
 //       per consumer, so that sorting a group orders it by distance and
 //       then by consumer index (the greedy protocol's order).
 //   k_flow_small / k_flow_big
-//       sort each group (a warp-register bitonic network for groups of at
-//       most 32, a CTA network in shared or global memory beyond that), then
-//       walk it in FP64 exactly as the algorithm does: f = min(s_i, c_j),
+//       sort each group (in one thread's registers for groups of at most 8,
+//       a warp-register bitonic network up to 32, a CTA network in shared or
+//       global memory beyond that), then walk it in FP64 exactly as the
+//       algorithm does: f = min(s_i, c_j),
 //       s_i -= f, c_j -= f, until s_i is spent; each flow writes its plan
 //       entry and its cost term f * D_ij (FP64 ground distance).
 //   k_compact_count / k_compact_scatter
@@ -315,8 +316,14 @@ __global__ void k_group_count(const unsigned long long* __restrict__ nnkey, int 
   atomicAdd(cnt + p, 1);
 }
 
+// Groups of at most FLOW_THREAD_MAX consumers are served by one thread each:
+// the greedy walk is a chain of dependent FP64 operations, and a lane-level
+// chain costs the FP64 pipe one instruction per 32 groups instead of one per
+// group.
+constexpr int FLOW_THREAD_MAX = 8;
+
 __global__ void k_group_alloc(const int* __restrict__ cnt, int mt, int2* __restrict__ seg, int* __restrict__ seglist,
-                              int* __restrict__ biglist, DevState* st) {
+                              int* __restrict__ biglist, int* __restrict__ medlist, DevState* st) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int L = p < mt ? cnt[p] : 0;
@@ -337,10 +344,15 @@ __global__ void k_group_alloc(const int* __restrict__ cnt, int mt, int2* __restr
   unsigned bb = 0;
   if (lane == 0 && big) bb = atomicAdd((unsigned*)&st->nbig, (unsigned)__popc(big));
   bb = __shfl_sync(0xffffffffu, bb, 0);
+  const unsigned med = __ballot_sync(0xffffffffu, L > FLOW_THREAD_MAX && L <= 32);
+  unsigned mb = 0;
+  if (lane == 0 && med) mb = atomicAdd((unsigned*)&st->nmed, (unsigned)__popc(med));
+  mb = __shfl_sync(0xffffffffu, mb, 0);
   if (p < mt) {
     seg[p] = make_int2((int)(base + x - L), L);
     if (L > 0) seglist[sb + __popc(ne & lt)] = p;
     if (L > 32) biglist[bb + __popc(big & lt)] = p;
+    if (L > FLOW_THREAD_MAX && L <= 32) medlist[mb + __popc(med & lt)] = p;
   }
 }
 
@@ -367,6 +379,7 @@ struct FlowArgs {
   const int2* seg;
   const int* seglist;
   const int* biglist;
+  const int* medlist;
   unsigned long long* member;
   double* s;
   double* c;
@@ -413,13 +426,12 @@ NNS_DEV int warp_serve(const FlowArgs& A, int i, double& s, unsigned long long k
   double myf = 0.0, mycn = 0.0;
   int served = 0;
   for (int l = 0; l < cnt; ++l) {
-    if (!(s > 0.0)) break;
-    const double cl = __shfl_sync(0xffffffffu, c, l);
-    const double f = s < cl ? s : cl;
-    s = __dsub_rn(s, f);
+    if (!residual_positive(s)) break;
+    double cl = __shfl_sync(0xffffffffu, c, l);
+    const double f = greedy_step(s, cl);
     if (lane == l) {
       myf = f;
-      mycn = __dsub_rn(cl, f);
+      mycn = cl;
     }
     served = l + 1;
   }
@@ -444,14 +456,110 @@ NNS_DEV int warp_serve(const FlowArgs& A, int i, double& s, unsigned long long k
   return served;
 }
 
+// One thread: sort the group's keys (distance bits, position) ascending in
+// registers, walk them with the supplier's residual, write the flows.
+NNS_DEV void thread_serve(const FlowArgs& A, int p, int2 sg, bool active) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long key[FLOW_THREAD_MAX];
+#pragma unroll
+  for (int k = 0; k < FLOW_THREAD_MAX; ++k) key[k] = (active && k < sg.y) ? A.member[sg.x + k] : ~0ULL;
+  // insertion network over the fixed-size array (padding ~0 stays last)
+#pragma unroll
+  for (int a = 1; a < FLOW_THREAD_MAX; ++a)
+#pragma unroll
+    for (int b = a; b > 0; --b) {
+      const unsigned long long lo = key[b - 1], hi = key[b];
+      key[b - 1] = lo < hi ? lo : hi;
+      key[b] = lo < hi ? hi : lo;
+    }
+  int i = 0;
+  double s = 0.0;
+  int jv[FLOW_THREAD_MAX];
+  double cv[FLOW_THREAD_MAX];
+  if (active) {
+    i = A.ia[p];
+    s = A.s[i];
+  }
+#pragma unroll
+  for (int k = 0; k < FLOW_THREAD_MAX; ++k) {
+    jv[k] = 0;
+    cv[k] = 0.0;
+    if (active && k < sg.y) {
+      jv[k] = A.ja[(int)(key[k] & 0xffffffffULL)];
+      cv[k] = A.c[jv[k]];
+    }
+  }
+  double fv[FLOW_THREAD_MAX];
+  int served = 0;
+  bool live = active;
+#pragma unroll
+  for (int k = 0; k < FLOW_THREAD_MAX; ++k) {
+    fv[k] = 0.0;
+    if (live && k < sg.y) {
+      if (!residual_positive(s)) {
+        live = false;
+      } else {
+        fv[k] = greedy_step(s, cv[k]);
+        served = k + 1;
+      }
+    }
+  }
+  // plan slots: one atomic per warp
+  int incl = served;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  unsigned long long base = 0;
+  if (lane == 31 && incl) base = atomicAdd(&A.st->nnz, (unsigned long long)incl);
+  base = __shfl_sync(0xffffffffu, base, 31) + (unsigned long long)(incl - served);
+  if (!active) return;
+  const float* xi = A.x + (size_t)i * A.d;
+#pragma unroll
+  for (int k = 0; k < FLOW_THREAD_MAX; ++k) {
+    if (k < served) {
+      const int j = jv[k];
+      A.c[j] = cv[k];
+      const double Dij = cost_dist64(xi, A.y + (size_t)j * A.d, A.d, A.metric);
+      const unsigned long long slot = base + k;
+      A.terms[slot] = __dmul_rn(fv[k], Dij);
+      if (A.plan_i) {
+        if ((long long)slot < A.plan_cap) {
+          A.plan_i[slot] = i;
+          A.plan_j[slot] = j;
+          A.plan_f[slot] = fv[k];
+        } else {
+          atomicOr(&A.st->err, EF_CAPACITY);
+        }
+      }
+    }
+  }
+  A.s[i] = s;
+}
+
+// Groups of at most 32 consumers.  Each warp takes 32 groups of the group
+// list at a time and serves those of at most FLOW_THREAD_MAX one per lane;
+// then the warps serve the groups of 9..32 one per warp.
 __global__ void k_flow_small(FlowArgs A) {
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
+  const int warp = blockIdx.x * wpb + (threadIdx.x >> 5), nwarps = gridDim.x * wpb;
   const int nseg = A.st->nseg;
-  for (int w = blockIdx.x * wpb + (threadIdx.x >> 5); w < nseg; w += gridDim.x * wpb) {
-    const int p = A.seglist[w];
+  for (int w0 = warp * 32; w0 < nseg; w0 += nwarps * 32) {
+    const int w = w0 + lane;
+    int p = -1;
+    int2 sg = make_int2(0, 0);
+    if (w < nseg) {
+      p = A.seglist[w];
+      sg = A.seg[p];
+    }
+    thread_serve(A, p, sg, p >= 0 && sg.y <= FLOW_THREAD_MAX);
+  }
+  const int nmed = A.st->nmed;
+  for (int w = warp; w < nmed; w += nwarps) {
+    const int p = A.medlist[w];
     const int2 sg = A.seg[p];
-    if (sg.y > 32) continue;
     unsigned long long key = lane < sg.y ? A.member[sg.x + lane] : ~0ULL;
     key = warp_sort_u64(key);
     const int i = A.ia[p];
@@ -535,6 +643,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_flow_big(FlowArgs A) {
 __global__ void k_round_reset(DevState* st) {
   st->nseg = 0;
   st->nbig = 0;
+  st->nmed = 0;
   st->seg_cursor = 0;
 }
 
@@ -542,11 +651,11 @@ int launch_big_round(SolveBufs& B, int mt, int nt, cudaStream_t st) {
   const int cur = B.cur;
   k_round_reset<<<1, 1, 0, st>>>(B.st);
   k_group_count<<<(nt + 255) / 256, 256, 0, st>>>(B.nnkey, nt, mt, B.cnt, &B.st->err);
-  k_group_alloc<<<(mt + 255) / 256, 256, 0, st>>>(B.cnt, mt, B.seg, B.seglist, B.biglist, B.st);
+  k_group_alloc<<<(mt + 255) / 256, 256, 0, st>>>(B.cnt, mt, B.seg, B.seglist, B.biglist, B.medlist, B.st);
   k_group_scatter<<<(nt + 255) / 256, 256, 0, st>>>(B.nnkey, nt, B.cnt, B.seg, B.member);
-  FlowArgs F{B.x, B.y, B.d, B.metric, B.ia[cur], B.ja[cur], B.seg, B.seglist, B.biglist, B.member,
+  FlowArgs F{B.x, B.y, B.d, B.metric, B.ia[cur], B.ja[cur], B.seg, B.seglist, B.biglist, B.medlist, B.member,
              B.s, B.c, B.terms, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, B.st};
-  int warps = (nt + 31) / 32;
+  int warps = (nt + 31) / 32;  // each warp takes 32 groups at a time; groups <= nt
   int blocks = (warps + 7) / 8;
   if (blocks > 152 * 16) blocks = 152 * 16;
   k_flow_small<<<blocks, 256, 0, st>>>(F);

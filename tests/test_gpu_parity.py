@@ -72,7 +72,7 @@ def test_single_pair_256_d2(ctx):
     assert_parity(gpu_solve(ctx, p.x, p.a, p.y, p.b, "l2"), ref)
 
 
-@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 8])
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("metric", ["l2", "sql2", "l1"])
 def test_random_pairs_all_d(ctx, d, metric):
     rng = np.random.default_rng(100 + d)
@@ -89,6 +89,18 @@ def test_multi_round_colour_clusters(ctx):
     p = wl.color_transfer(seed=3, n=20011)
     ref = oracle.solve_pair(p, "sql2")
     assert_parity(gpu_solve(ctx, p.x, p.a, p.y, p.b, "sql2"), ref)
+
+
+@pytest.mark.parametrize("ratio", [4, 12, 25, 60])
+def test_group_sizes_in_multi_cta_rounds(ctx, ratio):
+    # n / m consumers per supplier on average: groups of a few (one thread
+    # each), of 9..32 (one warp each) and beyond 32 (one CTA each) in the
+    # multi-CTA rounds
+    n = 6000
+    p = wl.uniform_pair(n // ratio, n, 2, 1000 + ratio, "dirichlet")
+    for metric in ("l2", "sql2"):
+        ref = oracle.solve_pair(p, metric)
+        assert_parity(gpu_solve(ctx, p.x, p.a, p.y, p.b, metric), ref)
 
 
 def test_zero_weights_and_duplicates(ctx):
