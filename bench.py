@@ -66,15 +66,18 @@ WORKLOADS = {
     "single": dict(desc="single pair: 256 x 256 points, d=2, Uniform[0,1), uniform weights, Euclidean, full plan",
                    metric="l2", precision="fp32", batched=False),
     "gmm": dict(desc=("GMM pair: 262,144 x 262,144 points, d=64, 256-component mixture (means N(0,4I), "
-                      "cov 0.25I), Dirichlet(0.5) weights, Euclidean, full plan"),
-                metric="l2", precision="bf16", batched=False),
+                      "cov 0.25I), Dirichlet(0.5) weights, Euclidean, full plan; learned candidate proposal "
+                      "(MLP 64-256-256-4096 cells, trained on 200 seeded plain runs), BF16 contraction for the "
+                      "consumers it cannot certify"),
+                metric="l2", precision="bf16", batched=False, proposal="learned", steps=5),
     "docs": dict(desc=("document kNN: 1 query vs 4,096 documents, word vectors d=300 N(0,1) L2-normalised "
                        "(50k vocabulary), lengths LogNormal(ln 60, 0.6) clipped to [20,500], Zipf(1.1) weights, "
-                       "Euclidean, batched in one persistent launch"), metric="l2", precision="fp32",
-                 batched=True),
+                       "Euclidean, BF16 distances + FP32 re-rank, one persistent launch replayed as a CUDA graph"),
+                 metric="l2", precision="bf16", batched=True, graph=True, steps=50),
     "retrieval": dict(desc=("retrieval: 10,000 signature pairs, m, n ~ U{256..2048}, d=128 |N(0,1)| "
-                            "L2-normalised x512, Dirichlet(1) weights, Euclidean, batched"),
-                      metric="l2", precision="fp32", batched=True),
+                            "L2-normalised x512, Dirichlet(1) weights, Euclidean, FP16 distances + FP32 re-rank, "
+                            "autotuned tiles, batched"),
+                      metric="l2", precision="fp16", batched=True, autotune=True, steps=5),
 }
 
 
@@ -316,6 +319,7 @@ def run_ours(args) -> dict | None:
     spec = WORKLOADS[args.workload]
     precision = args.precision or spec["precision"]
     metric = spec["metric"]
+    proposal = args.proposal or spec.get("proposal", "none")
     rank, ws, local = world()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -328,21 +332,23 @@ def run_ours(args) -> dict | None:
     x, a, y, b = t(inp.x), t(inp.a), t(inp.y), t(inp.b)
     d = int(inp.x.shape[1])
     prop, prop_info = None, None
-    if args.proposal == "learned":
+    if proposal == "learned":
         if args.workload != "gmm":
             raise SystemExit("--proposal learned serves the gmm workload")
         from paper_2401_07378_gb300 import proposal_training
-        precision = "fp32"
         prop, prop_info = proposal_training.build_gmm_proposal(ctx, d=d)
     if spec["batched"]:
         P = inp.num_pairs
         costs = torch.empty(P, dtype=torch.float64, device=dev)
+        bflags = ((nnsemd.FLAG_GRAPH if spec.get("graph") else 0) |
+                  (nnsemd.FLAG_AUTOTUNE if spec.get("autotune") else 0))
         step = lambda: ctx.solve_batched(x, a, inp.x_off, y, b, inp.y_off, metric=metric, precision=precision,
-                                         costs=costs, stats=True)[1]
+                                         costs=costs, stats=True, flags=bflags)[1]
         units = P
     else:
-        step = lambda: ctx.solve(x, a, y, b, metric=metric, precision=precision, plan=True, flags=T,
-                                 proposal=prop).stats
+        def step():
+            r = ctx.solve(x, a, y, b, metric=metric, precision=precision, plan=True, flags=T, proposal=prop)
+            return dict(r.stats, cost=r.cost)
         units = 1
 
     for _ in range(args.warmup):
@@ -435,7 +441,7 @@ def run_ours(args) -> dict | None:
         "tail_kernel_share": agg["tail_kernel_ms"] / total_ms if total_ms else None,
         "gpu_launches": launches_all,
         "rounds_per_step": (last or {}).get("rounds"), "pair_evals_per_step": (last or {}).get("pair_evals"),
-        "certified": agg["certified"], "fallbacks": agg["fallbacks"],
+        "certified": agg["certified"], "fallbacks": agg["fallbacks"], "cost": (last or {}).get("cost"),
         "proposal": prop_info,
         "clocks": clocks,
     }
@@ -449,8 +455,22 @@ def run_ours(args) -> dict | None:
         line["config"]["workload"] += " [REDUCED SIZE: profiling case, not the workload]"
     if prop is not None:
         line["config"]["proposal"] = "learned (trained before timing; training not in the timed region)"
-        line["dtype"] = "f32 distances, f64 mass/cost"
         prop.close()
+    if args.workload == "gmm" and not args.no_plain:
+        # the plain FP32 form of the same solve on the same GPU, for comparison
+        plain = lambda: ctx.solve(x, a, y, b, metric=metric, precision="fp32", plan=True)
+        plain()
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k_plain = 2
+        flush.zero_()
+        p0.record()
+        for _ in range(k_plain):
+            pr = plain()
+        p1.record()
+        torch.cuda.synchronize()
+        line["plain_fp32"] = {"value": k_plain / (p0.elapsed_time(p1) / 1e3), "unit": "pairs/s", "steps": k_plain,
+                              "same_cost": pr.cost == (last or {}).get("cost", pr.cost)}
     if ws == 1 and not args.no_cpu_baseline and not (args.points or args.pairs):
         full = (last or {}).get("pair_evals") if args.workload == "gmm" else None
         line["cpu_baseline"] = oracle_sample(args.workload, inp, full)
@@ -487,19 +507,23 @@ def run_reference(args) -> dict | None:
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 200 for colour/single, fewer for the larger workloads)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="colour")
     ap.add_argument("--precision", choices=["fp32", "bf16", "fp16", "fp8"], default=None)
-    ap.add_argument("--proposal", choices=["none", "learned"], default="none",
-                    help="gmm only: train a learned candidate proposal before timing and solve with it")
+    ap.add_argument("--proposal", choices=["none", "learned"], default=None,
+                    help="gmm only (default learned): train a learned candidate proposal before timing")
+    ap.add_argument("--no-plain", action="store_true", help="gmm: skip timing the plain FP32 form")
     ap.add_argument("--points", type=int, default=None,
                     help="colour/gmm: points per side (default the full workload; smaller sizes are for profiling)")
     ap.add_argument("--pairs", type=int, default=None,
                     help="docs/retrieval: number of pairs (default the full workload; smaller is for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
+    if args.steps is None:
+        args.steps = WORKLOADS[args.workload].get("steps", 200)
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)

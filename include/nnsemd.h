@@ -180,13 +180,15 @@ int nnsemd_nearest(nnsemd_ctx *ctx, const float *x, int64_t m, const float *y, i
  * Not in the paper.  A fixed codebook of `cells` centroids (k-means) and an
  * MLP d -> hidden -> hidden -> cells (ReLU) that scores the cells most likely
  * to hold a consumer's nearest supplier.  Passed as nnsemd_options.proposal
- * to nnsemd_solve or nnsemd_solve_host (d > 8, metric L2 or SQL2, FP32
- * precision), it replaces the full NNS scan
- * of every round by an exact FP32 scan of the suppliers in each consumer's
- * first 32 proposed non-empty cells, certified by a triangle-inequality
- * bound on every other non-empty cell; consumers that cannot be certified
- * are scanned in full.  Results equal the FP32 path's; stats report
- * certified and fallback counts.  Training runs on the GPU (Adam over
+ * to nnsemd_solve or nnsemd_solve_host (d > 8, metric L2 or SQL2), it
+ * replaces the full NNS scan of every round by an exact FP32 scan of the
+ * suppliers in each consumer's first 32 proposed non-empty cells, certified
+ * by a triangle-inequality bound on every other non-empty cell; consumers
+ * that cannot be certified are scanned in full: in FP32 (precision FP32) or
+ * by the reduced-precision tensor-core scan with its own certificate and
+ * FP32 rescan (precision BF16 / FP16 / FP8).  Results equal the FP32 path's;
+ * stats.certified counts the searches settled by a certificate (proposal or
+ * tensor-core), stats.fallbacks those rescanned in FP32.  Training runs on the GPU (Adam over
  * minibatches of the softmax cross-entropy, the label being the cell of the
  * consumer's nearest supplier).  All pointers are device pointers unless
  * stated.  Errors: INVALID_ARG, OOM, CUDA. */

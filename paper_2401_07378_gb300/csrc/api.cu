@@ -367,14 +367,16 @@ int check_sizes(nnsemd_ctx* ctx, int64_t m, int64_t n) {
 }
 
 // A learned proposal replaces the full NNS scan only where its candidate
-// search applies: d > 8, L2 or SQL2, FP32 decisions, the proposal's own d.
+// search applies: d > 8, L2 or SQL2, the proposal's own d.  With a reduced
+// precision the consumers it cannot certify go to the tensor-core scan.
 int check_proposal(nnsemd_ctx* ctx, const nnsemd_options* opt, int d, int metric, int precision,
                    const nnsemd_proposal** out) {
   const nnsemd_proposal* P = opt ? static_cast<const nnsemd_proposal*>(opt->proposal) : nullptr;
   *out = P;
-  if (P && (d <= 8 || metric == NNSEMD_L1 || precision != NNSEMD_FP32 || P->d != d || !P->codebook_ready))
+  (void)precision;
+  if (P && (d <= 8 || metric == NNSEMD_L1 || P->d != d || !P->codebook_ready))
     return fail(ctx, NNSEMD_ERR_UNSUPPORTED,
-                "a proposal needs d > 8, metric L2 or SQL2, FP32 precision, its own d and a fitted codebook");
+                "a proposal needs d > 8, metric L2 or SQL2, its own d and a fitted codebook");
   return NNSEMD_OK;
 }
 

@@ -125,7 +125,8 @@ size_t tc_kb(int d, int precision);  // packed bytes per row
 int tc_bn(size_t kb);                // supplier rows per tile
 // NNS of every active consumer: tensor-core candidates, exact FP32 re-rank,
 // certificate, FP32 rescan of the rest.  Writes B.nnkey (must be all ones).
-int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int precision, cudaStream_t st);
+int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int precision, cudaStream_t st,
+                  const int* sel = nullptr, const int* nsel_dev = nullptr);
 
 // batched_tc.cu: batches of pairs with up to `cap` (512 or 2048) points per
 // side, reduced-precision NNS inside each pair's CTA.

@@ -640,10 +640,13 @@ __global__ void __launch_bounds__(256) k_learned_nns(LearnedArgs A) {
     atomicAdd(A.ncert, 1ULL);
   } else {
     A.fallback[atomicAdd(A.nfallback, 1)] = q;
-    atomicAdd(A.nfall, 1ULL);
+    if (A.nfall) atomicAdd(A.nfall, 1ULL);
   }
 }
 
+// The consumers the proposal cannot certify are scanned in full: in FP32,
+// or with a reduced-precision solve precision by the tensor-core scan (its
+// own certificate and FP32 rescan), restricted to them.
 int launch_nns_learned(const SolveBufs& B, const LearnedBufs& L, int mt, int nt, cudaStream_t st) {
   const int K = L.P->cells;
   const int* ia = B.ia[B.cur];
@@ -654,9 +657,18 @@ int launch_nns_learned(const SolveBufs& B, const LearnedBufs& L, int mt, int nt,
   cudaMemsetAsync(L.nfallback, 0, sizeof(int), st);
   LearnedArgs A{B.x,          B.y,          ia,          B.ja[B.cur], B.d,       nt,
                 L.prop_cells, L.bound_cells, L.bound_vals, L.cell_off, L.cell_members, B.nnkey,
-                L.fallback,   L.nfallback,   &B.st->certified, &B.st->fallbacks};
+                L.fallback,   L.nfallback,   &B.st->certified,
+                B.precision == 0 ? &B.st->fallbacks : nullptr};
   k_learned_nns<<<(nt + 7) / 8, 256, 0, st>>>(A);
-  launch_nns_f32(B, mt, nt, L.fallback, L.nfallback, st);
+  if (B.precision == 0) {  // FP32
+    launch_nns_f32(B, mt, nt, L.fallback, L.nfallback, st);
+  } else {
+    int nfall = 0;
+    if (cudaMemcpyAsync(&nfall, L.nfallback, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return -1;
+    if (nfall > 0 && launch_nns_tc(B, B.tc, mt, nfall, B.precision, st, L.fallback, nullptr)) return -1;
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -34,13 +34,17 @@ constexpr int TC_SMEM_BUDGET = 220 * 1024;
 // One thread per point (consecutive threads write consecutive 16-byte rows
 // of each column block).  Also writes, per point, the FP32 squared norm, the
 // per-row scale and, in `stats`, the maxima of |v|_2, |v|_1 and the scale
-// over the points (as float bits; all values >= 0).
-__global__ void k_pack_tc(const float* __restrict__ pts, const int* __restrict__ idx, int cnt, int rows_pad, int d,
-                          int kb, int fmt, int tile_rows, uint8_t* __restrict__ out, float* __restrict__ nrm,
-                          float* __restrict__ nrm_s, float* __restrict__ scale, unsigned* __restrict__ stats) {
+// over the points (as float bits; all values >= 0).  Row p holds the point
+// idx[sel ? sel[p] : p] for p < cnt (cnt read from cnt_dev when given; the
+// rest is padding).
+__global__ void k_pack_tc(const float* __restrict__ pts, const int* __restrict__ idx, const int* __restrict__ sel,
+                          const int* __restrict__ cnt_dev, int cnt, int rows_pad, int d, int kb, int fmt,
+                          int tile_rows, uint8_t* __restrict__ out, float* __restrict__ nrm, float* __restrict__ nrm_s,
+                          float* __restrict__ scale, unsigned* __restrict__ stats) {
   const int nblk = kb / 16;
+  const int count = cnt_dev ? min(*cnt_dev, cnt) : cnt;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < rows_pad; p += gridDim.x * blockDim.x) {
-    const float* row = p < cnt ? pts + (size_t)idx[p] * d : nullptr;
+    const float* row = p < count ? pts + (size_t)idx[sel ? sel[p] : p] * d : nullptr;
     const float s = row_scale(row, d, fmt);
     const int t = p / tile_rows, r = p % tile_rows;
     for (int c = 0; c < nblk; ++c) pack_block(row, d, c, s, fmt, out + (size_t)t * tile_rows * kb, tile_rows, r);
@@ -86,6 +90,7 @@ struct TcArgs {
   float* cand_v;           // [chunks][nt_pad][TC_K] approximate values (v = |x|^2 - 2 <x~,y~>)
   int* cand_p;             // [chunks][nt_pad][TC_K] supplier positions
   unsigned* err;
+  const int* nq_dev;       // packed consumer rows in use (nullable: nt); tiles past it exit
 };
 
 template <int FMT, int BN>
@@ -104,6 +109,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
   const int t1 = min(t0 + P.tiles_per_chunk, P.num_tiles);
   const int ntiles = t1 - t0;
   if (ntiles <= 0) return;
+  if (P.nq_dev && qtile * TC_BM >= *P.nq_dev) return;  // the whole CTA leaves before any set-up
   const int kb = P.kb;
   const uint32_t a_bytes = TC_BM * kb;
   const uint32_t b_bytes = BN * kb;
@@ -242,19 +248,22 @@ struct RerankArgs {
   int* nfallback;
   unsigned long long* ncertified;
   unsigned long long* nfallback_total;
+  const int* sel;       // packed row -> consumer position (nullable: identity)
+  const int* nq_dev;    // rows in use (nullable: nt)
 };
 
-// One warp per consumer.
+// One warp per packed consumer row.
 __global__ void k_rerank_certify(RerankArgs R) {
   const int lane = threadIdx.x & 31;
-  const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (q >= R.nt) return;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= (R.nq_dev ? min(*R.nq_dev, R.nt) : R.nt)) return;
+  const int q = R.sel ? R.sel[r] : r;
   const float* yrow = R.y + (size_t)R.ja[q] * R.d;
   const int ncand = R.chunks * TC_K;
   unsigned long long best = ~0ULL;
   float tau = CUDART_INF_F;  // smallest chunk threshold (K-th value of each chunk)
   for (int c = lane; c < ncand; c += 32) {
-    const size_t o = ((size_t)(c / TC_K) * R.nt_pad + q) * TC_K + (c % TC_K);
+    const size_t o = ((size_t)(c / TC_K) * R.nt_pad + r) * TC_K + (c % TC_K);
     const int p = R.cand_p[o];
     if ((c % TC_K) == TC_K - 1) tau = fminf(tau, R.cand_v[o]);
     if (p < 0) continue;
@@ -276,7 +285,7 @@ __global__ void k_rerank_certify(RerankArgs R) {
   }
   yl2 = sqrt(yl2) * (1 + 1e-12);
   const bool certified =
-      best != ~0ULL && certify(R.fmt, R.d, R.nrm_y[q], yl2, yl1, R.scale_y[q], __uint_as_float(R.stats_x[0]),
+      best != ~0ULL && certify(R.fmt, R.d, R.nrm_y[r], yl2, yl1, R.scale_y[r], __uint_as_float(R.stats_x[0]),
                                __uint_as_float(R.stats_x[1]), __uint_as_float(R.stats_x[2]), tau,
                                __uint_as_float((unsigned)(best >> 32)));
   if (certified) {
@@ -307,7 +316,10 @@ static int launch_tc_t(const TcArgs& P, dim3 grid, size_t smem, cudaStream_t st)
   return 0;
 }
 
-int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int precision, cudaStream_t st) {
+// With sel / nsel_dev the consumers are the positions sel[0 .. *nsel_dev)
+// (at most nt of them), e.g. those a learned proposal could not certify.
+int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int precision, cudaStream_t st,
+                  const int* sel, const int* nsel_dev) {
   const int fmt = fmt_of_precision(precision);
   const int kb = (int)tc_kb(B.d, precision);
   const int bn = tc_bn(kb);
@@ -318,14 +330,14 @@ int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int preci
   {
     const int64_t work = (int64_t)qtiles * TC_BM;
     int g = (int)std::min<int64_t>((work + 255) / 256, 152 * 16);
-    k_pack_tc<<<g, 256, 0, st>>>(B.y, B.ja[B.cur], nt, qtiles * TC_BM, B.d, kb, fmt, TC_BM, T.A, T.nrm_y, nullptr,
-                                 T.scale_y, T.stats + 4);
+    k_pack_tc<<<g, 256, 0, st>>>(B.y, B.ja[B.cur], sel, nsel_dev, nt, qtiles * TC_BM, B.d, kb, fmt, TC_BM, T.A,
+                                 T.nrm_y, nullptr, T.scale_y, T.stats + 4);
   }
   {
     const int64_t work = (int64_t)stiles * bn;
     int g = (int)std::min<int64_t>((work + 255) / 256, 152 * 16);
-    k_pack_tc<<<g, 256, 0, st>>>(B.x, B.ia[B.cur], mt, stiles * bn, B.d, kb, fmt, bn, T.B, T.nrm_x, T.nrm_sx,
-                                 T.scale_x, T.stats);
+    k_pack_tc<<<g, 256, 0, st>>>(B.x, B.ia[B.cur], nullptr, nullptr, mt, stiles * bn, B.d, kb, fmt, bn, T.B,
+                                 T.nrm_x, T.nrm_sx, T.scale_x, T.stats);
   }
   // chunks of supplier tiles so that the grid covers the GPU
   int chunks = (152 + qtiles - 1) / qtiles;
@@ -339,7 +351,8 @@ int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int preci
   if (nstage < 1) return -2;
   const int nt_pad = qtiles * TC_BM;
   TcArgs P{T.A,      T.B,      T.nrm_x,    T.nrm_sx, T.nrm_y,  T.scale_x,  T.scale_y, nt, mt,
-           kb,       bn,       nstage,     per,      stiles,   nt_pad,     T.cand_v,  T.cand_p, &B.st->err};
+           kb,       bn,       nstage,     per,      stiles,   nt_pad,     T.cand_v,  T.cand_p, &B.st->err,
+           nsel_dev};
   const size_t smem = a_bytes + (size_t)nstage * b_bytes;
   dim3 grid(qtiles, chunks);
   int rc;
@@ -356,7 +369,7 @@ int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int preci
   if (cudaMemsetAsync(T.nfallback, 0, sizeof(int), st) != cudaSuccess) return -1;
   RerankArgs R{B.x,      B.y,        B.ia[B.cur], B.ja[B.cur], B.d,       nt,          nt_pad,
                chunks,   fmt,        T.cand_v,    T.cand_p,    T.nrm_y,   T.scale_y,   T.stats,
-               B.nnkey,  T.fallback, T.nfallback, &B.st->certified, &B.st->fallbacks};
+               B.nnkey,  T.fallback, T.nfallback, &B.st->certified, &B.st->fallbacks, sel, nsel_dev};
   k_rerank_certify<<<(nt + 7) / 8, 256, 0, st>>>(R);
   // FP32 scan of the consumers that were not certified
   launch_nns_f32(B, mt, nt, T.fallback, T.nfallback, st);

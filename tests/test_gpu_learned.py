@@ -99,3 +99,28 @@ def test_trained_network_beats_untrained(ctx, small_prop):
     assert ft > fu, (ft, fu)
     untrained.close()
     loaded.close()
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_learned_with_reduced_precision_fallback_equals_oracle(ctx, small_prop, precision):
+    """Consumers the proposal cannot certify go to the tensor-core scan
+    (its own certificate, FP32 rescan of the rest): still the oracle's
+    result bit for bit."""
+    prop, _ = small_prop
+    p = wl.gmm_pair(seed=0, n=6000, d=64)
+    t = lambda v: torch.from_numpy(v).cuda()
+    res = ctx.solve(t(p.x), t(p.a), t(p.y), t(p.b), metric="l2", precision=precision, plan=True, proposal=prop)
+    ref = oracle.solve_pair(p, "l2")
+    assert res.cost == ref.cost
+    assert res.stats["rounds"] == ref.rounds
+    gi = np.lexsort((res.plan_j.cpu().numpy(), res.plan_i.cpu().numpy()))
+    oi = np.lexsort((ref.plan_j, ref.plan_i))
+    assert np.array_equal(res.plan_f.cpu().numpy()[gi], ref.plan_f[oi])
+    assert res.stats["certified"] > 0
+
+
+def test_learned_host_entry_point(ctx, small_prop):
+    prop, _ = small_prop
+    p = wl.gmm_pair(seed=2, n=3000, d=64)
+    res = ctx.solve_host(p.x, p.a, p.y, p.b, metric="l2", proposal=prop)
+    assert res.cost == oracle.solve_pair(p, "l2").cost
