@@ -80,6 +80,18 @@ struct CtaOut {
   double* s_glob;                // residual write-back by original index (nullable)
   double* c_glob;
   unsigned* err;
+  // Deferred costing (fl_i nullable): every flow's original (i, j, f) is
+  // recorded in fl_* (global, slot = running flow count) during the rounds,
+  // and the cost terms and plan entries of all of them are computed in one
+  // pass after the last round from the original coordinates x, y (row
+  // stride d).  The FP64 distance chain then costs its latency once per
+  // solve instead of once per round.
+  int32_t* fl_i;
+  int32_t* fl_j;
+  double* fl_f;
+  const float* x;
+  const float* y;
+  int d;
 };
 
 // --------------------------------------------------------------------------
@@ -344,6 +356,7 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
                         long long& rounds, long long& pair_evals, long long round_limit) {
   const int tid = threadIdx.x;
   const int T = blockDim.x;
+  const unsigned long long nnz0 = nnz;
   for (;;) {
     const int mt = S.mt, nt = S.nt;
     if (mt == 0 || nt == 0) break;
@@ -383,8 +396,10 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
     }
     __syncthreads();
     // ---- flow (greedy protocol), one supplier per thread: the residual
-    // chain only; each flow (p, q) and f is recorded in mem / nnk, which are
-    // free after the ordering step (every consumer flows at most once)
+    // chain only; each flow is recorded (deferred costing: its original
+    // indices and f in O.fl_*; otherwise (p, q) and f in mem / nnk, which are
+    // free after the ordering step; every consumer flows at most once)
+    const bool deferred = O.fl_i != nullptr;
     for (int p = tid; p < mt; p += T) {
       const int b = S.off[p], en = S.off[p + 1];
       if (b == en) continue;
@@ -396,8 +411,16 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
         const double f = greedy_step(s, c);
         S.cres[q] = c;
         const unsigned k = atomicAdd(&S.nflow, 1u);
-        S.mem[k] = ((unsigned long long)p << 32) | (unsigned)q;
-        S.nnk[k] = (unsigned long long)__double_as_longlong(f);
+        if (deferred) {
+          const unsigned long long slot = nnz + k;
+          O.fl_i[slot] = S.iidx[p];
+          O.fl_j[slot] = S.jidx[q];
+          O.fl_f[slot] = f;
+          if (O.c_glob) O.c_glob[S.jidx[q]] = c;
+        } else {
+          S.mem[k] = ((unsigned long long)p << 32) | (unsigned)q;
+          S.nnk[k] = (unsigned long long)__double_as_longlong(f);
+        }
       }
       S.sres[p] = s;
       if (O.s_glob) O.s_glob[S.iidx[p]] = s;
@@ -405,7 +428,7 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
     __syncthreads();
     // ---- cost terms and plan entries of the round's flows, one per thread
     const unsigned nflow = S.nflow;
-    for (unsigned k = tid; k < nflow; k += T) {
+    for (unsigned k = deferred ? nflow : tid; k < nflow; k += T) {
       const unsigned long long pq = S.mem[k];
       const int p = (int)(pq >> 32), q = (int)(pq & 0xffffffffULL);
       const double f = __longlong_as_double((long long)S.nnk[k]);
@@ -430,6 +453,26 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
     pair_evals += (long long)mt * nt;
     // ---- weights update: retire spent points, compact
     cta_compact(S, G);
+  }
+  if (O.fl_i) {
+    // deferred costing: the terms and plan entries of every flow of the loop
+    for (unsigned long long k = nnz0 + tid; k < nnz; k += T) {
+      const int i = O.fl_i[k], j = O.fl_j[k];
+      const double f = O.fl_f[k];
+      const double term = __dmul_rn(f, cost_dist64(O.x + (size_t)i * O.d, O.y + (size_t)j * O.d, O.d, metric));
+      if (O.terms) O.terms[k] = term;
+      if (O.acc) xs_add(O.acc, term);
+      if (O.plan_i) {
+        if ((long long)k < O.plan_cap) {
+          O.plan_i[k] = i;
+          O.plan_j[k] = j;
+          O.plan_f[k] = f;
+        } else {
+          atomicOr(O.err, EF_CAPACITY);
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 

@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_finish_hd(SolveBufs B, long 
     S.cres[q] = B.c[S.jidx[q]];
   }
   __syncthreads();
-  CtaOut O{B.terms, nullptr, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, B.s, B.c, &B.st->err};
+  CtaOut O{B.terms, nullptr, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, B.s, B.c, &B.st->err,
+           B.fl_i, B.fl_j, B.fl_f, B.x, B.y, B.d};
   unsigned long long nnz = B.st->nnz;
   long long rounds = B.st->rounds, pe = B.st->pair_evals;
   cta_rounds(S, H.G, B.metric, O, nnz, rounds, pe, round_limit);

@@ -62,6 +62,9 @@ struct SolveBufs {
   int* medlist;    // [m] groups of 9..32 consumers
   unsigned long long* member;  // [n] group members: key32 bits << 32 | consumer position
   double* terms;   // [m+n] per-flow cost terms f * D_ij
+  int32_t* fl_i;   // [m+n] flow record of the one-CTA rounds (deferred costing)
+  int32_t* fl_j;
+  double* fl_f;
   int* blockcounts;            // compaction scratch
   unsigned long long* xs_acc;  // 4 exact-sum accumulators of XS_LIMBS limbs
   DevState* st;

@@ -311,7 +311,8 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_finish(SolveBufs B, long lon
     S.nt = nt;
   }
   __syncthreads();
-  CtaOut O{B.terms, nullptr, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, B.s, B.c, &B.st->err};
+  CtaOut O{B.terms, nullptr, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, B.s, B.c, &B.st->err,
+           B.fl_i, B.fl_j, B.fl_f, B.x, B.y, B.d};
   unsigned long long nnz = B.st->nnz;
   long long rounds = B.st->rounds, pe = B.st->pair_evals;
   cta_rounds(S, L.G, B.metric, O, nnz, rounds, pe, round_limit);
@@ -368,7 +369,8 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_solve_small(SolveBufs B, con
   for (int i = tid; i < XS_LIMBS; i += blockDim.x) S.acc[i] = 0ULL;
   __syncthreads();
   cta_compact(S, L.G);  // drop zero weights
-  CtaOut O{nullptr, S.acc, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, nullptr, nullptr, &B.st->err};
+  CtaOut O{nullptr, S.acc, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, nullptr, nullptr, &B.st->err,
+           B.fl_i, B.fl_j, B.fl_f, B.x, B.y, B.d};
   unsigned long long nnz = 0;
   long long rounds = 0, pe = 0;
   cta_rounds(S, L.G, B.metric, O, nnz, rounds, pe, (long long)m + n);
