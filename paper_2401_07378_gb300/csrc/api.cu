@@ -144,8 +144,8 @@ size_t layout_solve(void* base, int64_t m, int64_t n, int d, SolveBufs& B, int p
     T.scale_x = C.take<float>(srows);
     T.scale_y = C.take<float>(qrows);
     T.stats = C.take<unsigned>(8);
-    T.max_chunks = 152;
-    const int64_t cand = (152 + qrows / 128) * 128 * 16;  // chunks x padded consumers x 16 candidates
+    T.max_chunks = TC_TARGET_CTAS;
+    const int64_t cand = (TC_TARGET_CTAS + qrows / 128) * 128 * 16;  // chunks x padded consumers x 16 candidates
     T.cand_v = C.take<float>(cand);
     T.cand_p = C.take<int>(cand);
     T.fallback = C.take<int>(n);

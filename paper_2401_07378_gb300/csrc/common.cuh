@@ -231,6 +231,18 @@ NNS_DEV bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned limit = 
   return false;
 }
 
+// The same for a thread that usually waits long (a pipeline role that is
+// not the bottleneck): after a short spin it sleeps between polls so that
+// it leaves the issue slots to the warps doing the work.  Gives up after
+// `limit` polls (about a second).
+NNS_DEV bool mbar_wait_backoff(uint64_t* bar, unsigned parity, unsigned limit = 1u << 22) {
+  for (unsigned it = 0; it < limit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (it >= 16) __nanosleep(128);
+  }
+  return false;
+}
+
 // Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from
 // global to this CTA's shared memory, completing on `bar`.
 NNS_DEV void tma_load_1d(void* dst_smem, const void* src_gmem, unsigned bytes, uint64_t* bar) {

@@ -12,6 +12,7 @@ namespace nnsemd {
 // packed active list is padded to (with NaN coordinates) so that a tile
 // never reads past its buffer.
 constexpr int K1_TS = 256;
+constexpr int TC_TARGET_CTAS = 152 * 4;  // K2 grid target (consumer tiles x supplier chunks)
 constexpr int PAD_POINTS = K1_TS;
 // Largest active set the single-CTA solver keeps in shared memory (d <= 8:
 // with coordinates; d > 8: per-point state only, coordinates stay in L2).

@@ -28,8 +28,11 @@
 
 namespace nnsemd {
 
-constexpr int TC_THREADS = 192;  // 6 warps
-constexpr int TC_SMEM_BUDGET = 220 * 1024;
+// warp 0 operand copies, warp 1 MMA, warp 2 column-norm copies, then the
+// epilogue warps (two per TMEM lane quarter)
+constexpr int TC_EPI_WARPS = 8;
+constexpr int TC_THREADS = 32 * (3 + TC_EPI_WARPS);
+constexpr int TC_SMEM_BUDGET = 180 * 1024;  // dynamic: A tile + B stages (static: norms, lists, staging)
 
 // One thread per point (consecutive threads write consecutive 16-byte rows
 // of each column block).  Also writes, per point, the FP32 squared norm, the
@@ -100,8 +103,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
   __shared__ __align__(8) uint64_t bar_empty[8];
   __shared__ __align__(8) uint64_t bar_acc_full[2];
   __shared__ __align__(8) uint64_t bar_acc_empty[2];
+  __shared__ __align__(8) uint64_t bar_nrm_full[2];
   __shared__ __align__(8) uint64_t bar_a;
   __shared__ uint32_t tmem_slot;
+  __shared__ __align__(16) float nrm_buf[2][3][BN];     // per accumulator: |x|^2, |x| rounded up, scale
+  __shared__ float merge_v[TC_K][TC_BM];                // second-half top-K lists, merged at the end
+  __shared__ int merge_p[TC_K][TC_BM];
+  __shared__ float stage[16][TC_EPI_WARPS * 32];         // per epilogue thread: one 16-column block
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int qtile = blockIdx.x;
@@ -118,6 +126,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
   const int NST = P.nstage;
   constexpr uint32_t NCOLS = 2 * BN;  // two accumulators
   constexpr uint32_t TMEM_ALLOC = NCOLS < 32 ? 32 : NCOLS;
+  constexpr uint32_t NRM_BYTES = 3 * BN * sizeof(float);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -126,7 +135,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&bar_acc_full[b], 1);
-      mbar_init(&bar_acc_empty[b], 4 * 32);
+      mbar_init(&bar_acc_empty[b], TC_EPI_WARPS * 32);
+      mbar_init(&bar_nrm_full[b], 1);
     }
     mbar_init(&bar_a, 1);
     mbar_fence_init();
@@ -139,13 +149,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
   bool ok = true;
 
   if (warp == 0) {
-    // ---------------- producer: TMA bulk copies ----------------
+    // ---------------- producer: TMA bulk copies of the operand tiles ----------------
     if (lane == 0) {
       mbar_expect_tx(&bar_a, a_bytes);
       tma_load_1d(sA, P.A + (size_t)qtile * a_bytes, a_bytes, &bar_a);
       for (int t = 0; t < ntiles && ok; ++t) {
         const int s = t % NST, u = t / NST;
-        ok = mbar_wait_bounded(&bar_empty[s], (u & 1) ^ 1);
+        ok = mbar_wait_backoff(&bar_empty[s], (u & 1) ^ 1);
         if (!ok) break;
         mbar_expect_tx(&bar_full[s], b_bytes);
         tma_load_1d(sB + (size_t)s * b_bytes, P.B + (size_t)(t0 + t) * b_bytes, b_bytes, &bar_full[s]);
@@ -162,8 +172,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
       for (int t = 0; t < ntiles && ok; ++t) {
         const int s = t % NST, u = t / NST;
         const int b = t & 1, v = t >> 1;
-        ok = mbar_wait_bounded(&bar_full[s], u & 1);
-        if (ok) ok = mbar_wait_bounded(&bar_acc_empty[b], (v & 1) ^ 1);
+        ok = mbar_wait_backoff(&bar_full[s], u & 1);
+        if (ok) ok = mbar_wait_backoff(&bar_acc_empty[b], (v & 1) ^ 1);
         if (!ok) break;
         tc_fence_after();
         const uint32_t b0 = smem_u32(sB + (size_t)s * b_bytes);
@@ -177,9 +187,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
         mma_commit(&bar_acc_full[b]);
       }
     }
+  } else if (warp == 2) {
+    // ---------------- producer: the column norms of each tile, per accumulator ----------------
+    if (lane == 0) {
+      for (int t = 0; t < ntiles && ok; ++t) {
+        const int b = t & 1, v = t >> 1;
+        ok = mbar_wait_backoff(&bar_acc_empty[b], (v & 1) ^ 1);
+        if (!ok) break;
+        const size_t col = (size_t)(t0 + t) * BN;
+        mbar_expect_tx(&bar_nrm_full[b], NRM_BYTES);
+        tma_load_1d(nrm_buf[b][0], P.nrm_x + col, BN * sizeof(float), &bar_nrm_full[b]);
+        tma_load_1d(nrm_buf[b][1], P.nrm_sx + col, BN * sizeof(float), &bar_nrm_full[b]);
+        tma_load_1d(nrm_buf[b][2], P.scale_x + col, BN * sizeof(float), &bar_nrm_full[b]);
+      }
+    }
   } else {
     // ---------------- epilogue: TMEM -> top-K per consumer ----------------
+    // Two warps per TMEM lane quarter; each takes half of the tile's columns
+    // and keeps its own top-K, and the halves merge at the end.
+    const int e = warp - 3;
+    const int etid = e * 32 + lane;
     const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+    const int half = e >> 2;
     const int row = quarter * 32 + lane;
     const int q = qtile * TC_BM + row;
     const float sy = (q < P.nt) ? P.scale_y[q] : 1.f;
@@ -188,36 +217,79 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
     int tp[TC_K];
 #pragma unroll
     for (int k = 0; k < TC_K; ++k) { tv[k] = CUDART_INF_F; tp[k] = -1; }
+    constexpr int HALF = BN / 2;
     for (int t = 0; t < ntiles; ++t) {
       const int b = t & 1, v = t >> 1;
       if (ok) ok = mbar_wait_bounded(&bar_acc_full[b], v & 1);
+      if (ok) ok = mbar_wait_bounded(&bar_nrm_full[b], v & 1);
       tc_fence_after();
       if (ok) {
         const int tile = t0 + t;
-        const float* nx = P.nrm_x + (size_t)tile * BN;
-        const float* ns = P.nrm_sx + (size_t)tile * BN;
-        const float* sx = P.scale_x + (size_t)tile * BN;
-        for (int c0 = 0; c0 < BN; c0 += 16) {
+        const float* nx = nrm_buf[b][0];
+        const float* ns = nrm_buf[b][1];
+        const float* sx = nrm_buf[b][2];
+        for (int c0 = half * HALF; c0 < (half + 1) * HALF; c0 += 16) {
           uint32_t r[16];
           tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c0), r);
+          float val[16];
+          float mn = CUDART_INF_F;
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const float acc = __uint_as_float(r[e]);
-            const float w = (FMT == FMT_BF16) ? -2.f : -2.f * sy * __ldg(sx + c0 + e);
-            const float val = __fmaf_rn(-cy, __ldg(ns + c0 + e), __fmaf_rn(w, acc, __ldg(nx + c0 + e)));
-            topk_insert(tv, tp, val, tile * BN + c0 + e);
+          for (int k = 0; k < 16; k += 4) {
+            const float4 vx = *reinterpret_cast<const float4*>(nx + c0 + k);
+            const float4 vs = *reinterpret_cast<const float4*>(ns + c0 + k);
+            const float4 vc = *reinterpret_cast<const float4*>(sx + c0 + k);
+            const float cx[4] = {vx.x, vx.y, vx.z, vx.w};
+            const float cs[4] = {vs.x, vs.y, vs.z, vs.w};
+            const float cc[4] = {vc.x, vc.y, vc.z, vc.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const float acc = __uint_as_float(r[k + j]);
+              const float w = (FMT == FMT_BF16) ? -2.f : -2.f * sy * cc[j];
+              val[k + j] = __fmaf_rn(-cy, cs[j], __fmaf_rn(w, acc, cx[j]));
+            }
+            mn = fmin3(mn, fminf(val[k], val[k + 1]), fminf(val[k + 2], val[k + 3]));
+          }
+          if (mn < tv[TC_K - 1]) {
+            // the few columns that beat the current K-th value: park the
+            // block's values, then one (rolled) insertion per such column
+            const float thr = tv[TC_K - 1];
+            unsigned msk = 0;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              msk |= (val[k] < thr ? 1u : 0u) << k;
+              stage[k][etid] = val[k];
+            }
+#pragma unroll 1
+            while (msk) {
+              const int k = __ffs(msk) - 1;
+              msk &= msk - 1;
+              topk_insert(tv, tp, stage[k][etid], tile * BN + c0 + k);
+            }
           }
         }
       }
       tc_fence_before();
       mbar_arrive(&bar_acc_empty[b]);
     }
-    if (q < P.nt) {
-      const size_t o = ((size_t)blockIdx.y * P.nt_pad + q) * TC_K;
+    // merge: the second-half warps hand their lists to the first-half warps
+    if (half == 1) {
 #pragma unroll
       for (int k = 0; k < TC_K; ++k) {
-        P.cand_v[o + k] = tv[k];
-        P.cand_p[o + k] = tp[k];
+        merge_v[k][row] = tv[k];
+        merge_p[k][row] = tp[k];
+      }
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(TC_EPI_WARPS * 32) : "memory");
+    if (half == 0) {
+#pragma unroll
+      for (int k = 0; k < TC_K; ++k) topk_insert(tv, tp, merge_v[k][row], merge_p[k][row]);
+      if (q < P.nt) {
+        const size_t o = ((size_t)blockIdx.y * P.nt_pad + q) * TC_K;
+#pragma unroll
+        for (int k = 0; k < TC_K; ++k) {
+          P.cand_v[o + k] = tv[k];
+          P.cand_p[o + k] = tp[k];
+        }
       }
     }
   }
@@ -339,8 +411,8 @@ int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int preci
     k_pack_tc<<<g, 256, 0, st>>>(B.x, B.ia[B.cur], nullptr, nullptr, mt, stiles * bn, B.d, kb, fmt, bn, T.B,
                                  T.nrm_x, T.nrm_sx, T.scale_x, T.stats);
   }
-  // chunks of supplier tiles so that the grid covers the GPU
-  int chunks = (152 + qtiles - 1) / qtiles;
+  // chunks of supplier tiles so that the grid covers the GPU several times
+  int chunks = (TC_TARGET_CTAS + qtiles - 1) / qtiles;
   if (chunks > stiles) chunks = stiles;
   if (chunks > T.max_chunks) chunks = T.max_chunks;
   const int per = (stiles + chunks - 1) / chunks;
