@@ -576,6 +576,16 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
     (fits ? small : large).push_back(p);
     if (fits) small_max = std::max(small_max, std::max(m, n));
   }
+  // FP32, d > 8: pairs of at most HD_SMALL_CAP points per side go to the
+  // 256-thread kernel (several pairs per SM); they come first in the list
+  int ntiny = 0;
+  if (!tc && d > 8) {
+    std::stable_partition(small.begin(), small.end(), [&](int p) {
+      return x_off[p + 1] - x_off[p] <= HD_SMALL_CAP && y_off[p + 1] - y_off[p] <= HD_SMALL_CAP;
+    });
+    for (int p : small)
+      if (x_off[p + 1] - x_off[p] <= HD_SMALL_CAP && y_off[p + 1] - y_off[p] <= HD_SMALL_CAP) ++ntiny;
+  }
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
   const int grid = (int)std::min<size_t>(small.size(), 152);
@@ -618,6 +628,7 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
   long long* pe_d = W.take<long long>(num_pairs);
   uint8_t* scratch = W.take<uint8_t>(tc ? slot * grid : 0);
   unsigned* q_d = reinterpret_cast<unsigned*>(ctr_d);
+  unsigned* q2_d = reinterpret_cast<unsigned*>(ctr_d + 3);  // queue of the 256-thread kernel
   CK(cudaMemcpyAsync(xo_d, x_off, (num_pairs + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(yo_d, y_off, (num_pairs + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
   if (!small.empty())
@@ -632,7 +643,22 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
                 costs_out, rounds_d, pe_d, q_d, q_d + 1};
     if (tc)
       return launch_batched_tc(A, precision, cap, kb, tbn, tns, scratch, slot, ctr_d + 1, ctr_d + 2, g, s);
-    return d <= 8 ? launch_batched_lowd(A, g, s) : launch_batched_hd(A, g, s);
+    if (d <= 8) return launch_batched_lowd(A, g, s);
+    int r = 0;
+    const int nbig = nsmall - ntiny;
+    if (nbig > 0) {
+      BatchArgs Ab = A;
+      Ab.pair_ids = ids_d + ntiny;
+      Ab.num = nbig;
+      r |= launch_batched_hd(Ab, std::min(nbig, 152), s);
+    }
+    if (ntiny > 0) {
+      BatchArgs At = A;
+      At.num = ntiny;
+      At.queue = q2_d;
+      r |= launch_batched_hd_small(At, std::min(ntiny, 152 * 4), s);
+    }
+    return r;
   };
   if (!small.empty() && tc && (flags & NNSEMD_FLAG_AUTOTUNE) && !ctx->tuned.count(tkey)) {
     // time every feasible (tile rows, stages) on a sample of the batch
@@ -670,7 +696,7 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
                                           (uintptr_t)b_packed, (uintptr_t)costs_out, (uintptr_t)ctx->ws,
                                           (uintptr_t)num_pairs, (uintptr_t)small.size(), (uintptr_t)d,
                                           (uintptr_t)metric, (uintptr_t)precision, (uintptr_t)cap, (uintptr_t)bn,
-                                          (uintptr_t)nstage};
+                                          (uintptr_t)nstage, (uintptr_t)ntiny};
       BatchGraph* g = nullptr;
       for (auto& e : ctx->graphs)
         if (e.key == key) g = &e;

@@ -83,6 +83,7 @@ struct BtcArgs {
 template <bool KIND8, int CAP>
 struct GeoTC {
   static constexpr int kDP = 0;
+  static constexpr int kThreads = FIN_THREADS;
   struct PX {};
   const float* x;  // this pair's coordinates
   const float* y;

@@ -101,6 +101,7 @@ struct CtaOut {
 template <int D, int DP, bool L1, int CAP>
 struct GeoSmem {
   static constexpr int kDP = DP;
+  static constexpr int kThreads = FIN_THREADS;  // threads of the CTA
   float xs[CAP * DP];
   float ys[CAP * DP];
   struct PX { float v[DP]; };
@@ -246,13 +247,14 @@ NNS_DEV void group_nns_tile(const float* __restrict__ x, const int* __restrict__
   }
 }
 
-template <bool L1, int CAP>
+template <bool L1, int CAP, int NT = FIN_THREADS>
 struct GeoGlobal {
   static constexpr int kDP = 0;
+  static constexpr int kThreads = NT;  // threads of the CTA (a multiple of TG_THREADS)
   const float* x;  // [m][d] original coordinates (global)
   const float* y;  // [n][d]
   int d;
-  TileSmem tiles[FIN_THREADS / TG_THREADS];
+  TileSmem tiles[NT / TG_THREADS];
   struct PX {};
   NNS_DEV void load_x(int, PX&) const {}
   NNS_DEV void store_x(int, const PX&) {}
@@ -292,7 +294,7 @@ struct GeoGlobal {
 // Stable compaction of both active lists to the points with weight left.
 template <int CAP, class Geo>
 NNS_DEV void cta_compact(CtaCore<CAP>& S, Geo& G) {
-  constexpr int IT = (CAP + FIN_THREADS - 1) / FIN_THREADS;
+  constexpr int IT = (CAP + Geo::kThreads - 1) / Geo::kThreads;
   const int tid = threadIdx.x;
   const int mt = S.mt, nt = S.nt;
   bool ks[IT], kc[IT];
@@ -326,10 +328,11 @@ NNS_DEV void cta_compact(CtaCore<CAP>& S, Geo& G) {
   __syncthreads();
 }
 
-// Exclusive scan of in[0..n) into out[0..n) (n <= CAP), returns the total.
-template <int CAP>
+// Exclusive scan of in[0..n) into out[0..n) (n <= CAP, NT threads), returns
+// the total.
+template <int CAP, int NT>
 NNS_DEV int block_scan_array(const int* in, int* out, int n, int* wt) {
-  constexpr int IT = (CAP + FIN_THREADS - 1) / FIN_THREADS;
+  constexpr int IT = (CAP + NT - 1) / NT;
   int v[IT];
   int s = 0;
 #pragma unroll
@@ -373,7 +376,7 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
     for (int q = tid; q < nt; q += T) atomicAdd(&S.cnt[(int)(S.nnk[q] & 0xffffffffULL)], 1);
     __syncthreads();
     {
-      const int tot = block_scan_array<CAP>(S.cnt, S.off, mt, S.wt);
+      const int tot = block_scan_array<CAP, Geo::kThreads>(S.cnt, S.off, mt, S.wt);
       if (tid == 0) S.off[mt] = tot;
     }
     __syncthreads();

@@ -175,4 +175,66 @@ int launch_batched_hd(const BatchArgs& A, int grid, cudaStream_t st) {
   return A.metric == METRIC_L1 ? batched_hd_t<true>(A, grid, st) : batched_hd_t<false>(A, grid, st);
 }
 
+// Pairs of at most HD_SMALL_CAP points per side: a 256-thread CTA each, four
+// resident per SM, so that four pairs' latency-bound round loops overlap on
+// every SM (a 1,024-thread CTA spends most of a small pair's round in its
+// barriers: its NNS tile has one 256-thread group's worth of consumers).
+template <bool L1>
+struct HighdSmallSmem {
+  CtaCore<HD_SMALL_CAP> S;
+  GeoGlobal<L1, HD_SMALL_CAP, HD_SMALL_THREADS> G;
+};
+
+template <bool L1>
+__global__ void __launch_bounds__(HD_SMALL_THREADS, 4) k_batched_hd_small(BatchArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  HighdSmallSmem<L1>& H = *reinterpret_cast<HighdSmallSmem<L1>*>(smem_raw);
+  __shared__ int s_item;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) s_item = (int)atomicAdd(A.queue, 1u);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= A.num) break;
+    const int pr = A.pair_ids[item];
+    const int64_t xo = A.x_off[pr], yo = A.y_off[pr];
+    const int m = (int)(A.x_off[pr + 1] - xo), n = (int)(A.y_off[pr + 1] - yo);
+    if (m > HD_SMALL_CAP || n > HD_SMALL_CAP) {  // the host routes only small pairs here
+      if (tid == 0) atomicOr(A.err, EF_INTERNAL);
+      break;
+    }
+    if (tid == 0) {
+      H.G.x = A.x + xo * A.d;
+      H.G.y = A.y + yo * A.d;
+      H.G.d = A.d;
+    }
+    __syncthreads();
+    double cost = 0.0;
+    long long rounds = 0, pe = 0;
+    const bool ok = cta_solve_pair(H.S, H.G, nullptr, nullptr, A.x + xo * A.d, A.a + xo, m, A.y + yo * A.d,
+                                   A.b + yo, n, A.d, A.metric, A.err, cost, rounds, pe);
+    if (tid == 0) {
+      A.costs[pr] = ok ? cost : CUDART_NAN;
+      if (A.rounds) A.rounds[pr] = rounds;
+      if (A.pair_evals) A.pair_evals[pr] = pe;
+    }
+    __syncthreads();
+  }
+}
+
+template <bool L1>
+static int batched_hd_small_t(const BatchArgs& A, int grid, cudaStream_t st) {
+  const size_t smem = sizeof(HighdSmallSmem<L1>);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_batched_hd_small<L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return -1;
+  k_batched_hd_small<L1><<<grid, HD_SMALL_THREADS, smem, st>>>(A);
+  return 0;
+}
+
+int launch_batched_hd_small(const BatchArgs& A, int grid, cudaStream_t st) {
+  return A.metric == METRIC_L1 ? batched_hd_small_t<true>(A, grid, st) : batched_hd_small_t<false>(A, grid, st);
+}
+
 }  // namespace nnsemd

@@ -121,6 +121,11 @@ int launch_batched_lowd(const BatchArgs& A, int grid, cudaStream_t st);
 int launch_nns_f32(const SolveBufs& B, int mt, int ncons, const int* cons, const int* ncons_dev, cudaStream_t st);
 int launch_finish_hd(const SolveBufs& B, int64_t round_limit, cudaStream_t st);
 int launch_batched_hd(const BatchArgs& A, int grid, cudaStream_t st);
+// Batched FP32 solver for pairs of at most HD_SMALL_CAP points per side
+// (d > 8), HD_SMALL_THREADS threads per pair, several pairs per SM.
+constexpr int HD_SMALL_CAP = 512;
+constexpr int HD_SMALL_THREADS = 256;
+int launch_batched_hd_small(const BatchArgs& A, int grid, cudaStream_t st);
 // All d coordinates of both sides finite (else EF_NONFINITE).
 void launch_check_finite(const float* v, int64_t count, unsigned* err, cudaStream_t st);
 

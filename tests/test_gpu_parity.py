@@ -172,6 +172,27 @@ def test_batched_mixes_small_and_large_pairs(ctx):
         assert costs[p] == oracle.solve_pair(pr, "sql2").cost
 
 
+@pytest.mark.parametrize("metric", ["l2", "l1"])
+def test_batched_high_d_both_kernels(ctx, metric):
+    # d > 8, FP32: pairs of at most 512 points per side run on the 256-thread
+    # kernel, larger ones on the 1,024-thread kernel, beyond 2,048 multi-CTA
+    sizes = [(1, 1), (3, 700), (512, 512), (513, 40), (200, 300), (60, 480), (900, 1100), (2100, 300), (37, 12)]
+    pairs = [wl.uniform_pair(m, n, 24, 500 + s, "dirichlet") for s, (m, n) in enumerate(sizes)]
+    rb = wl.random_batch(40, 77, 24, 5, 520)
+    pairs += [rb.pair(k) for k in range(rb.num_pairs)]
+    batch = wl.Batch.pack(pairs)
+    costs, stats = ctx.solve_batched(dev(batch.x, torch.float32), dev(batch.a, torch.float64), batch.x_off,
+                                     dev(batch.y, torch.float32), dev(batch.b, torch.float64), batch.y_off,
+                                     metric=metric)
+    costs = costs.cpu().numpy()
+    rounds = 0
+    for p, pr in enumerate(pairs):
+        ref = oracle.solve_pair(pr, metric)
+        assert costs[p] == ref.cost, p
+        rounds += ref.rounds
+    assert stats["rounds"] == rounds
+
+
 def test_errors_are_reported(ctx):
     from paper_2401_07378_gb300.nnsemd import NNSEMDError
     x = np.zeros((4, 2), np.float32)
