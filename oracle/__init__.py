@@ -73,12 +73,14 @@ def _load():
             f = lib.oracle_nnsemd
             P = ctypes.c_void_p
             f.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, P, P, P, P,
-                          ctypes.c_int32, ctypes.c_int32,
+                          ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
                           ctypes.c_int64, P, P, P, P,
                           ctypes.c_int64, P, P,
                           ctypes.c_int64, P, P,
                           ctypes.POINTER(_Stats)]
             f.restype = ctypes.c_int
+            lib.oracle_splitmix64_output.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+            lib.oracle_splitmix64_output.restype = ctypes.c_uint64
             if lib.oracle_stats_size() != ctypes.sizeof(_Stats):
                 raise RuntimeError("oracle stats layout mismatch")
             _lib = lib
@@ -129,12 +131,24 @@ def normalise(w: np.ndarray) -> np.ndarray:
     return w / total
 
 
-def solve(x, a, y, b, metric: str = "l2", decide: str = "fp32", trace: bool = False) -> OracleResult:
-    """Run NNS-EMD (Alg. 1, greedy protocol) on one pair.
+PROTOCOLS = {"greedy": 0, "random": 1}
+
+
+def splitmix64_output(seed: int, k: int) -> int:
+    """Output number k (k >= 1) of SplitMix64 seeded with `seed` (the
+    generator of the random protocol's order; see nnsemd_oracle.c)."""
+    return int(_load().oracle_splitmix64_output(seed, k))
+
+
+def solve(x, a, y, b, metric: str = "l2", decide: str = "fp32", trace: bool = False,
+          protocol: str = "greedy", seed: int = 0) -> OracleResult:
+    """Run NNS-EMD (Alg. 1) on one pair.
 
     x: [m, d] float32 suppliers S with weights a; y: [n, d] float32 consumers
     C with weights b.  ``decide`` is the precision of the argmin and greedy
     order decisions ("fp32" or "fp64"); mass and cost are FP64 either way.
+    ``protocol``: "greedy" (the paper's default) or "random" (a supplier
+    serves its consumers in a seeded random order, Sec. III-A).
     """
     lib = _load()
     x = np.ascontiguousarray(x, np.float32)
@@ -170,7 +184,7 @@ def solve(x, a, y, b, metric: str = "l2", decide: str = "fp32", trace: bool = Fa
         c[:] = c0
         rc = lib.oracle_nnsemd(
             m, n, d, x.ctypes.data, s.ctypes.data, y.ctypes.data, c.ctypes.data,
-            METRICS[metric], 1 if decide == "fp32" else 0,
+            METRICS[metric], 1 if decide == "fp32" else 0, PROTOCOLS[protocol], seed,
             cap, pi.ctypes.data, pj.ctypes.data, pf.ctypes.data, pt.ctypes.data,
             rcap, m_t.ctypes.data, n_t.ctypes.data,
             tcap if trace else 0, tj.ctypes.data if trace else None,
@@ -194,5 +208,6 @@ def solve(x, a, y, b, metric: str = "l2", decide: str = "fp32", trace: bool = Fa
         trace_nn=tn[: int(np.sum(n_t[: st.rounds]))].copy() if trace else None)
 
 
-def solve_pair(pair, metric: str = "l2", decide: str = "fp32", trace: bool = False) -> OracleResult:
-    return solve(pair.x, pair.a, pair.y, pair.b, metric, decide, trace)
+def solve_pair(pair, metric: str = "l2", decide: str = "fp32", trace: bool = False, protocol: str = "greedy",
+               seed: int = 0) -> OracleResult:
+    return solve(pair.x, pair.a, pair.y, pair.b, metric, decide, trace, protocol, seed)

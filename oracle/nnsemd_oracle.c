@@ -11,6 +11,7 @@
  *     for every j in n(t):  NNS(j) = argmin_{i in m(t)} D_ij      (NNS op.)
  *     for every i in m(t):
  *        a_i = { j : NNS(j) = i }, sorted by D_ij ascending      (greedy prot.)
+ *                                   or in a random order         (random prot.)
  *        walk a_i while s_i > 0:
  *          f = min(s_i, c_j); s_i -= f; c_j -= f; R += f*D_ij; F_ij += f
  *     t += 1
@@ -34,6 +35,12 @@
  *    single-precision GPU kernels, and checks each such decision against the
  *    FP64 one: where the two pick differently, the FP64 distances must be
  *    within 1e-6 relative (a near-tie) or the call reports a violation.
+ *
+ *  - Random protocol (Sec. III-A names it; the paper fixes no generator):
+ *    a group is served in ascending order of a 32-bit key per consumer, the
+ *    upper half of SplitMix64 output number c + 1 of the generator seeded
+ *    with `seed`, for the counter c = (t << 32) | j (round t from 0, original
+ *    consumer index j); equal keys go to the lower j.
  *
  * FP32 squared distance:  t_k = fl32(x_k - y_k);  acc = fl32(t_0 * t_0);
  *                         acc = fmaf(t_k, t_k, acc) for k = 1..d-1.
@@ -102,18 +109,43 @@ static double cost_dist(const float *xi, const float *yj, int d, int metric)
     return metric == METRIC_L2 ? sqrt(k) : k;
 }
 
+/* SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014): the generator adds 0x9E3779B97F4A7C15 to its
+ * state per step and outputs the state passed through the mixing function
+ * below, so output number k (k >= 1) of the generator seeded with `seed` is
+ * mix(seed + k * 0x9E3779B97F4A7C15), all arithmetic modulo 2^64. */
+uint64_t oracle_splitmix64_output(uint64_t seed, uint64_t k)
+{
+    uint64_t z = seed + k * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* Random-protocol key of consumer j in round t (see the header). */
+static uint32_t rp_key(uint64_t seed, int64_t t, int64_t j)
+{
+    const uint64_t c = ((uint64_t)t << 32) | (uint64_t)(uint32_t)j;
+    return (uint32_t)(oracle_splitmix64_output(seed, c + 1) >> 32);
+}
+
 /* One member of a supplier's group a_i: its consumer and its sort keys. */
 typedef struct {
     int64_t j;
     float k32;
     double k64;
     int use32;
+    int random;     /* random protocol: order by rk */
+    uint32_t rk;
 } member_t;
 
 static int cmp_member(const void *pa, const void *pb)
 {
     const member_t *a = (const member_t *)pa, *b = (const member_t *)pb;
-    if (a->use32) {
+    if (a->random) {
+        if (a->rk < b->rk) return -1;
+        if (a->rk > b->rk) return 1;
+    } else if (a->use32) {
         if (a->k32 < b->k32) return -1;
         if (a->k32 > b->k32) return 1;
     } else {
@@ -145,12 +177,13 @@ typedef struct {
  */
 int oracle_nnsemd(int64_t m, int64_t n, int32_t d, const float *x, double *s,
                   const float *y, double *c, int32_t metric, int32_t decide_fp32,
+                  int32_t protocol, uint64_t seed,
                   int64_t plan_cap, int32_t *pi, int32_t *pj, double *pf, double *pterm,
                   int64_t round_cap, int64_t *m_t, int64_t *n_t,
                   int64_t trace_cap, int32_t *trace_j, int32_t *trace_nn,
                   oracle_stats *st)
 {
-    if (m < 0 || n < 0 || d < 1 || !st || (metric < 0 || metric > 2))
+    if (m < 0 || n < 0 || d < 1 || !st || (metric < 0 || metric > 2) || protocol < 0 || protocol > 1)
         return ORC_ERR_ARG;
     memset(st, 0, sizeof(*st));
     int64_t *I = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
@@ -226,11 +259,13 @@ int oracle_nnsemd(int64_t m, int64_t n, int32_t d, const float *x, double *s,
                 e.k64 = key64(xi, y + e.j * d, d, metric);
                 e.k32 = decide_fp32 ? key32(xi, y + e.j * d, d, metric) : 0.0f;
                 e.use32 = decide_fp32;
+                e.random = protocol == 1;
+                e.rk = protocol == 1 ? rp_key(seed, st->rounds, e.j) : 0u;
                 grp[L++] = e;
             }
             if (L == 0) continue;
             qsort(grp, (size_t)L, sizeof(member_t), cmp_member);
-            if (decide_fp32) {
+            if (decide_fp32 && protocol == 0) {
                 /* every inversion against the FP64 order must be a near-tie */
                 double run_max = grp[0].k64;
                 for (int64_t l = 1; l < L; ++l) {
