@@ -343,11 +343,12 @@ def run_ours(args) -> dict | None:
         bflags = ((nnsemd.FLAG_GRAPH if spec.get("graph") else 0) |
                   (nnsemd.FLAG_AUTOTUNE if spec.get("autotune") else 0))
         step = lambda: ctx.solve_batched(x, a, inp.x_off, y, b, inp.y_off, metric=metric, precision=precision,
-                                         costs=costs, stats=True, flags=bflags)[1]
+                                         costs=costs, stats=True, flags=bflags, protocol=args.protocol)[1]
         units = P
     else:
         def step():
-            r = ctx.solve(x, a, y, b, metric=metric, precision=precision, plan=True, flags=T, proposal=prop)
+            r = ctx.solve(x, a, y, b, metric=metric, precision=precision, plan=True, flags=T, proposal=prop,
+                          protocol=args.protocol)
             return dict(r.stats, cost=r.cost)
         units = 1
 
@@ -390,7 +391,7 @@ def run_ours(args) -> dict | None:
                     torch.empty(cap, dtype=torch.int32).pin_memory(),
                     torch.empty(cap, dtype=torch.float64).pin_memory())
         host_step = lambda: ctx.solve_host(hx, ha, hy, hb, metric=metric, precision=precision, plan=True,
-                                           plan_out=plan_out, proposal=prop)
+                                           plan_out=plan_out, proposal=prop, protocol=args.protocol)
         for _ in range(min(args.warmup, 2)):
             host_step()
         torch.cuda.synchronize()
@@ -435,6 +436,7 @@ def run_ours(args) -> dict | None:
         "dtype": "f32 distances, f64 mass/cost" if precision == "fp32" else f"{precision} contraction, f32 re-rank, f64 mass/cost",
         "data": "synthetic",
         "config": {"workload": spec["desc"], "name": args.workload, "d": d, "metric": metric, "precision": precision,
+                   "protocol": args.protocol,
                    "l2": "flushed before every step (256 MiB write)",
                    "parallelism": f"{ws} independent problems, one per GPU" if ws > 1 else "1 GPU"},
         "roofline": rl,
@@ -516,6 +518,8 @@ def main(argv=None):
     ap.add_argument("--proposal", choices=["none", "learned"], default=None,
                     help="gmm only (default learned): train a learned candidate proposal before timing")
     ap.add_argument("--no-plain", action="store_true", help="gmm: skip timing the plain FP32 form")
+    ap.add_argument("--protocol", choices=["greedy", "random"], default="greedy",
+                    help="serving order of a supplier's consumers (Sec. III-A); random uses seed 0")
     ap.add_argument("--points", type=int, default=None,
                     help="colour/gmm: points per side (default the full workload; smaller sizes are for profiling)")
     ap.add_argument("--pairs", type=int, default=None,

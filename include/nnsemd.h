@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define NNSEMD_ABI_VERSION 1
+#define NNSEMD_ABI_VERSION 2
 
 typedef enum {
   NNSEMD_OK = 0,
@@ -93,12 +93,24 @@ typedef struct {
 #define NNSEMD_FLAG_GRAPH 4         /* nnsemd_solve_batched: capture the device work of the call in a CUDA
                                        graph and replay it while the buffers and sizes repeat */
 
+/* How a supplier serves the consumers that picked it (Sec. III-A):
+ * GREEDY (the paper's default, Alg. 1) in ascending distance, equal
+ * distances by ascending consumer index; RANDOM in a seeded random order:
+ * ascending 32-bit key, the upper half of SplitMix64 (Steele, Lea and Flood
+ * 2014) output number c + 1 of the generator seeded with options.seed, for
+ * the counter c = (round << 32) | consumer index (rounds counted from 0,
+ * original consumer indices), equal keys by ascending consumer index. */
+typedef enum { NNSEMD_PROTOCOL_GREEDY = 0, NNSEMD_PROTOCOL_RANDOM = 1 } nnsemd_protocol;
+
 typedef struct {
   int32_t metric;               /* nnsemd_metric */
   int32_t precision;            /* nnsemd_precision */
   int32_t rerank_k;             /* candidates per consumer kept by a reduced-precision scan (0 = default 8) */
   int32_t flags;                /* NNSEMD_FLAG_* bits, 0 for none */
   const void *proposal;         /* learned candidate proposal, NULL = full scan */
+  int32_t protocol;             /* nnsemd_protocol (0 = greedy) */
+  int32_t reserved;             /* must be 0 */
+  uint64_t seed;                /* random protocol: generator seed */
 } nnsemd_options;
 
 typedef struct {

@@ -197,6 +197,9 @@ int check_opts(nnsemd_ctx* ctx, const nnsemd_options* opt, int d, int& metric, i
       return fail(ctx, NNSEMD_ERR_INVALID_ARG, "unknown options.flags bits");
     if (opt->precision < NNSEMD_FP32 || opt->precision > NNSEMD_FP8)
       return fail(ctx, NNSEMD_ERR_INVALID_ARG, "unknown precision %d", opt->precision);
+    if (opt->protocol != NNSEMD_PROTOCOL_GREEDY && opt->protocol != NNSEMD_PROTOCOL_RANDOM)
+      return fail(ctx, NNSEMD_ERR_INVALID_ARG, "unknown protocol %d", opt->protocol);
+    if (opt->reserved != 0) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "options.reserved must be 0");
     if (opt->precision != NNSEMD_FP32) {
       if (!precision) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "reduced precision is served by nnsemd_solve only");
       if (d <= 8) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "reduced precision serves d > 8 (d = %d)", d);
@@ -283,6 +286,7 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
                            : (mt <= FIN_MAX_HD && nt <= FIN_MAX_HD && (int64_t)mt * nt * B.d <= FIN_HD_WORK);
     if (tail) {
       if (timed) CK(cudaEventRecord(ctx->ev[2], st));
+      B.round0 = rounds;
       const int lrc = lowd ? launch_finish(B, round_limit - rounds, st) : launch_finish_hd(B, round_limit - rounds, st);
       if (lrc) return fail(ctx, NNSEMD_ERR_CUDA, "finisher launch");
       if (timed) CK(cudaEventRecord(ctx->ev[3], st));
@@ -311,7 +315,7 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
       if (timed) CK(cudaEventRecord(ctx->ev[1], st));
     }
     if (nrc) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "NNS launch failed for d=%d (%d)", B.d, nrc);
-    launch_big_round(B, mt, nt, st);
+    launch_big_round(B, mt, nt, rounds, st);
     L += 10;
     CK(cudaGetLastError());
     B.cur ^= 1;
@@ -464,6 +468,8 @@ int nnsemd_solve(nnsemd_ctx* ctx, const float* x, const double* a, int64_t m, co
   B.d = d;
   B.dp = packed_dim(d);
   B.metric = metric;
+  B.protocol = opt ? opt->protocol : 0;
+  B.seed = opt ? opt->seed : 0;
   B.plan_i = plan ? plan->i : nullptr;
   B.plan_j = plan ? plan->j : nullptr;
   B.plan_f = plan ? plan->f : nullptr;
@@ -526,6 +532,8 @@ int nnsemd_solve_host(nnsemd_ctx* ctx, const float* x, const double* a, int64_t 
   B.d = d;
   B.dp = packed_dim(d);
   B.metric = metric;
+  B.protocol = opt ? opt->protocol : 0;
+  B.seed = opt ? opt->seed : 0;
   B.plan_i = plan ? pi : nullptr;
   B.plan_j = plan ? pj : nullptr;
   B.plan_f = plan ? pf : nullptr;
@@ -640,7 +648,7 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
     if (cudaMemsetAsync(rounds_d, 0, num_pairs * sizeof(long long), s) != cudaSuccess) return -1;
     if (cudaMemsetAsync(pe_d, 0, num_pairs * sizeof(long long), s) != cudaSuccess) return -1;
     BatchArgs A{x_packed, a_packed, xo_d, y_packed, b_packed, yo_d, ids_d, nsmall, d, metric,
-                costs_out, rounds_d, pe_d, q_d, q_d + 1};
+                costs_out, rounds_d, pe_d, q_d, q_d + 1, opt ? opt->protocol : 0, opt ? opt->seed : 0ULL};
     if (tc)
       return launch_batched_tc(A, precision, cap, kb, tbn, tns, scratch, slot, ctr_d + 1, ctr_d + 2, g, s);
     if (d <= 8) return launch_batched_lowd(A, g, s);
@@ -696,7 +704,8 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
                                           (uintptr_t)b_packed, (uintptr_t)costs_out, (uintptr_t)ctx->ws,
                                           (uintptr_t)num_pairs, (uintptr_t)small.size(), (uintptr_t)d,
                                           (uintptr_t)metric, (uintptr_t)precision, (uintptr_t)cap, (uintptr_t)bn,
-                                          (uintptr_t)nstage, (uintptr_t)ntiny};
+                                          (uintptr_t)nstage, (uintptr_t)ntiny,
+                                          (uintptr_t)(opt ? opt->protocol : 0), (uintptr_t)(opt ? opt->seed : 0)};
       BatchGraph* g = nullptr;
       for (auto& e : ctx->graphs)
         if (e.key == key) g = &e;
@@ -736,6 +745,8 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
     B.d = d;
     B.dp = packed_dim(d);
     B.metric = metric;
+    B.protocol = opt ? opt->protocol : 0;
+    B.seed = opt ? opt->seed : 0;
     double cost = 0;
     int64_t nnz = 0;
     nnsemd_stats s1{};

@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_batched_tc(BtcArgs A) {
     double cost = 0.0;
     long long rounds = 0, pe = 0;
     const bool ok = cta_solve_pair(S, G, nullptr, nullptr, B.x + xo * B.d, B.a + xo, m, B.y + yo * B.d, B.b + yo, n,
-                                   B.d, B.metric, B.err, cost, rounds, pe);
+                                   B.d, B.metric, B.err, cost, rounds, pe, B.protocol, B.seed);
     if (tid == 0) {
       B.costs[pr] = ok ? cost : CUDART_NAN;
       if (B.rounds) B.rounds[pr] = rounds;

@@ -94,6 +94,20 @@ NNS_DEV unsigned long long pack_key(float k, unsigned idx) {
   return ((unsigned long long)__float_as_uint(k) << 32) | idx;
 }
 
+// Random-protocol key of consumer j (original index) in round t: the upper
+// half of SplitMix64 (Steele, Lea and Flood 2014) output number c + 1 of the
+// generator seeded with `seed`, c = (t << 32) | j.  The generator adds
+// 0x9E3779B97F4A7C15 to its state per step and mixes the state into its
+// output; output k is therefore mix(seed + k * 0x9E3779B97F4A7C15).
+NNS_DEV unsigned rp_key32(unsigned long long seed, long long t, int j) {
+  const unsigned long long c = ((unsigned long long)t << 32) | (unsigned)j;
+  unsigned long long z = seed + (c + 1ULL) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z ^= z >> 31;
+  return (unsigned)(z >> 32);
+}
+
 // One step of the greedy protocol (Alg. 1): f = min(s, c); s -= f; c -= f.
 // Residuals are finite and never negative (they start positive and every
 // step leaves x - x = +0 or the difference of the larger and the smaller),

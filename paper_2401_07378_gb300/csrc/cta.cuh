@@ -92,6 +92,11 @@ struct CtaOut {
   const float* x;
   const float* y;
   int d;
+  // serving order: greedy (0) or random (1) with the seed and the global
+  // index of the loop's first round (the random protocol's keys)
+  int protocol;
+  unsigned long long seed;
+  long long round_base;
 };
 
 // --------------------------------------------------------------------------
@@ -384,7 +389,10 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
       const unsigned long long key = S.nnk[q];
       const int p = (int)(key & 0xffffffffULL);
       const int slot = S.off[p] + atomicSub(&S.cnt[p], 1) - 1;
-      S.mem[slot] = (key & 0xffffffff00000000ULL) | (unsigned)q;
+      const unsigned long long order =
+          O.protocol == 1 ? ((unsigned long long)rp_key32(O.seed, O.round_base + rounds, S.jidx[q]) << 32)
+                          : (key & 0xffffffff00000000ULL);
+      S.mem[slot] = order | (unsigned)q;
     }
     __syncthreads();
     // ---- greedy order: rank of each member inside its group
@@ -528,7 +536,7 @@ NNS_DEV bool cta_load_side(const float* pts, const double* w, int cnt, int d, fl
 template <int CAP, class Geo>
 NNS_DEV bool cta_solve_pair(CtaCore<CAP>& S, Geo& G, float* xs, float* ys, const float* x, const double* a, int m,
                             const float* y, const double* b, int n, int d, int metric, unsigned* err, double& cost,
-                            long long& rounds, long long& pe) {
+                            long long& rounds, long long& pe, int protocol = 0, unsigned long long seed = 0) {
   bool ok = cta_load_side<Geo::kDP, CAP>(x, a, m, d, xs, S.sres, S.iidx, S, err);
   if (ok) ok = cta_load_side<Geo::kDP, CAP>(y, b, n, d, ys, S.cres, S.jidx, S, err);
   if (!ok) return false;
@@ -540,6 +548,8 @@ NNS_DEV bool cta_solve_pair(CtaCore<CAP>& S, Geo& G, float* xs, float* ys, const
   __syncthreads();
   cta_compact(S, G);  // drop zero weights
   CtaOut O{nullptr, S.acc, nullptr, nullptr, nullptr, 0, nullptr, nullptr, err};
+  O.protocol = protocol;
+  O.seed = seed;
   unsigned long long nnz = 0;
   rounds = 0;
   pe = 0;

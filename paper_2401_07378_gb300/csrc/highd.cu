@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_finish_hd(SolveBufs B, long 
   }
   __syncthreads();
   CtaOut O{B.terms, nullptr, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, B.s, B.c, &B.st->err,
-           B.fl_i, B.fl_j, B.fl_f, B.x, B.y, B.d};
+           B.fl_i, B.fl_j, B.fl_f, B.x, B.y, B.d, B.protocol, B.seed, B.round0};
   unsigned long long nnz = B.st->nnz;
   long long rounds = B.st->rounds, pe = B.st->pair_evals;
   cta_rounds(S, H.G, B.metric, O, nnz, rounds, pe, round_limit);
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_batched_hd(BatchArgs A) {
     double cost = 0.0;
     long long rounds = 0, pe = 0;
     const bool ok = cta_solve_pair(H.S, H.G, nullptr, nullptr, A.x + xo * A.d, A.a + xo, m, A.y + yo * A.d,
-                                   A.b + yo, n, A.d, A.metric, A.err, cost, rounds, pe);
+                                   A.b + yo, n, A.d, A.metric, A.err, cost, rounds, pe, A.protocol, A.seed);
     if (tid == 0) {
       A.costs[pr] = ok ? cost : CUDART_NAN;
       if (A.rounds) A.rounds[pr] = rounds;
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(HD_SMALL_THREADS, 4) k_batched_hd_small(BatchA
     double cost = 0.0;
     long long rounds = 0, pe = 0;
     const bool ok = cta_solve_pair(H.S, H.G, nullptr, nullptr, A.x + xo * A.d, A.a + xo, m, A.y + yo * A.d,
-                                   A.b + yo, n, A.d, A.metric, A.err, cost, rounds, pe);
+                                   A.b + yo, n, A.d, A.metric, A.err, cost, rounds, pe, A.protocol, A.seed);
     if (tid == 0) {
       A.costs[pr] = ok ? cost : CUDART_NAN;
       if (A.rounds) A.rounds[pr] = rounds;

@@ -43,6 +43,9 @@ struct TcBufs {
 // Buffers of one single-pair solve (device pointers inside the workspace).
 struct SolveBufs {
   int precision;   // nnsemd_precision of the NNS step (0 = FP32)
+  int protocol;    // nnsemd_protocol (0 greedy, 1 random)
+  unsigned long long seed;  // random protocol seed
+  long long round0;         // rounds run before the one-CTA tail (random-protocol keys)
   TcBufs tc;       // used when precision != 0
   const float* x;  // original coordinates [m][d]
   const float* y;  // [n][d]
@@ -89,7 +92,7 @@ void launch_leftover(const SolveBufs& B, cudaStream_t st);
 // Initial packing of both sides: active = positive weight, coordinates checked.
 int launch_initial_pack(SolveBufs& B, cudaStream_t st);
 // One multi-CTA round on the current active lists (mt, nt known on the host).
-int launch_big_round(SolveBufs& B, int mt, int nt, cudaStream_t st);
+int launch_big_round(SolveBufs& B, int mt, int nt, long long round, cudaStream_t st);
 
 // lowd.cu ------------------------------------------------------------------
 int launch_nns_lowd(const SolveBufs& B, int mt, int nt, cudaStream_t st);
@@ -111,6 +114,8 @@ struct BatchArgs {
   long long* pair_evals; // [P] (nullable)
   unsigned* queue;       // work-queue counter (device, zeroed)
   unsigned* err;
+  int protocol;          // nnsemd_protocol
+  unsigned long long seed;
 };
 int launch_batched_lowd(const BatchArgs& A, int grid, cudaStream_t st);
 

@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_finish(SolveBufs B, long lon
   }
   __syncthreads();
   CtaOut O{B.terms, nullptr, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, B.s, B.c, &B.st->err,
-           B.fl_i, B.fl_j, B.fl_f, B.x, B.y, B.d};
+           B.fl_i, B.fl_j, B.fl_f, B.x, B.y, B.d, B.protocol, B.seed, B.round0};
   unsigned long long nnz = B.st->nnz;
   long long rounds = B.st->rounds, pe = B.st->pair_evals;
   cta_rounds(S, L.G, B.metric, O, nnz, rounds, pe, round_limit);
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_solve_small(SolveBufs B, con
   __syncthreads();
   cta_compact(S, L.G);  // drop zero weights
   CtaOut O{nullptr, S.acc, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, nullptr, nullptr, &B.st->err,
-           B.fl_i, B.fl_j, B.fl_f, B.x, B.y, B.d};
+           B.fl_i, B.fl_j, B.fl_f, B.x, B.y, B.d, B.protocol, B.seed, 0};
   unsigned long long nnz = 0;
   long long rounds = 0, pe = 0;
   cta_rounds(S, L.G, B.metric, O, nnz, rounds, pe, (long long)m + n);
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_batched_lowd(BatchArgs A) {
     double cost = 0.0;
     long long rounds = 0, pe = 0;
     const bool ok = cta_solve_pair(L.S, L.G, L.G.xs, L.G.ys, A.x + xo * A.d, A.a + xo, m, A.y + yo * A.d, A.b + yo,
-                                   n, A.d, A.metric, A.err, cost, rounds, pe);
+                                   n, A.d, A.metric, A.err, cost, rounds, pe, A.protocol, A.seed);
     if (tid == 0) {
       A.costs[pr] = ok ? cost : CUDART_NAN;
       if (A.rounds) A.rounds[pr] = rounds;

@@ -356,14 +356,19 @@ __global__ void k_group_alloc(const int* __restrict__ cnt, int mt, int2* __restr
   }
 }
 
+// Member key: the serving order (greedy: the distance key bits; random:
+// the round's SplitMix64 key of the consumer) << 32 | consumer position.
 __global__ void k_group_scatter(const unsigned long long* __restrict__ nnkey, int nt, int* __restrict__ cnt,
-                                const int2* __restrict__ seg, unsigned long long* __restrict__ member) {
+                                const int2* __restrict__ seg, unsigned long long* __restrict__ member,
+                                const int* __restrict__ ja, int protocol, unsigned long long seed, long long round) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nt) return;
   const unsigned long long key = nnkey[q];
   const int p = (int)(key & 0xffffffffULL);
   const int slot = seg[p].x + atomicSub(cnt + p, 1) - 1;
-  member[slot] = (key & 0xffffffff00000000ULL) | (unsigned)q;
+  const unsigned long long order =
+      protocol == 1 ? ((unsigned long long)rp_key32(seed, round, ja[q]) << 32) : (key & 0xffffffff00000000ULL);
+  member[slot] = order | (unsigned)q;
 }
 
 // --------------------------------------------------------------------------
@@ -647,12 +652,13 @@ __global__ void k_round_reset(DevState* st) {
   st->seg_cursor = 0;
 }
 
-int launch_big_round(SolveBufs& B, int mt, int nt, cudaStream_t st) {
+int launch_big_round(SolveBufs& B, int mt, int nt, long long round, cudaStream_t st) {
   const int cur = B.cur;
   k_round_reset<<<1, 1, 0, st>>>(B.st);
   k_group_count<<<(nt + 255) / 256, 256, 0, st>>>(B.nnkey, nt, mt, B.cnt, &B.st->err);
   k_group_alloc<<<(mt + 255) / 256, 256, 0, st>>>(B.cnt, mt, B.seg, B.seglist, B.biglist, B.medlist, B.st);
-  k_group_scatter<<<(nt + 255) / 256, 256, 0, st>>>(B.nnkey, nt, B.cnt, B.seg, B.member);
+  k_group_scatter<<<(nt + 255) / 256, 256, 0, st>>>(B.nnkey, nt, B.cnt, B.seg, B.member, B.ja[cur], B.protocol,
+                                                    B.seed, round);
   FlowArgs F{B.x, B.y, B.d, B.metric, B.ia[cur], B.ja[cur], B.seg, B.seglist, B.biglist, B.medlist, B.member,
              B.s, B.c, B.terms, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, B.st};
   int warps = (nt + 31) / 32;  // each warp takes 32 groups at a time; groups <= nt

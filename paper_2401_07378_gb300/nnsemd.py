@@ -38,7 +38,8 @@ class nnsemd_config(ctypes.Structure):
 
 class nnsemd_options(ctypes.Structure):
     _fields_ = [("metric", ctypes.c_int32), ("precision", ctypes.c_int32), ("rerank_k", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("proposal", ctypes.c_void_p)]
+                ("flags", ctypes.c_int32), ("proposal", ctypes.c_void_p), ("protocol", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
 
 class nnsemd_plan(ctypes.Structure):
@@ -113,9 +114,18 @@ def abi_version() -> int:
     return _lib.nnsemd_abi_version()
 
 
-def _options(metric: str, precision: str, rerank_k: int, flags: int = 0, proposal=None) -> nnsemd_options:
+ABI_VERSION = 2  # the nnsemd.h this binding mirrors
+if abi_version() != ABI_VERSION:
+    raise ImportError(f"libnnsemd.so has ABI {abi_version()}, this binding expects {ABI_VERSION}: rebuild")
+
+
+PROTOCOL = {"greedy": 0, "random": 1}
+
+
+def _options(metric: str, precision: str, rerank_k: int, flags: int = 0, proposal=None, protocol: str = "greedy",
+             seed: int = 0) -> nnsemd_options:
     return nnsemd_options(METRIC[metric], PRECISION[precision], rerank_k, flags,
-                          proposal._h.value if proposal is not None else None)
+                          proposal._h.value if proposal is not None else None, PROTOCOL[protocol], 0, seed)
 
 
 def _ptr(t) -> int:
@@ -157,7 +167,8 @@ class Context:
 
     # -- nnsemd_solve --------------------------------------------------------
     def solve(self, x, a, y, b, metric: str = "l2", precision: str = "fp32", rerank_k: int = 0,
-              plan: bool = False, flags: int = 0, proposal=None) -> SolveResult:
+              plan: bool = False, flags: int = 0, proposal=None, protocol: str = "greedy",
+              seed: int = 0) -> SolveResult:
         """Device tensors: x [m,d] float32, a [m] float64, y [n,d] float32, b [n] float64.
         ``proposal``: a trained Proposal (d > 8) replacing the full NNS scan."""
         import torch
@@ -167,7 +178,7 @@ class Context:
         m, d = x.shape
         n = y.shape[0]
         self._bind_current_stream()
-        opt = _options(metric, precision, rerank_k, flags, proposal)
+        opt = _options(metric, precision, rerank_k, flags, proposal, protocol, seed)
         cost = ctypes.c_double()
         st = nnsemd_stats()
         pl = None
@@ -188,7 +199,8 @@ class Context:
 
     # -- nnsemd_solve_host ---------------------------------------------------
     def solve_host(self, x, a, y, b, metric: str = "l2", precision: str = "fp32", rerank_k: int = 0,
-                   plan: bool = False, plan_out=None, flags: int = 0, proposal=None) -> SolveResult:
+                   plan: bool = False, plan_out=None, flags: int = 0, proposal=None, protocol: str = "greedy",
+                   seed: int = 0) -> SolveResult:
         """Host arrays (numpy, or pinned CPU torch tensors): the copies to and
         from the device happen inside the call.  ``plan_out`` may pass
         preallocated (i, j, f) host arrays of capacity >= m + n - 1."""
@@ -201,7 +213,7 @@ class Context:
         m, d = x.shape
         n = y.shape[0]
         self._bind_current_stream()
-        opt = _options(metric, precision, rerank_k, flags, proposal)
+        opt = _options(metric, precision, rerank_k, flags, proposal, protocol, seed)
         cost = ctypes.c_double()
         st = nnsemd_stats()
         pl = None
@@ -223,7 +235,8 @@ class Context:
 
     # -- nnsemd_solve_batched ------------------------------------------------
     def solve_batched(self, x, a, x_off, y, b, y_off, metric: str = "l2", precision: str = "fp32",
-                      rerank_k: int = 0, costs=None, stats: bool = True, flags: int = 0):
+                      rerank_k: int = 0, costs=None, stats: bool = True, flags: int = 0, protocol: str = "greedy",
+                      seed: int = 0):
         """Packed device tensors plus host offset arrays (np.int64, P+1).
         Returns the device tensor of P costs (and the stats dict)."""
         import torch
@@ -234,7 +247,7 @@ class Context:
         if costs is None:
             costs = torch.empty(P, dtype=torch.float64, device=x.device)
         self._bind_current_stream()
-        opt = _options(metric, precision, rerank_k, flags)
+        opt = _options(metric, precision, rerank_k, flags, None, protocol, seed)
         st = nnsemd_stats()
         rc = _lib.nnsemd_solve_batched(self._h, P, _ptr(x), _ptr(a), x_off.ctypes.data, _ptr(y), _ptr(b),
                                        y_off.ctypes.data, d, ctypes.byref(opt), _ptr(costs),
