@@ -180,6 +180,21 @@ int nnsemd_solve_batched(nnsemd_ctx *ctx, int32_t num_pairs,
                          int32_t d, const nnsemd_options *opt,
                          double *costs_out, nnsemd_stats *stats);
 
+/* ---- one histogram against many -----------------------------------------
+ * The EMD-kNN primitive of the paper's classification and retrieval
+ * experiments (Sec. IV-B, IV-C): one query histogram compared with every
+ * histogram of a collection.  Pair p has suppliers x_packed rows
+ * x_off[p] .. x_off[p+1]-1 (weights a_packed, device) and, as consumers, the
+ * same n points y / b (device) for every p, which are stored once.  Offsets
+ * are HOST arrays of P+1 entries starting at 0; costs_out is a DEVICE array
+ * of P doubles.  Everything else (options, statistics, errors, the
+ * asynchrony) is as for nnsemd_solve_batched, whose results it equals. */
+int nnsemd_solve_one_to_many(nnsemd_ctx *ctx, int32_t num_pairs,
+                             const float *x_packed, const double *a_packed, const int64_t *x_off,
+                             const float *y, const double *b, int64_t n,
+                             int32_t d, const nnsemd_options *opt,
+                             double *costs_out, nnsemd_stats *stats);
+
 /* ---- the NNS operation alone --------------------------------------------
  * Round one of Alg. 1 (Sec. III-A, NNS step): for every consumer j, the
  * nearest supplier nn_out[j] (device int32 [n]), ties to the lowest index,

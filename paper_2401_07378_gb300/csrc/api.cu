@@ -555,9 +555,12 @@ int nnsemd_solve_host(nnsemd_ctx* ctx, const float* x, const double* a, int64_t 
   return NNSEMD_OK;
 }
 
-int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_packed, const double* a_packed,
-                         const int64_t* x_off, const float* y_packed, const double* b_packed, const int64_t* y_off,
-                         int32_t d, const nnsemd_options* opt, double* costs_out, nnsemd_stats* stats) {
+// The batched solver.  With y_off == nullptr every pair's consumers are the
+// same n_shared rows of y_packed / b_packed (one-to-many).
+static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_packed, const double* a_packed,
+                              const int64_t* x_off, const float* y_packed, const double* b_packed,
+                              const int64_t* y_off, int64_t n_shared, int32_t d, const nnsemd_options* opt,
+                              double* costs_out, nnsemd_stats* stats) {
   if (!ctx) return NNSEMD_ERR_INVALID_ARG;
   ctx->err.clear();
   int metric, precision;
@@ -570,14 +573,17 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
     if (stats) std::memset(stats, 0, sizeof(*stats));
     return NNSEMD_OK;
   }
-  if (!x_packed || !a_packed || !x_off || !y_packed || !b_packed || !y_off || !costs_out)
+  if (!x_packed || !a_packed || !x_off || !y_packed || !b_packed || (!y_off && n_shared < 1) || !costs_out)
     return fail(ctx, NNSEMD_ERR_INVALID_ARG, "null pointer argument");
-  if (x_off[0] != 0 || y_off[0] != 0) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "offsets must start at 0");
+  if (x_off[0] != 0 || (y_off && y_off[0] != 0)) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "offsets must start at 0");
+  if (!y_off && n_shared > (1LL << 30)) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "n above 2^30");
   if (opt && opt->proposal) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "proposals serve nnsemd_solve only");
+  auto y_begin = [&](int p) -> int64_t { return y_off ? y_off[p] : 0; };
+  auto y_len = [&](int p) -> int64_t { return y_off ? y_off[p + 1] - y_off[p] : n_shared; };
   std::vector<int> small, large;
   int64_t small_max = 0;
   for (int p = 0; p < num_pairs; ++p) {
-    const int64_t m = x_off[p + 1] - x_off[p], n = y_off[p + 1] - y_off[p];
+    const int64_t m = x_off[p + 1] - x_off[p], n = y_len(p);
     if (m < 1 || n < 1) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "pair %d has an empty side", p);
     const int cap = d <= 8 ? FIN_MAX : FIN_MAX_HD;
     const bool fits = m <= cap && n <= cap;
@@ -589,10 +595,10 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
   int ntiny = 0;
   if (!tc && d > 8) {
     std::stable_partition(small.begin(), small.end(), [&](int p) {
-      return x_off[p + 1] - x_off[p] <= HD_SMALL_CAP && y_off[p + 1] - y_off[p] <= HD_SMALL_CAP;
+      return x_off[p + 1] - x_off[p] <= HD_SMALL_CAP && y_len(p) <= HD_SMALL_CAP;
     });
     for (int p : small)
-      if (x_off[p + 1] - x_off[p] <= HD_SMALL_CAP && y_off[p + 1] - y_off[p] <= HD_SMALL_CAP) ++ntiny;
+      if (x_off[p + 1] - x_off[p] <= HD_SMALL_CAP && y_len(p) <= HD_SMALL_CAP) ++ntiny;
   }
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
@@ -622,7 +628,7 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
   int64_t maxm = 0, maxn = 0;
   for (int p : large) {
     maxm = std::max(maxm, x_off[p + 1] - x_off[p]);
-    maxn = std::max(maxn, y_off[p + 1] - y_off[p]);
+    maxn = std::max(maxn, y_len(p));
   }
   SolveBufs B{};
   if (!large.empty()) bytes += layout_solve(nullptr, maxm, maxn, d, B, precision);
@@ -638,7 +644,7 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
   unsigned* q_d = reinterpret_cast<unsigned*>(ctr_d);
   unsigned* q2_d = reinterpret_cast<unsigned*>(ctr_d + 3);  // queue of the 256-thread kernel
   CK(cudaMemcpyAsync(xo_d, x_off, (num_pairs + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(yo_d, y_off, (num_pairs + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  if (y_off) CK(cudaMemcpyAsync(yo_d, y_off, (num_pairs + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
   if (!small.empty())
     CK(cudaMemcpyAsync(ids_d, small.data(), small.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   long long L = 0;
@@ -648,7 +654,8 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
     if (cudaMemsetAsync(rounds_d, 0, num_pairs * sizeof(long long), s) != cudaSuccess) return -1;
     if (cudaMemsetAsync(pe_d, 0, num_pairs * sizeof(long long), s) != cudaSuccess) return -1;
     BatchArgs A{x_packed, a_packed, xo_d, y_packed, b_packed, yo_d, ids_d, nsmall, d, metric,
-                costs_out, rounds_d, pe_d, q_d, q_d + 1, opt ? opt->protocol : 0, opt ? opt->seed : 0ULL};
+                costs_out, rounds_d, pe_d, q_d, q_d + 1, opt ? opt->protocol : 0, opt ? opt->seed : 0ULL,
+                y_off ? 0 : (int)n_shared};
     if (tc)
       return launch_batched_tc(A, precision, cap, kb, tbn, tns, scratch, slot, ctr_d + 1, ctr_d + 2, g, s);
     if (d <= 8) return launch_batched_lowd(A, g, s);
@@ -705,7 +712,8 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
                                           (uintptr_t)num_pairs, (uintptr_t)small.size(), (uintptr_t)d,
                                           (uintptr_t)metric, (uintptr_t)precision, (uintptr_t)cap, (uintptr_t)bn,
                                           (uintptr_t)nstage, (uintptr_t)ntiny,
-                                          (uintptr_t)(opt ? opt->protocol : 0), (uintptr_t)(opt ? opt->seed : 0)};
+                                          (uintptr_t)(opt ? opt->protocol : 0), (uintptr_t)(opt ? opt->seed : 0),
+                                          (uintptr_t)(y_off ? 0 : n_shared)};
       BatchGraph* g = nullptr;
       for (auto& e : ctx->graphs)
         if (e.key == key) g = &e;
@@ -739,9 +747,9 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
   for (int p : large) {
     layout_solve((char*)ctx->ws + head, maxm, maxn, d, B, precision);
     B.x = x_packed + x_off[p] * d;
-    B.y = y_packed + y_off[p] * d;
+    B.y = y_packed + y_begin(p) * d;
     B.m = x_off[p + 1] - x_off[p];
-    B.n = y_off[p + 1] - y_off[p];
+    B.n = y_len(p);
     B.d = d;
     B.dp = packed_dim(d);
     B.metric = metric;
@@ -750,7 +758,7 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
     double cost = 0;
     int64_t nnz = 0;
     nnsemd_stats s1{};
-    rc = run_solve(ctx, B, a_packed + x_off[p], b_packed + y_off[p], &cost, &nnz, &s1);
+    rc = run_solve(ctx, B, a_packed + x_off[p], b_packed + y_begin(p), &cost, &nnz, &s1);
     if (rc) return rc;
     CK(cudaMemcpyAsync(costs_out + p, &B.st->cost, sizeof(double), cudaMemcpyDeviceToDevice, st));
     extra_rounds += s1.rounds;
@@ -780,6 +788,27 @@ int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_pack
     stats->kernel_launches = L;
   }
   return NNSEMD_OK;
+}
+
+int nnsemd_solve_batched(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_packed, const double* a_packed,
+                         const int64_t* x_off, const float* y_packed, const double* b_packed, const int64_t* y_off,
+                         int32_t d, const nnsemd_options* opt, double* costs_out, nnsemd_stats* stats) {
+  if (ctx && !y_off) {
+    ctx->err.clear();
+    return fail(ctx, NNSEMD_ERR_INVALID_ARG, "null pointer argument");
+  }
+  return solve_batched_impl(ctx, num_pairs, x_packed, a_packed, x_off, y_packed, b_packed, y_off, 0, d, opt,
+                            costs_out, stats);
+}
+
+int nnsemd_solve_one_to_many(nnsemd_ctx* ctx, int32_t num_pairs, const float* x_packed, const double* a_packed,
+                             const int64_t* x_off, const float* y, const double* b, int64_t n, int32_t d,
+                             const nnsemd_options* opt, double* costs_out, nnsemd_stats* stats) {
+  if (ctx && n < 1) {
+    ctx->err.clear();
+    return fail(ctx, NNSEMD_ERR_INVALID_ARG, "the shared consumer set is empty (n=%lld)", (long long)n);
+  }
+  return solve_batched_impl(ctx, num_pairs, x_packed, a_packed, x_off, y, b, nullptr, n, d, opt, costs_out, stats);
 }
 
 const char* nnsemd_last_error(const nnsemd_ctx* ctx) {

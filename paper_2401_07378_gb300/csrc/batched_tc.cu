@@ -392,8 +392,8 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_batched_tc(BtcArgs A) {
     __syncthreads();
     if (item >= B.num) break;
     const int pr = B.pair_ids[item];
-    const int64_t xo = B.x_off[pr], yo = B.y_off[pr];
-    const int m = (int)(B.x_off[pr + 1] - xo), n = (int)(B.y_off[pr + 1] - yo);
+    const int64_t xo = B.x_off[pr], yo = B.n_shared ? 0 : B.y_off[pr];
+    const int m = (int)(B.x_off[pr + 1] - xo), n = B.n_shared ? B.n_shared : (int)(B.y_off[pr + 1] - yo);
     if (tid == 0) {
       G.x = B.x + xo * B.d;
       G.y = B.y + yo * B.d;

@@ -141,8 +141,8 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_batched_hd(BatchArgs A) {
     __syncthreads();
     if (item >= A.num) break;
     const int pr = A.pair_ids[item];
-    const int64_t xo = A.x_off[pr], yo = A.y_off[pr];
-    const int m = (int)(A.x_off[pr + 1] - xo), n = (int)(A.y_off[pr + 1] - yo);
+    const int64_t xo = A.x_off[pr], yo = A.n_shared ? 0 : A.y_off[pr];
+    const int m = (int)(A.x_off[pr + 1] - xo), n = A.n_shared ? A.n_shared : (int)(A.y_off[pr + 1] - yo);
     if (tid == 0) {
       H.G.x = A.x + xo * A.d;
       H.G.y = A.y + yo * A.d;
@@ -198,8 +198,8 @@ __global__ void __launch_bounds__(HD_SMALL_THREADS, 4) k_batched_hd_small(BatchA
     __syncthreads();
     if (item >= A.num) break;
     const int pr = A.pair_ids[item];
-    const int64_t xo = A.x_off[pr], yo = A.y_off[pr];
-    const int m = (int)(A.x_off[pr + 1] - xo), n = (int)(A.y_off[pr + 1] - yo);
+    const int64_t xo = A.x_off[pr], yo = A.n_shared ? 0 : A.y_off[pr];
+    const int m = (int)(A.x_off[pr + 1] - xo), n = A.n_shared ? A.n_shared : (int)(A.y_off[pr + 1] - yo);
     if (m > HD_SMALL_CAP || n > HD_SMALL_CAP) {  // the host routes only small pairs here
       if (tid == 0) atomicOr(A.err, EF_INTERNAL);
       break;

@@ -116,6 +116,7 @@ struct BatchArgs {
   unsigned* err;
   int protocol;          // nnsemd_protocol
   unsigned long long seed;
+  int n_shared;          // > 0: every pair's consumers are rows 0..n_shared-1 of y (y_off unused)
 };
 int launch_batched_lowd(const BatchArgs& A, int grid, cudaStream_t st);
 

@@ -433,8 +433,8 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_batched_lowd(BatchArgs A) {
     __syncthreads();
     if (item >= A.num) break;
     const int pr = A.pair_ids[item];
-    const int64_t xo = A.x_off[pr], yo = A.y_off[pr];
-    const int m = (int)(A.x_off[pr + 1] - xo), n = (int)(A.y_off[pr + 1] - yo);
+    const int64_t xo = A.x_off[pr], yo = A.n_shared ? 0 : A.y_off[pr];
+    const int m = (int)(A.x_off[pr + 1] - xo), n = A.n_shared ? A.n_shared : (int)(A.y_off[pr + 1] - yo);
     double cost = 0.0;
     long long rounds = 0, pe = 0;
     const bool ok = cta_solve_pair(L.S, L.G, L.G.xs, L.G.ys, A.x + xo * A.d, A.a + xo, m, A.y + yo * A.d, A.b + yo,

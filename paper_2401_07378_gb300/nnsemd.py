@@ -90,8 +90,10 @@ for _f in ("nnsemd_nearest", "nnsemd_proposal_create", "nnsemd_proposal_destroy"
            "nnsemd_proposal_train", "nnsemd_proposal_loss_grad", "nnsemd_proposal_info", "nnsemd_proposal_params",
            "nnsemd_proposal_save", "nnsemd_proposal_load"):
     getattr(_lib, _f).restype = ctypes.c_int
+_lib.nnsemd_solve_one_to_many.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _I64, ctypes.c_int32,
+                                          ctypes.POINTER(nnsemd_options), _P, ctypes.POINTER(nnsemd_stats)]
 for _f in ("nnsemd_create", "nnsemd_destroy", "nnsemd_set_stream", "nnsemd_solve", "nnsemd_solve_host",
-           "nnsemd_solve_batched"):
+           "nnsemd_solve_batched", "nnsemd_solve_one_to_many"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -255,6 +257,28 @@ class Context:
         self._check(rc)
         return costs, (st.as_dict() if stats else None)
 
+
+    # -- nnsemd_solve_one_to_many ---------------------------------------------
+    def solve_one_to_many(self, x, a, x_off, y, b, metric: str = "l2", precision: str = "fp32",
+                          rerank_k: int = 0, costs=None, stats: bool = True, flags: int = 0,
+                          protocol: str = "greedy", seed: int = 0):
+        """Packed supplier histograms (device x, a; host x_off, P+1 entries)
+        against one consumer histogram (device y [n, d], b [n]).  Returns the
+        device tensor of P costs (and the stats dict)."""
+        import torch
+        x_off = np.ascontiguousarray(x_off, np.int64)
+        P = len(x_off) - 1
+        d = x.shape[1]
+        if costs is None:
+            costs = torch.empty(P, dtype=torch.float64, device=x.device)
+        self._bind_current_stream()
+        opt = _options(metric, precision, rerank_k, flags, None, protocol, seed)
+        st = nnsemd_stats()
+        rc = _lib.nnsemd_solve_one_to_many(self._h, P, _ptr(x), _ptr(a), x_off.ctypes.data, _ptr(y), _ptr(b),
+                                           y.shape[0], d, ctypes.byref(opt), _ptr(costs),
+                                           ctypes.byref(st) if stats else None)
+        self._check(rc)
+        return costs, (st.as_dict() if stats else None)
 
     # -- nnsemd_nearest ------------------------------------------------------
     def nearest(self, x, y, metric: str = "l2"):

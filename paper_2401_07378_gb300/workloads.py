@@ -190,6 +190,68 @@ def doc_knn(num_docs: int = 4096, seed: int = 0, vocab_size: int = 50000, d: int
     return Batch.pack(pairs)
 
 
+@dataclass
+class LabelledDocs:
+    """A labelled collection for EMD-kNN: documents packed as suppliers
+    (x, a, x_off) with one class label each, and held-out queries of known
+    class."""
+
+    x: np.ndarray
+    a: np.ndarray
+    x_off: np.ndarray
+    labels: np.ndarray
+    queries: list          # [(y [n, d] float32, b [n] float64)]
+    query_labels: np.ndarray
+
+
+def labelled_documents(classes: int = 3, docs_per_class: int = 20, queries_per_class: int = 2, seed: int = 0,
+                       vocab_size: int = 2000, d: int = 32, topic_words: int = 150, on_topic: float = 0.8,
+                       median: float = 40.0, sigma: float = 0.5, lo: int = 10, hi: int = 120,
+                       s: float = 1.1) -> LabelledDocs:
+    """Synthetic labelled documents (stand-in for a labelled corpus such as
+    20news, Sec. IV-B): each class owns a topic, the ``topic_words`` words
+    whose vectors point most along a random class direction (so a topic is a
+    region of the word-vector space); a document of the class draws a share
+    ``on_topic`` of its distinct words from its topic, Zipf over the topic's
+    ranking, weighted by that rank's Zipf term frequency, and the rest from
+    the whole vocabulary, Zipf over the vocabulary, weighted likewise."""
+    vocab = vocabulary(vocab_size, d, seed + 1)
+    rng = np.random.default_rng(seed)
+    topics = []
+    for _ in range(classes):
+        u = rng.standard_normal(d)
+        topics.append(np.argsort(-(vocab.astype(np.float64) @ u), kind="stable")[:topic_words])
+    p_all = _zipf_probs(vocab_size, s)
+    p_top = _zipf_probs(topic_words, s)
+
+    def doc(c: int):
+        length = int(np.clip(np.round(rng.lognormal(np.log(median), sigma)), lo, hi))
+        k_top = min(topic_words, int(round(on_topic * length)))
+        ranks = rng.choice(topic_words, size=k_top, replace=False, p=p_top)
+        weight = {int(topics[c][r]): (r + 1.0) ** (-s) for r in ranks}
+        while len(weight) < length:
+            i = int(rng.choice(vocab_size, p=p_all))
+            weight.setdefault(i, (i + 1.0) ** (-s))
+        ids = np.array(sorted(weight))
+        return vocab[ids], np.array([weight[i] for i in ids.tolist()])
+
+    xs, ws, labels = [], [], []
+    for c in range(classes):
+        for _ in range(docs_per_class):
+            x, w = doc(c)
+            xs.append(x)
+            ws.append(w)
+            labels.append(c)
+    x_off = np.concatenate([[0], np.cumsum([len(w) for w in ws])]).astype(np.int64)
+    queries, qlabels = [], []
+    for c in range(classes):
+        for _ in range(queries_per_class):
+            queries.append(doc(c))
+            qlabels.append(c)
+    return LabelledDocs(np.concatenate(xs).astype(np.float32), np.concatenate(ws), x_off, np.array(labels),
+                        queries, np.array(qlabels))
+
+
 def retrieval(num_pairs: int = 10000, seed: int = 0, d: int = 128, lo: int = 256, hi: int = 2048) -> Batch:
     """Signature pairs of SIFT-like descriptors: m, n ~ Uniform{lo..hi}
     independently; descriptors |N(0,1)| then L2-normalised and scaled by 512;
