@@ -307,3 +307,22 @@ done:
  * wrapper grows its buffers and retries.  This helper reports the struct size
  * so the wrapper can check its ctypes layout. */
 int oracle_stats_size(void) { return (int)sizeof(oracle_stats); }
+
+/*
+ * Nearest of k points (centroids) for each of N points: the FP32 squared
+ * distance key of the NNS operation (key32, metric squared L2), lowest
+ * centroid index on ties.  The assignment step of the k-means colour
+ * quantisation that precedes the colour-transfer EMD (Sec. IV-D).
+ */
+void oracle_assign(const float *pts, int64_t N, const float *cent, int64_t k, int32_t d, int32_t *out)
+{
+    for (int64_t p = 0; p < N; ++p) {
+        float best = 0.0f;
+        int64_t bi = -1;
+        for (int64_t c = 0; c < k; ++c) {
+            const float v = key32(cent + c * d, pts + p * d, d, METRIC_SQL2);
+            if (bi < 0 || v < best) { best = v; bi = c; }
+        }
+        out[p] = (int32_t)bi;
+    }
+}
