@@ -195,6 +195,41 @@ int nnsemd_solve_one_to_many(nnsemd_ctx *ctx, int32_t num_pairs,
                              int32_t d, const nnsemd_options *opt,
                              double *costs_out, nnsemd_stats *stats);
 
+/* ---- colour transfer (the application of Sec. IV-D) ---------------------
+ * The pipeline: quantise both images' colours with nnsemd_kmeans, solve the
+ * NNS-EMD between the palettes (reference palette = suppliers with the
+ * cluster sizes as weights, source palette = consumers) with a plan, map
+ * every source palette colour to the barycentre of the reference colours it
+ * receives (nnsemd_barycentric), and recolour the source pixels
+ * (nnsemd_recolour).  All pointers are device pointers; every step is
+ * deterministic (exact sums), and the calls return when the work is done.
+ * Coordinates must be finite and >= 0 (NONFINITE otherwise). */
+
+/* k-means of pts [N][d] into k clusters: initial centroids are the points
+ * at indices floor((2c+1) N / 2k); each of `iters` steps assigns every point
+ * to its nearest centroid (the NNS operation's FP32 squared-distance key,
+ * lowest index on ties) and sets each centroid coordinate to
+ * float(correctly rounded sum of its points' coordinates / count) (a
+ * centroid without points keeps its value); then a final assignment.
+ * Outputs: centroids_out [k][d] float, labels_out [N] int32 (the final
+ * assignment), counts_out [k] int64 (points per label).  Errors:
+ * INVALID_ARG (k > N, sizes), NONFINITE, OOM, CUDA. */
+int nnsemd_kmeans(nnsemd_ctx *ctx, const float *pts, int64_t N, int32_t d, int32_t k, int32_t iters,
+                  float *centroids_out, int32_t *labels_out, int64_t *counts_out);
+
+/* Barycentric map of a plan (device arrays plan->i / j / f, plan->nnz
+ * entries, i into x [m][d], j into y [n][d]): y_out[j] = float(S_j / W_j),
+ * S_j the correctly rounded sum over the flows into j of f * x_i (FP64
+ * products), W_j the correctly rounded sum of their f; consumers without a
+ * flow keep y[j].  Errors: INVALID_ARG, NONFINITE, OOM, CUDA. */
+int nnsemd_barycentric(nnsemd_ctx *ctx, const nnsemd_plan *plan, const float *x, int64_t m, const float *y,
+                       int64_t n, int32_t d, float *y_out);
+
+/* out [N][d] = palette[labels[p]] ([k][d]).  Errors: INVALID_ARG (a label
+ * outside [0, k)), CUDA. */
+int nnsemd_recolour(nnsemd_ctx *ctx, const int32_t *labels, int64_t N, const float *palette, int32_t k,
+                    int32_t d, float *out);
+
 /* ---- the NNS operation alone --------------------------------------------
  * Round one of Alg. 1 (Sec. III-A, NNS step): for every consumer j, the
  * nearest supplier nn_out[j] (device int32 [n]), ties to the lowest index,

@@ -92,8 +92,12 @@ for _f in ("nnsemd_nearest", "nnsemd_proposal_create", "nnsemd_proposal_destroy"
     getattr(_lib, _f).restype = ctypes.c_int
 _lib.nnsemd_solve_one_to_many.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _I64, ctypes.c_int32,
                                           ctypes.POINTER(nnsemd_options), _P, ctypes.POINTER(nnsemd_stats)]
+_lib.nnsemd_kmeans.argtypes = [_P, _P, _I64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]
+_lib.nnsemd_barycentric.argtypes = [_P, ctypes.POINTER(nnsemd_plan), _P, _I64, _P, _I64, ctypes.c_int32, _P]
+_lib.nnsemd_recolour.argtypes = [_P, _P, _I64, _P, ctypes.c_int32, ctypes.c_int32, _P]
 for _f in ("nnsemd_create", "nnsemd_destroy", "nnsemd_set_stream", "nnsemd_solve", "nnsemd_solve_host",
-           "nnsemd_solve_batched", "nnsemd_solve_one_to_many"):
+           "nnsemd_solve_batched", "nnsemd_solve_one_to_many", "nnsemd_kmeans", "nnsemd_barycentric",
+           "nnsemd_recolour"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -279,6 +283,36 @@ class Context:
                                            ctypes.byref(st) if stats else None)
         self._check(rc)
         return costs, (st.as_dict() if stats else None)
+
+    # -- colour transfer -----------------------------------------------------
+    def kmeans(self, pts, k: int, iters: int):
+        """Device pts [N, d] float32 -> (centroids [k, d], labels [N] int32, counts [k] int64), device."""
+        import torch
+        N, d = pts.shape
+        cent = torch.empty(k, d, dtype=torch.float32, device=pts.device)
+        lab = torch.empty(N, dtype=torch.int32, device=pts.device)
+        cnt = torch.empty(k, dtype=torch.int64, device=pts.device)
+        self._bind_current_stream()
+        self._check(_lib.nnsemd_kmeans(self._h, _ptr(pts), N, d, k, iters, _ptr(cent), _ptr(lab), _ptr(cnt)))
+        return cent, lab, cnt
+
+    def barycentric(self, plan_i, plan_j, plan_f, x, y):
+        """Device plan arrays (int32, int32, float64), x [m, d], y [n, d] -> y' [n, d]."""
+        import torch
+        out = torch.empty_like(y)
+        pl = nnsemd_plan(plan_f.numel(), plan_f.numel(), _ptr(plan_i), _ptr(plan_j), _ptr(plan_f))
+        self._bind_current_stream()
+        self._check(_lib.nnsemd_barycentric(self._h, ctypes.byref(pl), _ptr(x), x.shape[0], _ptr(y), y.shape[0],
+                                            y.shape[1], _ptr(out)))
+        return out
+
+    def recolour(self, labels, palette):
+        import torch
+        out = torch.empty(labels.shape[0], palette.shape[1], dtype=torch.float32, device=labels.device)
+        self._bind_current_stream()
+        self._check(_lib.nnsemd_recolour(self._h, _ptr(labels), labels.shape[0], _ptr(palette), palette.shape[0],
+                                         palette.shape[1], _ptr(out)))
+        return out
 
     # -- nnsemd_nearest ------------------------------------------------------
     def nearest(self, x, y, metric: str = "l2"):
