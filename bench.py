@@ -417,10 +417,15 @@ def run_ours(args) -> dict | None:
 
     lowd = d <= 8
     if spec["batched"]:
-        # the persistent batched kernel is the step: its NNS work against the FP32 pipe
-        rl = roofline(d, "fp32", agg.get("nns_kernel_pairs", 0) or (last or {}).get("pair_evals", 0) * args.steps,
+        # the persistent batched kernel is the step: its NNS work against the
+        # FP32 pipe, or the tensor pipe when the contraction runs there
+        rl = roofline(d, precision, agg.get("nns_kernel_pairs", 0) or (last or {}).get("pair_evals", 0) * args.steps,
                       args.steps, total_ms, total_ms, lowd)
-        rl["kernel"] = "k_batched_lowd" if lowd else "k_batched_hd (persistent, one pair per CTA)"
+        if precision == "fp32":
+            rl["kernel"] = ("k_batched_lowd" if lowd else
+                            "k_batched_hd / k_batched_hd_small (persistent, one pair per CTA)")
+        else:
+            rl["kernel"] = f"k_batched_tc<{precision}> (persistent, one pair per CTA, tcgen05 NNS per round)"
         rl["traffic"] = None
     else:
         rl = roofline(d, precision, agg["nns_kernel_pairs"], agg["nns_kernel_launches"], agg["nns_kernel_ms"],
