@@ -295,7 +295,8 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
       break;
     }
     if (rounds >= round_limit) return fail(ctx, NNSEMD_ERR_ITER_LIMIT, "round limit m + n exceeded");
-    CK(cudaMemsetAsync(B.nnkey, 0xff, (size_t)nt * sizeof(unsigned long long), st));
+    // B.nnkey[0 .. nt) is all ones here: the compaction that produced the
+    // active lists reset the key of every surviving consumer
     int nrc;
     if (learned) {
       if (timed) CK(cudaEventRecord(ctx->ev[0], st));

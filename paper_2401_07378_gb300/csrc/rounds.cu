@@ -6,7 +6,7 @@
 //       with one 64-bit member key (key32 bits << 32 | consumer position)
 //       per consumer, so that sorting a group orders it by distance and
 //       then by consumer index (the greedy protocol's order).
-//   k_flow_small / k_flow_big
+//   k_flow (groups of <= 32: one thread or one warp each; longer: one CTA)
 //       sort each group (in one thread's registers for groups of at most 8,
 //       a warp-register bitonic network up to 32, a CTA network in shared or
 //       global memory beyond that), then walk it in FP64 exactly as the
@@ -135,6 +135,7 @@ struct CompactSide {
   int* count_out;       // survivors
   int nblocks;
   int check;            // check coordinates for finiteness
+  unsigned long long* key_reset;  // nullable: set key_reset[survivor position] = ~0 (next NNS's argmin keys)
 };
 
 struct CompactArgs {
@@ -230,6 +231,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_compact_scatter(CompactArgs A) {
   for (int k = 0; k < CP_ITEMS; ++k) {
     if (!flags[k]) continue;
     const int pos = base + k;
+    if (S.key_reset) S.key_reset[pos_out] = ~0ULL;
     if (!S.pts_in) {  // index-only list (d > 8: coordinates stay in place)
       S.idx_out[pos_out++] = origs[k];
       continue;
@@ -296,7 +298,7 @@ int launch_initial_pack(SolveBufs& B, cudaStream_t st) {
   A.side[0] = CompactSide{packed ? B.x : nullptr, B.d, nullptr, B.s, packed ? B.xa[B.cur] : nullptr, B.ia[B.cur],
                           (int)B.m, &B.st->mt, 0, 1};
   A.side[1] = CompactSide{packed ? B.y : nullptr, B.d, nullptr, B.c, packed ? B.ya[B.cur] : nullptr, B.ja[B.cur],
-                          (int)B.n, &B.st->nt, 0, 1};
+                          (int)B.n, &B.st->nt, 0, 1, B.nnkey};
   A.blockcounts = B.blockcounts;
   A.err = &B.st->err;
   compact_launch(A, B.dp, st);
@@ -308,8 +310,14 @@ int launch_initial_pack(SolveBufs& B, cudaStream_t st) {
 // --------------------------------------------------------------------------
 
 __global__ void k_group_count(const unsigned long long* __restrict__ nnkey, int nt, int mt, int* __restrict__ cnt,
-                              unsigned* err) {
+                              unsigned* err, DevState* st) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q == 0) {  // this round's group lists start empty (read from k_group_alloc on)
+    st->nseg = 0;
+    st->nbig = 0;
+    st->nmed = 0;
+    st->seg_cursor = 0;
+  }
   if (q >= nt) return;
   const unsigned p = (unsigned)(nnkey[q] & 0xffffffffULL);
   if (p >= (unsigned)mt) { atomicOr(err, EF_INTERNAL); return; }
@@ -546,10 +554,10 @@ NNS_DEV void thread_serve(const FlowArgs& A, int p, int2 sg, bool active) {
 // Groups of at most 32 consumers.  Each warp takes 32 groups of the group
 // list at a time and serves those of at most FLOW_THREAD_MAX one per lane;
 // then the warps serve the groups of 9..32 one per warp.
-__global__ void k_flow_small(FlowArgs A) {
+NNS_DEV void flow_small_blocks(const FlowArgs& A, int bid, int nblocks) {
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
-  const int warp = blockIdx.x * wpb + (threadIdx.x >> 5), nwarps = gridDim.x * wpb;
+  const int warp = bid * wpb + (threadIdx.x >> 5), nwarps = nblocks * wpb;
   const int nseg = A.st->nseg;
   for (int w0 = warp * 32; w0 < nseg; w0 += nwarps * 32) {
     const int w = w0 + lane;
@@ -609,10 +617,9 @@ NNS_DEV void block_sort_u64(Ptr a, int L) {
   }
 }
 
-__global__ void __launch_bounds__(BIG_THREADS) k_flow_big(FlowArgs A) {
-  __shared__ unsigned long long keys[BIG_SMEM_KEYS];
+NNS_DEV void flow_big_blocks(const FlowArgs& A, unsigned long long* keys, int bid, int nblocks) {
   const int nbig = A.st->nbig;
-  for (int b = blockIdx.x; b < nbig; b += gridDim.x) {
+  for (int b = bid; b < nbig; b += nblocks) {
     const int p = A.biglist[b];
     const int2 sg = A.seg[p];
     const int L = sg.y;
@@ -641,38 +648,40 @@ __global__ void __launch_bounds__(BIG_THREADS) k_flow_big(FlowArgs A) {
   }
 }
 
+// The flow step of a multi-CTA round in one launch: the first `nsmall`
+// blocks serve the groups of at most 32 consumers, the others the longer
+// groups (one block per group, keys sorted in shared memory).
+__global__ void __launch_bounds__(BIG_THREADS) k_flow(FlowArgs A, int nsmall) {
+  __shared__ unsigned long long keys[BIG_SMEM_KEYS];
+  if ((int)blockIdx.x < nsmall) flow_small_blocks(A, blockIdx.x, nsmall);
+  else flow_big_blocks(A, keys, blockIdx.x - nsmall, gridDim.x - nsmall);
+}
+
 // --------------------------------------------------------------------------
 // one multi-CTA round (the NNS operation is launched by the caller)
 // --------------------------------------------------------------------------
 
-__global__ void k_round_reset(DevState* st) {
-  st->nseg = 0;
-  st->nbig = 0;
-  st->nmed = 0;
-  st->seg_cursor = 0;
-}
-
 int launch_big_round(SolveBufs& B, int mt, int nt, long long round, cudaStream_t st) {
   const int cur = B.cur;
-  k_round_reset<<<1, 1, 0, st>>>(B.st);
-  k_group_count<<<(nt + 255) / 256, 256, 0, st>>>(B.nnkey, nt, mt, B.cnt, &B.st->err);
+  k_group_count<<<(nt + 255) / 256, 256, 0, st>>>(B.nnkey, nt, mt, B.cnt, &B.st->err, B.st);
   k_group_alloc<<<(mt + 255) / 256, 256, 0, st>>>(B.cnt, mt, B.seg, B.seglist, B.biglist, B.medlist, B.st);
   k_group_scatter<<<(nt + 255) / 256, 256, 0, st>>>(B.nnkey, nt, B.cnt, B.seg, B.member, B.ja[cur], B.protocol,
                                                     B.seed, round);
   FlowArgs F{B.x, B.y, B.d, B.metric, B.ia[cur], B.ja[cur], B.seg, B.seglist, B.biglist, B.medlist, B.member,
              B.s, B.c, B.terms, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, B.st};
-  int warps = (nt + 31) / 32;  // each warp takes 32 groups at a time; groups <= nt
+  // enough warps for every group of 9..32 at once (at most nt / 9 of them);
+  // the thread-per-group pass needs nt / 32
+  int warps = (nt + 8) / 9;
   int blocks = (warps + 7) / 8;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_flow_small<<<blocks, 256, 0, st>>>(F);
-  k_flow_big<<<152, BIG_THREADS, 0, st>>>(F);
+  k_flow<<<blocks + 152, BIG_THREADS, 0, st>>>(F, blocks);
   // weights update: compact into the other buffer
   CompactArgs A{};
   const bool packed = B.dp > 0;
   A.side[0] = CompactSide{packed ? B.xa[cur] : nullptr, B.dp, B.ia[cur], B.s, packed ? B.xa[cur ^ 1] : nullptr,
                           B.ia[cur ^ 1], mt, &B.st->mt, 0, 0};
   A.side[1] = CompactSide{packed ? B.ya[cur] : nullptr, B.dp, B.ja[cur], B.c, packed ? B.ya[cur ^ 1] : nullptr,
-                          B.ja[cur ^ 1], nt, &B.st->nt, 0, 0};
+                          B.ja[cur ^ 1], nt, &B.st->nt, 0, 0, B.nnkey};
   A.blockcounts = B.blockcounts;
   A.err = &B.st->err;
   compact_launch(A, B.dp, st);
