@@ -344,17 +344,20 @@ __global__ void k_rerank_certify(RerankArgs R) {
     const unsigned long long key = pack_key(acc, (unsigned)p);
     best = key < best ? key : best;
   }
+  // |y|_2^2 and |y|_1 in FP64, split over the lanes
+  double yl2 = 0.0, yl1 = 0.0;
+  for (int k = lane; k < R.d; k += 32) {
+    yl2 += (double)yrow[k] * yrow[k];
+    yl1 += fabs((double)yrow[k]);
+  }
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
     best = ob < best ? ob : best;
     tau = fminf(tau, __shfl_xor_sync(0xffffffffu, tau, o));
+    yl2 += __shfl_xor_sync(0xffffffffu, yl2, o);
+    yl1 += __shfl_xor_sync(0xffffffffu, yl1, o);
   }
   if (lane != 0) return;
-  double yl2 = 0.0, yl1 = 0.0;
-  for (int k = 0; k < R.d; ++k) {
-    yl2 += (double)yrow[k] * yrow[k];
-    yl1 += fabs((double)yrow[k]);
-  }
   yl2 = sqrt(yl2) * (1 + 1e-12);
   const bool certified =
       best != ~0ULL && certify(R.fmt, R.d, R.nrm_y[r], yl2, yl1, R.scale_y[r], __uint_as_float(R.stats_x[0]),
