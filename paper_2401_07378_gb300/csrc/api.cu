@@ -7,7 +7,10 @@
 //            the initial active sets (positive weight);
 //   rounds   while both active sets are larger than one CTA can hold: the
 //            multi-CTA round (K1 NNS, grouping, greedy flow, compaction);
-//   tail     once they fit, every remaining round in one CTA (k_finish);
+//   tail     once they fit, every remaining round in one launch: for d <= 8
+//            on a thread-block cluster (k_finish_cl, up to 2048 points per
+//            side) where the device can co-schedule one, else in one CTA
+//            (k_finish, k_finish_hd);
 //   final    R and the leftover mass as correctly rounded sums.
 // The host reads the two active counts after each multi-CTA round (a few
 // bytes from pinned memory) to size the next round's grids.
@@ -276,18 +279,23 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
   long long rounds = 0, pair_evals = 0;
   const long long round_limit = B.m + B.n;
   const bool lowd = B.dp > 0;
+  // the cluster tail takes over once both active sets fit it
+  const int clcap = lowd ? finish_cluster_cap(B.d, B.metric) : 0;
   if (learned) {
     // once per solve: supplier cells and radii, consumer proposals and bounds
     if (learned_prepare(*learned, B.x, B.m, B.y, B.n, B.d, st)) return fail(ctx, NNSEMD_ERR_CUDA, "proposal preparation");
     L += 8 + 8 * ((B.n + learned->chunk - 1) / learned->chunk);
   }
   while (mt > 0 && nt > 0) {
-    const bool tail = lowd ? (mt <= FIN_MAX && nt <= FIN_MAX && (int64_t)mt * nt <= FIN_PAIRS)
-                           : (mt <= FIN_MAX_HD && nt <= FIN_MAX_HD && (int64_t)mt * nt * B.d <= FIN_HD_WORK);
+    const bool tail = clcap ? (mt <= clcap && nt <= clcap)
+                      : lowd ? (mt <= FIN_MAX && nt <= FIN_MAX && (int64_t)mt * nt <= FIN_PAIRS)
+                             : (mt <= FIN_MAX_HD && nt <= FIN_MAX_HD && (int64_t)mt * nt * B.d <= FIN_HD_WORK);
     if (tail) {
       if (timed) CK(cudaEventRecord(ctx->ev[2], st));
       B.round0 = rounds;
-      const int lrc = lowd ? launch_finish(B, round_limit - rounds, st) : launch_finish_hd(B, round_limit - rounds, st);
+      const int lrc = clcap  ? launch_finish_cluster(B, round_limit - rounds, st)
+                      : lowd ? launch_finish(B, round_limit - rounds, st)
+                             : launch_finish_hd(B, round_limit - rounds, st);
       if (lrc) return fail(ctx, NNSEMD_ERR_CUDA, "finisher launch");
       if (timed) CK(cudaEventRecord(ctx->ev[3], st));
       tail_ran = true;

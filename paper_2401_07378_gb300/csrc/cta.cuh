@@ -9,10 +9,17 @@
 //                       memory and move with the compaction;
 //   GeoGlobal (d > 8)   coordinates stay in global memory (L2) and are read
 //                       by original index; the NNS step runs 64 x 64 tiles
-//                       staged in shared memory by 256-thread groups.
+//                       staged in shared memory by 256-thread groups;
+//   GeoSmemCluster      GeoSmem on every CTA of a thread-block cluster: each
+//                       CTA holds the whole state, finds the nearest
+//                       supplier of its slice of the consumers and sends the
+//                       keys to every CTA through distributed shared memory;
+//                       the rest of the round runs, identically, in every
+//                       CTA (one of them writes the results).
 // Grouping, greedy order, flow and compaction are the same for both.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <math_constants.h>
 
 #include "common.cuh"
@@ -97,6 +104,9 @@ struct CtaOut {
   int protocol;
   unsigned long long seed;
   long long round_base;
+  // nonzero: run the rounds without writing any flow, plan entry, cost term
+  // or residual out (a CTA of a cluster whose results another CTA writes)
+  int quiet;
 };
 
 // --------------------------------------------------------------------------
@@ -159,6 +169,63 @@ struct GeoSmem {
       if (q < nt && part == 0) S.nnk[q] = bk;
     }
     __syncthreads();
+  }
+};
+
+// The NNS step of GeoSmem spread over the CTAs of a cluster.  CTA r of R
+// scans the consumers [r nt / R, (r+1) nt / R) against every active supplier
+// and stores each key into the receive buffer of every CTA of the cluster;
+// one cluster barrier (release / acquire) then makes all nt keys visible in
+// every CTA.  The receive buffer alternates between two halves by round: a
+// CTA can write round t + 1's keys into a peer before the peer has copied
+// out round t's, never round t + 2's (that needs the peer at the barrier of
+// round t + 1).  Every CTA holds identical state, so every later step gives
+// identical results in all of them.
+template <int D, int DP, bool L1, int CAP>
+struct GeoSmemCluster : GeoSmem<D, DP, L1, CAP> {
+  unsigned long long xk[2][CAP];  // receive buffers (round parity)
+  int par;                        // half of xk used by the next round
+
+  template <int C>
+  NNS_DEV void nns(CtaCore<C>& S, int mt, int nt) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned rank = cl.block_rank(), ncl = cl.num_blocks();
+    const int h = par;
+    const int q0 = (int)((long long)nt * rank / ncl), q1 = (int)((long long)nt * (rank + 1) / ncl);
+    const int tid = threadIdx.x, T = blockDim.x, ns = q1 - q0;
+    int split = 1;
+    while (split < 32 && ns * split * 2 <= T) split <<= 1;
+    for (int base = 0; base < ns; base += T / split) {
+      const int q = q0 + base + tid / split, part = tid & (split - 1);
+      unsigned long long bk = ~0ULL;
+      if (q < q1) {
+        float yv[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) yv[k] = this->ys[q * DP + k];
+        float best = CUDART_INF_F;
+        int bp = -1;
+        for (int p = part; p < mt; p += split) {
+          const float v =
+              L1 ? key32<METRIC_L1>(this->xs + p * DP, yv, D) : key32<METRIC_SQL2>(this->xs + p * DP, yv, D);
+          if (bp < 0 || v < best) { best = v; bp = p; }
+        }
+        if (bp >= 0) bk = pack_key(best, (unsigned)bp);
+      }
+      for (int o = 1; o < split; o <<= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, bk, o);
+        bk = other < bk ? other : bk;
+      }
+      // the split lanes of a consumer share its stores to the cluster
+      if (q < q1)
+        for (unsigned r = part; r < ncl; r += split) cl.map_shared_rank(&xk[h][0], r)[q] = bk;
+    }
+    cl.sync();
+    for (int q = tid; q < nt; q += T) S.nnk[q] = xk[h][q];
+    __syncthreads();
+    // every thread read `par` before this barrier; the next read follows
+    // the barriers of the rest of the round
+    if (tid == 0) par = h ^ 1;
   }
 };
 
@@ -422,7 +489,8 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
         const double f = greedy_step(s, c);
         S.cres[q] = c;
         const unsigned k = atomicAdd(&S.nflow, 1u);
-        if (deferred) {
+        if (O.quiet) {
+        } else if (deferred) {
           const unsigned long long slot = nnz + k;
           O.fl_i[slot] = S.iidx[p];
           O.fl_j[slot] = S.jidx[q];
@@ -439,7 +507,7 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
     __syncthreads();
     // ---- cost terms and plan entries of the round's flows, one per thread
     const unsigned nflow = S.nflow;
-    for (unsigned k = deferred ? nflow : tid; k < nflow; k += T) {
+    for (unsigned k = (deferred || O.quiet) ? nflow : tid; k < nflow; k += T) {
       const unsigned long long pq = S.mem[k];
       const int p = (int)(pq >> 32), q = (int)(pq & 0xffffffffULL);
       const double f = __longlong_as_double((long long)S.nnk[k]);

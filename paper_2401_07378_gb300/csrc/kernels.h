@@ -18,6 +18,11 @@ constexpr int PAD_POINTS = K1_TS;
 // with coordinates; d > 8: per-point state only, coordinates stay in L2).
 constexpr int FIN_MAX = 1024;
 constexpr int FIN_MAX_HD = 2048;
+// Point capacity per side of the cluster tail (d <= 8): its whole state,
+// the coordinates at DP floats per point and the key exchange buffers fit
+// one CTA's shared memory up to 2048 points for DP <= 4, 1024 for DP = 8.
+constexpr int FIN_CL_MAX = 2048;
+__host__ __device__ constexpr int fin_cl_cap(int dp) { return dp <= 4 ? FIN_CL_MAX : 1024; }
 
 __host__ __device__ inline int padded_dim(int d) { return d <= 2 ? 2 : (d <= 4 ? 4 : 8); }
 __host__ __device__ inline int64_t pad_points(int64_t n) { return (n + PAD_POINTS - 1) / PAD_POINTS * PAD_POINTS; }
@@ -98,6 +103,11 @@ int launch_big_round(SolveBufs& B, int mt, int nt, long long round, cudaStream_t
 int launch_nns_lowd(const SolveBufs& B, int mt, int nt, cudaStream_t st);
 // Run all remaining rounds of the current active lists in one CTA.
 int launch_finish(const SolveBufs& B, int64_t round_limit, cudaStream_t st);
+// The same on a thread-block cluster (k_finish_cl), for active sets of at
+// most finish_cluster_cap(d) points per side.  finish_cluster_cap returns 0
+// when this device cannot co-schedule the cluster (the one-CTA tail serves).
+int finish_cluster_cap(int d, int metric);
+int launch_finish_cluster(const SolveBufs& B, int64_t round_limit, cudaStream_t st);
 // A whole pair with m, n <= FIN_MAX and d <= 8 in one launch (writes st->cost,
 // nnz, rounds, pair_evals, leftover and the plan).
 int launch_solve_small(const SolveBufs& B, const double* a, const double* b, cudaStream_t st);

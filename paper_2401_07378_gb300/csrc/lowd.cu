@@ -18,7 +18,12 @@
 //                     memory.  Used for the tail rounds of a large solve and,
 //                     one pair per CTA, for batches of small pairs (Sec. III-D
 //                     batch processing).
+// k_finish_cl      -- the tail rounds on a thread-block cluster: the NNS step
+//                     split over the cluster's CTAs (keys exchanged through
+//                     distributed shared memory), up to 2048 points per side.
 #include <math_constants.h>
+
+#include <atomic>
 
 #include "common.cuh"
 #include "cta.cuh"
@@ -345,6 +350,170 @@ int launch_finish(const SolveBufs& B, int64_t round_limit, cudaStream_t st) {
     default: return -1;
   }
 #undef FIN_CASE
+}
+
+// --------------------------------------------------------------------------
+// the tail on a thread-block cluster (d <= 8)
+// --------------------------------------------------------------------------
+
+#ifndef NNSEMD_TAIL_CLUSTER
+#define NNSEMD_TAIL_CLUSTER 16  // preferred cluster size (8 where 16 cannot be co-scheduled)
+#endif
+
+template <int D, int DP, bool L1>
+struct LowdClusterSmem {
+  static constexpr int CAP = fin_cl_cap(DP);
+  CtaCore<CAP> S;
+  GeoSmemCluster<D, DP, L1, CAP> G;
+};
+
+// Every CTA of the cluster loads the current active lists and runs every
+// remaining round; the NNS step is split over the cluster (GeoSmemCluster),
+// the other steps run redundantly on identical state, and CTA 0 alone writes
+// flows, residuals and the solve state.
+template <int D, int DP, bool L1>
+__global__ void __launch_bounds__(FIN_THREADS, 1) k_finish_cl(SolveBufs B, long long round_limit) {
+  namespace cg = cooperative_groups;
+  using Sm = LowdClusterSmem<D, DP, L1>;
+  constexpr int CAP = Sm::CAP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Sm& L = *reinterpret_cast<Sm*>(smem_raw);
+  CtaCore<CAP>& S = L.S;
+  cg::cluster_group cl = cg::this_cluster();
+  const bool leader = cl.block_rank() == 0;
+  const int tid = threadIdx.x;
+  const int mt = B.st->mt, nt = B.st->nt;
+  if (mt > CAP || nt > CAP) {  // the same decision in every CTA
+    if (tid == 0 && leader) atomicOr(&B.st->err, EF_INTERNAL);
+    return;
+  }
+  const float* xa = B.xa[B.cur];
+  const float* ya = B.ya[B.cur];
+  for (int p = tid; p < mt; p += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < DP; ++k) L.G.xs[p * DP + k] = xa[(size_t)p * DP + k];
+    S.iidx[p] = B.ia[B.cur][p];
+    S.sres[p] = B.s[S.iidx[p]];
+  }
+  for (int q = tid; q < nt; q += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < DP; ++k) L.G.ys[q * DP + k] = ya[(size_t)q * DP + k];
+    S.jidx[q] = B.ja[B.cur][q];
+    S.cres[q] = B.c[S.jidx[q]];
+  }
+  if (tid == 0) {
+    S.mt = mt;
+    S.nt = nt;
+    L.G.par = 0;
+  }
+  // every CTA of the cluster is running before any writes a peer's memory
+  cl.sync();
+  CtaOut O{nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, &B.st->err,
+           nullptr, nullptr, nullptr, B.x, B.y, B.d, B.protocol, B.seed, B.round0, 1};
+  if (leader)
+    O = CtaOut{B.terms, nullptr, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, B.s, B.c, &B.st->err,
+               B.fl_i, B.fl_j, B.fl_f, B.x, B.y, B.d, B.protocol, B.seed, B.round0, 0};
+  unsigned long long nnz = B.st->nnz;
+  long long rounds = B.st->rounds, pe = B.st->pair_evals;
+  cta_rounds(S, L.G, B.metric, O, nnz, rounds, pe, round_limit);
+  if (tid == 0 && leader) {
+    B.st->nnz = nnz;
+    B.st->rounds = rounds;
+    B.st->pair_evals = pe;
+    B.st->mt = S.mt;
+    B.st->nt = S.nt;
+  }
+  // no CTA leaves while a peer may still address its shared memory
+  cl.sync();
+}
+
+// Cluster size usable for k_finish_cl<D, DP, L1> on `dev` (cached): the
+// preferred size if the device can co-schedule one such cluster, else 8,
+// else 0.
+template <int D, int DP, bool L1>
+static int finish_cl_size(int dev) {
+  static std::atomic<int> cache[64];
+  if (dev < 0 || dev >= 64) return 0;
+  const int c = cache[dev].load();
+  if (c) return c > 0 ? c : 0;
+  const size_t smem = sizeof(LowdClusterSmem<D, DP, L1>);
+  int found = -1;
+  if (cudaFuncSetAttribute(k_finish_cl<D, DP, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+          cudaSuccess &&
+      cudaFuncSetAttribute(k_finish_cl<D, DP, L1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+          cudaSuccess) {
+    for (int cs : {NNSEMD_TAIL_CLUSTER, 8}) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cs;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(cs);
+      cfg.blockDim = dim3(FIN_THREADS);
+      cfg.dynamicSmemBytes = smem;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, k_finish_cl<D, DP, L1>, &cfg) == cudaSuccess && n > 0) {
+        found = cs;
+        break;
+      }
+    }
+  }
+  cudaGetLastError();  // a refused size is an answer, not an error of the solve
+  cache[dev].store(found);
+  return found > 0 ? found : 0;
+}
+
+template <int D, int DP, bool L1>
+static int finish_cl_t(const SolveBufs& B, long long round_limit, cudaStream_t st) {
+  static_assert(sizeof(LowdClusterSmem<D, DP, L1>) <= 227 * 1024, "cluster tail state exceeds shared memory");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  const int cs = finish_cl_size<D, DP, L1>(dev);
+  if (cs == 0) return -1;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(cs);
+  cfg.blockDim = dim3(FIN_THREADS);
+  cfg.dynamicSmemBytes = sizeof(LowdClusterSmem<D, DP, L1>);
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_finish_cl<D, DP, L1>, B, round_limit) == cudaSuccess ? 0 : -1;
+}
+
+int finish_cluster_cap(int d, int metric) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  const bool l1 = metric == METRIC_L1;
+#define FCL_CASE(DD, DPP) \
+  case DD:                \
+    return (l1 ? finish_cl_size<DD, DPP, true>(dev) : finish_cl_size<DD, DPP, false>(dev)) ? fin_cl_cap(DPP) : 0;
+  switch (d) {
+    FCL_CASE(1, 2) FCL_CASE(2, 2) FCL_CASE(3, 4) FCL_CASE(4, 4)
+    FCL_CASE(5, 8) FCL_CASE(6, 8) FCL_CASE(7, 8) FCL_CASE(8, 8)
+    default: return 0;
+  }
+#undef FCL_CASE
+}
+
+int launch_finish_cluster(const SolveBufs& B, int64_t round_limit, cudaStream_t st) {
+  const bool l1 = B.metric == METRIC_L1;
+#define FCL_CASE(DD, DPP) \
+  case DD:                \
+    return l1 ? finish_cl_t<DD, DPP, true>(B, round_limit, st) : finish_cl_t<DD, DPP, false>(B, round_limit, st);
+  switch (B.d) {
+    FCL_CASE(1, 2) FCL_CASE(2, 2) FCL_CASE(3, 4) FCL_CASE(4, 4)
+    FCL_CASE(5, 8) FCL_CASE(6, 8) FCL_CASE(7, 8) FCL_CASE(8, 8)
+    default: return -1;
+  }
+#undef FCL_CASE
 }
 
 // --------------------------------------------------------------------------
