@@ -173,18 +173,47 @@ struct GeoSmem {
 };
 
 // The NNS step of GeoSmem spread over the CTAs of a cluster.  CTA r of R
-// scans the consumers [r nt / R, (r+1) nt / R) against every active supplier
-// and stores each key into the receive buffer of every CTA of the cluster;
-// one cluster barrier (release / acquire) then makes all nt keys visible in
-// every CTA.  The receive buffer alternates between two halves by round: a
-// CTA can write round t + 1's keys into a peer before the peer has copied
-// out round t's, never round t + 2's (that needs the peer at the barrier of
-// round t + 1).  Every CTA holds identical state, so every later step gives
-// identical results in all of them.
-template <int D, int DP, bool L1, int CAP>
+// (R >= 8) scans the consumers [r nt / R, (r+1) nt / R) against every active
+// supplier and stores each key into the receive buffer of every CTA of the
+// cluster; one cluster barrier (release / acquire) then makes all nt keys
+// visible in every CTA.  The receive buffer alternates between two halves by
+// round: a CTA can write round t + 1's keys into a peer before the peer has
+// copied out round t's, never round t + 2's (that needs the peer at the
+// barrier of round t + 1).  Every CTA holds identical state, so every later
+// step gives identical results in all of them.
+//
+// Inside a CTA a warp takes 64 consumers of the slice (two per lane, packed
+// in FP32x2 registers) and a contiguous chunk of the suppliers; all lanes
+// read the same supplier (a shared-memory broadcast), so one load feeds 64
+// pairs.  Each lane keeps the first minimum of its chunk (ascending
+// positions); the chunks merge through a 64-bit atomicMin on (key bits,
+// position), which keeps the lowest-index tie-break.
+template <int D, int DP, bool L1, int CAP, int NT>
 struct GeoSmemCluster : GeoSmem<D, DP, L1, CAP> {
-  unsigned long long xk[2][CAP];  // receive buffers (round parity)
-  int par;                        // half of xk used by the next round
+  static constexpr int kThreads = NT;     // threads of each CTA
+  static constexpr int kSlice = CAP / 8;  // consumers per CTA at most (R >= 8)
+  unsigned long long xk[2][CAP];          // receive buffers (round parity)
+  unsigned long long red[kSlice];         // the slice's keys, merged over chunks
+  int par;                                // half of xk used by the next round
+
+  NNS_DEV float key_one(const float* xv, const float* yv) const {
+    return L1 ? key32<METRIC_L1>(xv, yv, D) : key32<METRIC_SQL2>(xv, yv, D);
+  }
+  // keys of supplier p against the two consumers packed in y2
+  NNS_DEV unsigned long long key_two(int p, const unsigned long long* y2, const float* ya, const float* yb) const {
+    float xv[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) xv[k] = this->xs[p * DP + k];
+    if (L1) return f2_pack(key_one(xv, ya), key_one(xv, yb));
+    unsigned long long t = f2_sub(f2_pack(xv[0], xv[0]), y2[0]);
+    unsigned long long acc = f2_mul(t, t);
+#pragma unroll
+    for (int k = 1; k < D; ++k) {
+      t = f2_sub(f2_pack(xv[k], xv[k]), y2[k]);
+      acc = f2_fma(t, t, acc);
+    }
+    return acc;
+  }
 
   template <int C>
   NNS_DEV void nns(CtaCore<C>& S, int mt, int nt) {
@@ -192,33 +221,43 @@ struct GeoSmemCluster : GeoSmem<D, DP, L1, CAP> {
     cg::cluster_group cl = cg::this_cluster();
     const unsigned rank = cl.block_rank(), ncl = cl.num_blocks();
     const int h = par;
-    const int q0 = (int)((long long)nt * rank / ncl), q1 = (int)((long long)nt * (rank + 1) / ncl);
+    // (32-bit arithmetic: nt, mt <= CAP and R, chunks <= 32)
+    const int q0 = (int)((unsigned)nt * rank / ncl), q1 = (int)((unsigned)nt * (rank + 1) / ncl);
     const int tid = threadIdx.x, T = blockDim.x, ns = q1 - q0;
-    int split = 1;
-    while (split < 32 && ns * split * 2 <= T) split <<= 1;
-    for (int base = 0; base < ns; base += T / split) {
-      const int q = q0 + base + tid / split, part = tid & (split - 1);
-      unsigned long long bk = ~0ULL;
-      if (q < q1) {
-        float yv[D];
+    for (int i = tid; i < ns; i += T) red[i] = ~0ULL;
+    __syncthreads();
+    const int cgroups = (ns + 63) >> 6, nw = T >> 5, w = tid >> 5, lane = tid & 31;
+    if (cgroups > 0 && w < nw / cgroups * cgroups) {
+      const int chunks = nw / cgroups, ch = w / cgroups;
+      const int qa = 64 * (w % cgroups) + lane, qb = qa + 32;  // slice positions
+      float ya[D], yb[D];
+      unsigned long long y2[D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) yv[k] = this->ys[q * DP + k];
-        float best = CUDART_INF_F;
-        int bp = -1;
-        for (int p = part; p < mt; p += split) {
-          const float v =
-              L1 ? key32<METRIC_L1>(this->xs + p * DP, yv, D) : key32<METRIC_SQL2>(this->xs + p * DP, yv, D);
-          if (bp < 0 || v < best) { best = v; bp = p; }
+      for (int k = 0; k < D; ++k) {
+        ya[k] = qa < ns ? this->ys[(q0 + qa) * DP + k] : 0.f;
+        yb[k] = qb < ns ? this->ys[(q0 + qb) * DP + k] : 0.f;
+        y2[k] = f2_pack(ya[k], yb[k]);
+      }
+      const int s0 = (int)((unsigned)(mt * ch) / (unsigned)chunks);
+      const int s1 = (int)((unsigned)(mt * (ch + 1)) / (unsigned)chunks);
+      if (s0 < s1) {
+        unsigned long long kk = key_two(s0, y2, ya, yb);
+        float ba = f2_lo(kk), bb = f2_hi(kk);
+        int pa = s0, pb = s0;
+        for (int p = s0 + 1; p < s1; ++p) {
+          kk = key_two(p, y2, ya, yb);
+          const float ka = f2_lo(kk), kb = f2_hi(kk);
+          if (ka < ba) { ba = ka; pa = p; }
+          if (kb < bb) { bb = kb; pb = p; }
         }
-        if (bp >= 0) bk = pack_key(best, (unsigned)bp);
+        if (qa < ns) atomicMin(&red[qa], pack_key(ba, (unsigned)pa));
+        if (qb < ns) atomicMin(&red[qb], pack_key(bb, (unsigned)pb));
       }
-      for (int o = 1; o < split; o <<= 1) {
-        const unsigned long long other = __shfl_xor_sync(0xffffffffu, bk, o);
-        bk = other < bk ? other : bk;
-      }
-      // the split lanes of a consumer share its stores to the cluster
-      if (q < q1)
-        for (unsigned r = part; r < ncl; r += split) cl.map_shared_rank(&xk[h][0], r)[q] = bk;
+    }
+    __syncthreads();
+    for (int i = tid; i < ns * (int)ncl; i += T) {
+      const int r = i / ns, q = i - r * ns;
+      cl.map_shared_rank(&xk[h][0], r)[q0 + q] = red[q];
     }
     cl.sync();
     for (int q = tid; q < nt; q += T) S.nnk[q] = xk[h][q];

@@ -359,12 +359,16 @@ int launch_finish(const SolveBufs& B, int64_t round_limit, cudaStream_t st) {
 #ifndef NNSEMD_TAIL_CLUSTER
 #define NNSEMD_TAIL_CLUSTER 16  // preferred cluster size (8 where 16 cannot be co-scheduled)
 #endif
+#ifndef NNSEMD_TAIL_THREADS
+#define NNSEMD_TAIL_THREADS 512  // threads per CTA of the cluster tail
+#endif
+constexpr int FIN_CL_THREADS = NNSEMD_TAIL_THREADS;
 
 template <int D, int DP, bool L1>
 struct LowdClusterSmem {
   static constexpr int CAP = fin_cl_cap(DP);
   CtaCore<CAP> S;
-  GeoSmemCluster<D, DP, L1, CAP> G;
+  GeoSmemCluster<D, DP, L1, CAP, FIN_CL_THREADS> G;
 };
 
 // Every CTA of the cluster loads the current active lists and runs every
@@ -372,7 +376,7 @@ struct LowdClusterSmem {
 // the other steps run redundantly on identical state, and CTA 0 alone writes
 // flows, residuals and the solve state.
 template <int D, int DP, bool L1>
-__global__ void __launch_bounds__(FIN_THREADS, 1) k_finish_cl(SolveBufs B, long long round_limit) {
+__global__ void __launch_bounds__(FIN_CL_THREADS, 1) k_finish_cl(SolveBufs B, long long round_limit) {
   namespace cg = cooperative_groups;
   using Sm = LowdClusterSmem<D, DP, L1>;
   constexpr int CAP = Sm::CAP;
@@ -383,7 +387,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_finish_cl(SolveBufs B, long 
   const bool leader = cl.block_rank() == 0;
   const int tid = threadIdx.x;
   const int mt = B.st->mt, nt = B.st->nt;
-  if (mt > CAP || nt > CAP) {  // the same decision in every CTA
+  if (mt > CAP || nt > CAP || cl.num_blocks() < 8) {  // the same decision in every CTA
     if (tid == 0 && leader) atomicOr(&B.st->err, EF_INTERNAL);
     return;
   }
@@ -450,7 +454,7 @@ static int finish_cl_size(int dev) {
       at[0].val.clusterDim.y = 1;
       at[0].val.clusterDim.z = 1;
       cfg.gridDim = dim3(cs);
-      cfg.blockDim = dim3(FIN_THREADS);
+      cfg.blockDim = dim3(FIN_CL_THREADS);
       cfg.dynamicSmemBytes = smem;
       cfg.attrs = at;
       cfg.numAttrs = 1;
@@ -480,7 +484,7 @@ static int finish_cl_t(const SolveBufs& B, long long round_limit, cudaStream_t s
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(cs);
-  cfg.blockDim = dim3(FIN_THREADS);
+  cfg.blockDim = dim3(FIN_CL_THREADS);
   cfg.dynamicSmemBytes = sizeof(LowdClusterSmem<D, DP, L1>);
   cfg.stream = st;
   cfg.attrs = at;
