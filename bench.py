@@ -257,19 +257,30 @@ def oracle_sample(name: str, inputs=None, full_work: int | None = None) -> dict:
 # arms
 # ---------------------------------------------------------------------------
 
-def source_hash(path: str) -> str:
-    with open(path, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()
+K1_BEGIN = "// K1: fused FP32 distance + argmin"
+K1_END = "// one-CTA solver"
+
+
+def k1_source_hash() -> str:
+    """sha256 over K1's source: its section of lowd.cu (from the K1 banner to
+    the next section's) followed by common.cuh, whose helpers it inlines."""
+    csrc = os.path.join(ROOT, "paper_2401_07378_gb300", "csrc")
+    with open(os.path.join(csrc, "lowd.cu")) as fh:
+        text = fh.read()
+    begin = text.index(K1_BEGIN)
+    part = text[begin:text.index(K1_END, begin)]
+    with open(os.path.join(csrc, "common.cuh")) as fh:
+        part += fh.read()
+    return hashlib.sha256(part.encode()).hexdigest()
 
 
 def measured_traffic() -> float | None:
     """DRAM bytes per K1 launch from the committed ncu capture, if it was
-    taken on the current kernel source."""
+    taken on the current K1 source."""
     try:
         with open(COUNTERS_FILE) as fh:
             c = json.load(fh)
-        src = os.path.join(ROOT, "paper_2401_07378_gb300", "csrc", "lowd.cu")
-        if c.get("source_sha256") != source_hash(src):
+        if c.get("source_sha256") != k1_source_hash():
             return None
         return float(c["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
