@@ -263,13 +263,10 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
   CK(cudaMemsetAsync(B.st, 0, sizeof(DevState), st));
   CK(cudaMemsetAsync(B.xs_acc, 0, 4 * XS_LIMBS * sizeof(unsigned long long), st));
   CK(cudaMemsetAsync(B.cnt, 0, B.m * sizeof(int), st));
-  launch_xs_accum(a, B.m, B.xs_acc, &B.st->err, true, st);
-  launch_xs_accum(b, B.n, B.xs_acc + XS_LIMBS, &B.st->err, true, st);
-  launch_normalise(a, B.m, B.xs_acc, &B.st->total_a, B.s, &B.st->err, st);
-  launch_normalise(b, B.n, B.xs_acc + XS_LIMBS, &B.st->total_b, B.c, &B.st->err, st);
+  launch_setup_sums(B, a, b, st);
   B.cur = 0;
   launch_initial_pack(B, st);
-  L += 6;
+  L += 4;
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(ctx->hstate, B.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -345,7 +342,7 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
     nt = ctx->hstate->nt;
   }
   launch_leftover(B, st);
-  L += 8;
+  L += 2;
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(ctx->hstate, B.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));

@@ -123,7 +123,7 @@ struct GeoTC {
   }
 
   template <int C>
-  NNS_DEV void nns(CtaCore<C>& S, int mt, int nt) {
+  NNS_DEV const unsigned long long* nns(CtaCore<C>& S, int mt, int nt, long long = 0) {
     const int tid = threadIdx.x, T = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int qtiles = (nt + TC_BM - 1) / TC_BM;
@@ -330,6 +330,7 @@ struct GeoTC {
       }
     }
     __syncthreads();
+    return S.nnk;
   }
 };
 

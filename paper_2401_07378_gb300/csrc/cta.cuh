@@ -141,9 +141,10 @@ struct GeoSmem {
   NNS_DEV double dist64(const CtaCore<C>& S, int p, int q, int metric) const {
     return cost_dist64(xs + p * DP, ys + q * DP, D, metric);
   }
-  // S.nnk[q] = (key32 bits << 32 | p) of the nearest active supplier
+  // S.nnk[q] = (key32 bits << 32 | p) of the nearest active supplier;
+  // returns S.nnk (every NNS policy returns the array holding the keys)
   template <int C>
-  NNS_DEV void nns(CtaCore<C>& S, int mt, int nt) const {
+  NNS_DEV const unsigned long long* nns(CtaCore<C>& S, int mt, int nt, long long = 0) const {
     const int tid = threadIdx.x, T = blockDim.x;
     int split = 1;
     while (split < 32 && nt * split * 2 <= T) split <<= 1;
@@ -169,6 +170,7 @@ struct GeoSmem {
       if (q < nt && part == 0) S.nnk[q] = bk;
     }
     __syncthreads();
+    return S.nnk;
   }
 };
 
@@ -176,11 +178,12 @@ struct GeoSmem {
 // (R >= 8) scans the consumers [r nt / R, (r+1) nt / R) against every active
 // supplier and stores each key into the receive buffer of every CTA of the
 // cluster; one cluster barrier (release / acquire) then makes all nt keys
-// visible in every CTA.  The receive buffer alternates between two halves by
-// round: a CTA can write round t + 1's keys into a peer before the peer has
-// copied out round t's, never round t + 2's (that needs the peer at the
-// barrier of round t + 1).  Every CTA holds identical state, so every later
-// step gives identical results in all of them.
+// visible in every CTA, and the round's later steps read them there.  The
+// receive buffer alternates between two halves by round parity: a CTA can
+// write round t + 1's keys into a peer while the peer still reads round t's,
+// never round t + 2's (that needs the peer at the barrier of round t + 1,
+// after its round t).  Every CTA holds identical state, so every later step
+// gives identical results in all of them.
 //
 // Inside a CTA a warp takes 64 consumers of the slice (two per lane, packed
 // in FP32x2 registers) and a contiguous chunk of the suppliers; all lanes
@@ -193,8 +196,7 @@ struct GeoSmemCluster : GeoSmem<D, DP, L1, CAP> {
   static constexpr int kThreads = NT;     // threads of each CTA
   static constexpr int kSlice = CAP / 8;  // consumers per CTA at most (R >= 8)
   unsigned long long xk[2][CAP];          // receive buffers (round parity)
-  unsigned long long red[kSlice];         // the slice's keys, merged over chunks
-  int par;                                // half of xk used by the next round
+  unsigned long long red[kSlice];         // the slice's keys merged over chunks; all ones between rounds
 
   NNS_DEV float key_one(const float* xv, const float* yv) const {
     return L1 ? key32<METRIC_L1>(xv, yv, D) : key32<METRIC_SQL2>(xv, yv, D);
@@ -215,17 +217,20 @@ struct GeoSmemCluster : GeoSmem<D, DP, L1, CAP> {
     return acc;
   }
 
+  // Set red to all ones (before the first round; each round restores it).
+  NNS_DEV void init() {
+    for (int i = threadIdx.x; i < kSlice; i += blockDim.x) red[i] = ~0ULL;
+  }
+
   template <int C>
-  NNS_DEV void nns(CtaCore<C>& S, int mt, int nt) {
+  NNS_DEV const unsigned long long* nns(CtaCore<C>&, int mt, int nt, long long round) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     const unsigned rank = cl.block_rank(), ncl = cl.num_blocks();
-    const int h = par;
+    const int h = (int)(round & 1);
     // (32-bit arithmetic: nt, mt <= CAP and R, chunks <= 32)
     const int q0 = (int)((unsigned)nt * rank / ncl), q1 = (int)((unsigned)nt * (rank + 1) / ncl);
     const int tid = threadIdx.x, T = blockDim.x, ns = q1 - q0;
-    for (int i = tid; i < ns; i += T) red[i] = ~0ULL;
-    __syncthreads();
     const int cgroups = (ns + 63) >> 6, nw = T >> 5, w = tid >> 5, lane = tid & 31;
     if (cgroups > 0 && w < nw / cgroups * cgroups) {
       const int chunks = nw / cgroups, ch = w / cgroups;
@@ -260,11 +265,10 @@ struct GeoSmemCluster : GeoSmem<D, DP, L1, CAP> {
       cl.map_shared_rank(&xk[h][0], r)[q0 + q] = red[q];
     }
     cl.sync();
-    for (int q = tid; q < nt; q += T) S.nnk[q] = xk[h][q];
-    __syncthreads();
-    // every thread read `par` before this barrier; the next read follows
-    // the barriers of the rest of the round
-    if (tid == 0) par = h ^ 1;
+    // restore red for the next round (whose atomics follow this round's
+    // barriers)
+    for (int i = tid; i < ns; i += T) red[i] = ~0ULL;
+    return xk[h];
   }
 };
 
@@ -376,7 +380,7 @@ struct GeoGlobal {
     return cost_dist64(x + (size_t)S.iidx[p] * d, y + (size_t)S.jidx[q] * d, d, metric);
   }
   template <int C>
-  NNS_DEV void nns(CtaCore<C>& S, int mt, int nt) {
+  NNS_DEV const unsigned long long* nns(CtaCore<C>& S, int mt, int nt, long long = 0) {
     const int g = threadIdx.x / TG_THREADS, gt = threadIdx.x % TG_THREADS;
     const int ngroups = blockDim.x / TG_THREADS;
     for (int c0 = g * TG_M; c0 < nt; c0 += ngroups * TG_M) {
@@ -392,6 +396,7 @@ struct GeoGlobal {
         }
     }
     __syncthreads();
+    return S.nnk;
   }
 };
 
@@ -403,35 +408,63 @@ struct GeoGlobal {
 // --------------------------------------------------------------------------
 
 // Stable compaction of both active lists to the points with weight left.
+// Warp w owns positions [32 IT w, 32 IT (w + 1)), lane l the positions
+// 32 IT w + 32 k + l (coalesced shared-memory accesses); ballots give each
+// kept point its rank inside the warp and one block scan the warps' offsets.
+// Every kept value is loaded before the scan's barriers and stored after
+// them, so the in-place moves never overwrite a value not yet read.
 template <int CAP, class Geo>
 NNS_DEV void cta_compact(CtaCore<CAP>& S, Geo& G) {
   constexpr int IT = (CAP + Geo::kThreads - 1) / Geo::kThreads;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int base = (tid >> 5) * 32 * IT;
+  const unsigned lt = (1u << lane) - 1u;
   const int mt = S.mt, nt = S.nt;
-  bool ks[IT], kc[IT];
+  unsigned bs[IT], bc[IT];
   double sv[IT], cv[IT];
   int iv[IT], jv[IT];
   typename Geo::PX px[IT], py[IT];
   int ns = 0, nc = 0;
 #pragma unroll
   for (int k = 0; k < IT; ++k) {
-    const int p = tid * IT + k;
-    ks[k] = p < mt && residual_positive(S.sres[p]);
-    kc[k] = p < nt && residual_positive(S.cres[p]);
-    if (ks[k]) { sv[k] = S.sres[p]; iv[k] = S.iidx[p]; G.load_x(p, px[k]); }
-    if (kc[k]) { cv[k] = S.cres[p]; jv[k] = S.jidx[p]; G.load_y(p, py[k]); }
-    ns += ks[k];
-    nc += kc[k];
+    const int p = base + 32 * k + lane;
+    bool ks = false, kc = false;
+    if (p < mt) {
+      sv[k] = S.sres[p];
+      ks = residual_positive(sv[k]);
+      if (ks) { iv[k] = S.iidx[p]; G.load_x(p, px[k]); }
+    }
+    if (p < nt) {
+      cv[k] = S.cres[p];
+      kc = residual_positive(cv[k]);
+      if (kc) { jv[k] = S.jidx[p]; G.load_y(p, py[k]); }
+    }
+    bs[k] = __ballot_sync(0xffffffffu, ks);
+    bc[k] = __ballot_sync(0xffffffffu, kc);
+    ns += __popc(bs[k]);
+    nc += __popc(bc[k]);
   }
   int tot;
-  const int ex = block_scan_excl(ns | (nc << 16), S.wt, tot);
+  const int ex = __shfl_sync(0xffffffffu, block_scan_excl(lane == 0 ? (ns | (nc << 16)) : 0, S.wt, tot), 0);
   int ps = ex & 0xffff, pc = ex >> 16;
 #pragma unroll
   for (int k = 0; k < IT; ++k) {
-    if (ks[k]) { S.sres[ps] = sv[k]; S.iidx[ps] = iv[k]; G.store_x(ps, px[k]); ++ps; }
-    if (kc[k]) { S.cres[pc] = cv[k]; S.jidx[pc] = jv[k]; G.store_y(pc, py[k]); ++pc; }
+    if ((bs[k] >> lane) & 1u) {
+      const int d = ps + __popc(bs[k] & lt);
+      S.sres[d] = sv[k];
+      S.iidx[d] = iv[k];
+      G.store_x(d, px[k]);
+    }
+    if ((bc[k] >> lane) & 1u) {
+      const int d = pc + __popc(bc[k] & lt);
+      S.cres[d] = cv[k];
+      S.jidx[d] = jv[k];
+      G.store_y(d, py[k]);
+    }
+    ps += __popc(bs[k]);
+    pc += __popc(bc[k]);
   }
-  __syncthreads();
+  // every thread read the old counts before the scan's barriers
   if (tid == 0) {
     S.mt = tot & 0xffff;
     S.nt = tot >> 16;
@@ -478,13 +511,13 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
       if (tid == 0) atomicOr(O.err, EF_ITER);
       break;
     }
-    // ---- NNS: nearest active supplier of every active consumer
-    G.nns(S, mt, nt);
+    // group counters of this round (the NNS step ends with a barrier)
     for (int p = tid; p < mt; p += T) S.cnt[p] = 0;
     if (tid == 0) S.nflow = 0;
-    __syncthreads();
+    // ---- NNS: nearest active supplier of every active consumer
+    const unsigned long long* nk = G.nns(S, mt, nt, rounds);
     // ---- group the consumers by their supplier
-    for (int q = tid; q < nt; q += T) atomicAdd(&S.cnt[(int)(S.nnk[q] & 0xffffffffULL)], 1);
+    for (int q = tid; q < nt; q += T) atomicAdd(&S.cnt[(int)(nk[q] & 0xffffffffULL)], 1);
     __syncthreads();
     {
       const int tot = block_scan_array<CAP, Geo::kThreads>(S.cnt, S.off, mt, S.wt);
@@ -492,7 +525,7 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
     }
     __syncthreads();
     for (int q = tid; q < nt; q += T) {
-      const unsigned long long key = S.nnk[q];
+      const unsigned long long key = nk[q];
       const int p = (int)(key & 0xffffffffULL);
       const int slot = S.off[p] + atomicSub(&S.cnt[p], 1) - 1;
       const unsigned long long order =
@@ -505,7 +538,7 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
     for (int r = tid; r < nt; r += T) {
       const unsigned long long e = S.mem[r];
       const int q = (int)(e & 0xffffffffULL);
-      const int p = (int)(S.nnk[q] & 0xffffffffULL);
+      const int p = (int)(nk[q] & 0xffffffffULL);
       const int b = S.off[p], en = S.off[p + 1];
       int rank = 0;
       for (int u = b; u < en; ++u) rank += S.mem[u] < e;

@@ -94,6 +94,9 @@ void launch_normalise(const double* w, int64_t n, unsigned long long* acc, doubl
 void launch_xs_round(unsigned long long* acc, double* out, cudaStream_t st);
 // sum of residuals (leftover mass) into st->leftover
 void launch_leftover(const SolveBufs& B, cudaStream_t st);
+// Exact totals of a and b and their normalisation into B.s / B.c (two
+// launches; B.xs_acc cleared by the caller).
+void launch_setup_sums(const SolveBufs& B, const double* a, const double* b, cudaStream_t st);
 // Initial packing of both sides: active = positive weight, coordinates checked.
 int launch_initial_pack(SolveBufs& B, cudaStream_t st);
 // One multi-CTA round on the current active lists (mt, nt known on the host).

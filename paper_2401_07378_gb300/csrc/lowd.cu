@@ -408,8 +408,8 @@ __global__ void __launch_bounds__(FIN_CL_THREADS, 1) k_finish_cl(SolveBufs B, lo
   if (tid == 0) {
     S.mt = mt;
     S.nt = nt;
-    L.G.par = 0;
   }
+  L.G.init();
   // every CTA of the cluster is running before any writes a peer's memory
   cl.sync();
   CtaOut O{nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, &B.st->err,

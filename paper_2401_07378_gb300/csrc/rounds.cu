@@ -58,8 +58,60 @@ __global__ void k_xs_round(unsigned long long* acc, double* out) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *out = xs_round(acc);
 }
 
+// Up to three exact sums in one launch: job j adds v_j[0..n_j) (n_j from
+// n_dev when given) into acc_j.  The jobs' index ranges are concatenated
+// and split over the grid; each warp adds into its own shared-memory copy of
+// the accumulators (the values of a job often share an exponent, so the
+// limbs they touch are the same: 32 lanes contend per copy instead of the
+// whole block), and the block adds the per-warp sums into global memory.
+struct XsJob {
+  const double* v;
+  int64_t n;
+  const unsigned long long* n_dev;
+  unsigned long long* acc;
+};
+constexpr int XS_THREADS = 256;
+
+__global__ void __launch_bounds__(XS_THREADS) k_xs_accum_multi(XsJob j0, XsJob j1, XsJob j2, int njobs,
+                                                               unsigned* err, int check) {
+  constexpr int NW = XS_THREADS / 32;
+  __shared__ unsigned long long sacc[3][NW][XS_LIMBS];
+  for (int i = threadIdx.x; i < 3 * NW * XS_LIMBS; i += blockDim.x) (&sacc[0][0][0])[i] = 0ULL;
+  __syncthreads();
+  const int64_t n0 = j0.n_dev ? (int64_t)*j0.n_dev : j0.n;
+  const int64_t n1 = njobs > 1 ? (j1.n_dev ? (int64_t)*j1.n_dev : j1.n) : 0;
+  const int64_t n2 = njobs > 2 ? (j2.n_dev ? (int64_t)*j2.n_dev : j2.n) : 0;
+  const int64_t e1 = n0, e2 = n0 + n1, e3 = n0 + n1 + n2;
+  const int w = threadIdx.x >> 5;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < e3; i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = i < e1 ? 0 : (i < e2 ? 1 : 2);
+    const double v = j == 0 ? j0.v[i] : (j == 1 ? j1.v[i - e1] : j2.v[i - e2]);
+    if (check) {
+      if (!isfinite(v)) { atomicOr(err, EF_NONFINITE); continue; }
+      if (v < 0.0) { atomicOr(err, EF_NEGATIVE); continue; }
+    }
+    xs_add(sacc[j][w], v);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < njobs * XS_LIMBS; i += blockDim.x) {
+    const int j = i / XS_LIMBS, L = i - j * XS_LIMBS;
+    unsigned long long t = 0;
+#pragma unroll
+    for (int u = 0; u < NW; ++u) t += sacc[j][u][L];
+    if (t) atomicAdd((j == 0 ? j0.acc : (j == 1 ? j1.acc : j2.acc)) + L, t);
+  }
+}
+
+// out0 / out1 = the correctly rounded values of acc0 / acc1.
+__global__ void k_xs_round2(unsigned long long* acc0, double* out0, unsigned long long* acc1, double* out1) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *out0 = xs_round(acc0);
+  if (blockIdx.x == 0 && threadIdx.x == 32 && acc1) *out1 = xs_round(acc1);
+}
+
 // out[i] = w[i] / total, the total rounded from acc by the first thread of
 // every block (each block rounds its own copy: no inter-block ordering).
+// Blocks [0, split) normalise the first array, the others the second
+// (k_normalise2).
 __global__ void k_normalise(const double* __restrict__ w, int64_t n, const unsigned long long* __restrict__ acc,
                             double* total_out, double* __restrict__ out, unsigned* err) {
   __shared__ unsigned long long a[XS_LIMBS];
@@ -76,6 +128,37 @@ __global__ void k_normalise(const double* __restrict__ w, int64_t n, const unsig
   __syncthreads();
   const double t = total;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double wi = w[i];
+    out[i] = (t > 0.0 && isfinite(wi) && wi > 0.0) ? __ddiv_rn(wi, t) : 0.0;
+  }
+}
+
+// Both sides' normalisation in one launch: blocks [0, ga) take (w0, n0, acc0),
+// the others (w1, n1, acc1); each block rounds its side's total itself.
+__global__ void k_normalise2(const double* __restrict__ w0, int64_t n0, const unsigned long long* __restrict__ acc0,
+                             double* total0, double* __restrict__ out0, const double* __restrict__ w1, int64_t n1,
+                             const unsigned long long* __restrict__ acc1, double* total1, double* __restrict__ out1,
+                             int ga, unsigned* err) {
+  __shared__ unsigned long long a[XS_LIMBS];
+  __shared__ double total;
+  const bool second = (int)blockIdx.x >= ga;
+  const unsigned long long* acc = second ? acc1 : acc0;
+  const int bid = second ? blockIdx.x - ga : blockIdx.x, nb = second ? gridDim.x - ga : ga;
+  for (int i = threadIdx.x; i < XS_LIMBS; i += blockDim.x) a[i] = acc[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    total = xs_round(a);
+    if (bid == 0) {
+      *(second ? total1 : total0) = total;
+      if (!(total > 0.0)) atomicOr(err, EF_ZERO_MASS);
+    }
+  }
+  __syncthreads();
+  const double t = total;
+  const double* w = second ? w1 : w0;
+  double* out = second ? out1 : out0;
+  const int64_t n = second ? n1 : n0;
+  for (int64_t i = bid * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)nb * blockDim.x) {
     const double wi = w[i];
     out[i] = (t > 0.0 && isfinite(wi) && wi > 0.0) ? __ddiv_rn(wi, t) : 0.0;
   }
@@ -103,17 +186,23 @@ void launch_normalise(const double* w, int64_t n, unsigned long long* acc, doubl
 
 void launch_xs_round(unsigned long long* acc, double* out, cudaStream_t st) { k_xs_round<<<1, 32, 0, st>>>(acc, out); }
 
+void launch_setup_sums(const SolveBufs& B, const double* a, const double* b, cudaStream_t st) {
+  XsJob ja{a, B.m, nullptr, B.xs_acc}, jb{b, B.n, nullptr, B.xs_acc + XS_LIMBS};
+  k_xs_accum_multi<<<xs_grid(B.m + B.n), XS_THREADS, 0, st>>>(ja, jb, jb, 2, &B.st->err, 1);
+  const int ga = xs_grid(B.m), gb = xs_grid(B.n);
+  k_normalise2<<<ga + gb, 256, 0, st>>>(a, B.m, B.xs_acc, &B.st->total_a, B.s, b, B.n, B.xs_acc + XS_LIMBS,
+                                        &B.st->total_b, B.c, ga, &B.st->err);
+}
+
+// The leftover mass (residuals of both sides) and R (the exact sum of the
+// nnz cost terms) in two launches; their accumulators were cleared with the
+// others when the solve started.
 void launch_leftover(const SolveBufs& B, cudaStream_t st) {
   unsigned long long* acc = B.xs_acc + 3 * XS_LIMBS;
-  k_xs_clear<<<1, 256, 0, st>>>(acc, XS_LIMBS);
-  k_xs_accum<<<xs_grid(B.m), 256, 0, st>>>(B.s, B.m, nullptr, acc, &B.st->err, 0);
-  k_xs_accum<<<xs_grid(B.n), 256, 0, st>>>(B.c, B.n, nullptr, acc, &B.st->err, 0);
-  k_xs_round<<<1, 32, 0, st>>>(acc, &B.st->leftover);
-  // R: the exact sum of the nnz cost terms
   unsigned long long* cacc = B.xs_acc + 2 * XS_LIMBS;
-  k_xs_clear<<<1, 256, 0, st>>>(cacc, XS_LIMBS);
-  k_xs_accum<<<152 * 2, 256, 0, st>>>(B.terms, 0, &B.st->nnz, cacc, &B.st->err, 0);
-  k_xs_round<<<1, 32, 0, st>>>(cacc, &B.st->cost);
+  XsJob js{B.s, B.m, nullptr, acc}, jc{B.c, B.n, nullptr, acc}, jt{B.terms, 0, &B.st->nnz, cacc};
+  k_xs_accum_multi<<<152 * 2, XS_THREADS, 0, st>>>(js, jc, jt, 3, &B.st->err, 0);
+  k_xs_round2<<<1, 64, 0, st>>>(acc, &B.st->leftover, cacc, &B.st->cost);
 }
 
 // --------------------------------------------------------------------------
