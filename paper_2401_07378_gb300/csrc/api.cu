@@ -12,11 +12,15 @@
 //            side) where the device can co-schedule one, else in one CTA
 //            (k_finish, k_finish_hd);
 //   final    R and the leftover mass as correctly rounded sums.
-// The host reads the two active counts after each multi-CTA round (a few
-// bytes from pinned memory) to size the next round's grids.
+// The host reads the two active counts of each multi-CTA round to size the
+// next round's grids: the compaction's count kernel writes them into mapped
+// host memory as soon as they are known, and the host launches the next
+// round while the scatter still runs (no stream synchronisation per round).
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -191,6 +195,29 @@ int map_err_bits(nnsemd_ctx* ctx, unsigned bits) {
   return fail(ctx, NNSEMD_ERR_CUDA, "internal consistency check failed on the device (0x%x)", bits);
 }
 
+// Wait (spinning) until the compaction of a round has published its active
+// counts under sequence number `seq` (mapped host memory, written by the
+// last block of the count kernel).  Fails instead of waiting forever if the
+// stream stops or two minutes pass.
+int wait_counts(nnsemd_ctx* ctx, cudaStream_t st, int seq, int& mt, int& nt, unsigned& err) {
+  volatile int* h = ctx->hmap;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (unsigned it = 1; h[0] != seq; ++it) {
+    if ((it & 4095u) != 0) continue;
+    const cudaError_t q = cudaStreamQuery(st);
+    if (q != cudaSuccess && q != cudaErrorNotReady)
+      return fail(ctx, NNSEMD_ERR_CUDA, "waiting for a round: %s", cudaGetErrorString(q));
+    if (q == cudaSuccess && h[0] != seq) return fail(ctx, NNSEMD_ERR_CUDA, "a round's counts were not published");
+    if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(120))
+      return fail(ctx, NNSEMD_ERR_TIMEOUT, "a round did not finish within two minutes");
+  }
+  std::atomic_thread_fence(std::memory_order_acquire);
+  mt = h[1];
+  nt = h[2];
+  err = (unsigned)h[3];
+  return 0;
+}
+
 int check_opts(nnsemd_ctx* ctx, const nnsemd_options* opt, int d, int& metric, int* precision = nullptr) {
   metric = NNSEMD_L2;
   if (precision) *precision = NNSEMD_FP32;
@@ -321,6 +348,11 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
       if (timed) CK(cudaEventRecord(ctx->ev[1], st));
     }
     if (nrc) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "NNS launch failed for d=%d (%d)", B.d, nrc);
+    // the compaction's count kernel publishes the next active counts as soon
+    // as they are known; the host sizes and launches the next round while
+    // the scatter still runs
+    B.notify = ctx->dmap;
+    B.notify_seq = ++ctx->notify_seq;
     launch_big_round(B, mt, nt, rounds, st);
     L += 10;
     CK(cudaGetLastError());
@@ -329,17 +361,17 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
     pair_evals += (long long)mt * nt;
     nns_launches += 1;
     nns_pairs += (long long)mt * nt;
-    CK(cudaMemcpyAsync(ctx->hstate, B.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    unsigned err_bits = 0;
+    rc = wait_counts(ctx, st, B.notify_seq, mt, nt, err_bits);
+    if (rc) return rc;
     if (timed) {
       float ms = 0.f;
+      CK(cudaEventSynchronize(ctx->ev[1]));
       CK(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
       nns_ms += ms;
     }
-    rc = map_err_bits(ctx, ctx->hstate->err);
+    rc = map_err_bits(ctx, err_bits);
     if (rc) return rc;
-    mt = ctx->hstate->mt;
-    nt = ctx->hstate->nt;
   }
   launch_leftover(B, st);
   L += 2;
@@ -406,7 +438,18 @@ int nnsemd_create(nnsemd_ctx** out, const nnsemd_config* cfg) {
   ctx->stream = cfg ? (cudaStream_t)cfg->stream : nullptr;
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e == cudaSuccess) e = cudaMallocHost(&ctx->hstate, sizeof(DevState));
+  if (e == cudaSuccess) {
+    void* hm = nullptr;
+    e = cudaHostAlloc(&hm, 64, cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+      std::memset(hm, 0, 64);
+      ctx->hmap = static_cast<volatile int*>(hm);
+      e = cudaHostGetDevicePointer((void**)&ctx->dmap, hm, 0);
+    }
+  }
   if (e != cudaSuccess) {
+    if (ctx->hmap) cudaFreeHost((void*)ctx->hmap);
+    if (ctx->hstate) cudaFreeHost(ctx->hstate);
     int rc = fail(nullptr, NNSEMD_ERR_CUDA, "device %d: %s", ctx->device, cudaGetErrorString(e));
     delete ctx;
     return rc;
@@ -416,6 +459,7 @@ int nnsemd_create(nnsemd_ctx** out, const nnsemd_config* cfg) {
     if (rc) {
       g_create_err = ctx->err;
       cudaFreeHost(ctx->hstate);
+      cudaFreeHost((void*)ctx->hmap);
       delete ctx;
       return rc;
     }
@@ -430,6 +474,7 @@ int nnsemd_destroy(nnsemd_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->hstate) cudaFreeHost(ctx->hstate);
+  if (ctx->hmap) cudaFreeHost((void*)ctx->hmap);
   for (cudaEvent_t e : ctx->ev)
     if (e) cudaEventDestroy(e);
   for (auto& g : ctx->graphs)

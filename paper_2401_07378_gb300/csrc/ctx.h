@@ -25,6 +25,9 @@ struct nnsemd_ctx {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   nnsemd::DevState* hstate = nullptr;  // pinned mirror of the device state
+  volatile int* hmap = nullptr;        // mapped pinned words: a round's active counts (host view)
+  int* dmap = nullptr;                 // the same words, device view
+  int notify_seq = 0;                  // sequence number of the last requested notification
   std::string err;
   long long launches = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // kernel timing (NNSEMD_FLAG_TIME_KERNELS)

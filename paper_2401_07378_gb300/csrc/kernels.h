@@ -76,6 +76,12 @@ struct SolveBufs {
   double* fl_f;
   int* blockcounts;            // compaction scratch
   unsigned long long* xs_acc;  // 4 exact-sum accumulators of XS_LIMBS limbs
+  // Early notification of the active counts (nullable): the compaction's
+  // count kernel writes {seq, m_t, n_t, error bits} of the round here (host
+  // memory mapped into the device) as soon as the counts are known, before
+  // the scatter that moves the points has run.
+  volatile int* notify;
+  int notify_seq;
   DevState* st;
   // caller's plan arrays (nullable) and capacity
   int32_t* plan_i;

@@ -231,6 +231,9 @@ struct CompactArgs {
   CompactSide side[2];
   int* blockcounts;     // [side0 blocks + side1 blocks]
   unsigned* err;
+  volatile int* notify; // nullable: {seq, side0 count, side1 count, error bits} in mapped host memory
+  int notify_seq;
+  unsigned* ticket;     // zero before the count launch; the last block resets it
 };
 
 NNS_DEV int cp_block_side(const CompactArgs& A, int b, int& local) {
@@ -262,6 +265,33 @@ __global__ void __launch_bounds__(CP_THREADS) k_compact_count(CompactArgs A) {
     int t = 0;
     for (int w = 0; w < CP_THREADS / 32; ++w) t += red[w];
     A.blockcounts[blockIdx.x] = t;
+  }
+  if (!A.notify) return;
+  // The last block to finish adds up both sides' counts and publishes them
+  // with the error bits (every block fenced its count before its ticket).
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(A.ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x >= 32) return;
+  __threadfence();
+  const volatile int* bc = A.blockcounts;
+  const int nb0 = A.side[0].nblocks, nb = nb0 + A.side[1].nblocks;
+  int t0 = 0, t1 = 0;
+  for (int b = threadIdx.x; b < nb; b += 32) (b < nb0 ? t0 : t1) += bc[b];
+  for (int o = 16; o > 0; o >>= 1) {
+    t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+    t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+  }
+  if (threadIdx.x == 0) {
+    A.notify[1] = t0;
+    A.notify[2] = t1;
+    A.notify[3] = (int)*(volatile unsigned*)A.err;
+    __threadfence_system();
+    A.notify[0] = A.notify_seq;
+    *A.ticket = 0u;
   }
 }
 
@@ -389,6 +419,9 @@ int launch_initial_pack(SolveBufs& B, cudaStream_t st) {
   A.side[1] = CompactSide{packed ? B.y : nullptr, B.d, nullptr, B.c, packed ? B.ya[B.cur] : nullptr, B.ja[B.cur],
                           (int)B.n, &B.st->nt, 0, 1, B.nnkey};
   A.blockcounts = B.blockcounts;
+  A.notify = B.notify;
+  A.notify_seq = B.notify_seq;
+  A.ticket = &B.st->ticket;
   A.err = &B.st->err;
   compact_launch(A, B.dp, st);
   return 0;
@@ -773,6 +806,9 @@ int launch_big_round(SolveBufs& B, int mt, int nt, long long round, cudaStream_t
                           B.ja[cur ^ 1], nt, &B.st->nt, 0, 0, B.nnkey};
   A.blockcounts = B.blockcounts;
   A.err = &B.st->err;
+  A.notify = B.notify;
+  A.notify_seq = B.notify_seq;
+  A.ticket = &B.st->ticket;
   compact_launch(A, B.dp, st);
   return 0;
 }
