@@ -605,8 +605,9 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
     // ---- weights update: retire spent points, compact
     cta_compact(S, G);
   }
-  if (O.fl_i) {
+  if (O.fl_i && (O.terms || O.acc || O.plan_i)) {
     // deferred costing: the terms and plan entries of every flow of the loop
+    // (a solve whose later pass costs all its flows records them only)
     for (unsigned long long k = nnz0 + tid; k < nnz; k += T) {
       const int i = O.fl_i[k], j = O.fl_j[k];
       const double f = O.fl_f[k];

@@ -11,8 +11,11 @@
 //       a warp-register bitonic network up to 32, a CTA network in shared or
 //       global memory beyond that), then walk it in FP64 exactly as the
 //       algorithm does: f = min(s_i, c_j),
-//       s_i -= f, c_j -= f, until s_i is spent; each flow writes its plan
-//       entry and its cost term f * D_ij (FP64 ground distance).
+//       s_i -= f, c_j -= f, until s_i is spent; each flow records its
+//       original (i, j) and f.
+//   k_final_sums
+//       after the last round: the cost term f * D_ij (FP64 ground distance)
+//       and plan entry of every recorded flow, R and the leftover mass.
 //   k_compact_count / k_compact_scatter
 //       weights update: stable compaction of both active lists to the points
 //       whose residual is still positive, gathering their coordinates into
@@ -99,6 +102,71 @@ __global__ void __launch_bounds__(XS_THREADS) k_xs_accum_multi(XsJob j0, XsJob j
 #pragma unroll
     for (int u = 0; u < NW; ++u) t += sacc[j][u][L];
     if (t) atomicAdd((j == 0 ? j0.acc : (j == 1 ? j1.acc : j2.acc)) + L, t);
+  }
+}
+
+// The end of a solve in one pass: the leftover mass (residuals s[0..m) and
+// c[0..n)) into acc_left, and, for every recorded flow k < nnz, its cost
+// term f * D_ij (FP64 ground distance from the original coordinates) into
+// acc_cost and its plan entry (when a plan is requested).  The flows of all
+// rounds are costed here at once, with every lane busy, instead of inside
+// the latency-bound flow steps.
+struct FinalArgs {
+  const double* s;
+  int64_t m;
+  const double* c;
+  int64_t n;
+  const int32_t* fl_i;
+  const int32_t* fl_j;
+  const double* fl_f;
+  const unsigned long long* nnz;
+  const float* x;
+  const float* y;
+  int d, metric;
+  int32_t* plan_i;  // nullable
+  int32_t* plan_j;
+  double* plan_f;
+  long long plan_cap;
+  unsigned long long* acc_left;
+  unsigned long long* acc_cost;
+  unsigned* err;
+};
+
+__global__ void __launch_bounds__(XS_THREADS) k_final_sums(FinalArgs A) {
+  constexpr int NW = XS_THREADS / 32;
+  __shared__ unsigned long long sacc[2][NW][XS_LIMBS];
+  for (int i = threadIdx.x; i < 2 * NW * XS_LIMBS; i += blockDim.x) (&sacc[0][0][0])[i] = 0ULL;
+  __syncthreads();
+  const int64_t e1 = A.m, e2 = A.m + A.n, e3 = e2 + (int64_t)*A.nnz;
+  const int w = threadIdx.x >> 5;
+  bool over = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < e3; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < e2) {
+      xs_add(sacc[0][w], i < e1 ? A.s[i] : A.c[i - e1]);
+      continue;
+    }
+    const int64_t k = i - e2;
+    const int fi = A.fl_i[k], fj = A.fl_j[k];
+    const double f = A.fl_f[k];
+    xs_add(sacc[1][w], __dmul_rn(f, cost_dist64(A.x + (size_t)fi * A.d, A.y + (size_t)fj * A.d, A.d, A.metric)));
+    if (A.plan_i) {
+      if (k < A.plan_cap) {
+        A.plan_i[k] = fi;
+        A.plan_j[k] = fj;
+        A.plan_f[k] = f;
+      } else {
+        over = true;
+      }
+    }
+  }
+  if (over) atomicOr(A.err, EF_CAPACITY);
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * XS_LIMBS; i += blockDim.x) {
+    const int j = i / XS_LIMBS, L = i - j * XS_LIMBS;
+    unsigned long long t = 0;
+#pragma unroll
+    for (int u = 0; u < NW; ++u) t += sacc[j][u][L];
+    if (t) atomicAdd((j == 0 ? A.acc_left : A.acc_cost) + L, t);
   }
 }
 
@@ -194,14 +262,15 @@ void launch_setup_sums(const SolveBufs& B, const double* a, const double* b, cud
                                         &B.st->total_b, B.c, ga, &B.st->err);
 }
 
-// The leftover mass (residuals of both sides) and R (the exact sum of the
-// nnz cost terms) in two launches; their accumulators were cleared with the
-// others when the solve started.
+// The leftover mass (residuals of both sides), the cost terms and plan
+// entries of every recorded flow, and R (their exact sum) in two launches;
+// the accumulators were cleared with the others when the solve started.
 void launch_leftover(const SolveBufs& B, cudaStream_t st) {
   unsigned long long* acc = B.xs_acc + 3 * XS_LIMBS;
   unsigned long long* cacc = B.xs_acc + 2 * XS_LIMBS;
-  XsJob js{B.s, B.m, nullptr, acc}, jc{B.c, B.n, nullptr, acc}, jt{B.terms, 0, &B.st->nnz, cacc};
-  k_xs_accum_multi<<<152 * 2, XS_THREADS, 0, st>>>(js, jc, jt, 3, &B.st->err, 0);
+  FinalArgs F{B.s,    B.m,    B.c,    B.n,      B.fl_i,   B.fl_j,   B.fl_f,        &B.st->nnz, B.x, B.y,
+              B.d,    B.metric, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, acc, cacc, &B.st->err};
+  k_final_sums<<<152 * 2, XS_THREADS, 0, st>>>(F);
   k_xs_round2<<<1, 64, 0, st>>>(acc, &B.st->leftover, cacc, &B.st->cost);
 }
 
@@ -506,9 +575,6 @@ __global__ void k_group_scatter(const unsigned long long* __restrict__ nnkey, in
 // --------------------------------------------------------------------------
 
 struct FlowArgs {
-  const float* x;  // original coordinates
-  const float* y;
-  int d, metric;
   const int* ia;   // current active lists
   const int* ja;
   const int2* seg;
@@ -518,11 +584,12 @@ struct FlowArgs {
   unsigned long long* member;
   double* s;
   double* c;
-  double* terms;
-  int32_t* plan_i;
-  int32_t* plan_j;
-  double* plan_f;
-  long long plan_cap;
+  // flow record, slot = running flow count (original i, j and f); the cost
+  // terms and plan entries of all flows are made in one pass after the
+  // last round (k_final_sums)
+  int32_t* fl_i;
+  int32_t* fl_j;
+  double* fl_f;
   DevState* st;
 };
 
@@ -575,18 +642,10 @@ NNS_DEV int warp_serve(const FlowArgs& A, int i, double& s, unsigned long long k
   base = __shfl_sync(0xffffffffu, base, 0);
   if (lane < served) {
     A.c[j] = mycn;
-    const double Dij = cost_dist64(A.x + (size_t)i * A.d, A.y + (size_t)j * A.d, A.d, A.metric);
     const unsigned long long slot = base + lane;
-    A.terms[slot] = __dmul_rn(myf, Dij);
-    if (A.plan_i) {
-      if ((long long)slot < A.plan_cap) {
-        A.plan_i[slot] = i;
-        A.plan_j[slot] = j;
-        A.plan_f[slot] = myf;
-      } else {
-        atomicOr(&A.st->err, EF_CAPACITY);
-      }
-    }
+    A.fl_i[slot] = i;
+    A.fl_j[slot] = j;
+    A.fl_f[slot] = myf;
   }
   return served;
 }
@@ -650,24 +709,15 @@ NNS_DEV void thread_serve(const FlowArgs& A, int p, int2 sg, bool active) {
   if (lane == 31 && incl) base = atomicAdd(&A.st->nnz, (unsigned long long)incl);
   base = __shfl_sync(0xffffffffu, base, 31) + (unsigned long long)(incl - served);
   if (!active) return;
-  const float* xi = A.x + (size_t)i * A.d;
 #pragma unroll
   for (int k = 0; k < FLOW_THREAD_MAX; ++k) {
     if (k < served) {
       const int j = jv[k];
       A.c[j] = cv[k];
-      const double Dij = cost_dist64(xi, A.y + (size_t)j * A.d, A.d, A.metric);
       const unsigned long long slot = base + k;
-      A.terms[slot] = __dmul_rn(fv[k], Dij);
-      if (A.plan_i) {
-        if ((long long)slot < A.plan_cap) {
-          A.plan_i[slot] = i;
-          A.plan_j[slot] = j;
-          A.plan_f[slot] = fv[k];
-        } else {
-          atomicOr(&A.st->err, EF_CAPACITY);
-        }
-      }
+      A.fl_i[slot] = i;
+      A.fl_j[slot] = j;
+      A.fl_f[slot] = fv[k];
     }
   }
   A.s[i] = s;
@@ -789,8 +839,8 @@ int launch_big_round(SolveBufs& B, int mt, int nt, long long round, cudaStream_t
   k_group_alloc<<<(mt + 255) / 256, 256, 0, st>>>(B.cnt, mt, B.seg, B.seglist, B.biglist, B.medlist, B.st);
   k_group_scatter<<<(nt + 255) / 256, 256, 0, st>>>(B.nnkey, nt, B.cnt, B.seg, B.member, B.ja[cur], B.protocol,
                                                     B.seed, round);
-  FlowArgs F{B.x, B.y, B.d, B.metric, B.ia[cur], B.ja[cur], B.seg, B.seglist, B.biglist, B.medlist, B.member,
-             B.s, B.c, B.terms, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, B.st};
+  FlowArgs F{B.ia[cur], B.ja[cur], B.seg,  B.seglist, B.biglist, B.medlist, B.member,
+             B.s,       B.c,       B.fl_i, B.fl_j,    B.fl_f,    B.st};
   // enough warps for every group of 9..32 at once (at most nt / 9 of them);
   // the thread-per-group pass needs nt / 32
   int warps = (nt + 8) / 9;
