@@ -292,14 +292,19 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
   CK(cudaMemsetAsync(B.cnt, 0, B.m * sizeof(int), st));
   launch_setup_sums(B, a, b, st);
   B.cur = 0;
+  // the initial packing publishes the active counts like every round's
+  // compaction (with the weight and coordinate checks' error bits)
+  B.notify = ctx->dmap;
+  B.notify_seq = ++ctx->notify_seq;
   launch_initial_pack(B, st);
   L += 4;
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(ctx->hstate, B.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  int rc = map_err_bits(ctx, ctx->hstate->err);
+  int mt = 0, nt = 0;
+  unsigned err0 = 0;
+  int rc = wait_counts(ctx, st, B.notify_seq, mt, nt, err0);
   if (rc) return rc;
-  int mt = ctx->hstate->mt, nt = ctx->hstate->nt;
+  rc = map_err_bits(ctx, err0);
+  if (rc) return rc;
   long long rounds = 0, pair_evals = 0;
   const long long round_limit = B.m + B.n;
   const bool lowd = B.dp > 0;

@@ -316,15 +316,23 @@ __global__ void __launch_bounds__(CP_THREADS) k_compact_count(CompactArgs A) {
   const int sd = cp_block_side(A, blockIdx.x, lb);
   const CompactSide& S = A.side[sd];
   int c = 0;
+  bool bad = false;
   const int base = lb * CP_BLOCK + threadIdx.x * CP_ITEMS;
 #pragma unroll
   for (int k = 0; k < CP_ITEMS; ++k) {
     const int pos = base + k;
     if (pos < S.count) {
       const int orig = S.idx_in ? S.idx_in[pos] : pos;
-      c += S.resid[orig] > 0.0;
+      const bool keep = S.resid[orig] > 0.0;
+      c += keep;
+      // with `check`, the kept points' coordinates are checked here too, so
+      // that an early notification already carries the error
+      if (S.check && keep && S.pts_in)
+        for (int e = 0; e < S.in_stride; ++e) bad |= !isfinite(S.pts_in[(size_t)pos * S.in_stride + e]);
     }
   }
+  // (thread 0 raises the flag, before its fence and ticket below)
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(A.err, EF_NONFINITE);
   // block reduction
   __shared__ int red[CP_THREADS / 32];
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
