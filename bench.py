@@ -473,6 +473,14 @@ def run_ours(args) -> dict | None:
         else:
             rl["kernel"] = f"k_batched_tc<{precision}> (persistent, one pair per CTA, tcgen05 NNS per round)"
         rl["traffic"] = None
+    elif agg["nns_kernel_launches"] == 0 and agg["tail_kernel_ms"] > 0:
+        # a pair small enough for one launch (k_solve_small): that kernel runs
+        # every round, so its NNS work over its own time
+        rl = roofline(d, precision, (last or {}).get("pair_evals", 0) * args.steps, args.steps,
+                      agg["tail_kernel_ms"], total_ms, lowd)
+        rl["kernel"] = "k_solve_small (the whole pair in one launch: every round's NNS, grouping, flow, compaction)"
+        rl["traffic"] = None
+        rl["note"] = "latency-bound: the NNS work is a small part of each round"
     else:
         rl = roofline(d, precision, agg["nns_kernel_pairs"], agg["nns_kernel_launches"], agg["nns_kernel_ms"],
                       total_ms, lowd)
