@@ -16,8 +16,8 @@
  * Conventions fixed by this library (the paper leaves them open):
  *  - Weights are normalised to unit mass (Sec. II-A) by dividing each by the
  *    correctly rounded sum of its side.  Zero weights are allowed (the point
- *    never takes part and its coordinates are not read); negative or
- *    non-finite weights are errors.
+ *    never takes part); negative or non-finite weights are errors, and so
+ *    is a non-finite coordinate of any point, whatever its weight.
  *  - Argmin ties go to the lowest supplier index, greedy-order ties to the
  *    lowest consumer index.
  *  - Metric NNSEMD_L2 (Euclidean, the paper's choice) and NNSEMD_SQL2 order

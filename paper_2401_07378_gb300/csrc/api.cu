@@ -176,7 +176,6 @@ size_t layout_solve(void* base, int64_t m, int64_t n, int d, SolveBufs& B, int p
   B.biglist = C.take<int>(m);
   B.medlist = C.take<int>(m);
   B.member = C.take<unsigned long long>(n);
-  B.terms = C.take<double>(m + n);
   B.fl_i = C.take<int32_t>(m + n);
   B.fl_j = C.take<int32_t>(m + n);
   B.fl_f = C.take<double>(m + n);

@@ -78,7 +78,6 @@ struct CtaCore {
 };
 
 struct CtaOut {
-  double* terms;                 // global per-flow terms (nullable)
   unsigned long long* acc;       // exact accumulator for R (shared, nullable)
   int32_t* plan_i;               // plan (nullable)
   int32_t* plan_j;
@@ -585,7 +584,6 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
       const double f = __longlong_as_double((long long)S.nnk[k]);
       const double term = __dmul_rn(f, G.dist64(S, p, q, metric));
       const unsigned long long slot = nnz + k;
-      if (O.terms) O.terms[slot] = term;
       if (O.acc) xs_add(O.acc, term);
       if (O.plan_i) {
         if ((long long)slot < O.plan_cap) {
@@ -605,14 +603,13 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
     // ---- weights update: retire spent points, compact
     cta_compact(S, G);
   }
-  if (O.fl_i && (O.terms || O.acc || O.plan_i)) {
+  if (O.fl_i && (O.acc || O.plan_i)) {
     // deferred costing: the terms and plan entries of every flow of the loop
     // (a solve whose later pass costs all its flows records them only)
     for (unsigned long long k = nnz0 + tid; k < nnz; k += T) {
       const int i = O.fl_i[k], j = O.fl_j[k];
       const double f = O.fl_f[k];
       const double term = __dmul_rn(f, cost_dist64(O.x + (size_t)i * O.d, O.y + (size_t)j * O.d, O.d, metric));
-      if (O.terms) O.terms[k] = term;
       if (O.acc) xs_add(O.acc, term);
       if (O.plan_i) {
         if ((long long)k < O.plan_cap) {
@@ -688,7 +685,7 @@ NNS_DEV bool cta_solve_pair(CtaCore<CAP>& S, Geo& G, float* xs, float* ys, const
   for (int i = threadIdx.x; i < XS_LIMBS; i += blockDim.x) S.acc[i] = 0ULL;
   __syncthreads();
   cta_compact(S, G);  // drop zero weights
-  CtaOut O{nullptr, S.acc, nullptr, nullptr, nullptr, 0, nullptr, nullptr, err};
+  CtaOut O{S.acc, nullptr, nullptr, nullptr, 0, nullptr, nullptr, err};
   O.protocol = protocol;
   O.seed = seed;
   unsigned long long nnz = 0;

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_finish_hd(SolveBufs B, long 
     S.cres[q] = B.c[S.jidx[q]];
   }
   __syncthreads();
-  CtaOut O{nullptr, nullptr, nullptr, nullptr, nullptr, 0, B.s, B.c, &B.st->err,
+  CtaOut O{nullptr, nullptr, nullptr, nullptr, 0, B.s, B.c, &B.st->err,
            B.fl_i, B.fl_j, B.fl_f, B.x, B.y, B.d, B.protocol, B.seed, B.round0};
   unsigned long long nnz = B.st->nnz;
   long long rounds = B.st->rounds, pe = B.st->pair_evals;

@@ -70,7 +70,6 @@ struct SolveBufs {
   int* biglist;    // [m] groups longer than a warp
   int* medlist;    // [m] groups of 9..32 consumers
   unsigned long long* member;  // [n] group members: key32 bits << 32 | consumer position
-  double* terms;   // [m+n] per-flow cost terms f * D_ij
   int32_t* fl_i;   // [m+n] flow record of the one-CTA rounds (deferred costing)
   int32_t* fl_j;
   double* fl_f;
@@ -90,15 +89,9 @@ struct SolveBufs {
   int64_t plan_cap;
 };
 
-// setup.cu / rounds.cu ----------------------------------------------------
-void launch_xs_clear(unsigned long long* acc, int count, cudaStream_t st);
-void launch_xs_accum(const double* v, int64_t n, unsigned long long* acc, unsigned* err, bool check,
-                     cudaStream_t st);
-// total = round(acc); if (w) out[i] = w[i] / total (0 if total == 0 -> EF_ZERO_MASS)
-void launch_normalise(const double* w, int64_t n, unsigned long long* acc, double* total, double* out,
-                      unsigned* err, cudaStream_t st);
-void launch_xs_round(unsigned long long* acc, double* out, cudaStream_t st);
-// sum of residuals (leftover mass) into st->leftover
+// rounds.cu ---------------------------------------------------------------
+// After the last round: the cost terms and plan entries of every recorded
+// flow, R into st->cost and the leftover mass into st->leftover.
 void launch_leftover(const SolveBufs& B, cudaStream_t st);
 // Exact totals of a and b and their normalisation into B.s / B.c (two
 // launches; B.xs_acc cleared by the caller).

@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_finish(SolveBufs B, long lon
     S.nt = nt;
   }
   __syncthreads();
-  CtaOut O{nullptr, nullptr, nullptr, nullptr, nullptr, 0, B.s, B.c, &B.st->err,
+  CtaOut O{nullptr, nullptr, nullptr, nullptr, 0, B.s, B.c, &B.st->err,
            B.fl_i, B.fl_j, B.fl_f, B.x, B.y, B.d, B.protocol, B.seed, B.round0};
   unsigned long long nnz = B.st->nnz;
   long long rounds = B.st->rounds, pe = B.st->pair_evals;
@@ -412,10 +412,10 @@ __global__ void __launch_bounds__(FIN_CL_THREADS, 1) k_finish_cl(SolveBufs B, lo
   L.G.init();
   // every CTA of the cluster is running before any writes a peer's memory
   cl.sync();
-  CtaOut O{nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, &B.st->err,
+  CtaOut O{nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, &B.st->err,
            nullptr, nullptr, nullptr, B.x, B.y, B.d, B.protocol, B.seed, B.round0, 1};
   if (leader)
-    O = CtaOut{nullptr, nullptr, nullptr, nullptr, nullptr, 0, B.s, B.c, &B.st->err,
+    O = CtaOut{nullptr, nullptr, nullptr, nullptr, 0, B.s, B.c, &B.st->err,
                B.fl_i, B.fl_j, B.fl_f, B.x, B.y, B.d, B.protocol, B.seed, B.round0, 0};
   unsigned long long nnz = B.st->nnz;
   long long rounds = B.st->rounds, pe = B.st->pair_evals;
@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_solve_small(SolveBufs B, con
   for (int i = tid; i < XS_LIMBS; i += blockDim.x) S.acc[i] = 0ULL;
   __syncthreads();
   cta_compact(S, L.G);  // drop zero weights
-  CtaOut O{nullptr, S.acc, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, nullptr, nullptr, &B.st->err,
+  CtaOut O{S.acc, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, nullptr, nullptr, &B.st->err,
            B.fl_i, B.fl_j, B.fl_f, B.x, B.y, B.d, B.protocol, B.seed, 0};
   unsigned long long nnz = 0;
   long long rounds = 0, pe = 0;

@@ -32,35 +32,6 @@ namespace nnsemd {
 // exact sums
 // --------------------------------------------------------------------------
 
-__global__ void k_xs_clear(unsigned long long* acc, int count) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) acc[i] = 0ULL;
-}
-
-// Accumulate v[0..n) (n from n_dev when given).  With `check`, non-finite or
-// negative values raise error bits and are skipped.
-__global__ void k_xs_accum(const double* __restrict__ v, int64_t n, const unsigned long long* n_dev,
-                           unsigned long long* gacc, unsigned* err, int check) {
-  __shared__ unsigned long long sacc[XS_LIMBS];
-  for (int i = threadIdx.x; i < XS_LIMBS; i += blockDim.x) sacc[i] = 0ULL;
-  __syncthreads();
-  const int64_t cnt = n_dev ? (int64_t)*n_dev : n;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
-    const double w = v[i];
-    if (check) {
-      if (!isfinite(w)) { atomicOr(err, EF_NONFINITE); continue; }
-      if (w < 0.0) { atomicOr(err, EF_NEGATIVE); continue; }
-    }
-    xs_add(sacc, w);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < XS_LIMBS; i += blockDim.x)
-    if (sacc[i]) atomicAdd(gacc + i, sacc[i]);
-}
-
-__global__ void k_xs_round(unsigned long long* acc, double* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *out = xs_round(acc);
-}
-
 // Up to three exact sums in one launch: job j adds v_j[0..n_j) (n_j from
 // n_dev when given) into acc_j.  The jobs' index ranges are concatenated
 // and split over the grid; each warp adds into its own shared-memory copy of
@@ -176,31 +147,6 @@ __global__ void k_xs_round2(unsigned long long* acc0, double* out0, unsigned lon
   if (blockIdx.x == 0 && threadIdx.x == 32 && acc1) *out1 = xs_round(acc1);
 }
 
-// out[i] = w[i] / total, the total rounded from acc by the first thread of
-// every block (each block rounds its own copy: no inter-block ordering).
-// Blocks [0, split) normalise the first array, the others the second
-// (k_normalise2).
-__global__ void k_normalise(const double* __restrict__ w, int64_t n, const unsigned long long* __restrict__ acc,
-                            double* total_out, double* __restrict__ out, unsigned* err) {
-  __shared__ unsigned long long a[XS_LIMBS];
-  __shared__ double total;
-  for (int i = threadIdx.x; i < XS_LIMBS; i += blockDim.x) a[i] = acc[i];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    total = xs_round(a);
-    if (blockIdx.x == 0) {
-      *total_out = total;
-      if (!(total > 0.0)) atomicOr(err, EF_ZERO_MASS);
-    }
-  }
-  __syncthreads();
-  const double t = total;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double wi = w[i];
-    out[i] = (t > 0.0 && isfinite(wi) && wi > 0.0) ? __ddiv_rn(wi, t) : 0.0;
-  }
-}
-
 // Both sides' normalisation in one launch: blocks [0, ga) take (w0, n0, acc0),
 // the others (w1, n1, acc1); each block rounds its side's total itself.
 __global__ void k_normalise2(const double* __restrict__ w0, int64_t n0, const unsigned long long* __restrict__ acc0,
@@ -237,22 +183,6 @@ static int xs_grid(int64_t n) {
   if (g > 152 * 4) g = 152 * 4;
   return (int)(g < 1 ? 1 : g);
 }
-
-void launch_xs_clear(unsigned long long* acc, int count, cudaStream_t st) {
-  k_xs_clear<<<1, 256, 0, st>>>(acc, count);
-}
-
-void launch_xs_accum(const double* v, int64_t n, unsigned long long* acc, unsigned* err, bool check,
-                     cudaStream_t st) {
-  k_xs_accum<<<xs_grid(n), 256, 0, st>>>(v, n, nullptr, acc, err, check ? 1 : 0);
-}
-
-void launch_normalise(const double* w, int64_t n, unsigned long long* acc, double* total, double* out,
-                      unsigned* err, cudaStream_t st) {
-  k_normalise<<<xs_grid(n), 256, 0, st>>>(w, n, acc, total, out, err);
-}
-
-void launch_xs_round(unsigned long long* acc, double* out, cudaStream_t st) { k_xs_round<<<1, 32, 0, st>>>(acc, out); }
 
 void launch_setup_sums(const SolveBufs& B, const double* a, const double* b, cudaStream_t st) {
   XsJob ja{a, B.m, nullptr, B.xs_acc}, jb{b, B.n, nullptr, B.xs_acc + XS_LIMBS};
@@ -323,11 +253,10 @@ __global__ void __launch_bounds__(CP_THREADS) k_compact_count(CompactArgs A) {
     const int pos = base + k;
     if (pos < S.count) {
       const int orig = S.idx_in ? S.idx_in[pos] : pos;
-      const bool keep = S.resid[orig] > 0.0;
-      c += keep;
-      // with `check`, the kept points' coordinates are checked here too, so
-      // that an early notification already carries the error
-      if (S.check && keep && S.pts_in)
+      c += S.resid[orig] > 0.0;
+      // with `check`, every point's coordinates are checked here (zero
+      // weight or not), so that the early notification carries the error
+      if (S.check && S.pts_in)
         for (int e = 0; e < S.in_stride; ++e) bad |= !isfinite(S.pts_in[(size_t)pos * S.in_stride + e]);
     }
   }

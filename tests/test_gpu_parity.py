@@ -222,6 +222,27 @@ def test_errors_are_reported(ctx):
     assert gpu_solve(ctx, p.x, p.a, p.y, p.b, "l2").cost == oracle.solve_pair(p, "l2").cost
 
 
+def test_errors_in_multi_round_solves(ctx):
+    # large enough for the multi-CTA rounds: the packing's count kernel
+    # reports a non-finite coordinate, also on a point of zero weight
+    from paper_2401_07378_gb300.nnsemd import NNSEMDError
+    p = wl.uniform_pair(3000, 2500, 3, 17, "dirichlet")
+    for zero_weight in (False, True):
+        x, a = p.x.copy(), p.a.copy()
+        x[1234, 2] = np.nan
+        if zero_weight:
+            a[1234] = 0.0
+        with pytest.raises(NNSEMDError) as e:
+            gpu_solve(ctx, x, a, p.y, p.b, "l2")
+        assert e.value.status == 2
+        y = p.y.copy()
+        y[77, 0] = np.inf
+        with pytest.raises(NNSEMDError) as e:
+            gpu_solve(ctx, p.x, p.a, y, p.b, "sql2")
+        assert e.value.status == 2
+    assert gpu_solve(ctx, p.x, p.a, p.y, p.b, "l2").cost == oracle.solve_pair(p, "l2").cost
+
+
 def test_colour_transfer_full_size(ctx):
     """The benchmark's workload (65,536 colours per image, d=3, squared
     Euclidean, full plan) in the benchmark's launch configuration, compared
