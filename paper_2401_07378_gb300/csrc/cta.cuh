@@ -596,7 +596,9 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
       }
       if (O.c_glob) O.c_glob[S.jidx[q]] = S.cres[q];
     }
-    __syncthreads();
+    // (the compaction rewrites what this loop reads; with the loop empty
+    // the flow step's barrier suffices)
+    if (!(deferred || O.quiet)) __syncthreads();
     nnz += nflow;
     rounds += 1;
     pair_evals += (long long)mt * nt;
