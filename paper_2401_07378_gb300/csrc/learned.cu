@@ -582,14 +582,53 @@ struct LearnedArgs {
   unsigned long long* nfall;
 };
 
-// One warp per active consumer.
+constexpr int LN_YMAX = 256;  // consumer rows up to this d are staged in shared memory
+
+// The FP32 key of key32<SQL2> (t = x_k - y_k, acc = t_0 t_0, then
+// acc = fma(t_k, t_k, acc) in ascending k), read four coordinates at a time:
+// x a 16-byte aligned global row, y a row in shared memory, d % 4 == 0.
+NNS_DEV float key32_sql2_v4(const float* __restrict__ x, const float* y, int d) {
+  const float4* x4 = reinterpret_cast<const float4*>(x);
+  const float4* y4 = reinterpret_cast<const float4*>(y);
+  float4 a = __ldg(x4), b = y4[0];
+  float t = __fsub_rn(a.x, b.x);
+  float acc = __fmul_rn(t, t);
+  t = __fsub_rn(a.y, b.y);
+  acc = __fmaf_rn(t, t, acc);
+  t = __fsub_rn(a.z, b.z);
+  acc = __fmaf_rn(t, t, acc);
+  t = __fsub_rn(a.w, b.w);
+  acc = __fmaf_rn(t, t, acc);
+  for (int i = 1; i < (d >> 2); ++i) {
+    a = __ldg(x4 + i);
+    b = y4[i];
+    t = __fsub_rn(a.x, b.x);
+    acc = __fmaf_rn(t, t, acc);
+    t = __fsub_rn(a.y, b.y);
+    acc = __fmaf_rn(t, t, acc);
+    t = __fsub_rn(a.z, b.z);
+    acc = __fmaf_rn(t, t, acc);
+    t = __fsub_rn(a.w, b.w);
+    acc = __fmaf_rn(t, t, acc);
+  }
+  return acc;
+}
+
+// One warp per active consumer.  When d % 4 == 0, d <= LN_YMAX and the
+// coordinates are 16-byte aligned, the consumer's row is staged in shared
+// memory (every lane reads it: broadcast) and the supplier rows are read
+// 16 bytes at a time; the key is the same FP32 chain either way.
 __global__ void __launch_bounds__(256) k_learned_nns(LearnedArgs A) {
   __shared__ int cand[8][PROP_TAKE];
+  __shared__ __align__(16) float ysm[8][LN_YMAX];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int q = blockIdx.x * 8 + wib;
   if (q >= A.nt) return;
   const int j = A.ja[q];
   const float* yrow = A.y + (size_t)j * A.d;
+  const bool vec = (A.d & 3) == 0 && A.d <= LN_YMAX && (reinterpret_cast<uintptr_t>(A.x) & 15) == 0;
+  if (vec)
+    for (int k = lane; k < A.d; k += 32) ysm[wib][k] = yrow[k];
   // the first PROP_TAKE proposed cells that still hold active suppliers
   const int* pl = A.prop_cells + (size_t)j * PROP_LIST;
   int ncand = 0;
@@ -609,7 +648,8 @@ __global__ void __launch_bounds__(256) k_learned_nns(LearnedArgs A) {
     const int b = A.cell_off[c], e = A.cell_off[c + 1];
     for (int u = b + lane; u < e; u += 32) {
       const int p = A.members[u];
-      const float key = key32<METRIC_SQL2>(A.x + (size_t)A.ia[p] * A.d, yrow, A.d);
+      const float* xr = A.x + (size_t)A.ia[p] * A.d;
+      const float key = vec ? key32_sql2_v4(xr, ysm[wib], A.d) : key32<METRIC_SQL2>(xr, yrow, A.d);
       const unsigned long long kk = pack_key(key, (unsigned)p);
       best = kk < best ? kk : best;
     }
