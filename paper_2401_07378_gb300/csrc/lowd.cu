@@ -216,6 +216,7 @@ struct K1Shape {
 static K1Shape k1_shape(int D, int mt, int nt) {
   const int PB = k1_p(D);
   constexpr double kWaveNs = 2000.0;
+  constexpr double kAloneFactor = 1.67;
   K1Shape best{PB, 64, 1, 1};
   double best_t = 1e30;
   const int Ps[2] = {PB, 2};
@@ -237,7 +238,11 @@ static K1Shape k1_shape(int D, int mt, int nt) {
       const double per_cta_ns = (double)P * chunk * pair_ns;
       const long long full = ctas / resident, rem = ctas % resident;
       double t = (double)full * (kWaveNs + per_cta_ns * per_sm);
-      if (rem) t += kWaveNs + per_cta_ns * (double)((rem + 151) / 152);
+      // a CTA alone on its SM leaves the FP32 pipe partly idle: it runs at
+      // about 60 % of two co-resident CTAs' combined rate (measured on the
+      // colour-transfer rounds)
+      const long long k = (rem + 151) / 152;
+      if (rem) t += kWaveNs + per_cta_ns * (k > 1 ? (double)k : kAloneFactor);
       if (t < best_t) {
         best_t = t;
         best = K1Shape{P, chunk, gx, gy};
