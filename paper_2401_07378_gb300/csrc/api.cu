@@ -678,6 +678,13 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
   C.take<long long>(num_pairs);
   C.take<long long>(num_pairs);
   C.take<uint8_t>(tc ? slot * grid : 0);
+  // flow records of the d > 8 solvers, one slice per CTA (the tensor-core
+  // kernel's grid; the 1,024- and the 256-thread FP32 kernels' grids)
+  const long long fl_big = tc ? 2LL * cap : 2LL * FIN_MAX_HD, fl_small = 2LL * HD_SMALL_CAP;
+  const size_t fl_n = d <= 8 || small.empty() ? 0 : (size_t)(152 * fl_big + (tc ? 0 : 152 * 4 * fl_small));
+  C.take<int32_t>(fl_n);
+  C.take<int32_t>(fl_n);
+  C.take<double>(fl_n);
   const size_t head = (C.off + 511) & ~(size_t)255;  // keeps the solve buffers 256-byte aligned
   size_t bytes = head;
   int64_t maxm = 0, maxn = 0;
@@ -696,6 +703,9 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
   long long* rounds_d = W.take<long long>(num_pairs);
   long long* pe_d = W.take<long long>(num_pairs);
   uint8_t* scratch = W.take<uint8_t>(tc ? slot * grid : 0);
+  int32_t* fl_i = W.take<int32_t>(fl_n);
+  int32_t* fl_j = W.take<int32_t>(fl_n);
+  double* fl_f = W.take<double>(fl_n);
   unsigned* q_d = reinterpret_cast<unsigned*>(ctr_d);
   unsigned* q2_d = reinterpret_cast<unsigned*>(ctr_d + 3);  // queue of the 256-thread kernel
   CK(cudaMemcpyAsync(xo_d, x_off, (num_pairs + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
@@ -711,7 +721,13 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
     BatchArgs A{x_packed, a_packed, xo_d, y_packed, b_packed, yo_d, ids_d, nsmall, d, metric,
                 costs_out, rounds_d, pe_d, q_d, q_d + 1, opt ? opt->protocol : 0, opt ? opt->seed : 0ULL,
                 y_off ? 0 : (int)n_shared};
-    if (tc)
+    if (fl_n) {
+      A.fl_i = fl_i;
+      A.fl_j = fl_j;
+      A.fl_f = fl_f;
+      A.fl_cap = fl_big;
+    }
+    if (tc)  // (grid <= 152 CTAs)
       return launch_batched_tc(A, precision, cap, kb, tbn, tns, scratch, slot, ctr_d + 1, ctr_d + 2, g, s);
     if (d <= 8) return launch_batched_lowd(A, g, s);
     int r = 0;
@@ -726,6 +742,12 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
       BatchArgs At = A;
       At.num = ntiny;
       At.queue = q2_d;
+      if (fl_n) {  // the slices after the 1,024-thread kernel's
+        At.fl_i = fl_i + 152 * fl_big;
+        At.fl_j = fl_j + 152 * fl_big;
+        At.fl_f = fl_f + 152 * fl_big;
+        At.fl_cap = fl_small;
+      }
       r |= launch_batched_hd_small(At, std::min(ntiny, 152 * 4), s);
     }
     return r;

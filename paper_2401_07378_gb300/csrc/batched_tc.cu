@@ -403,8 +403,11 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_batched_tc(BtcArgs A) {
     __syncthreads();
     double cost = 0.0;
     long long rounds = 0, pe = 0;
+    const size_t fo = (size_t)blockIdx.x * B.fl_cap;
     const bool ok = cta_solve_pair(S, G, nullptr, nullptr, B.x + xo * B.d, B.a + xo, m, B.y + yo * B.d, B.b + yo, n,
-                                   B.d, B.metric, B.err, cost, rounds, pe, B.protocol, B.seed);
+                                   B.d, B.metric, B.err, cost, rounds, pe, B.protocol, B.seed,
+                                   B.fl_i ? B.fl_i + fo : nullptr, B.fl_i ? B.fl_j + fo : nullptr,
+                                   B.fl_i ? B.fl_f + fo : nullptr, B.fl_cap);
     if (tid == 0) {
       B.costs[pr] = ok ? cost : CUDART_NAN;
       if (B.rounds) B.rounds[pr] = rounds;

@@ -106,6 +106,7 @@ struct CtaOut {
   // nonzero: run the rounds without writing any flow, plan entry, cost term
   // or residual out (a CTA of a cluster whose results another CTA writes)
   int quiet;
+  long long fl_cap;  // > 0: capacity of fl_* (a flow beyond it raises EF_CAPACITY)
 };
 
 // --------------------------------------------------------------------------
@@ -563,6 +564,10 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
         if (O.quiet) {
         } else if (deferred) {
           const unsigned long long slot = nnz + k;
+          if (O.fl_cap && (long long)slot >= O.fl_cap) {
+            atomicOr(O.err, EF_CAPACITY);
+            continue;
+          }
           O.fl_i[slot] = S.iidx[p];
           O.fl_j[slot] = S.jidx[q];
           O.fl_f[slot] = f;
@@ -676,7 +681,9 @@ NNS_DEV bool cta_load_side(const float* pts, const double* w, int cnt, int d, fl
 template <int CAP, class Geo>
 NNS_DEV bool cta_solve_pair(CtaCore<CAP>& S, Geo& G, float* xs, float* ys, const float* x, const double* a, int m,
                             const float* y, const double* b, int n, int d, int metric, unsigned* err, double& cost,
-                            long long& rounds, long long& pe, int protocol = 0, unsigned long long seed = 0) {
+                            long long& rounds, long long& pe, int protocol = 0, unsigned long long seed = 0,
+                            int32_t* fl_i = nullptr, int32_t* fl_j = nullptr, double* fl_f = nullptr,
+                            long long fl_cap = 0) {
   bool ok = cta_load_side<Geo::kDP, CAP>(x, a, m, d, xs, S.sres, S.iidx, S, err);
   if (ok) ok = cta_load_side<Geo::kDP, CAP>(y, b, n, d, ys, S.cres, S.jidx, S, err);
   if (!ok) return false;
@@ -690,6 +697,18 @@ NNS_DEV bool cta_solve_pair(CtaCore<CAP>& S, Geo& G, float* xs, float* ys, const
   CtaOut O{S.acc, nullptr, nullptr, nullptr, 0, nullptr, nullptr, err};
   O.protocol = protocol;
   O.seed = seed;
+  if (fl_i) {
+    // record the flows and cost them all after the last round (the FP64
+    // distance is then computed once per flow with the lanes in parallel,
+    // not on every round's critical path)
+    O.fl_i = fl_i;
+    O.fl_j = fl_j;
+    O.fl_f = fl_f;
+    O.fl_cap = fl_cap;
+    O.x = x;
+    O.y = y;
+    O.d = d;
+  }
   unsigned long long nnz = 0;
   rounds = 0;
   pe = 0;

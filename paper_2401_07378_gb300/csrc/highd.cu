@@ -151,8 +151,11 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_batched_hd(BatchArgs A) {
     __syncthreads();
     double cost = 0.0;
     long long rounds = 0, pe = 0;
+    const size_t fo = (size_t)blockIdx.x * A.fl_cap;
     const bool ok = cta_solve_pair(H.S, H.G, nullptr, nullptr, A.x + xo * A.d, A.a + xo, m, A.y + yo * A.d,
-                                   A.b + yo, n, A.d, A.metric, A.err, cost, rounds, pe, A.protocol, A.seed);
+                                   A.b + yo, n, A.d, A.metric, A.err, cost, rounds, pe, A.protocol, A.seed,
+                                   A.fl_i ? A.fl_i + fo : nullptr, A.fl_i ? A.fl_j + fo : nullptr,
+                                   A.fl_i ? A.fl_f + fo : nullptr, A.fl_cap);
     if (tid == 0) {
       A.costs[pr] = ok ? cost : CUDART_NAN;
       if (A.rounds) A.rounds[pr] = rounds;
@@ -212,8 +215,11 @@ __global__ void __launch_bounds__(HD_SMALL_THREADS, 4) k_batched_hd_small(BatchA
     __syncthreads();
     double cost = 0.0;
     long long rounds = 0, pe = 0;
+    const size_t fo = (size_t)blockIdx.x * A.fl_cap;
     const bool ok = cta_solve_pair(H.S, H.G, nullptr, nullptr, A.x + xo * A.d, A.a + xo, m, A.y + yo * A.d,
-                                   A.b + yo, n, A.d, A.metric, A.err, cost, rounds, pe, A.protocol, A.seed);
+                                   A.b + yo, n, A.d, A.metric, A.err, cost, rounds, pe, A.protocol, A.seed,
+                                   A.fl_i ? A.fl_i + fo : nullptr, A.fl_i ? A.fl_j + fo : nullptr,
+                                   A.fl_i ? A.fl_f + fo : nullptr, A.fl_cap);
     if (tid == 0) {
       A.costs[pr] = ok ? cost : CUDART_NAN;
       if (A.rounds) A.rounds[pr] = rounds;

@@ -129,6 +129,13 @@ struct BatchArgs {
   int protocol;          // nnsemd_protocol
   unsigned long long seed;
   int n_shared;          // > 0: every pair's consumers are rows 0..n_shared-1 of y (y_off unused)
+  // flow records (nullable): CTA b records a pair's flows in entries
+  // [b fl_cap, (b + 1) fl_cap) and costs them once after the pair's last
+  // round (d > 8 solvers)
+  int32_t* fl_i;
+  int32_t* fl_j;
+  double* fl_f;
+  long long fl_cap;
 };
 int launch_batched_lowd(const BatchArgs& A, int grid, cudaStream_t st);
 
