@@ -296,7 +296,7 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
   B.notify = ctx->dmap;
   B.notify_seq = ++ctx->notify_seq;
   launch_initial_pack(B, st);
-  L += 4;
+  L += B.dp > 0 ? 4 : 6;  // two sums, count + scatter (d > 8: two finiteness checks too)
   CK(cudaGetLastError());
   int mt = 0, nt = 0;
   unsigned err0 = 0;
@@ -350,6 +350,7 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
       if (timed) CK(cudaEventRecord(ctx->ev[0], st));
       nrc = lowd ? launch_nns_lowd(B, mt, nt, st) : launch_nns_f32(B, mt, nt, nullptr, nullptr, st);
       if (timed) CK(cudaEventRecord(ctx->ev[1], st));
+      L += 1;
     }
     if (nrc) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "NNS launch failed for d=%d (%d)", B.d, nrc);
     // the compaction's count kernel publishes the next active counts as soon
@@ -358,7 +359,7 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
     B.notify = ctx->dmap;
     B.notify_seq = ++ctx->notify_seq;
     launch_big_round(B, mt, nt, rounds, st);
-    L += 10;
+    L += 6;  // group count / alloc / scatter, flow, compaction count / scatter
     CK(cudaGetLastError());
     B.cur ^= 1;
     rounds += 1;
