@@ -300,10 +300,15 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
   CK(cudaGetLastError());
   int mt = 0, nt = 0;
   unsigned err0 = 0;
+  // a failure after this point returns only once the stream has drained:
+  // no work of this call outlives it
+  auto drained = [&](int status) {
+    cudaStreamSynchronize(st);
+    return status;
+  };
   int rc = wait_counts(ctx, st, B.notify_seq, mt, nt, err0);
-  if (rc) return rc;
-  rc = map_err_bits(ctx, err0);
-  if (rc) return rc;
+  if (!rc) rc = map_err_bits(ctx, err0);
+  if (rc) return drained(rc);
   long long rounds = 0, pair_evals = 0;
   const long long round_limit = B.m + B.n;
   const bool lowd = B.dp > 0;
@@ -311,7 +316,8 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
   const int clcap = lowd ? finish_cluster_cap(B.d, B.metric) : 0;
   if (learned) {
     // once per solve: supplier cells and radii, consumer proposals and bounds
-    if (learned_prepare(*learned, B.x, B.m, B.y, B.n, B.d, st)) return fail(ctx, NNSEMD_ERR_CUDA, "proposal preparation");
+    if (learned_prepare(*learned, B.x, B.m, B.y, B.n, B.d, st))
+      return drained(fail(ctx, NNSEMD_ERR_CUDA, "proposal preparation"));
     L += 8 + 8 * ((B.n + learned->chunk - 1) / learned->chunk);
   }
   while (mt > 0 && nt > 0) {
@@ -324,13 +330,13 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
       const int lrc = clcap  ? launch_finish_cluster(B, round_limit - rounds, st)
                       : lowd ? launch_finish(B, round_limit - rounds, st)
                              : launch_finish_hd(B, round_limit - rounds, st);
-      if (lrc) return fail(ctx, NNSEMD_ERR_CUDA, "finisher launch");
+      if (lrc) return drained(fail(ctx, NNSEMD_ERR_CUDA, "finisher launch"));
       if (timed) CK(cudaEventRecord(ctx->ev[3], st));
       tail_ran = true;
       L += 1;
       break;
     }
-    if (rounds >= round_limit) return fail(ctx, NNSEMD_ERR_ITER_LIMIT, "round limit m + n exceeded");
+    if (rounds >= round_limit) return drained(fail(ctx, NNSEMD_ERR_ITER_LIMIT, "round limit m + n exceeded"));
     // B.nnkey[0 .. nt) is all ones here: the compaction that produced the
     // active lists reset the key of every surviving consumer
     int nrc;
@@ -352,7 +358,7 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
       if (timed) CK(cudaEventRecord(ctx->ev[1], st));
       L += 1;
     }
-    if (nrc) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "NNS launch failed for d=%d (%d)", B.d, nrc);
+    if (nrc) return drained(fail(ctx, NNSEMD_ERR_UNSUPPORTED, "NNS launch failed for d=%d (%d)", B.d, nrc));
     // the compaction's count kernel publishes the next active counts as soon
     // as they are known; the host sizes and launches the next round while
     // the scatter still runs
@@ -368,7 +374,7 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
     nns_pairs += (long long)mt * nt;
     unsigned err_bits = 0;
     rc = wait_counts(ctx, st, B.notify_seq, mt, nt, err_bits);
-    if (rc) return rc;
+    if (rc) return drained(rc);
     if (timed) {
       float ms = 0.f;
       CK(cudaEventSynchronize(ctx->ev[1]));
@@ -376,7 +382,7 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
       nns_ms += ms;
     }
     rc = map_err_bits(ctx, err_bits);
-    if (rc) return rc;
+    if (rc) return drained(rc);
   }
   launch_leftover(B, st);
   L += 2;
