@@ -17,9 +17,12 @@ Other workloads (reported by hand, not by the driver):
   docs       1 query document vs 4,096 documents, word vectors d=300 (batched);
   retrieval  10,000 signature pairs, 256..2,048 descriptors of d=128 (batched).
 
-With N > 1 (torchrun, one rank per GPU) every rank solves its own pair(s)
-(seed = rank): the pairs are independent, so there is no collective on the
-data path ("weak" scaling); value = all ranks' pairs / max-over-ranks time.
+With N > 1 (torchrun, one rank per GPU): a batched workload (docs,
+retrieval) is ONE batch split over the ranks by estimated work (greedy
+longest-processing-time on m * n, shard.py), every rank solves its share and
+the P costs are all-gathered in pair order ("strong" scaling: the total work
+is fixed); a single-pair workload runs one independent pair per rank
+(seed = rank, "weak" scaling).  value = all ranks' pairs / max-over-ranks time.
 
 JSON line (rank 0):
   value / ms_per_step  device time of K steps with inputs resident in HBM
@@ -35,8 +38,19 @@ JSON line (rank 0):
                        supplier/consumer pair), the tensor pipe for the
                        tcgen05 kernel (2d flops per pair), timed by the
                        library with CUDA events around each launch;
-  cpu_baseline         the CPU oracle (single thread) on a bounded sample of
-                       the workload, scaled to the metric's unit.
+  cpu_baseline         the CPU oracle timed on all host cores: colour, the
+                       full pair (the oracle's multi-core twin); docs, every
+                       pair; retrieval, a seeded 200-pair subset; single, the
+                       pair solved repeatedly (one copy per core); gmm, a
+                       8,192-point instance scaled to the full pair;
+  accuracy             R of the GPU against the oracle on the same pairs:
+                       relative error against the FP64-decision oracle (the
+                       metric's "rel err vs FP64 oracle") and against the
+                       FP32-decision oracle (whose decisions the kernels
+                       take), the pairs checked and the oracle's FP32/FP64
+                       near-ties; the run fails (exit 3) above the tolerance
+                       (1e-5 for FP32 forms, 1e-3 for reduced precision and
+                       learned forms).
 """
 from __future__ import annotations
 
@@ -55,28 +69,30 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "NNS-EMD pairs/s at <=1e-3 rel err vs FP64 oracle; fused-kernel % of roofline"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-ORACLE_SAMPLE_N = 16384        # colour-transfer oracle sample: 16,384 points per side
+GMM_SAMPLE_N = 8192            # GMM oracle sample: 8,192 points per side (the full pair is out of reach)
+RETRIEVAL_SAMPLE = 200         # retrieval pairs the oracle checks (seeded subset)
+TOL_FP32 = 1e-5                # relative error bound of the FP32 forms against the FP64 oracle
+TOL_REDUCED = 1e-3             # ... of the reduced-precision and learned forms
 WORK_FILE = os.path.join(ROOT, "tests", "golden", "colour_transfer_oracle.json")
 COUNTERS_FILE = os.path.join(ROOT, "profiles", "k_nns_lowd_colour_transfer.json")
 
 WORKLOADS = {
-    "colour": dict(desc=("colour-transfer pair: 65,536 x 65,536 points, d=3, 8 Gaussian colour clusters "
+    "colour": dict(d=3, desc=("colour-transfer pair: 65,536 x 65,536 points, d=3, 8 Gaussian colour clusters "
                          "(sigma 0.08, clipped to [0,1)), uniform weights, squared-Euclidean ground distance, "
                          "full sparse plan returned"), metric="sql2", precision="fp32", batched=False),
-    "single": dict(desc="single pair: 256 x 256 points, d=2, Uniform[0,1), uniform weights, Euclidean, full plan",
+    "single": dict(d=2, desc="single pair: 256 x 256 points, d=2, Uniform[0,1), uniform weights, Euclidean, full plan",
                    metric="l2", precision="fp32", batched=False),
-    "gmm": dict(desc=("GMM pair: 262,144 x 262,144 points, d=64, 256-component mixture (means N(0,4I), "
+    "gmm": dict(d=64, desc=("GMM pair: 262,144 x 262,144 points, d=64, 256-component mixture (means N(0,4I), "
                       "cov 0.25I), Dirichlet(0.5) weights, Euclidean, full plan; learned candidate proposal "
                       "(MLP 64-256-256-4096 cells, trained on 200 seeded plain runs), BF16 contraction for the "
                       "consumers it cannot certify"),
                 metric="l2", precision="bf16", batched=False, proposal="learned", steps=5),
-    "docs": dict(desc=("document kNN: 1 query vs 4,096 documents, word vectors d=300 N(0,1) L2-normalised "
+    "docs": dict(d=300, desc=("document kNN: 1 query vs 4,096 documents, word vectors d=300 N(0,1) L2-normalised "
                        "(50k vocabulary), lengths LogNormal(ln 60, 0.6) clipped to [20,500], Zipf(1.1) weights, "
                        "Euclidean, BF16 distances + FP32 re-rank, one persistent launch replayed as a CUDA graph"),
                  metric="l2", precision="bf16", batched=True, graph=True, steps=50),
-    "retrieval": dict(desc=("retrieval: 10,000 signature pairs, m, n ~ U{256..2048}, d=128 |N(0,1)| "
+    "retrieval": dict(d=128, desc=("retrieval: 10,000 signature pairs, m, n ~ U{256..2048}, d=128 |N(0,1)| "
                             "L2-normalised x512, Dirichlet(1) weights, Euclidean, FP16 distances + FP32 re-rank, "
                             "autotuned tiles, batched"),
                       metric="l2", precision="fp16", batched=True, autotune=True, steps=5),
@@ -193,66 +209,113 @@ def make_inputs(name: str, rank: int, points: int | None = None, pairs: int | No
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle baseline (bounded sample, scaled to the metric's unit)
+# CPU oracle: timing on the host cores and the accuracy of the GPU's R
 # ---------------------------------------------------------------------------
 
-def full_pair_work() -> int | None:
-    """Sum of m_t * n_t of the full colour-transfer pair, as computed by the
-    oracle (tests/golden/make_oracle_values.py writes it)."""
+def golden_fp64_cost() -> float | None:
+    """R of the full colour-transfer pair under FP64 decisions, written by
+    tests/golden/make_oracle_values.py (calls only the oracle)."""
     try:
         with open(WORK_FILE) as fh:
-            return int(json.load(fh)["pair_evals"])
+            return float(json.load(fh)["fp64"]["cost"])
     except (OSError, KeyError, ValueError):
         return None
 
 
-def oracle_sample(name: str, inputs=None, full_work: int | None = None) -> dict:
-    """Time the oracle, as it stands, on a bounded sample; returns pairs/s."""
+def warm_pool(pool):
+    """Start every worker of an oracle process pool before any timing."""
+    list(pool.map(time.sleep, [0.2] * pool._max_workers))
+
+
+def retrieval_subset(num_pairs: int) -> list[int]:
+    """The seeded subset of retrieval pairs the oracle checks."""
+    import numpy as np
+    k = min(RETRIEVAL_SAMPLE, num_pairs)
+    return sorted(int(p) for p in np.random.default_rng(0).choice(num_pairs, size=k, replace=False))
+
+
+def oracle_time(name: str, inp, pool=None) -> dict:
+    """Time the oracle, as it stands, on the host cores over a bounded sample
+    of the workload ``inp``.  Returns the rate (pairs/s), the threads used,
+    a description of the sample and the oracle's results (pair index -> R
+    under FP32 decisions, and its FP32/FP64 near-ties).  ``pool``: the host
+    process pool (oracle.process_pool) of the many-pair samples."""
     import oracle
     from paper_2401_07378_gb300 import workloads
-    spec = WORKLOADS[name]
+    cores = max(1, oracle.max_threads()) if name in ("colour", "gmm") else pool._max_workers
+    metric = WORKLOADS[name]["metric"]
+    costs, ties = {}, 0
     t0 = time.perf_counter()
     if name == "colour":
-        p = workloads.color_transfer(seed=0, n=ORACLE_SAMPLE_N)
-        r = oracle.solve_pair(p, spec["metric"])
+        r = oracle.solve_pair(inp, metric, threads=0)
         dt = time.perf_counter() - t0
-        work = full_work or full_pair_work()
-        scale = (work / r.pair_evals) if work else (65536 / ORACLE_SAMPLE_N) ** 2
-        value = 1.0 / (dt * scale)
-        sample = (f"one {ORACLE_SAMPLE_N}-point instance of the same generator: {dt:.2f} s for {r.pair_evals} "
-                  f"pair evaluations, scaled by NNS work to the full pair ({work} evaluations, oracle-computed)")
+        costs[0], ties = r.cost, r.near_ties
+        value = 1.0 / dt
+        sample = (f"the full pair, solved once by the oracle's multi-core twin on {cores} host threads "
+                  f"({dt:.2f} s, {r.rounds} rounds, {r.pair_evals} pair evaluations)")
     elif name == "single":
-        p = inputs
-        done = 0
+        done, batch = 0, cores * 8
         while True:
-            oracle.solve_pair(p, spec["metric"])
-            done += 1
+            rs = oracle.solve_many([inp] * batch, metric, pool=pool)
+            done += batch
             dt = time.perf_counter() - t0
-            if dt > 5.0:
+            if dt > 3.0:
                 break
+        costs[0], ties = rs[0].cost, rs[0].near_ties
         value = done / dt
-        sample = f"the full pair solved {done} times in {dt:.2f} s"
+        sample = f"the full pair solved {done} times, one copy per host process on {cores} processes, in {dt:.2f} s"
     elif name == "gmm":
-        n = 8192
-        p = workloads.gmm_pair(seed=0, n=n)
-        r = oracle.solve_pair(p, spec["metric"])
+        p = workloads.gmm_pair(seed=0, n=GMM_SAMPLE_N)
+        r = oracle.solve_pair(p, metric, threads=0)
         dt = time.perf_counter() - t0
-        scale = (full_work / r.pair_evals) if full_work else (262144 / n) ** 2
+        scale = (262144 / GMM_SAMPLE_N) ** 2
         value = 1.0 / (dt * scale)
-        sample = (f"one {n}-point instance of the same generator: {dt:.2f} s for {r.pair_evals} pair evaluations, "
-                  f"scaled by NNS work to the full pair ({full_work} evaluations as counted by the GPU run)")
+        sample = (f"one {GMM_SAMPLE_N}-point instance of the same generator on {cores} host threads: {dt:.2f} s "
+                  f"for {r.pair_evals} pair evaluations, scaled to 262,144 points by (262144/{GMM_SAMPLE_N})^2 "
+                  f"(assumes the NNS work grows as m * n; the oracle's own count on the sample)")
     else:
-        batch = inputs
-        done = 0
-        for k in range(batch.num_pairs):
-            oracle.solve_pair(batch.pair(k), spec["metric"])
-            done += 1
-            dt = time.perf_counter() - t0
-            if dt > 10.0:
-                break
-        value = done / dt
-        sample = f"the first {done} pairs of the batch in {dt:.2f} s"
-    return {"value": value, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": sample}
+        ids = list(range(inp.num_pairs)) if name == "docs" else retrieval_subset(inp.num_pairs)
+        rs = oracle.solve_many([inp.pair(k) for k in ids], metric, pool=pool)
+        dt = time.perf_counter() - t0
+        for k, r in zip(ids, rs):
+            costs[k] = r.cost
+            ties += r.near_ties
+        value = len(ids) / dt
+        which = "every pair of the batch" if name == "docs" else f"a seeded {len(ids)}-pair subset of the batch"
+        sample = f"{which}, one pair per host process on {cores} processes, in {dt:.2f} s"
+    return {"value": value, "cores": cores, "sample": sample, "seconds": dt, "costs": costs, "near_ties": ties}
+
+
+def accuracy(name: str, inp, gpu_costs: dict, orc: dict, tol: float, pool=None) -> dict:
+    """Relative error |R_gpu - R_oracle| / R_oracle (Sec. IV-F's definition,
+    taken against the oracle) over the pairs the oracle solved, against the
+    FP32-decision oracle and against the FP64-decision oracle."""
+    import oracle
+    metric = WORKLOADS[name]["metric"]
+    out = {"pairs_checked": 0, "rel_err_vs_fp32_decision_oracle": None, "rel_err_vs_fp64_oracle": None,
+           "oracle_near_ties_fp32_vs_fp64": orc.get("near_ties"), "tolerance": tol}
+    if not orc["costs"]:
+        out["note"] = ("the oracle cannot solve the full pair in bounded time; parity of this form is tested "
+                       "against the oracle at 16,384 points per side (tests/test_gpu_full_size.py)")
+        out["ok"] = None
+        return out
+    ids = sorted(orc["costs"])
+    rel = lambda g, o: abs(g - o) / abs(o) if o != 0 else abs(g - o)
+    out["pairs_checked"] = len(ids)
+    out["rel_err_vs_fp32_decision_oracle"] = max(rel(gpu_costs[k], orc["costs"][k]) for k in ids)
+    if name == "colour":
+        r64 = {0: golden_fp64_cost()}
+        out["fp64_source"] = "tests/golden/colour_transfer_oracle.json (oracle-written, FP64 decisions)"
+    elif name == "single":
+        r64 = {0: oracle.solve_pair(inp, metric, decide="fp64").cost}
+    else:
+        pairs = [inp.pair(k) for k in ids]
+        r64 = dict(zip(ids, (r.cost for r in oracle.solve_many(pairs, metric, decide="fp64", pool=pool))))
+    if all(v is not None for v in r64.values()):
+        out["rel_err_vs_fp64_oracle"] = max(rel(gpu_costs[k], r64[k]) for k in ids)
+    worst = max(v for v in (out["rel_err_vs_fp32_decision_oracle"], out["rel_err_vs_fp64_oracle"]) if v is not None)
+    out["ok"] = bool(worst <= tol)
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -297,14 +360,16 @@ def peaks():
         return {}
 
 
-def roofline(d: int, precision: str, pairs: int, launches: int, ms: float, total_ms: float, lowd: bool) -> dict:
+def roofline(d: int, precision: str, pairs: int, launches: int, ms: float, total_ms: float, lowd: bool,
+             sms: int) -> dict:
     pk = peaks()
     per_launch_s = ms / 1e3 / max(launches, 1)
     if precision == "fp32":
         clk = float(pk.get("sm_max_mhz", 2070.0))
-        peak = SM_COUNT * FP32_LANES_PER_SM * clk * 1e6 / 1e12
+        peak = sms * FP32_LANES_PER_SM * clk * 1e6 / 1e12
         ops = pairs * 2 * d / max(launches, 1)
-        basis = (f"152 SMs x 128 FP32 lanes x {clk:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json); "
+        basis = (f"{sms} SMs (the device's multiprocessor count) x 128 FP32 lanes x {clk:.0f} MHz "
+                 f"(sm_max_mhz of MEASURED_PEAKS.json); "
                  f"work = 2d FP32-pipe ops per supplier/consumer pair")
         bound = "alu"
         kernel = "k_nns_lowd (K1)" if lowd else "k_nns_f32_tiled"
@@ -324,10 +389,27 @@ def roofline(d: int, precision: str, pairs: int, launches: int, ms: float, total
             "share_of_step": ms / total_ms if total_ms else None}
 
 
+
+
+def bench_config(args, ws: int) -> dict:
+    """The workload's `config` (the same dict on both arms)."""
+    spec = WORKLOADS[args.workload]
+    precision = args.precision or spec["precision"]
+    if ws == 1:
+        par = "1 GPU"
+    elif spec["batched"]:
+        par = f"one batch split over {ws} GPUs by estimated work (greedy longest-processing-time), costs all-gathered"
+    else:
+        par = f"{ws} independent pairs, one per GPU"
+    return {"workload": spec["desc"], "name": args.workload, "d": spec["d"], "metric": spec["metric"],
+            "precision": precision, "protocol": args.protocol, "l2": "flushed before every step (256 MiB write)",
+            "parallelism": par}
+
+
 def run_ours(args) -> dict | None:
     import numpy as np
     import torch
-    from paper_2401_07378_gb300 import nnsemd
+    from paper_2401_07378_gb300 import nnsemd, shard
 
     spec = WORKLOADS[args.workload]
     precision = args.precision or spec["precision"]
@@ -337,19 +419,26 @@ def run_ours(args) -> dict | None:
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dist_init("nccl")
-    inp = make_inputs(args.workload, rank, args.points, args.pairs)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    # a batch is one workload split over the ranks; a single pair runs once per rank
+    full = make_inputs(args.workload, 0 if spec["batched"] else rank, args.points, args.pairs)
+    inp, shares = full, None
+    if spec["batched"] and ws > 1:
+        shares = shard.partition(shard.pair_work(full.x_off, full.y_off), ws)
+        inp = shard.sub_batch(full, shares[rank])
     ctx = nnsemd.Context(local)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     T = nnsemd.FLAG_TIME_KERNELS
     t = lambda v: torch.from_numpy(v).to(dev)
     x, a, y, b = t(inp.x), t(inp.a), t(inp.y), t(inp.b)
-    d = int(inp.x.shape[1])
+    d = int(full.x.shape[1])
     prop, prop_info = None, None
     if proposal == "learned":
         if args.workload != "gmm":
             raise SystemExit("--proposal learned serves the gmm workload")
         from paper_2401_07378_gb300 import proposal_training
         prop, prop_info = proposal_training.build_gmm_proposal(ctx, d=d)
+    costs = None
     if spec["batched"]:
         P = inp.num_pairs
         costs = torch.empty(P, dtype=torch.float64, device=dev)
@@ -376,7 +465,7 @@ def run_ours(args) -> dict | None:
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     agg = {"nns_kernel_ms": 0.0, "tail_kernel_ms": 0.0, "nns_kernel_pairs": 0, "nns_kernel_launches": 0,
-           "kernel_launches": 0, "certified": 0, "fallbacks": 0}
+           "kernel_launches": 0, "certified": 0, "fallbacks": 0, "near_ties": 0}
     last = None
     for k in range(args.steps):
         flush.zero_()
@@ -394,6 +483,13 @@ def run_ours(args) -> dict | None:
     total_ms = sum(step_ms)
     max_ms = dist_reduce(total_ms, "max", dev)
     launches_all = int(dist_reduce(float(agg["kernel_launches"]), "sum", dev))
+    # every pair's R, in pair order (a split batch is gathered from all ranks)
+    if spec["batched"]:
+        gpu_costs = (shard.gather_costs(costs, shares, full.num_pairs, rank, dev) if shares is not None
+                     else costs.cpu().numpy())
+    else:
+        gpu_costs = np.array([(last or {}).get("cost")], np.float64)
+    total_units = full.num_pairs if spec["batched"] else ws * units
 
     e2e = None
     if spec["batched"]:
@@ -426,7 +522,7 @@ def run_ours(args) -> dict | None:
             torch.cuda.synchronize()
             e2e_ms += e0.elapsed_time(e1)
         e2e_max = dist_reduce(e2e_ms, "max", dev)
-        e2e = {"value": ws * args.steps * units / (e2e_max / 1e3), "unit": "pairs/s",
+        e2e = {"value": args.steps * total_units / (e2e_max / 1e3), "unit": "pairs/s",
                "h2d_bytes_per_step": sum(v.numel() * v.element_size() for v in (hx, ha, hy, hb)),
                "d2h_bytes_per_step": P * 8}
     else:
@@ -453,7 +549,7 @@ def run_ours(args) -> dict | None:
             e2e_ms += e0.elapsed_time(e1)
             nnz = int(hres.plan_f.numel())
         e2e_max = dist_reduce(e2e_ms, "max", dev)
-        e2e = {"value": ws * args.steps * units / (e2e_max / 1e3), "unit": "pairs/s",
+        e2e = {"value": args.steps * total_units / (e2e_max / 1e3), "unit": "pairs/s",
                "h2d_bytes_per_step": sum(v.numel() * v.element_size() for v in (hx, ha, hy, hb)),
                "d2h_bytes_per_step": nnz * (4 + 4 + 8) + 8}
 
@@ -466,7 +562,7 @@ def run_ours(args) -> dict | None:
         # the persistent batched kernel is the step: its NNS work against the
         # FP32 pipe, or the tensor pipe when the contraction runs there
         rl = roofline(d, precision, agg.get("nns_kernel_pairs", 0) or (last or {}).get("pair_evals", 0) * args.steps,
-                      args.steps, total_ms, total_ms, lowd)
+                      args.steps, total_ms, total_ms, lowd, sms)
         if precision == "fp32":
             rl["kernel"] = ("k_batched_lowd" if lowd else
                             "k_batched_hd / k_batched_hd_small (persistent, one pair per CTA)")
@@ -477,32 +573,30 @@ def run_ours(args) -> dict | None:
         # a pair small enough for one launch (k_solve_small): that kernel runs
         # every round, so its NNS work over its own time
         rl = roofline(d, precision, (last or {}).get("pair_evals", 0) * args.steps, args.steps,
-                      agg["tail_kernel_ms"], total_ms, lowd)
+                      agg["tail_kernel_ms"], total_ms, lowd, sms)
         rl["kernel"] = "k_solve_small (the whole pair in one launch: every round's NNS, grouping, flow, compaction)"
         rl["traffic"] = None
         rl["note"] = "latency-bound: the NNS work is a small part of each round"
     else:
         rl = roofline(d, precision, agg["nns_kernel_pairs"], agg["nns_kernel_launches"], agg["nns_kernel_ms"],
-                      total_ms, lowd)
+                      total_ms, lowd, sms)
         if prop is not None:
             # the learned step scans candidates only: its rate is the full scan's work over its time
             rl["kernel"] = "learned NNS step (cell bookkeeping, k_learned_nns, FP32 rescan of the uncertified)"
             rl["note"] = "achieved counts the full scan's 2d ops per pair: an effective rate, not pipe utilisation"
     line = {
-        "metric": METRIC, "value": ws * args.steps * units / (max_ms / 1e3), "unit": "pairs/s", "n_gpus": ws,
+        "metric": METRIC, "value": args.steps * total_units / (max_ms / 1e3), "unit": "pairs/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": "strong" if (spec["batched"] and ws > 1) else "weak", "vs_baseline": None,
         "dtype": "f32 distances, f64 mass/cost" if precision == "fp32" else f"{precision} contraction, f32 re-rank, f64 mass/cost",
         "data": "synthetic",
-        "config": {"workload": spec["desc"], "name": args.workload, "d": d, "metric": metric, "precision": precision,
-                   "protocol": args.protocol,
-                   "l2": "flushed before every step (256 MiB write)",
-                   "parallelism": f"{ws} independent problems, one per GPU" if ws > 1 else "1 GPU"},
+        "config": bench_config(args, ws),
         "roofline": rl,
         "tail_kernel_share": agg["tail_kernel_ms"] / total_ms if total_ms else None,
         "gpu_launches": launches_all,
         "rounds_per_step": (last or {}).get("rounds"), "pair_evals_per_step": (last or {}).get("pair_evals"),
-        "certified": agg["certified"], "fallbacks": agg["fallbacks"], "cost": (last or {}).get("cost"),
+        "certified": agg["certified"], "fallbacks": agg["fallbacks"], "near_ties_reduced_precision": agg["near_ties"],
+        "cost": float(gpu_costs[0]) if not spec["batched"] else None,
         "proposal": prop_info,
         "clocks": clocks,
     }
@@ -528,36 +622,48 @@ def run_ours(args) -> dict | None:
         torch.cuda.synchronize()
         line["plain_fp32"] = {"value": k_plain / (p0.elapsed_time(p1) / 1e3), "unit": "pairs/s", "steps": k_plain,
                               "same_cost": pr.cost == (last or {}).get("cost", pr.cost)}
-    if ws == 1 and not args.no_cpu_baseline and not (args.points or args.pairs):
-        full = (last or {}).get("pair_evals") if args.workload == "gmm" else None
-        line["cpu_baseline"] = oracle_sample(args.workload, inp, full)
     ctx.close()
+    tol = TOL_FP32 if (precision == "fp32" and prop is None) else TOL_REDUCED
+    if ws == 1 and not args.no_cpu_baseline and not (args.points or args.pairs):
+        import oracle
+        with oracle.process_pool() as pool:
+            warm_pool(pool)
+            orc = oracle_time(args.workload, full, pool)
+            acc = accuracy(args.workload, full, dict(enumerate(gpu_costs.tolist())), orc, tol, pool)
+        line["cpu_baseline"] = {"value": orc["value"], "unit": "pairs/s", "cores": orc["cores"], "kind": "oracle",
+                                "sample": orc["sample"]}
+        line["accuracy"] = acc
+        line["rel_err_vs_fp64_oracle"] = acc["rel_err_vs_fp64_oracle"]
     return line
 
 
 def run_reference(args) -> dict | None:
+    """The oracle as it stands, timed on the host cores on the same workload
+    (each step the bounded sample of oracle_time); rank 0 only."""
     rank, ws, _ = world()
     if rank != 0:
         return None
+    import oracle
     name = args.workload
-    spec = WORKLOADS[name]
-    inp = make_inputs(name, 0) if name in ("single", "docs", "retrieval") else None
-    for _ in range(args.warmup):
-        oracle_sample(name, inp)
-    secs = []
-    sample = None
-    for _ in range(args.steps):
-        r = oracle_sample(name, inp)
-        secs.append(1.0 / r["value"])
-        sample = r["sample"]
-    total = sum(secs)
-    value = args.steps / total
+    full = make_inputs(name, 0, args.points, args.pairs)
+    with oracle.process_pool() as pool:
+        warm_pool(pool)
+        for _ in range(args.warmup):
+            oracle_time(name, full, pool)
+        secs, units, last = 0.0, 0.0, None
+        for _ in range(args.steps):
+            r = oracle_time(name, full, pool)
+            secs += r["seconds"]
+            units += r["value"] * r["seconds"]
+            last = r
+    value = units / secs
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64 (oracle; decisions also in f32)", "data": "synthetic",
-            "config": {"workload": spec["desc"], "name": name, "metric": spec["metric"]},
-            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "dtype": "f64 mass/cost, f32 decisions (the CPU oracle)", "data": "synthetic",
+            "config": bench_config(args, 1),
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -583,9 +689,15 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.steps is None:
         args.steps = WORKLOADS[args.workload].get("steps", 200)
+    if args.impl == "reference" and args.protocol != "greedy":
+        raise SystemExit("the reference arm times the greedy protocol")
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)
+        acc = line.get("accuracy") or {}
+        if acc.get("ok") is False:
+            print(f"accuracy check failed: {acc}", file=sys.stderr, flush=True)
+            sys.exit(3)
 
 
 if __name__ == "__main__":

@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define NNSEMD_ABI_VERSION 2
+#define NNSEMD_ABI_VERSION 3
 
 typedef enum {
   NNSEMD_OK = 0,
@@ -78,6 +78,8 @@ typedef enum {
 } nnsemd_precision;
 
 typedef struct nnsemd_ctx nnsemd_ctx;
+
+#define NNSEMD_MAX_RERANK_K 16
 
 typedef struct {
   int32_t device;               /* CUDA device ordinal */
@@ -105,7 +107,12 @@ typedef enum { NNSEMD_PROTOCOL_GREEDY = 0, NNSEMD_PROTOCOL_RANDOM = 1 } nnsemd_p
 typedef struct {
   int32_t metric;               /* nnsemd_metric */
   int32_t precision;            /* nnsemd_precision */
-  int32_t rerank_k;             /* candidates per consumer kept by a reduced-precision scan (0 = default 8) */
+  int32_t rerank_k;             /* reduced precision: approximate candidates per consumer re-ranked with the
+                                   exact FP32 key, 0..NNSEMD_MAX_RERANK_K (0 = all the scan keeps: 16 per
+                                   supplier chunk in nnsemd_solve, 8 per pair in the batched kernel, which
+                                   also caps larger values at 8).  Fewer candidates make the re-rank
+                                   cheaper and the certificate weaker (more FP32 rescans); results never
+                                   change.  Outside the range: INVALID_ARG. */
   int32_t flags;                /* NNSEMD_FLAG_* bits, 0 for none */
   const void *proposal;         /* learned candidate proposal, NULL = full scan */
   int32_t protocol;             /* nnsemd_protocol (0 = greedy) */
@@ -132,6 +139,11 @@ typedef struct {
   int64_t nns_kernel_launches;  /* number of those launches */
   int64_t nns_kernel_pairs;     /* sum of m_t * n_t they evaluated */
   double tail_kernel_ms;        /* NNSEMD_FLAG_TIME_KERNELS: duration of the one-CTA tail kernel */
+  int64_t near_ties;            /* reduced precision: consumer searches whose exact FP32 re-rank picked
+                                   another supplier than the one the operand-precision distances ranked
+                                   first (ties at that precision).  0 on the FP32 paths: their decisions
+                                   are the FP32 decisions themselves (the FP32 / FP64 near-ties of the
+                                   method are the oracle's to count). */
 } nnsemd_stats;
 
 /* Create a context bound to cfg->device and cfg->stream.  *out receives the
@@ -294,14 +306,15 @@ int nnsemd_proposal_load(nnsemd_ctx *ctx, const char *path, nnsemd_proposal **ou
  *   1 <= m, n <= NNSEMD_NOALLOC_MAX_POINTS, 1 <= d <= NNSEMD_NOALLOC_MAX_D,
  *   larger sizes return NNSEMD_ERR_UNSUPPORTED;
  *   metric: an nnsemd_metric;  cost_out: DEVICE pointer to one double (R);
- *   stream: cudaStream_t to launch on (NULL = default); the call returns
- *   after the stream has finished the solve (it reads back an error word).
+ *   stream: cudaStream_t to launch on (NULL = default); the call copies an
+ *   error word back and waits for the stream before it returns.
  * No context is needed.  Scratch (a few error and counter words) lives in a
  * 256-byte __device__ array of the library, held by every GPU that loads it
  * until the process exits; the kernel clears it at the start of each call.
- * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress) with the device current: make the first call on each
- * device before any stream capture.  All calls share the array, so calls that
+ * The first call on a device does a one-time set-up with that device current:
+ * it looks up the array's device address (cudaGetSymbolAddress) and sets the
+ * kernel's shared-memory limit.  Make that first call on each device before
+ * any stream capture begins there.  All calls share the array, so calls that
  * overlap on the GPU race: serialise them.  R equals nnsemd_solve's. */
 #define NNSEMD_NOALLOC_MAX_POINTS 1024
 #define NNSEMD_NOALLOC_MAX_D 8

@@ -15,11 +15,18 @@ no code with the CUDA library and must not fall back to it.
    (again ``math.fsum``); Algorithm 1's own left-to-right accumulation is
    returned beside it as ``cost_seq``.
 
+``solve(..., threads=k)`` with k != 1 runs the multi-core twin of the C
+oracle (``oracle_nnsemd_omp``: the NNS operation and the group sorts in
+parallel, the flows serial); the tests check that it returns exactly what
+the serial oracle returns.  ``solve_many`` runs the serial oracle on many
+pairs at once, one pair per host process.
+
 Zero weights are allowed and the corresponding points never take part
 (Sec. II-A: histograms are over the bins with positive weight).
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
 import ctypes
 import math
 import os
@@ -31,6 +38,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "nnsemd_oracle.c")
+_SRC_OMP = os.path.join(_HERE, "nnsemd_oracle_omp.c")  # includes _SRC, adds the multi-core twin
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libnnsemd_oracle.so")
 _lock = threading.Lock()
@@ -54,13 +62,17 @@ class _Stats(ctypes.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no fused multiply-adds, -O2)."""
+    """Compile the oracle with gcc (no fused multiply-adds, -O2), with OpenMP
+    for the multi-core twin where the compiler has it (else the twin runs on
+    one core)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_OMP))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        base = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp,
+                _SRC_OMP]
+        if subprocess.run(base + ["-fopenmp", "-lm"], capture_output=True).returncode != 0:
+            subprocess.run(base + ["-lm"], check=True)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -79,6 +91,10 @@ def _load():
                           ctypes.c_int64, P, P,
                           ctypes.POINTER(_Stats)]
             f.restype = ctypes.c_int
+            g = lib.oracle_nnsemd_omp
+            g.argtypes = f.argtypes[:-1] + [ctypes.c_int32, ctypes.POINTER(_Stats)]
+            g.restype = ctypes.c_int
+            lib.oracle_omp_max_threads.restype = ctypes.c_int
             lib.oracle_splitmix64_output.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
             lib.oracle_splitmix64_output.restype = ctypes.c_uint64
             if lib.oracle_stats_size() != ctypes.sizeof(_Stats):
@@ -134,6 +150,11 @@ def normalise(w: np.ndarray) -> np.ndarray:
 PROTOCOLS = {"greedy": 0, "random": 1}
 
 
+def max_threads() -> int:
+    """Host threads the multi-core twin uses with threads=0 (1 without OpenMP)."""
+    return int(_load().oracle_omp_max_threads())
+
+
 def splitmix64_output(seed: int, k: int) -> int:
     """Output number k (k >= 1) of SplitMix64 seeded with `seed` (the
     generator of the random protocol's order; see nnsemd_oracle.c)."""
@@ -141,7 +162,7 @@ def splitmix64_output(seed: int, k: int) -> int:
 
 
 def solve(x, a, y, b, metric: str = "l2", decide: str = "fp32", trace: bool = False,
-          protocol: str = "greedy", seed: int = 0) -> OracleResult:
+          protocol: str = "greedy", seed: int = 0, threads: int = 1) -> OracleResult:
     """Run NNS-EMD (Alg. 1) on one pair.
 
     x: [m, d] float32 suppliers S with weights a; y: [n, d] float32 consumers
@@ -149,6 +170,8 @@ def solve(x, a, y, b, metric: str = "l2", decide: str = "fp32", trace: bool = Fa
     order decisions ("fp32" or "fp64"); mass and cost are FP64 either way.
     ``protocol``: "greedy" (the paper's default) or "random" (a supplier
     serves its consumers in a seeded random order, Sec. III-A).
+    ``threads``: 1 runs the serial oracle; any other value the multi-core
+    twin on that many host threads (0 = all).
     """
     lib = _load()
     x = np.ascontiguousarray(x, np.float32)
@@ -182,13 +205,16 @@ def solve(x, a, y, b, metric: str = "l2", decide: str = "fp32", trace: bool = Fa
         st = _Stats()
         s[:] = s0
         c[:] = c0
-        rc = lib.oracle_nnsemd(
-            m, n, d, x.ctypes.data, s.ctypes.data, y.ctypes.data, c.ctypes.data,
-            METRICS[metric], 1 if decide == "fp32" else 0, PROTOCOLS[protocol], seed,
-            cap, pi.ctypes.data, pj.ctypes.data, pf.ctypes.data, pt.ctypes.data,
-            rcap, m_t.ctypes.data, n_t.ctypes.data,
-            tcap if trace else 0, tj.ctypes.data if trace else None,
-            tn.ctypes.data if trace else None, ctypes.byref(st))
+        args = (m, n, d, x.ctypes.data, s.ctypes.data, y.ctypes.data, c.ctypes.data,
+                METRICS[metric], 1 if decide == "fp32" else 0, PROTOCOLS[protocol], seed,
+                cap, pi.ctypes.data, pj.ctypes.data, pf.ctypes.data, pt.ctypes.data,
+                rcap, m_t.ctypes.data, n_t.ctypes.data,
+                tcap if trace else 0, tj.ctypes.data if trace else None,
+                tn.ctypes.data if trace else None)
+        if threads == 1:
+            rc = lib.oracle_nnsemd(*args, ctypes.byref(st))
+        else:
+            rc = lib.oracle_nnsemd_omp(*args, threads, ctypes.byref(st))
         if rc != 0:
             raise OracleError(f"oracle failed with status {rc}")
         if trace and int(np.sum(n_t[: st.rounds])) > tcap:
@@ -209,5 +235,38 @@ def solve(x, a, y, b, metric: str = "l2", decide: str = "fp32", trace: bool = Fa
 
 
 def solve_pair(pair, metric: str = "l2", decide: str = "fp32", trace: bool = False, protocol: str = "greedy",
-               seed: int = 0) -> OracleResult:
-    return solve(pair.x, pair.a, pair.y, pair.b, metric, decide, trace, protocol, seed)
+               seed: int = 0, threads: int = 1) -> OracleResult:
+    return solve(pair.x, pair.a, pair.y, pair.b, metric, decide, trace, protocol, seed, threads)
+
+
+def _solve_packed(job):
+    """Worker of solve_many: one pair given as (x, a, y, b, metric, decide, protocol, seed)."""
+    x, a, y, b, metric, decide, protocol, seed = job
+    return solve(x, a, y, b, metric, decide, False, protocol, seed)
+
+
+def process_pool(workers: int = 0):
+    """A pool of ``workers`` (0 = every core) host processes for solve_many,
+    started with ``spawn`` (safe after CUDA has been initialised in the
+    caller); each worker builds nothing and loads the oracle library once."""
+    import multiprocessing as mp
+    workers = workers or os.cpu_count() or 1
+    return cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"), initializer=_load)
+
+
+def solve_many(pairs, metric: str = "l2", decide: str = "fp32", protocol: str = "greedy", seed: int = 0,
+               workers: int = 0, pool=None) -> list[OracleResult]:
+    """The serial oracle on every pair of ``pairs``, several pairs at a time,
+    one pair per host process (``pool``, from process_pool; else a pool of
+    ``workers`` processes made for this call, 0 = every core; 1 runs in this
+    process).  Results in the order of ``pairs``."""
+    pairs = list(pairs)
+    jobs = [(p.x, p.a, p.y, p.b, metric, decide, protocol, seed) for p in pairs]
+    if pool is not None:
+        return list(pool.map(_solve_packed, jobs, chunksize=max(1, len(jobs) // (8 * pool._max_workers))))
+    workers = workers or os.cpu_count() or 1
+    if workers == 1 or len(pairs) <= 1:
+        return [_solve_packed(j) for j in jobs]
+    build()
+    with process_pool(workers) as ex:
+        return list(ex.map(_solve_packed, jobs, chunksize=max(1, len(jobs) // (8 * workers))))

@@ -3,18 +3,15 @@
  * smoke check and the CPU-baseline leg of the benchmark may load this file's
  * library; the product path never does.
  *
- * A plain, deliberately slow restatement of the paper's Algorithm 1
- * ("NNS-EMD with Greedy Protocol", Sec. III-A) in the order the paper gives:
- *
- *   while some weight is left:
- *     m(t) = { i : s_i > 0 },  n(t) = { j : c_j > 0 }            (Alg. 1)
- *     for every j in n(t):  NNS(j) = argmin_{i in m(t)} D_ij      (NNS op.)
- *     for every i in m(t):
- *        a_i = { j : NNS(j) = i }, sorted by D_ij ascending      (greedy prot.)
- *                                   or in a random order         (random prot.)
- *        walk a_i while s_i > 0:
- *          f = min(s_i, c_j); s_i -= f; c_j -= f; R += f*D_ij; F_ij += f
- *     t += 1
+ * A plain, deliberately slow statement of NNS-EMD with the greedy protocol
+ * (Alg. 1, Sec. III-A), written from the method's description.  Each round
+ * looks only at the points that still hold weight.  Every such consumer
+ * picks its nearest such supplier (the NNS operation), by a full double loop.
+ * Every supplier then takes the consumers that picked it, orders them by
+ * distance (greedy protocol) or by a seeded random key (random protocol),
+ * and hands each in turn the smaller of the two residuals until its own
+ * residual is gone, adding that amount times the ground distance to R and
+ * to the plan entry.  Rounds repeat until one side has no weight left.
  *
  * Readings of the paper taken here (the paper is silent or garbled on them):
  *  - Inner greedy loop: every consumer of the sorted group is visited while

@@ -56,6 +56,23 @@ int fail(nnsemd_ctx* ctx, int status, const char* fmt, ...) {
 
 }  // namespace
 
+int nnsemd::num_sms() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+  if (dev < 64) {
+    const int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+  }
+  int count = 0;
+  if (cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || count < 1) {
+    cudaGetLastError();
+    count = 1;
+  }
+  if (dev < 64) cache[dev].store(count, std::memory_order_relaxed);
+  return count;
+}
+
 int nnsemd::ctx_fail(nnsemd_ctx* ctx, int status, const char* fmt, ...) {
   char buf[512];
   va_list ap;
@@ -77,6 +94,15 @@ int cuda_fail(nnsemd_ctx* ctx, cudaError_t e, const char* where) {
   do {                                                        \
     cudaError_t e_ = (call);                                  \
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
+  } while (0)
+
+// The same inside a solve whose first kernels are already queued: the call
+// returns only once its stream has drained (drained() waits for it), so no
+// work of the failed call outlives it.
+#define CKD(call)                                                      \
+  do {                                                                 \
+    cudaError_t e_ = (call);                                           \
+    if (e_ != cudaSuccess) return drained(cuda_fail(ctx, e_, #call));  \
   } while (0)
 
 // Bump allocator over the context workspace (256-byte aligned slices).
@@ -151,8 +177,8 @@ size_t layout_solve(void* base, int64_t m, int64_t n, int d, SolveBufs& B, int p
     T.scale_x = C.take<float>(srows);
     T.scale_y = C.take<float>(qrows);
     T.stats = C.take<unsigned>(8);
-    T.max_chunks = TC_TARGET_CTAS;
-    const int64_t cand = (TC_TARGET_CTAS + qrows / 128) * 128 * 16;  // chunks x padded consumers x 16 candidates
+    T.max_chunks = tc_target_ctas();
+    const int64_t cand = (tc_target_ctas() + qrows / 128) * 128 * 16;  // chunks x padded consumers x 16 candidates
     T.cand_v = C.take<float>(cand);
     T.cand_p = C.take<int>(cand);
     T.fallback = C.take<int>(n);
@@ -229,6 +255,9 @@ int check_opts(nnsemd_ctx* ctx, const nnsemd_options* opt, int d, int& metric, i
     if (opt->protocol != NNSEMD_PROTOCOL_GREEDY && opt->protocol != NNSEMD_PROTOCOL_RANDOM)
       return fail(ctx, NNSEMD_ERR_INVALID_ARG, "unknown protocol %d", opt->protocol);
     if (opt->reserved != 0) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "options.reserved must be 0");
+    if (opt->rerank_k < 0 || opt->rerank_k > NNSEMD_MAX_RERANK_K)
+      return fail(ctx, NNSEMD_ERR_INVALID_ARG, "options.rerank_k = %d: outside 0..%d", opt->rerank_k,
+                  NNSEMD_MAX_RERANK_K);
     if (opt->precision != NNSEMD_FP32) {
       if (!precision) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "reduced precision is served by nnsemd_solve only");
       if (d <= 8) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "reduced precision serves d > 8 (d = %d)", d);
@@ -297,15 +326,15 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
   B.notify_seq = ++ctx->notify_seq;
   launch_initial_pack(B, st);
   L += B.dp > 0 ? 4 : 6;  // two sums, count + scatter (d > 8: two finiteness checks too)
-  CK(cudaGetLastError());
-  int mt = 0, nt = 0;
-  unsigned err0 = 0;
   // a failure after this point returns only once the stream has drained:
   // no work of this call outlives it
   auto drained = [&](int status) {
     cudaStreamSynchronize(st);
     return status;
   };
+  CKD(cudaGetLastError());
+  int mt = 0, nt = 0;
+  unsigned err0 = 0;
   int rc = wait_counts(ctx, st, B.notify_seq, mt, nt, err0);
   if (!rc) rc = map_err_bits(ctx, err0);
   if (rc) return drained(rc);
@@ -325,13 +354,13 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
                       : lowd ? (mt <= FIN_MAX && nt <= FIN_MAX && (int64_t)mt * nt <= FIN_PAIRS)
                              : (mt <= FIN_MAX_HD && nt <= FIN_MAX_HD && (int64_t)mt * nt * B.d <= FIN_HD_WORK);
     if (tail) {
-      if (timed) CK(cudaEventRecord(ctx->ev[2], st));
+      if (timed) CKD(cudaEventRecord(ctx->ev[2], st));
       B.round0 = rounds;
       const int lrc = clcap  ? launch_finish_cluster(B, round_limit - rounds, st)
                       : lowd ? launch_finish(B, round_limit - rounds, st)
                              : launch_finish_hd(B, round_limit - rounds, st);
       if (lrc) return drained(fail(ctx, NNSEMD_ERR_CUDA, "finisher launch"));
-      if (timed) CK(cudaEventRecord(ctx->ev[3], st));
+      if (timed) CKD(cudaEventRecord(ctx->ev[3], st));
       tail_ran = true;
       L += 1;
       break;
@@ -341,9 +370,9 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
     // active lists reset the key of every surviving consumer
     int nrc;
     if (learned) {
-      if (timed) CK(cudaEventRecord(ctx->ev[0], st));
+      if (timed) CKD(cudaEventRecord(ctx->ev[0], st));
       nrc = launch_nns_learned(B, *learned, mt, nt, st);
-      if (timed) CK(cudaEventRecord(ctx->ev[1], st));
+      if (timed) CKD(cudaEventRecord(ctx->ev[1], st));
       L += 6;
     } else if (B.precision != NNSEMD_FP32) {
       // tensor-core candidates + exact re-rank + certificate + FP32 rescan;
@@ -353,9 +382,9 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
       nrc = launch_nns_tc(B, B.tc, mt, nt, B.precision, st);
       L += 5;
     } else {
-      if (timed) CK(cudaEventRecord(ctx->ev[0], st));
+      if (timed) CKD(cudaEventRecord(ctx->ev[0], st));
       nrc = lowd ? launch_nns_lowd(B, mt, nt, st) : launch_nns_f32(B, mt, nt, nullptr, nullptr, st);
-      if (timed) CK(cudaEventRecord(ctx->ev[1], st));
+      if (timed) CKD(cudaEventRecord(ctx->ev[1], st));
       L += 1;
     }
     if (nrc) return drained(fail(ctx, NNSEMD_ERR_UNSUPPORTED, "NNS launch failed for d=%d (%d)", B.d, nrc));
@@ -366,7 +395,7 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
     B.notify_seq = ++ctx->notify_seq;
     launch_big_round(B, mt, nt, rounds, st);
     L += 6;  // group count / alloc / scatter, flow, compaction count / scatter
-    CK(cudaGetLastError());
+    CKD(cudaGetLastError());
     B.cur ^= 1;
     rounds += 1;
     pair_evals += (long long)mt * nt;
@@ -377,8 +406,8 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
     if (rc) return drained(rc);
     if (timed) {
       float ms = 0.f;
-      CK(cudaEventSynchronize(ctx->ev[1]));
-      CK(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
+      CKD(cudaEventSynchronize(ctx->ev[1]));
+      CKD(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
       nns_ms += ms;
     }
     rc = map_err_bits(ctx, err_bits);
@@ -386,9 +415,9 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
   }
   launch_leftover(B, st);
   L += 2;
-  CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(ctx->hstate, B.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  CKD(cudaGetLastError());
+  CKD(cudaMemcpyAsync(ctx->hstate, B.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+  CKD(cudaStreamSynchronize(st));
   rc = map_err_bits(ctx, ctx->hstate->err);
   if (rc) return rc;
   *cost = ctx->hstate->cost;
@@ -396,7 +425,7 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
   ctx->launches += L;
   if (timed && tail_ran) {
     float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]));
+    CKD(cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]));
     tail_ms = ms;
   }
   if (stats) {
@@ -407,6 +436,7 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
     stats->kernel_launches = L;
     stats->certified = (int64_t)ctx->hstate->certified;
     stats->fallbacks = (int64_t)ctx->hstate->fallbacks;
+    stats->near_ties = (int64_t)ctx->hstate->near_ties;
     stats->nns_kernel_ms = nns_ms;
     stats->nns_kernel_launches = nns_launches;
     stats->nns_kernel_pairs = nns_pairs;
@@ -536,6 +566,7 @@ int nnsemd_solve(nnsemd_ctx* ctx, const float* x, const double* a, int64_t m, co
   B.plan_j = plan ? plan->j : nullptr;
   B.plan_f = plan ? plan->f : nullptr;
   B.plan_cap = plan ? plan->capacity : 0;
+  B.tc.rerank_k = opt ? opt->rerank_k : 0;
   int64_t nnz = 0;
   rc = run_solve(ctx, B, a, b, cost_out, &nnz, stats, opt ? opt->flags : 0, P ? &Lb : nullptr);
   if (plan) plan->nnz = rc ? 0 : nnz;
@@ -600,6 +631,7 @@ int nnsemd_solve_host(nnsemd_ctx* ctx, const float* x, const double* a, int64_t 
   B.plan_j = plan ? pj : nullptr;
   B.plan_f = plan ? pf : nullptr;
   B.plan_cap = cap;
+  B.tc.rerank_k = opt ? opt->rerank_k : 0;
   int64_t nnz = 0;
   rc = run_solve(ctx, B, ad, bd, cost_out, &nnz, stats, opt ? opt->flags : 0, P ? &Lb : nullptr);
   if (rc) {
@@ -664,7 +696,8 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
   }
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
-  const int grid = (int)std::min<size_t>(small.size(), 152);
+  const int nsm = num_sms();
+  const int grid = (int)std::min<size_t>(small.size(), (size_t)nsm);
   // tensor-core kernel geometry: capacity class, bytes per packed row, tile
   // rows and pipeline stages (autotuned or default)
   const int cap = small_max <= 512 ? 512 : 2048;
@@ -681,14 +714,14 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
   C.take<int64_t>(num_pairs + 1);
   C.take<int64_t>(num_pairs + 1);
   C.take<int>(small.size() + 1);
-  C.take<unsigned long long>(4);
+  C.take<unsigned long long>(6);
   C.take<long long>(num_pairs);
   C.take<long long>(num_pairs);
   C.take<uint8_t>(tc ? slot * grid : 0);
   // flow records of the d > 8 solvers, one slice per CTA (the tensor-core
   // kernel's grid; the 1,024- and the 256-thread FP32 kernels' grids)
   const long long fl_big = tc ? 2LL * cap : 2LL * FIN_MAX_HD, fl_small = 2LL * HD_SMALL_CAP;
-  const size_t fl_n = d <= 8 || small.empty() ? 0 : (size_t)(152 * fl_big + (tc ? 0 : 152 * 4 * fl_small));
+  const size_t fl_n = d <= 8 || small.empty() ? 0 : (size_t)(nsm * fl_big + (tc ? 0 : nsm * 4 * fl_small));
   C.take<int32_t>(fl_n);
   C.take<int32_t>(fl_n);
   C.take<double>(fl_n);
@@ -706,7 +739,9 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
   int64_t* xo_d = W.take<int64_t>(num_pairs + 1);
   int64_t* yo_d = W.take<int64_t>(num_pairs + 1);
   int* ids_d = W.take<int>(small.size() + 1);
-  unsigned long long* ctr_d = W.take<unsigned long long>(4);  // [0]: queue | err << 32, [1] certified, [2] fallbacks
+  // [0]: queue | err << 32, [1] certified, [2] fallbacks, [3] the 256-thread
+  // kernel's queue, [4] near-ties
+  unsigned long long* ctr_d = W.take<unsigned long long>(6);
   long long* rounds_d = W.take<long long>(num_pairs);
   long long* pe_d = W.take<long long>(num_pairs);
   uint8_t* scratch = W.take<uint8_t>(tc ? slot * grid : 0);
@@ -722,7 +757,7 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
   long long L = 0;
   // the device work of the small pairs: clear the counters, one persistent launch
   auto issue = [&](cudaStream_t s, int nsmall, int g, int tbn, int tns) -> int {
-    if (cudaMemsetAsync(ctr_d, 0, 4 * sizeof(unsigned long long), s) != cudaSuccess) return -1;
+    if (cudaMemsetAsync(ctr_d, 0, 6 * sizeof(unsigned long long), s) != cudaSuccess) return -1;
     if (cudaMemsetAsync(rounds_d, 0, num_pairs * sizeof(long long), s) != cudaSuccess) return -1;
     if (cudaMemsetAsync(pe_d, 0, num_pairs * sizeof(long long), s) != cudaSuccess) return -1;
     BatchArgs A{x_packed, a_packed, xo_d, y_packed, b_packed, yo_d, ids_d, nsmall, d, metric,
@@ -734,8 +769,9 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
       A.fl_f = fl_f;
       A.fl_cap = fl_big;
     }
-    if (tc)  // (grid <= 152 CTAs)
-      return launch_batched_tc(A, precision, cap, kb, tbn, tns, scratch, slot, ctr_d + 1, ctr_d + 2, g, s);
+    if (tc)  // (grid <= one CTA per SM)
+      return launch_batched_tc(A, precision, cap, kb, tbn, tns, scratch, slot, ctr_d + 1, ctr_d + 2, ctr_d + 4,
+                               opt ? opt->rerank_k : 0, g, s);
     if (d <= 8) return launch_batched_lowd(A, g, s);
     int r = 0;
     const int nbig = nsmall - ntiny;
@@ -743,26 +779,26 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
       BatchArgs Ab = A;
       Ab.pair_ids = ids_d + ntiny;
       Ab.num = nbig;
-      r |= launch_batched_hd(Ab, std::min(nbig, 152), s);
+      r |= launch_batched_hd(Ab, std::min(nbig, nsm), s);
     }
     if (ntiny > 0) {
       BatchArgs At = A;
       At.num = ntiny;
       At.queue = q2_d;
       if (fl_n) {  // the slices after the 1,024-thread kernel's
-        At.fl_i = fl_i + 152 * fl_big;
-        At.fl_j = fl_j + 152 * fl_big;
-        At.fl_f = fl_f + 152 * fl_big;
+        At.fl_i = fl_i + nsm * fl_big;
+        At.fl_j = fl_j + nsm * fl_big;
+        At.fl_f = fl_f + nsm * fl_big;
         At.fl_cap = fl_small;
       }
-      r |= launch_batched_hd_small(At, std::min(ntiny, 152 * 4), s);
+      r |= launch_batched_hd_small(At, std::min(ntiny, nsm * 4), s);
     }
     return r;
   };
   if (!small.empty() && tc && (flags & NNSEMD_FLAG_AUTOTUNE) && !ctx->tuned.count(tkey)) {
     // time every feasible (tile rows, stages) on a sample of the batch
-    const int nsample = (int)std::min<size_t>(small.size(), 2 * 152);
-    const int gs = std::min(nsample, 152);
+    const int nsample = (int)std::min<size_t>(small.size(), 2 * (size_t)nsm);
+    const int gs = std::min(nsample, nsm);
     if (!ctx->ev[0])
       for (int k = 0; k < 4; ++k) CK(cudaEventCreate(&ctx->ev[k]));
     float best_ms = 1e30f;
@@ -797,6 +833,7 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
                                           (uintptr_t)metric, (uintptr_t)precision, (uintptr_t)cap, (uintptr_t)bn,
                                           (uintptr_t)nstage, (uintptr_t)ntiny,
                                           (uintptr_t)(opt ? opt->protocol : 0), (uintptr_t)(opt ? opt->seed : 0),
+                                          (uintptr_t)(opt ? opt->rerank_k : 0),
                                           (uintptr_t)(y_off ? 0 : n_shared)};
       BatchGraph* g = nullptr;
       for (auto& e : ctx->graphs)
@@ -827,7 +864,7 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
     L += 1;
   }
   long long extra_rounds = 0, extra_pe = 0;
-  long long extra_cert = 0, extra_fall = 0;
+  long long extra_cert = 0, extra_fall = 0, extra_near = 0;
   for (int p : large) {
     layout_solve((char*)ctx->ws + head, maxm, maxn, d, B, precision);
     B.x = x_packed + x_off[p] * d;
@@ -839,6 +876,7 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
     B.metric = metric;
     B.protocol = opt ? opt->protocol : 0;
     B.seed = opt ? opt->seed : 0;
+    B.tc.rerank_k = opt ? opt->rerank_k : 0;
     double cost = 0;
     int64_t nnz = 0;
     nnsemd_stats s1{};
@@ -849,11 +887,12 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
     extra_pe += s1.pair_evals;
     extra_cert += s1.certified;
     extra_fall += s1.fallbacks;
+    extra_near += s1.near_ties;
     L += s1.kernel_launches;
   }
   ctx->launches += L;
   if (stats) {
-    unsigned long long ctr[4] = {0, 0, 0, 0};
+    unsigned long long ctr[6] = {0, 0, 0, 0, 0, 0};
     std::vector<long long> r(num_pairs), pe(num_pairs);
     CK(cudaMemcpyAsync(ctr, ctr_d, sizeof(ctr), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(r.data(), rounds_d, num_pairs * sizeof(long long), cudaMemcpyDeviceToHost, st));
@@ -869,6 +908,7 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
     stats->pair_evals += extra_pe;
     stats->certified = (int64_t)ctr[1] + extra_cert;
     stats->fallbacks = (int64_t)ctr[2] + extra_fall;
+    stats->near_ties = (int64_t)ctr[4] + extra_near;
     stats->kernel_launches = L;
   }
   return NNSEMD_OK;

@@ -76,6 +76,8 @@ struct BtcArgs {
   int kb, bn, nstage, fmt;
   unsigned long long* certified;
   unsigned long long* fallbacks;
+  unsigned long long* near_ties;
+  int rk;                    // candidates re-ranked per consumer (1 .. BTC_K)
 };
 
 // The NNS policy of the batched tensor-core solver (coordinates in global
@@ -89,7 +91,7 @@ struct GeoTC {
   const float* y;
   int d;
   BtcScratch scr;
-  int kb, bn, nstage, fmt;
+  int kb, bn, nstage, fmt, rk;
   uint32_t tmem_base;
   unsigned* err;
   uint64_t bar_full[8];
@@ -104,7 +106,7 @@ struct GeoTC {
   unsigned prod_a, prod_b, mma_a, mma_b, mma_acc, epi_acc;
   unsigned stat_rx, stat_rx1, stat_sx;  // certificate maxima of this round (float bits)
   int nfb;
-  unsigned long long ncert, nfall;
+  unsigned long long ncert, nfall, nnear;
   int fb[CAP];
   // staging: tensor-core operand tiles or FP32 fallback tiles (never both at
   // once); the launch reserves max(sizeof(tiles), A + stages * B) bytes
@@ -281,7 +283,7 @@ struct GeoTC {
     for (int q = warp; q < nt; q += T / 32) {
       const float* yrow = y + (size_t)S.jidx[q] * d;
       unsigned long long best = ~0ULL;
-      if (lane < BTC_K) {
+      if (lane < rk) {
         const int p = scr.cand_p[(size_t)q * BTC_K + lane];
         if (p >= 0) best = pack_key(key32<METRIC_SQL2>(x + (size_t)S.iidx[p] * d, yrow, d), (unsigned)p);
       }
@@ -297,7 +299,10 @@ struct GeoTC {
         yl1 += __shfl_xor_sync(0xffffffffu, yl1, o);
       }
       if (lane == 0) {
-        const float tau = scr.cand_v[(size_t)q * BTC_K + BTC_K - 1];
+        // tau: the rk-th approximate value; the first candidate is the
+        // approximate best, and an exact best elsewhere is a near-tie
+        const float tau = scr.cand_v[(size_t)q * BTC_K + rk - 1];
+        if (best != ~0ULL && (int)(unsigned)best != scr.cand_p[(size_t)q * BTC_K]) atomicAdd(&nnear, 1ULL);
         const bool cert = best != ~0ULL && certify(fmt, d, scr.nrm_y[q], sqrt(yl2) * (1 + 1e-12), yl1,
                                                     scr.scale_y[q], rx, rx1, sxm, tau,
                                                     __uint_as_float((unsigned)(best >> 32)));
@@ -371,7 +376,8 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_batched_tc(BtcArgs A) {
     mbar_init(&G.bar_a_empty, 1);
     mbar_fence_init();
     G.prod_a = G.prod_b = G.mma_a = G.mma_b = G.mma_acc = G.epi_acc = 0u;
-    G.ncert = G.nfall = 0ULL;
+    G.ncert = G.nfall = G.nnear = 0ULL;
+    G.rk = A.rk;
     G.kb = A.kb;
     G.bn = A.bn;
     G.nstage = A.nstage;
@@ -418,6 +424,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_batched_tc(BtcArgs A) {
   if (tid == 0) {
     atomicAdd(A.certified, G.ncert);
     atomicAdd(A.fallbacks, G.nfall);
+    atomicAdd(A.near_ties, G.nnear);
   }
   tc_fence_before();
   __syncthreads();
@@ -447,9 +454,11 @@ int batched_tc_max_stages(int cap, int kb, int bn, int precision) {
 }
 
 int launch_batched_tc(const BatchArgs& base, int precision, int cap, int kb, int bn, int nstage, uint8_t* scratch,
-                      size_t slot_bytes, unsigned long long* certified, unsigned long long* fallbacks, int grid,
-                      cudaStream_t st) {
-  BtcArgs A{base, scratch, slot_bytes, kb, bn, nstage, fmt_of_precision(precision), certified, fallbacks};
+                      size_t slot_bytes, unsigned long long* certified, unsigned long long* fallbacks,
+                      unsigned long long* near_ties, int rerank_k, int grid, cudaStream_t st) {
+  const int rk = rerank_k >= 1 && rerank_k <= BTC_K ? rerank_k : BTC_K;
+  BtcArgs A{base, scratch, slot_bytes, kb, bn, nstage, fmt_of_precision(precision), certified, fallbacks,
+            near_ties, rk};
   const bool k8 = precision == 3;
   if (cap <= 512) return k8 ? batched_tc_t<true, 512>(A, grid, st) : batched_tc_t<false, 512>(A, grid, st);
   return k8 ? batched_tc_t<true, 2048>(A, grid, st) : batched_tc_t<false, 2048>(A, grid, st);

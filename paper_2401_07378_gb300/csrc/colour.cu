@@ -120,7 +120,7 @@ __global__ void k_recolour(const int* __restrict__ lab, int64_t N, const float* 
   }
 }
 
-int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8)); }
+int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, num_sms() * 8)); }
 
 int read_err(nnsemd_ctx* ctx, unsigned* err_d, cudaStream_t st) {
   unsigned h = 0;

@@ -46,6 +46,7 @@ struct DevState {
   double leftover;               // residual mass after the solve
   unsigned long long certified;  // reduced precision: consumer searches settled by the certificate
   unsigned long long fallbacks;  // reduced precision: consumer searches redone in FP32
+  unsigned long long near_ties;  // reduced precision: exact re-rank overturned the approximate first choice
   unsigned ticket;               // blocks of the current compaction count done (reset by its last block)
 };
 

@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(TG_THREADS)
 
 int launch_nns_f32(const SolveBufs& B, int mt, int ncons, const int* cons, const int* ncons_dev, cudaStream_t st) {
   const int gx = (ncons + TG_M - 1) / TG_M;
-  const int target = 152 * 6;
+  const int target = num_sms() * 6;
   int gy = (target + gx - 1) / gx;
   const int tiles = (mt + TG_N - 1) / TG_N;
   if (gy > tiles) gy = tiles;

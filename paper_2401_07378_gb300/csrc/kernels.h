@@ -12,7 +12,12 @@ namespace nnsemd {
 // packed active list is padded to (with NaN coordinates) so that a tile
 // never reads past its buffer.
 constexpr int K1_TS = 256;
-constexpr int TC_TARGET_CTAS = 152 * 4;  // K2 grid target (consumer tiles x supplier chunks)
+// Streaming multiprocessors of the current device (the device attribute
+// cudaDevAttrMultiProcessorCount, looked up once per device); grids are
+// sized in multiples of it.
+int num_sms();
+// K2 grid target (consumer tiles x supplier chunks): four CTAs per SM.
+inline int tc_target_ctas() { return 4 * num_sms(); }
 constexpr int PAD_POINTS = K1_TS;
 // Largest active set the single-CTA solver keeps in shared memory (d <= 8:
 // with coordinates; d > 8: per-point state only, coordinates stay in L2).
@@ -42,6 +47,7 @@ struct TcBufs {
   int* fallback;               // consumer positions to rescan
   int* nfallback;              // device counter (this round)
   int max_chunks;
+  int rerank_k;                // candidates per chunk re-ranked in FP32 (1..16; other values: 16)
   cudaEvent_t ev0, ev1;        // optional: recorded around the tensor-core kernel
 };
 
@@ -166,8 +172,10 @@ int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int preci
 // side, reduced-precision NNS inside each pair's CTA.
 size_t batched_tc_slot_bytes(int cap, int kb, int bn);
 int batched_tc_max_stages(int cap, int kb, int bn, int precision);
+// rerank_k: candidates re-ranked per consumer (1..8; other values: 8);
+// certified / fallbacks / near_ties: device counters the launch adds to.
 int launch_batched_tc(const BatchArgs& base, int precision, int cap, int kb, int bn, int nstage, uint8_t* scratch,
-                      size_t slot_bytes, unsigned long long* certified, unsigned long long* fallbacks, int grid,
-                      cudaStream_t st);
+                      size_t slot_bytes, unsigned long long* certified, unsigned long long* fallbacks,
+                      unsigned long long* near_ties, int rerank_k, int grid, cudaStream_t st);
 
 }  // namespace nnsemd

@@ -199,7 +199,7 @@ void adam_update(nnsemd_proposal* P, const float* grad, float lr, cudaStream_t s
   P->adam_step += 1;
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.f - powf(b1, (float)P->adam_step), c2 = 1.f - powf(b2, (float)P->adam_step);
-  k_adam<<<152 * 8, 256, 0, st>>>(P->params, P->adam_m, P->adam_v, grad, P->nparams, lr, b1, b2, c1, c2, 1e-8f);
+  k_adam<<<num_sms() * 8, 256, 0, st>>>(P->params, P->adam_m, P->adam_v, grad, P->nparams, lr, b1, b2, c1, c2, 1e-8f);
 }
 
 // --------------------------------------------------------------------------
@@ -242,7 +242,7 @@ int nearest_all(const float* x, int64_t m, const float* y, int64_t n, int d, int
                 unsigned long long* keys, int* out, cudaStream_t st) {
   if (cudaMemsetAsync(keys, 0xff, n * sizeof(unsigned long long), st) != cudaSuccess) return -1;
   const int gx = (int)((n + TG_M - 1) / TG_M);
-  int gy = (152 * 6 + gx - 1) / gx;
+  int gy = (num_sms() * 6 + gx - 1) / gx;
   const int tiles = (int)((m + TG_N - 1) / TG_N);
   if (gy > tiles) gy = tiles;
   const int chunk = ((tiles + gy - 1) / gy) * TG_N;
@@ -250,7 +250,7 @@ int nearest_all(const float* x, int64_t m, const float* y, int64_t n, int d, int
   dim3 grid(gx, gy);
   if (metric == METRIC_L1) k_nearest<true><<<grid, TG_THREADS, 0, st>>>(x, iota_m, (int)m, chunk, y, (int)n, d, keys);
   else k_nearest<false><<<grid, TG_THREADS, 0, st>>>(x, iota_m, (int)m, chunk, y, (int)n, d, keys);
-  k_keys_to_index<<<std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8)), 256, 0, st>>>(keys, n, out);
+  k_keys_to_index<<<std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, num_sms() * 8)), 256, 0, st>>>(keys, n, out);
   return 0;
 }
 
@@ -311,7 +311,7 @@ int kmeans_fit(nnsemd_proposal* P, const float* pts, int64_t N, int iters, uint6
     if (assign_cells(P, pts, N, assign_buf, st)) return -1;
     cudaMemsetAsync(sums, 0, (size_t)K * d * sizeof(float), st);
     cudaMemsetAsync(counts, 0, (size_t)K * sizeof(int), st);
-    k_km_accum<<<152 * 8, 256, 0, st>>>(pts, N, d, assign_buf, sums, counts);
+    k_km_accum<<<num_sms() * 8, 256, 0, st>>>(pts, N, d, assign_buf, sums, counts);
     k_km_divide<<<(K * d + 255) / 256, 256, 0, st>>>(P->centroids, sums, counts, K, d);
   }
   (void)g_dummy;
@@ -325,7 +325,7 @@ int assign_cells(const nnsemd_proposal* P, const float* pts, int64_t N, int* out
   unsigned long long* keys = nullptr;
   if (cudaMallocAsync(&iota, big * sizeof(int), st) != cudaSuccess) return -1;
   if (cudaMallocAsync(&keys, N * sizeof(unsigned long long), st) != cudaSuccess) return -1;
-  k_iota<<<152 * 4, 256, 0, st>>>(iota, big);
+  k_iota<<<num_sms() * 4, 256, 0, st>>>(iota, big);
   const int rc = nearest_all(P->centroids, P->cells, pts, N, P->d, METRIC_SQL2, iota, keys, out, st);
   cudaFreeAsync(iota, st);
   cudaFreeAsync(keys, st);
@@ -500,7 +500,7 @@ int learned_prepare(const LearnedBufs& L, const float* x, int64_t m, const float
   const int K = P->cells, h = P->hidden;
   if (assign_cells(P, x, m, L.cell_of_x, st)) return -1;
   cudaMemsetAsync(L.radius, 0, K * sizeof(float), st);
-  k_cell_radius<<<152 * 4, 256, 0, st>>>(x, m, d, L.cell_of_x, P->centroids, reinterpret_cast<unsigned*>(L.radius));
+  k_cell_radius<<<num_sms() * 4, 256, 0, st>>>(x, m, d, L.cell_of_x, P->centroids, reinterpret_cast<unsigned*>(L.radius));
   for (int64_t r0 = 0; r0 < n; r0 += L.chunk) {
     const int rows = (int)std::min<int64_t>(L.chunk, n - r0);
     const float* yc = y + (size_t)r0 * d;
@@ -509,14 +509,14 @@ int learned_prepare(const LearnedBufs& L, const float* x, int64_t m, const float
     float* H1 = L.tmp;               // rows x h
     float* H2 = L.tmp + (size_t)L.chunk * h;
     float* Z = L.tmp2;               // rows x K
-    k_standardise<<<152 * 4, 256, 0, st>>>(yc, rows, d, P->in_mean, P->in_scale, Xs);
+    k_standardise<<<num_sms() * 4, 256, 0, st>>>(yc, rows, d, P->in_mean, P->in_scale, Xs);
     mlp_forward(P, Xs, rows, H1, H2, Z, st);
     k_select_rows<true><<<rows, 256, K * sizeof(unsigned), st>>>(Z, rows, K, L.prop_cells + r0 * PROP_LIST, nullptr,
                                                                  PROP_LIST);
     // bounds: the cells with the smallest lower bound
     dim3 g2((K + 63) / 64, (rows + 63) / 64);
     k_centroid_d2<<<g2, 256, 0, st>>>(yc, rows, P->centroids, K, d, Z);
-    k_cell_lower_bound<<<152 * 8, 256, 0, st>>>(Z, rows, K, d, reinterpret_cast<const unsigned*>(L.radius));
+    k_cell_lower_bound<<<num_sms() * 8, 256, 0, st>>>(Z, rows, K, d, reinterpret_cast<const unsigned*>(L.radius));
     k_select_rows<false><<<rows, 256, K * sizeof(unsigned), st>>>(Z, rows, K, L.bound_cells + r0 * PROP_LIST,
                                                                   L.bound_vals + r0 * PROP_LIST, PROP_LIST);
   }

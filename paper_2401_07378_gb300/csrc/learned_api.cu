@@ -159,7 +159,7 @@ int nnsemd_proposal_fit(nnsemd_ctx* ctx, nnsemd_proposal* P, const float* pts, i
     return ctx_fail(ctx, NNSEMD_ERR_CUDA, "k-means failed");
   // input standardisation of the network from the same points
   PCK(cudaMemsetAsync(mom, 0, 2 * P->d * sizeof(double), st));
-  k_moments<<<152 * 4, 256, 0, st>>>(pts, N, P->d, mom, mom + P->d);
+  k_moments<<<num_sms() * 4, 256, 0, st>>>(pts, N, P->d, mom, mom + P->d);
   std::vector<double> hm(2 * P->d);
   PCK(cudaMemcpyAsync(hm.data(), mom, 2 * P->d * sizeof(double), cudaMemcpyDeviceToHost, st));
   PCK(cudaStreamSynchronize(st));
@@ -199,7 +199,7 @@ int nnsemd_proposal_loss_grad(nnsemd_ctx* ctx, const nnsemd_proposal* P, const f
   std::vector<int> iota(n);
   for (int i = 0; i < n; ++i) iota[i] = i;
   PCK(cudaMemcpyAsync(rows, iota.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
-  k_gather_std<<<152 * 4, 256, 0, st>>>(y, rows, n, d, P->in_mean, P->in_scale, Xs);
+  k_gather_std<<<num_sms() * 4, 256, 0, st>>>(y, rows, n, d, P->in_mean, P->in_scale, Xs);
   PCK(cudaMemsetAsync(loss, 0, sizeof(double), st));
   mlp_loss_grad(P, Xs, labels, n, H1, H2, Z, d1, d2, grad_out, loss, st);
   double hl = 0;
@@ -246,7 +246,7 @@ int nnsemd_proposal_train(nnsemd_ctx* ctx, nnsemd_proposal* P, const float* y, c
     PCK(cudaMemsetAsync(loss, 0, sizeof(double), st));
     int nb = 0;
     for (int64_t b0 = 0; b0 + batch <= N; b0 += batch, ++nb) {
-      k_gather_std<<<152 * 4, 256, 0, st>>>(y, order + b0, batch, d, P->in_mean, P->in_scale, Xs);
+      k_gather_std<<<num_sms() * 4, 256, 0, st>>>(y, order + b0, batch, d, P->in_mean, P->in_scale, Xs);
       k_gather_int<<<(batch + 255) / 256, 256, 0, st>>>(labels, order + b0, batch, blab);
       mlp_loss_grad(P, Xs, blab, batch, H1, H2, Z, d1, d2, grad, loss, st);
       adam_update(P, grad, lr, st);

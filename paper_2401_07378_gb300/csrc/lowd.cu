@@ -215,6 +215,7 @@ struct K1Shape {
 
 static K1Shape k1_shape(int D, int mt, int nt) {
   const int PB = k1_p(D);
+  const int nsm = num_sms();
   constexpr double kWaveNs = 2000.0;
   constexpr double kAloneFactor = 1.67;
   K1Shape best{PB, 64, 1, 1};
@@ -224,7 +225,7 @@ static K1Shape k1_shape(int D, int mt, int nt) {
     const int P = Ps[k];
     const int per_sm = k1_min_blocks(D, P);
     const double pair_ns = (P == 2 ? 10.2 : 7.9) * (D + 1) / 4.0;  // measured at d = 3
-    const long long resident = 152LL * per_sm;
+    const long long resident = (long long)nsm * per_sm;
     const int gx = (nt + K1_THREADS * P - 1) / (K1_THREADS * P);
     const int max_gy = (mt + 63) / 64;
     int last_chunk = -1;
@@ -241,7 +242,7 @@ static K1Shape k1_shape(int D, int mt, int nt) {
       // a CTA alone on its SM leaves the FP32 pipe partly idle: it runs at
       // about 60 % of two co-resident CTAs' combined rate (measured on the
       // colour-transfer rounds)
-      const long long k = (rem + 151) / 152;
+      const long long k = (rem + nsm - 1) / nsm;
       if (rem) t += kWaveNs + per_cta_ns * (k > 1 ? (double)k : kAloneFactor);
       if (t < best_t) {
         best_t = t;
@@ -713,24 +714,41 @@ __global__ void __launch_bounds__(FIN_THREADS, 1)
 template <int D, int DP, bool L1>
 static cudaError_t small_noalloc_t(const float* x, const double* a, int m, const float* y, const double* b, int n,
                                    int metric, double* cost_out, NoAllocScratch* scr, cudaStream_t st) {
-  const size_t smem = sizeof(LowdSmem<D, DP, L1>);
-  cudaError_t e =
-      cudaFuncSetAttribute(k_small_noalloc<D, DP, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_small_noalloc<D, DP, L1><<<1, FIN_THREADS, smem, st>>>(x, a, m, y, b, n, D, metric, cost_out, scr);
+  k_small_noalloc<D, DP, L1><<<1, FIN_THREADS, sizeof(LowdSmem<D, DP, L1>), st>>>(x, a, m, y, b, n, D, metric,
+                                                                                 cost_out, scr);
   return cudaGetLastError();
 }
-// Device address of the scratch array, looked up once per device with that
-// device current (in host code the array's name is only a stand-in).
+
+template <int D, int DP>
+static cudaError_t noalloc_allow_smem() {
+  cudaError_t e = cudaFuncSetAttribute(k_small_noalloc<D, DP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(LowdSmem<D, DP, false>));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_small_noalloc<D, DP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(LowdSmem<D, DP, true>));
+  return e;
+}
+
+// One-time set-up per device, with that device current: the device address
+// of the scratch array (in host code the array's name is only a stand-in)
+// and the shared-memory limit of every instantiation of the kernel.
 static std::mutex g_noalloc_mu;
 static void* g_noalloc_addr[256];
 
-static cudaError_t noalloc_scratch_address(int device, NoAllocScratch** out) {
+static cudaError_t noalloc_setup(int device, NoAllocScratch** out) {
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (device < 0 || device >= 256) return cudaErrorInvalidDevice;
   if (!g_noalloc_addr[device]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e == cudaSuccess) e = noalloc_allow_smem<1, 2>();
+    if (e == cudaSuccess) e = noalloc_allow_smem<2, 2>();
+    if (e == cudaSuccess) e = noalloc_allow_smem<3, 4>();
+    if (e == cudaSuccess) e = noalloc_allow_smem<4, 4>();
+    if (e == cudaSuccess) e = noalloc_allow_smem<5, 8>();
+    if (e == cudaSuccess) e = noalloc_allow_smem<6, 8>();
+    if (e == cudaSuccess) e = noalloc_allow_smem<7, 8>();
+    if (e == cudaSuccess) e = noalloc_allow_smem<8, 8>();
     if (e != cudaSuccess) return e;
     g_noalloc_addr[device] = p;
   }
@@ -751,7 +769,7 @@ extern "C" int nnsemd_solve_small_noalloc(const float* x, const double* a, int64
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess) return NNSEMD_ERR_CUDA;
   NoAllocScratch* scr = nullptr;
-  if (noalloc_scratch_address(device, &scr) != cudaSuccess) return NNSEMD_ERR_CUDA;
+  if (noalloc_setup(device, &scr) != cudaSuccess) return NNSEMD_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)stream;
   const bool l1 = metric == METRIC_L1;
   const int mi = (int)m, ni = (int)n;

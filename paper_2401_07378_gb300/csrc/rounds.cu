@@ -180,7 +180,7 @@ __global__ void k_normalise2(const double* __restrict__ w0, int64_t n0, const un
 
 static int xs_grid(int64_t n) {
   int64_t g = (n + 255) / 256;
-  if (g > 152 * 4) g = 152 * 4;
+  if (g > num_sms() * 4) g = num_sms() * 4;
   return (int)(g < 1 ? 1 : g);
 }
 
@@ -200,7 +200,7 @@ void launch_leftover(const SolveBufs& B, cudaStream_t st) {
   unsigned long long* cacc = B.xs_acc + 2 * XS_LIMBS;
   FinalArgs F{B.s,    B.m,    B.c,    B.n,      B.fl_i,   B.fl_j,   B.fl_f,        &B.st->nnz, B.x, B.y,
               B.d,    B.metric, B.plan_i, B.plan_j, B.plan_f, (long long)B.plan_cap, acc, cacc, &B.st->err};
-  k_final_sums<<<152 * 2, XS_THREADS, 0, st>>>(F);
+  k_final_sums<<<num_sms() * 2, XS_THREADS, 0, st>>>(F);
   k_xs_round2<<<1, 64, 0, st>>>(acc, &B.st->leftover, cacc, &B.st->cost);
 }
 
@@ -409,7 +409,7 @@ __global__ void k_check_finite(const float* __restrict__ v, int64_t count, unsig
 
 void launch_check_finite(const float* v, int64_t count, unsigned* err, cudaStream_t st) {
   int64_t g = (count + 1023) / 1024;
-  if (g > 152 * 8) g = 152 * 8;
+  if (g > num_sms() * 8) g = num_sms() * 8;
   k_check_finite<<<(int)(g < 1 ? 1 : g), 256, 0, st>>>(v, count, err);
 }
 
@@ -782,8 +782,9 @@ int launch_big_round(SolveBufs& B, int mt, int nt, long long round, cudaStream_t
   // the thread-per-group pass needs nt / 32
   int warps = (nt + 8) / 9;
   int blocks = (warps + 7) / 8;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  k_flow<<<blocks + 152, BIG_THREADS, 0, st>>>(F, blocks);
+  const int nsm = num_sms();
+  if (blocks > nsm * 16) blocks = nsm * 16;
+  k_flow<<<blocks + nsm, BIG_THREADS, 0, st>>>(F, blocks);
   // weights update: compact into the other buffer
   CompactArgs A{};
   const bool packed = B.dp > 0;

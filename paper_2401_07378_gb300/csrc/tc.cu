@@ -320,25 +320,38 @@ struct RerankArgs {
   int* nfallback;
   unsigned long long* ncertified;
   unsigned long long* nfallback_total;
+  unsigned long long* nnear;  // consumers whose exact best differs from the approximate best
   const int* sel;       // packed row -> consumer position (nullable: identity)
   const int* nq_dev;    // rows in use (nullable: nt)
+  int rk;               // candidates of each chunk re-ranked (1 .. TC_K)
 };
 
-// One warp per packed consumer row.
+// One warp per packed consumer row.  The first rk candidates of every chunk
+// are re-ranked; tau is the smallest rk-th approximate value over the chunks
+// (every supplier outside them lies at or above it).  A consumer whose exact
+// best differs from the candidate the approximate values ranked first (over
+// all chunks, lowest position on ties) is counted as a near-tie of the
+// operand precision.
 __global__ void k_rerank_certify(RerankArgs R) {
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= (R.nq_dev ? min(*R.nq_dev, R.nt) : R.nt)) return;
   const int q = R.sel ? R.sel[r] : r;
   const float* yrow = R.y + (size_t)R.ja[q] * R.d;
-  const int ncand = R.chunks * TC_K;
-  unsigned long long best = ~0ULL;
-  float tau = CUDART_INF_F;  // smallest chunk threshold (K-th value of each chunk)
+  const int rk = R.rk;
+  const int ncand = R.chunks * rk;
+  unsigned long long best = ~0ULL, abest = ~0ULL;
+  float tau = CUDART_INF_F;  // smallest chunk threshold (rk-th value of each chunk)
   for (int c = lane; c < ncand; c += 32) {
-    const size_t o = ((size_t)(c / TC_K) * R.nt_pad + r) * TC_K + (c % TC_K);
+    const int chunk = c / rk, k = c % rk;
+    const size_t o = ((size_t)chunk * R.nt_pad + r) * TC_K + k;
     const int p = R.cand_p[o];
-    if ((c % TC_K) == TC_K - 1) tau = fminf(tau, R.cand_v[o]);
+    if (k == rk - 1) tau = fminf(tau, R.cand_v[o]);
     if (p < 0) continue;
+    if (k == 0) {
+      const unsigned long long ak = ((unsigned long long)ordered_bits(R.cand_v[o]) << 32) | (unsigned)p;
+      abest = ak < abest ? ak : abest;
+    }
     // squared-Euclidean FP32 key (the contraction has no L1 form)
     const float acc = key32<METRIC_SQL2>(R.x + (size_t)R.ia[p] * R.d, yrow, R.d);
     const unsigned long long key = pack_key(acc, (unsigned)p);
@@ -353,11 +366,14 @@ __global__ void k_rerank_certify(RerankArgs R) {
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
     best = ob < best ? ob : best;
+    const unsigned long long oa = __shfl_xor_sync(0xffffffffu, abest, o);
+    abest = oa < abest ? oa : abest;
     tau = fminf(tau, __shfl_xor_sync(0xffffffffu, tau, o));
     yl2 += __shfl_xor_sync(0xffffffffu, yl2, o);
     yl1 += __shfl_xor_sync(0xffffffffu, yl1, o);
   }
   if (lane != 0) return;
+  if (best != ~0ULL && (unsigned)best != (unsigned)abest) atomicAdd(R.nnear, 1ULL);
   yl2 = sqrt(yl2) * (1 + 1e-12);
   const bool certified =
       best != ~0ULL && certify(R.fmt, R.d, R.nrm_y[r], yl2, yl1, R.scale_y[r], __uint_as_float(R.stats_x[0]),
@@ -404,18 +420,18 @@ int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int preci
   if (cudaMemsetAsync(T.stats, 0, 8 * sizeof(unsigned), st) != cudaSuccess) return -1;
   {
     const int64_t work = (int64_t)qtiles * TC_BM;
-    int g = (int)std::min<int64_t>((work + 255) / 256, 152 * 16);
+    int g = (int)std::min<int64_t>((work + 255) / 256, num_sms() * 16);
     k_pack_tc<<<g, 256, 0, st>>>(B.y, B.ja[B.cur], sel, nsel_dev, nt, qtiles * TC_BM, B.d, kb, fmt, TC_BM, T.A,
                                  T.nrm_y, nullptr, T.scale_y, T.stats + 4);
   }
   {
     const int64_t work = (int64_t)stiles * bn;
-    int g = (int)std::min<int64_t>((work + 255) / 256, 152 * 16);
+    int g = (int)std::min<int64_t>((work + 255) / 256, num_sms() * 16);
     k_pack_tc<<<g, 256, 0, st>>>(B.x, B.ia[B.cur], nullptr, nullptr, mt, stiles * bn, B.d, kb, fmt, bn, T.B,
                                  T.nrm_x, T.nrm_sx, T.scale_x, T.stats);
   }
   // chunks of supplier tiles so that the grid covers the GPU several times
-  int chunks = (TC_TARGET_CTAS + qtiles - 1) / qtiles;
+  int chunks = (tc_target_ctas() + qtiles - 1) / qtiles;
   if (chunks > stiles) chunks = stiles;
   if (chunks > T.max_chunks) chunks = T.max_chunks;
   const int per = (stiles + chunks - 1) / chunks;
@@ -442,9 +458,11 @@ int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int preci
   if (T.ev1) cudaEventRecord(T.ev1, st);
   // exact re-rank and certificate
   if (cudaMemsetAsync(T.nfallback, 0, sizeof(int), st) != cudaSuccess) return -1;
+  const int rk = T.rerank_k >= 1 && T.rerank_k <= TC_K ? T.rerank_k : TC_K;
   RerankArgs R{B.x,      B.y,        B.ia[B.cur], B.ja[B.cur], B.d,       nt,          nt_pad,
                chunks,   fmt,        T.cand_v,    T.cand_p,    T.nrm_y,   T.scale_y,   T.stats,
-               B.nnkey,  T.fallback, T.nfallback, &B.st->certified, &B.st->fallbacks, sel, nsel_dev};
+               B.nnkey,  T.fallback, T.nfallback, &B.st->certified, &B.st->fallbacks, &B.st->near_ties,
+               sel,      nsel_dev,   rk};
   k_rerank_certify<<<(nt + 7) / 8, 256, 0, st>>>(R);
   // FP32 scan of the consumers that were not certified
   launch_nns_f32(B, mt, nt, T.fallback, T.nfallback, st);

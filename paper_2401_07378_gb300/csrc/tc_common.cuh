@@ -156,6 +156,14 @@ NNS_DEV void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 // copies (async proxy) issued after a barrier.
 NNS_DEV void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
+// Unsigned image of a float that orders like the float itself (negative
+// values included): flip every bit of a negative value, the sign bit of a
+// non-negative one.
+NNS_DEV unsigned ordered_bits(float v) {
+  const unsigned b = __float_as_uint(v);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
 // Insert (v, p) into an ascending top-K list kept in registers; equal values
 // keep their arrival order.
 template <int K>

@@ -47,19 +47,39 @@ def test_two_rank_reductions_over_gloo(tmp_path):
 
 def test_reference_arm_line(monkeypatch, capsys):
     import bench
-    monkeypatch.setattr(bench, "ORACLE_SAMPLE_N", 1024)
     for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
         monkeypatch.delenv(k, raising=False)
-    bench.main(["--impl", "reference", "--steps", "2", "--warmup", "0"])
+    bench.main(["--impl", "reference", "--workload", "single", "--steps", "2", "--warmup", "0"])
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "pairs/s" and line["value"] > 0
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == (os.cpu_count() or 1)
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    args = bench.argparse.Namespace(workload="single", precision=None, protocol="greedy")
+    assert line["config"] == bench.bench_config(args, 1)
+
+
+def test_accuracy_flags_a_planted_error():
+    """The bench's accuracy check against oracle costs: exact costs pass, a
+    relative error above the tolerance fails (the mistake is planted in the
+    GPU side's numbers, on the CPU)."""
+    import bench
+    from paper_2401_07378_gb300 import workloads as wl
+    inp = wl.doc_knn(num_docs=6, seed=2, vocab_size=2000)
+    import oracle
+    rs = [oracle.solve_pair(inp.pair(k), "l2") for k in range(6)]
+    orc = {"costs": {k: r.cost for k, r in enumerate(rs)}, "near_ties": 0}
+    good = {k: r.cost for k, r in enumerate(rs)}
+    acc = bench.accuracy("docs", inp, good, orc, 1e-3, None)
+    assert acc["ok"] and acc["pairs_checked"] == 6 and acc["rel_err_vs_fp32_decision_oracle"] == 0.0
+    bad = dict(good)
+    bad[4] *= 1 + 2e-3
+    acc = bench.accuracy("docs", inp, bad, orc, 1e-3, None)
+    assert acc["ok"] is False and acc["rel_err_vs_fp32_decision_oracle"] > 1e-3
 
 
 def test_reference_arm_non_zero_rank_prints_nothing(monkeypatch, capsys):
     import bench
     monkeypatch.setenv("RANK", "1")
     monkeypatch.setenv("WORLD_SIZE", "2")
-    bench.main(["--impl", "reference", "--steps", "1", "--warmup", "0"])
+    bench.main(["--impl", "reference", "--workload", "single", "--steps", "1", "--warmup", "0"])
     assert capsys.readouterr().out.strip() == ""
