@@ -208,7 +208,10 @@ NNS_DEV void topk_insert(float (&tv)[K], int (&tp)[K], float v, int p) {
 // (ny + tau - E)(1 - gamma).
 // --------------------------------------------------------------------------
 
-NNS_DEV double quant_unit(int fmt) { return fmt == FMT_BF16 ? 0x1p-8 : (fmt == FMT_F16 ? 0x1p-11 : 0x1p-4); }
+// (host and device: the CPU tests evaluate the certificate's arithmetic too)
+__host__ __device__ inline double quant_unit(int fmt) {
+  return fmt == FMT_BF16 ? 0x1p-8 : (fmt == FMT_F16 ? 0x1p-11 : 0x1p-4);
+}
 
 // c_j of the epilogue, from the consumer's FP32 squared norm (rounded up).
 NNS_DEV float quant_coeff(int fmt, float ny) {
@@ -220,9 +223,12 @@ NNS_DEV float quant_coeff(int fmt, float ny) {
 // below 2e-5 for d <= 300 and far below 1e-4 for any d the kernels serve).
 NNS_DEV float norm_up(float l2sq) { return sqrtf(l2sq) * (1.f + 1e-4f); }
 
-NNS_DEV bool certify(int fmt, int d, double ny, double yl2, double yl1, double sy, double rx, double rx1, double sxm,
-                     float tau, float best_key) {
-  if (!(tau < CUDART_INF_F)) return true;  // every supplier of every chunk was a candidate
+// The bound a best exact FP32 key must stay strictly below to be certified:
+// (ny + tau - E)(1 - gamma)(1 - 2^-30) when positive (the last factor covers
+// the rounding of this double-precision evaluation), else the non-positive
+// ny + tau - E itself, which no key (>= 0) is below.
+__host__ __device__ inline double certify_floor(int fmt, int d, double ny, double yl2, double yl1, double sy,
+                                                double rx, double rx1, double sxm, float tau) {
   const double u32 = 0x1p-24;
   const double uq = quant_unit(fmt);
   const double gam = d * u32 / (1.0 - d * u32);
@@ -235,8 +241,14 @@ NNS_DEV bool certify(int fmt, int d, double ny, double yl2, double yl1, double s
   const double c = 2.0 * (2.0 * uq + uq * uq) * yl2 * (1.0 + 1e-5);
   const double E = gam * (ny + rx * rx) + 2.0 * (dot_eta + dot_acc) +
                    2.0 * u32 * (rx * rx + 2.0 * xt * yt + c * rx) + 1e-30;
-  const double floor_true = (ny + (double)tau - E) * (1.0 - gam) * (1.0 - 0x1p-30);
-  return (double)best_key < floor_true;
+  const double base = ny + (double)tau - E;  // <= 0: no key is certified (keys are >= 0)
+  return base > 0.0 ? base * (1.0 - gam) * (1.0 - 0x1p-30) : base;
+}
+
+__host__ __device__ inline bool certify(int fmt, int d, double ny, double yl2, double yl1, double sy, double rx,
+                                        double rx1, double sxm, float tau, float best_key) {
+  if (!(tau <= 3.402823466e38f)) return true;  // tau = +inf: every supplier of every chunk was a candidate
+  return (double)best_key < certify_floor(fmt, d, ny, yl2, yl1, sy, rx, rx1, sxm, tau);
 }
 
 }  // namespace nnsemd
