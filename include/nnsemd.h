@@ -74,7 +74,12 @@ typedef enum {
   NNSEMD_FP32 = 0,  /* direct-difference FP32 distances on CUDA cores (d <= 8) or tiles (d > 8) */
   NNSEMD_BF16 = 1,  /* tcgen05 BF16 contraction proposes candidates, FP32 re-rank decides */
   NNSEMD_FP16 = 2,  /* the same with FP16 operands */
-  NNSEMD_FP8 = 3    /* the same with E4M3 operands and a per-row scale */
+  NNSEMD_FP8 = 3,   /* the same with E4M3 operands and a per-row scale */
+  NNSEMD_BF16X3 = 4 /* BF16 split: each coordinate as a high part h = bf16(v) and a low part
+                       l = bf16(v - h); one BF16 contraction of length 3d gives
+                       <h(x),h(y)> + <l(x),h(y)> + <h(x),l(y)>, within about 3 * 2^-16 |x||y| of
+                       <x,y> (a single BF16 copy: about 2^-7 |x||y|), so far more candidates are
+                       certified; three times the tensor work; served for d up to 128 */
 } nnsemd_precision;
 
 typedef struct nnsemd_ctx nnsemd_ctx;

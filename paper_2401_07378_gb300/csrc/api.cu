@@ -40,6 +40,7 @@ namespace {
 
 constexpr int64_t FIN_PAIRS = 1LL << 19;     // d <= 8 tail threshold on m_t * n_t
 constexpr int64_t FIN_HD_WORK = 1LL << 23;   // d > 8 tail threshold on m_t * n_t * d
+constexpr double KC_BUDGET_BYTES = 8.0e9;    // largest workspace of the batched distance caches
 thread_local std::string g_create_err;
 
 int fail(nnsemd_ctx* ctx, int status, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
@@ -250,7 +251,7 @@ int check_opts(nnsemd_ctx* ctx, const nnsemd_options* opt, int d, int& metric, i
     metric = opt->metric;
     if (opt->flags & ~(NNSEMD_FLAG_TIME_KERNELS | NNSEMD_FLAG_AUTOTUNE | NNSEMD_FLAG_GRAPH))
       return fail(ctx, NNSEMD_ERR_INVALID_ARG, "unknown options.flags bits");
-    if (opt->precision < NNSEMD_FP32 || opt->precision > NNSEMD_FP8)
+    if (opt->precision < NNSEMD_FP32 || opt->precision > NNSEMD_BF16X3)
       return fail(ctx, NNSEMD_ERR_INVALID_ARG, "unknown precision %d", opt->precision);
     if (opt->protocol != NNSEMD_PROTOCOL_GREEDY && opt->protocol != NNSEMD_PROTOCOL_RANDOM)
       return fail(ctx, NNSEMD_ERR_INVALID_ARG, "unknown protocol %d", opt->protocol);
@@ -262,6 +263,9 @@ int check_opts(nnsemd_ctx* ctx, const nnsemd_options* opt, int d, int& metric, i
       if (!precision) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "reduced precision is served by nnsemd_solve only");
       if (d <= 8) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "reduced precision serves d > 8 (d = %d)", d);
       if (opt->metric == NNSEMD_L1) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "the L1 distance has no contraction form");
+      if (!tc_supported(d, opt->precision))
+        return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "d = %d is too large for precision %d's operand tiles", d,
+                    opt->precision);
       *precision = opt->precision;
     }
   }
@@ -675,14 +679,17 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
   auto y_begin = [&](int p) -> int64_t { return y_off ? y_off[p] : 0; };
   auto y_len = [&](int p) -> int64_t { return y_off ? y_off[p + 1] - y_off[p] : n_shared; };
   std::vector<int> small, large;
-  int64_t small_max = 0;
+  int64_t small_max = 0, small_mn = 0;
   for (int p = 0; p < num_pairs; ++p) {
     const int64_t m = x_off[p + 1] - x_off[p], n = y_len(p);
     if (m < 1 || n < 1) return fail(ctx, NNSEMD_ERR_INVALID_ARG, "pair %d has an empty side", p);
     const int cap = d <= 8 ? FIN_MAX : FIN_MAX_HD;
     const bool fits = m <= cap && n <= cap;
     (fits ? small : large).push_back(p);
-    if (fits) small_max = std::max(small_max, std::max(m, n));
+    if (fits) {
+      small_max = std::max(small_max, std::max(m, n));
+      small_mn = std::max(small_mn, m * n);
+    }
   }
   // FP32, d > 8: pairs of at most HD_SMALL_CAP points per side go to the
   // 256-thread kernel (several pairs per SM); they come first in the list
@@ -706,8 +713,18 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
   int nstage = tc ? batched_tc_max_stages(cap, kb, bn, precision) : 0;
   if (tc && !small.empty() && nstage < 1) return fail(ctx, NNSEMD_ERR_UNSUPPORTED, "d = %d too large for the batched tensor-core kernel", d);
   const auto tkey = std::make_tuple(d, precision, cap);
-  if (tc && ctx->tuned.count(tkey)) std::tie(bn, nstage) = ctx->tuned[tkey];
-  const size_t slot = tc ? std::max(batched_tc_slot_bytes(cap, kb, 64), batched_tc_slot_bytes(cap, kb, 128)) : 0;
+  int kc_use = 1;
+  if (tc && ctx->tuned.count(tkey)) std::tie(bn, nstage, kc_use) = ctx->tuned[tkey];
+  // the tensor-core kernel's distance cache: every pair's first round fills
+  // it and later rounds read it, when all the batch's cache slots fit the
+  // budget (else the kernel runs the tensor cores in every round); the
+  // autotuner may also turn it off
+  long long kc_cap = tc ? (long long)small_mn : 0;
+  auto slot_of = [&](long long kc) {
+    return std::max(batched_tc_slot_bytes(cap, kb, 64, kc), batched_tc_slot_bytes(cap, kb, 128, kc));
+  };
+  if (tc && (double)slot_of(kc_cap) * grid > KC_BUDGET_BYTES) kc_cap = 0;
+  const size_t slot = tc ? slot_of(kc_cap) : 0;
   // workspace: offsets, pair list, queue/error/counters, per-pair counters,
   // tensor-core scratch slots, then the buffers of the large pairs
   Carve C(nullptr);
@@ -756,7 +773,7 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
     CK(cudaMemcpyAsync(ids_d, small.data(), small.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   long long L = 0;
   // the device work of the small pairs: clear the counters, one persistent launch
-  auto issue = [&](cudaStream_t s, int nsmall, int g, int tbn, int tns) -> int {
+  auto issue = [&](cudaStream_t s, int nsmall, int g, int tbn, int tns, long long tkc) -> int {
     if (cudaMemsetAsync(ctr_d, 0, 6 * sizeof(unsigned long long), s) != cudaSuccess) return -1;
     if (cudaMemsetAsync(rounds_d, 0, num_pairs * sizeof(long long), s) != cudaSuccess) return -1;
     if (cudaMemsetAsync(pe_d, 0, num_pairs * sizeof(long long), s) != cudaSuccess) return -1;
@@ -771,7 +788,7 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
     }
     if (tc)  // (grid <= one CTA per SM)
       return launch_batched_tc(A, precision, cap, kb, tbn, tns, scratch, slot, ctr_d + 1, ctr_d + 2, ctr_d + 4,
-                               opt ? opt->rerank_k : 0, g, s);
+                               opt ? opt->rerank_k : 0, tkc, g, s);
     if (d <= 8) return launch_batched_lowd(A, g, s);
     int r = 0;
     const int nbig = nsmall - ntiny;
@@ -796,34 +813,38 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
     return r;
   };
   if (!small.empty() && tc && (flags & NNSEMD_FLAG_AUTOTUNE) && !ctx->tuned.count(tkey)) {
-    // time every feasible (tile rows, stages) on a sample of the batch
+    // time every feasible (tile rows, stages, cache on / off) on a sample of the batch
     const int nsample = (int)std::min<size_t>(small.size(), 2 * (size_t)nsm);
     const int gs = std::min(nsample, nsm);
     if (!ctx->ev[0])
       for (int k = 0; k < 4; ++k) CK(cudaEventCreate(&ctx->ev[k]));
     float best_ms = 1e30f;
-    std::pair<int, int> best{bn, nstage};
-    for (int tbn : {64, 128}) {
-      if (tbn == 128 && kb > 384) continue;
-      const int maxs = batched_tc_max_stages(cap, kb, tbn, precision);
-      for (int tns = 1; tns <= maxs; ++tns) {
-        if (issue(st, nsample, gs, tbn, tns)) return fail(ctx, NNSEMD_ERR_CUDA, "autotune launch");
-        CK(cudaEventRecord(ctx->ev[0], st));
-        if (issue(st, nsample, gs, tbn, tns)) return fail(ctx, NNSEMD_ERR_CUDA, "autotune launch");
-        CK(cudaEventRecord(ctx->ev[1], st));
-        CK(cudaEventSynchronize(ctx->ev[1]));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
-        if (ms < best_ms) {
-          best_ms = ms;
-          best = {tbn, tns};
+    std::tuple<int, int, int> best{bn, nstage, kc_use};
+    for (int tkc = kc_cap ? 1 : 0; tkc >= 0; --tkc)
+      for (int tbn : {64, 128}) {
+        if (tbn == 128 && kb > 384) continue;
+        const int maxs = batched_tc_max_stages(cap, kb, tbn, precision);
+        for (int tns = 1; tns <= maxs; ++tns) {
+          if (issue(st, nsample, gs, tbn, tns, tkc ? kc_cap : 0))
+            return fail(ctx, NNSEMD_ERR_CUDA, "autotune launch");
+          CK(cudaEventRecord(ctx->ev[0], st));
+          if (issue(st, nsample, gs, tbn, tns, tkc ? kc_cap : 0))
+            return fail(ctx, NNSEMD_ERR_CUDA, "autotune launch");
+          CK(cudaEventRecord(ctx->ev[1], st));
+          CK(cudaEventSynchronize(ctx->ev[1]));
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = {tbn, tns, tkc};
+          }
+          L += 2;
         }
-        L += 2;
       }
-    }
     ctx->tuned[tkey] = best;
-    std::tie(bn, nstage) = best;
+    std::tie(bn, nstage, kc_use) = best;
   }
+  if (!kc_use) kc_cap = 0;
   if (!small.empty()) {
     int brc = 0;
     if (flags & NNSEMD_FLAG_GRAPH) {
@@ -831,7 +852,7 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
                                           (uintptr_t)b_packed, (uintptr_t)costs_out, (uintptr_t)ctx->ws,
                                           (uintptr_t)num_pairs, (uintptr_t)small.size(), (uintptr_t)d,
                                           (uintptr_t)metric, (uintptr_t)precision, (uintptr_t)cap, (uintptr_t)bn,
-                                          (uintptr_t)nstage, (uintptr_t)ntiny,
+                                          (uintptr_t)nstage, (uintptr_t)ntiny, (uintptr_t)kc_cap,
                                           (uintptr_t)(opt ? opt->protocol : 0), (uintptr_t)(opt ? opt->seed : 0),
                                           (uintptr_t)(opt ? opt->rerank_k : 0),
                                           (uintptr_t)(y_off ? 0 : n_shared)};
@@ -842,7 +863,7 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
         if (!ctx->capture_stream) CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-        brc = issue(ctx->capture_stream, (int)small.size(), grid, bn, nstage);
+        brc = issue(ctx->capture_stream, (int)small.size(), grid, bn, nstage, kc_cap);
         cudaError_t ce = cudaStreamEndCapture(ctx->capture_stream, &graph);
         if (brc || ce != cudaSuccess) {
           if (graph) cudaGraphDestroy(graph);
@@ -857,7 +878,7 @@ static int solve_batched_impl(nnsemd_ctx* ctx, int32_t num_pairs, const float* x
       }
       CK(cudaGraphLaunch(g->exec, st));
     } else {
-      brc = issue(st, (int)small.size(), grid, bn, nstage);
+      brc = issue(st, (int)small.size(), grid, bn, nstage, kc_cap);
     }
     if (brc) return fail(ctx, NNSEMD_ERR_CUDA, "batched launch (%d)", brc);
     CK(cudaGetLastError());

@@ -41,9 +41,18 @@ struct BtcScratch {
   float* scale_y;
   float* cand_v;    // [cap][BTC_K]
   int* cand_p;
+  // distance cache of a pair with m * n <= kc_cap (see GeoTC::nns_cached),
+  // indexed [original consumer][original supplier]
+  float* vcache;    // approximate ranking values v' of the tensor-core pass
+  float* kcache;    // exact FP32 keys, NaN until computed
+  float* ny_o;      // per original consumer: FP32 squared norm, scale, FP64 norms
+  float* sy_o;
+  double* yl2_o;
+  double* yl1_o;
 };
 
-__host__ __device__ inline size_t btc_slot_layout(uint8_t* base, int cap, int kb, int bn, BtcScratch* out) {
+__host__ __device__ inline size_t btc_slot_layout(uint8_t* base, int cap, int kb, int bn, BtcScratch* out,
+                                                  long long kc_cap = 0) {
   size_t off = 0;
   auto take = [&](size_t bytes) {
     off = (off + 255) & ~(size_t)255;
@@ -63,11 +72,19 @@ __host__ __device__ inline size_t btc_slot_layout(uint8_t* base, int cap, int kb
   s.scale_y = (float*)take(qrows * sizeof(float));
   s.cand_v = (float*)take((size_t)cap * BTC_K * sizeof(float));
   s.cand_p = (int*)take((size_t)cap * BTC_K * sizeof(int));
+  s.vcache = (float*)take((size_t)kc_cap * sizeof(float));
+  s.kcache = (float*)take((size_t)kc_cap * sizeof(float));
+  s.ny_o = (float*)take(kc_cap ? (size_t)cap * sizeof(float) : 0);
+  s.sy_o = (float*)take(kc_cap ? (size_t)cap * sizeof(float) : 0);
+  s.yl2_o = (double*)take(kc_cap ? (size_t)cap * sizeof(double) : 0);
+  s.yl1_o = (double*)take(kc_cap ? (size_t)cap * sizeof(double) : 0);
   if (out) *out = s;
   return (off + 255) & ~(size_t)255;
 }
 
-size_t batched_tc_slot_bytes(int cap, int kb, int bn) { return btc_slot_layout(nullptr, cap, kb, bn, nullptr); }
+size_t batched_tc_slot_bytes(int cap, int kb, int bn, long long kc_cap) {
+  return btc_slot_layout(nullptr, cap, kb, bn, nullptr, kc_cap);
+}
 
 struct BtcArgs {
   BatchArgs base;
@@ -78,6 +95,7 @@ struct BtcArgs {
   unsigned long long* fallbacks;
   unsigned long long* near_ties;
   int rk;                    // candidates re-ranked per consumer (1 .. BTC_K)
+  long long kc_cap;          // distance-cache entries per CTA (0: no cache)
 };
 
 // The NNS policy of the batched tensor-core solver (coordinates in global
@@ -107,6 +125,10 @@ struct GeoTC {
   unsigned stat_rx, stat_rx1, stat_sx;  // certificate maxima of this round (float bits)
   int nfb;
   unsigned long long ncert, nfall, nnear;
+  // distance cache of the current pair: on (m * n fits), filled (after the
+  // pair's first round), the pair's supplier and consumer counts (the row
+  // length and the number of rows)
+  int kc_on, kc_ready, kc_m, kc_n;
   int fb[CAP];
   // staging: tensor-core operand tiles or FP32 fallback tiles (never both at
   // once); the launch reserves max(sizeof(tiles), A + stages * B) bytes
@@ -124,8 +146,130 @@ struct GeoTC {
     return cost_dist64(x + (size_t)S.iidx[p] * d, y + (size_t)S.jidx[q] * d, d, metric);
   }
 
+  // The NNS step of a round from the pair's distance cache (the tensor-core
+  // pass of its first round filled every v'): one warp per active consumer.
+  //   1. the rk active suppliers with the smallest v' (each lane keeps the
+  //      best rk of its share of the suppliers, then rk warp-wide minima
+  //      merge the lists; ties by position);
+  //   2. their exact FP32 keys, from the key cache or computed (and cached)
+  //      by one lane each, in the definition's sequential order;
+  //   3. the certificate of the best of them against tau, the rk-th v'
+  //      (every other active supplier has v' >= tau; with no other active
+  //      supplier every one was a candidate and the best is the answer);
+  //   4. otherwise the exact key of every active supplier (cached or
+  //      computed), the smallest with its position.
+  // The per-supplier maxima of the certificate are those of the first
+  // round's active suppliers, a superset of every later round's, so the
+  // bound only gets more conservative.  Exact keys are written and read by
+  // the warp that owns the consumer in that round; a barrier separates
+  // rounds, so a key cached by one warp is seen by the next.
+  template <int C>
+  NNS_DEV const unsigned long long* nns_cached(CtaCore<C>& S, int mt, int nt) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const double rx = __uint_as_float(stat_rx), rx1 = __uint_as_float(stat_rx1), sxm = __uint_as_float(stat_sx);
+    const int K = rk < mt ? rk : mt;
+    for (int q = warp; q < nt; q += T / 32) {
+      const int j = S.jidx[q];
+      const float* vrow = scr.vcache + (size_t)j * kc_m;
+      float* krow = scr.kcache + (size_t)j * kc_m;
+      const float* yrow = y + (size_t)j * d;
+      // 1. candidates: this lane's best BTC_K, then the warp's best K
+      float tv[BTC_K];
+      int tp[BTC_K];
+#pragma unroll
+      for (int k = 0; k < BTC_K; ++k) { tv[k] = CUDART_INF_F; tp[k] = -1; }
+      for (int p = lane; p < mt; p += 32) topk_insert(tv, tp, vrow[S.iidx[p]], p);
+      unsigned long long sel = ~0ULL, first = ~0ULL, kth = ~0ULL;
+      for (int k = 0; k < K; ++k) {
+        const unsigned long long mine =
+            tp[0] >= 0 ? ((unsigned long long)ordered_bits(tv[0]) << 32) | (unsigned)tp[0] : ~0ULL;
+        unsigned long long w = mine;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const unsigned long long other = __shfl_xor_sync(0xffffffffu, w, o);
+          w = other < w ? other : w;
+        }
+        if (mine == w && w != ~0ULL) {  // the winning lane drops its head
+#pragma unroll
+          for (int i = 0; i + 1 < BTC_K; ++i) {
+            tv[i] = tv[i + 1];
+            tp[i] = tp[i + 1];
+          }
+          tv[BTC_K - 1] = CUDART_INF_F;
+          tp[BTC_K - 1] = -1;
+        }
+        if (lane == k) sel = w;
+        if (k == 0) first = w;
+        kth = w;
+      }
+      // 2. exact keys of the candidates
+      unsigned long long best = ~0ULL;
+      if (lane < K && sel != ~0ULL) {
+        const int p = (int)(unsigned)sel;
+        const int i = S.iidx[p];
+        float key = krow[i];
+        if (key != key) {
+          key = key32<METRIC_SQL2>(x + (size_t)i * d, yrow, d);
+          krow[i] = key;
+        }
+        best = pack_key(key, (unsigned)p);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+        best = other < best ? other : best;
+      }
+      // 3. the certificate (tau = +inf: no other active supplier)
+      bool cert = false;
+      if (lane == 0) {
+        const unsigned tb = (unsigned)(kth >> 32);
+        const float tau = mt > K ? __uint_as_float((tb & 0x80000000u) ? (tb & 0x7fffffffu) : ~tb) : CUDART_INF_F;
+        cert = best != ~0ULL && certify(fmt, d, scr.ny_o[j], scr.yl2_o[j], scr.yl1_o[j], scr.sy_o[j], rx, rx1, sxm,
+                                        tau, __uint_as_float((unsigned)(best >> 32)));
+      }
+      cert = __shfl_sync(0xffffffffu, cert, 0);
+      if (cert) {
+        if (lane == 0) {
+          S.nnk[q] = best;
+          atomicAdd(&ncert, 1ULL);
+          if ((unsigned)best != (unsigned)first) atomicAdd(&nnear, 1ULL);
+        }
+        continue;
+      }
+      // 4. the exact scan
+      unsigned long long m2 = ~0ULL;
+      for (int p = lane; p < mt; p += 32) {
+        const int i = S.iidx[p];
+        float key = krow[i];
+        if (key != key) {
+          key = key32<METRIC_SQL2>(x + (size_t)i * d, yrow, d);
+          krow[i] = key;
+        }
+        const unsigned long long kk = pack_key(key, (unsigned)p);
+        m2 = kk < m2 ? kk : m2;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, m2, o);
+        m2 = other < m2 ? other : m2;
+      }
+      if (lane == 0) {
+        S.nnk[q] = m2;
+        atomicAdd(&nfall, 1ULL);
+        if ((unsigned)m2 != (unsigned)first) atomicAdd(&nnear, 1ULL);
+      }
+    }
+    __syncthreads();
+    return S.nnk;
+  }
+
   template <int C>
   NNS_DEV const unsigned long long* nns(CtaCore<C>& S, int mt, int nt, long long = 0) {
+    if (kc_on && kc_ready) return nns_cached(S, mt, nt);
+    // with the cache on, this is the pair's first round: the tensor-core
+    // pass fills the cache (every v' of the pair) instead of keeping top-K
+    const bool fill = kc_on != 0;
     const int tid = threadIdx.x, T = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int qtiles = (nt + TC_BM - 1) / TC_BM;
@@ -135,6 +279,11 @@ struct GeoTC {
     if (tid == 0) {
       stat_rx = stat_rx1 = stat_sx = 0u;
       nfb = 0;
+    }
+    if (fill) {
+      // no exact key of the pair is known yet
+      const long long total = (long long)kc_m * (long long)kc_n;
+      for (long long e = tid; e < total; e += T) scr.kcache[e] = CUDART_NAN_F;
     }
     __syncthreads();
     {
@@ -149,7 +298,7 @@ struct GeoTC {
         const float s = row_scale(row, d, fmt);
         const int rows = sup ? bn : TC_BM;
         uint8_t* tile = (sup ? scr.B : scr.A) + (size_t)(p / rows) * rows * kb;
-        for (int c = 0; c < nblk; ++c) pack_block(row, d, c, s, fmt, tile, rows, p % rows);
+        for (int c = 0; c < nblk; ++c) pack_block(row, d, c, s, fmt, tile, rows, p % rows, sup);
         {
           float* nrm = sup ? scr.nrm_x : scr.nrm_y;
           float* scl = sup ? scr.scale_x : scr.scale_y;
@@ -163,6 +312,18 @@ struct GeoTC {
               atomicMax(&stat_rx, __float_as_uint(norm_up(l2sq)));
               atomicMax(&stat_rx1, __float_as_uint(l1 * (1.f + 1e-4f)));
               atomicMax(&stat_sx, __float_as_uint(s));
+            } else if (fill) {
+              // what the certificate needs of this consumer in every round
+              const int j = S.jidx[p];
+              double a2 = 0.0, a1 = 0.0;
+              for (int k = 0; k < d; ++k) {
+                a2 += (double)row[k] * row[k];
+                a1 += fabs((double)row[k]);
+              }
+              scr.ny_o[j] = l2sq;
+              scr.sy_o[j] = s;
+              scr.yl2_o[j] = sqrt(a2) * (1 + 1e-12);
+              scr.yl1_o[j] = a1;
             }
           } else {
             nrm[p] = CUDART_INF_F;
@@ -200,7 +361,7 @@ struct GeoTC {
       }
     } else if (warp == 1) {
       if (lane == 0) {
-        const uint32_t idesc = make_idesc(fmt == FMT_BF16 ? 1 : 0, TC_BM, bn);
+        const uint32_t idesc = make_idesc(fmt_is_bf16(fmt) ? 1 : 0, TC_BM, bn);
         const int ksteps = kb / 32;
         const uint32_t a0 = smem_u32(sA);
         for (int qt = 0; qt < qtiles && ok; ++qt) {
@@ -249,22 +410,29 @@ struct GeoTC {
             const float* nx = scr.nrm_x + (size_t)st * bn;
             const float* ns = scr.nrm_sx + (size_t)st * bn;
             const float* sx = scr.scale_x + (size_t)st * bn;
+            // fill: this consumer's row of the cache, by original supplier index
+            float* vrow = (fill && q < nt) ? scr.vcache + (size_t)S.jidx[q] * kc_m : nullptr;
             for (int c0 = 0; c0 < bn; c0 += 16) {
               uint32_t r[16];
               tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + b * (uint32_t)bn + (uint32_t)c0, r);
 #pragma unroll
               for (int e = 0; e < 16; ++e) {
                 const float acc = __uint_as_float(r[e]);
-                const float w = fmt == FMT_BF16 ? -2.f : -2.f * sy * sx[c0 + e];
+                const float w = fmt_is_bf16(fmt) ? -2.f : -2.f * sy * sx[c0 + e];
                 const float val = __fmaf_rn(-cy, ns[c0 + e], __fmaf_rn(w, acc, nx[c0 + e]));
-                topk_insert(tv, tp, val, st * bn + c0 + e);
+                const int col = st * bn + c0 + e;
+                if (fill) {
+                  if (vrow && col < mt) vrow[S.iidx[col]] = val;
+                } else {
+                  topk_insert(tv, tp, val, col);
+                }
               }
             }
           }
           tc_fence_before();
           mbar_arrive(&bar_acc_empty[b]);
         }
-        if (q < nt) {
+        if (q < nt && !fill) {
 #pragma unroll
           for (int k = 0; k < BTC_K; ++k) {
             scr.cand_v[(size_t)q * BTC_K + k] = tv[k];
@@ -278,6 +446,13 @@ struct GeoTC {
     __syncthreads();
     tc_fence_after();
     if (tid == 64) epi_acc += (unsigned)(qtiles * stiles);
+    if (fill) {
+      // the cache holds every v' of the pair; this and every later round
+      // are answered from it
+      if (tid == 0) kc_ready = 1;
+      __syncthreads();
+      return nns_cached(S, mt, nt);
+    }
     // ---- 3. exact re-rank + certificate (a warp per consumer)
     const double rx = __uint_as_float(stat_rx), rx1 = __uint_as_float(stat_rx1), sxm = __uint_as_float(stat_sx);
     for (int q = warp; q < nt; q += T / 32) {
@@ -383,7 +558,7 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_batched_tc(BtcArgs A) {
     G.nstage = A.nstage;
     G.fmt = A.fmt;
     G.err = A.base.err;
-    btc_slot_layout(A.scratch + (size_t)blockIdx.x * A.slot_bytes, CAP, A.kb, A.bn, &G.scr);
+    btc_slot_layout(A.scratch + (size_t)blockIdx.x * A.slot_bytes, CAP, A.kb, A.bn, &G.scr, A.kc_cap);
   }
   if (warp == 1) tmem_alloc(&tmem_slot, ncols);
   tc_fence_before();
@@ -405,6 +580,10 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_batched_tc(BtcArgs A) {
       G.x = B.x + xo * B.d;
       G.y = B.y + yo * B.d;
       G.d = B.d;
+      G.kc_on = (long long)m * n <= A.kc_cap ? 1 : 0;
+      G.kc_ready = 0;
+      G.kc_m = m;
+      G.kc_n = n;
     }
     __syncthreads();
     double cost = 0.0;
@@ -455,10 +634,10 @@ int batched_tc_max_stages(int cap, int kb, int bn, int precision) {
 
 int launch_batched_tc(const BatchArgs& base, int precision, int cap, int kb, int bn, int nstage, uint8_t* scratch,
                       size_t slot_bytes, unsigned long long* certified, unsigned long long* fallbacks,
-                      unsigned long long* near_ties, int rerank_k, int grid, cudaStream_t st) {
+                      unsigned long long* near_ties, int rerank_k, long long kc_cap, int grid, cudaStream_t st) {
   const int rk = rerank_k >= 1 && rerank_k <= BTC_K ? rerank_k : BTC_K;
   BtcArgs A{base, scratch, slot_bytes, kb, bn, nstage, fmt_of_precision(precision), certified, fallbacks,
-            near_ties, rk};
+            near_ties, rk, kc_cap};
   const bool k8 = precision == 3;
   if (cap <= 512) return k8 ? batched_tc_t<true, 512>(A, grid, st) : batched_tc_t<false, 512>(A, grid, st);
   return k8 ? batched_tc_t<true, 2048>(A, grid, st) : batched_tc_t<false, 2048>(A, grid, st);

@@ -31,8 +31,9 @@ struct nnsemd_ctx {
   std::string err;
   long long launches = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // kernel timing (NNSEMD_FLAG_TIME_KERNELS)
-  // autotuner: (d, precision, cap) -> (bn, stages) of the batched tensor-core kernel
-  std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;
+  // autotuner: (d, precision, cap) -> (bn, stages, distance cache on) of the
+  // batched tensor-core kernel
+  std::map<std::tuple<int, int, int>, std::tuple<int, int, int>> tuned;
   std::vector<BatchGraph> graphs;
   cudaStream_t capture_stream = nullptr;
 };

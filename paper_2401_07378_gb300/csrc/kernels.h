@@ -163,6 +163,7 @@ void launch_check_finite(const float* v, int64_t count, unsigned* err, cudaStrea
 // tc.cu (reduced precision, d > 8, squared-Euclidean order) ----------------
 size_t tc_kb(int d, int precision);  // packed bytes per row
 int tc_bn(size_t kb);                // supplier rows per tile
+bool tc_supported(int d, int precision);  // the operand tiles of K2 fit its shared memory
 // NNS of every active consumer: tensor-core candidates, exact FP32 re-rank,
 // certificate, FP32 rescan of the rest.  Writes B.nnkey (must be all ones).
 int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int precision, cudaStream_t st,
@@ -170,12 +171,14 @@ int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int preci
 
 // batched_tc.cu: batches of pairs with up to `cap` (512 or 2048) points per
 // side, reduced-precision NNS inside each pair's CTA.
-size_t batched_tc_slot_bytes(int cap, int kb, int bn);
+// kc_cap: entries of each CTA's distance cache (pairs with m * n <= kc_cap
+// are answered from it after their first round; 0 turns it off).
+size_t batched_tc_slot_bytes(int cap, int kb, int bn, long long kc_cap);
 int batched_tc_max_stages(int cap, int kb, int bn, int precision);
 // rerank_k: candidates re-ranked per consumer (1..8; other values: 8);
 // certified / fallbacks / near_ties: device counters the launch adds to.
 int launch_batched_tc(const BatchArgs& base, int precision, int cap, int kb, int bn, int nstage, uint8_t* scratch,
                       size_t slot_bytes, unsigned long long* certified, unsigned long long* fallbacks,
-                      unsigned long long* near_ties, int rerank_k, int grid, cudaStream_t st);
+                      unsigned long long* near_ties, int rerank_k, long long kc_cap, int grid, cudaStream_t st);
 
 }  // namespace nnsemd

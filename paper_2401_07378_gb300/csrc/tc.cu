@@ -50,7 +50,8 @@ __global__ void k_pack_tc(const float* __restrict__ pts, const int* __restrict__
     const float* row = p < count ? pts + (size_t)idx[sel ? sel[p] : p] * d : nullptr;
     const float s = row_scale(row, d, fmt);
     const int t = p / tile_rows, r = p % tile_rows;
-    for (int c = 0; c < nblk; ++c) pack_block(row, d, c, s, fmt, out + (size_t)t * tile_rows * kb, tile_rows, r);
+    for (int c = 0; c < nblk; ++c)
+      pack_block(row, d, c, s, fmt, out + (size_t)t * tile_rows * kb, tile_rows, r, nrm_s != nullptr);
     {
       if (row) {
         float l2sq, l1;
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      constexpr int AB = FMT == FMT_BF16 ? 1 : 0;
+      constexpr int AB = fmt_is_bf16(FMT) ? 1 : 0;
       const uint32_t idesc = make_idesc(AB, TC_BM, BN);
       const int ksteps = kb / 32;
       ok = mbar_wait_bounded(&bar_a, 0);
@@ -228,25 +229,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
         const float* nx = nrm_buf[b][0];
         const float* ns = nrm_buf[b][1];
         const float* sx = nrm_buf[b][2];
-        for (int c0 = half * HALF; c0 < (half + 1) * HALF; c0 += 16) {
-          uint32_t r[16];
-          tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + c0), r);
+        // all of this warp's columns of the accumulator at once (one wait
+        // for NB loads in flight), then two columns per packed FP32x2 step
+        constexpr int NB = HALF / 16;
+        uint32_t rr[NB][16];
+#pragma unroll
+        for (int bb = 0; bb < NB; ++bb)
+          tmem_ld16_async(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + half * HALF + 16 * bb),
+                          rr[bb]);
+        tmem_ld_wait(rr);
+        const unsigned long long mcy2 = f2_pack(-cy, -cy);
+        const unsigned long long w2c = f2_pack(-2.f, -2.f);
+        const unsigned long long wsy2 = f2_pack(-2.f * sy, -2.f * sy);
+#pragma unroll
+        for (int bb = 0; bb < NB; ++bb) {
+          const int c0 = half * HALF + 16 * bb;
+          const uint32_t(&r)[16] = rr[bb];
           float val[16];
           float mn = CUDART_INF_F;
 #pragma unroll
           for (int k = 0; k < 16; k += 4) {
             const float4 vx = *reinterpret_cast<const float4*>(nx + c0 + k);
             const float4 vs = *reinterpret_cast<const float4*>(ns + c0 + k);
-            const float4 vc = *reinterpret_cast<const float4*>(sx + c0 + k);
-            const float cx[4] = {vx.x, vx.y, vx.z, vx.w};
-            const float cs[4] = {vs.x, vs.y, vs.z, vs.w};
-            const float cc[4] = {vc.x, vc.y, vc.z, vc.w};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const float acc = __uint_as_float(r[k + j]);
-              const float w = (FMT == FMT_BF16) ? -2.f : -2.f * sy * cc[j];
-              val[k + j] = __fmaf_rn(-cy, cs[j], __fmaf_rn(w, acc, cx[j]));
+            unsigned long long w01 = w2c, w23 = w2c;
+            if (!fmt_is_bf16(FMT)) {
+              // w = (-2 sy) sx: both powers of two, so the product is exact
+              const float4 vc = *reinterpret_cast<const float4*>(sx + c0 + k);
+              w01 = f2_mul(wsy2, f2_pack(vc.x, vc.y));
+              w23 = f2_mul(wsy2, f2_pack(vc.z, vc.w));
             }
+            const unsigned long long a01 = f2_pack(__uint_as_float(r[k]), __uint_as_float(r[k + 1]));
+            const unsigned long long a23 = f2_pack(__uint_as_float(r[k + 2]), __uint_as_float(r[k + 3]));
+            const unsigned long long v01 = f2_fma(mcy2, f2_pack(vs.x, vs.y), f2_fma(w01, a01, f2_pack(vx.x, vx.y)));
+            const unsigned long long v23 = f2_fma(mcy2, f2_pack(vs.z, vs.w), f2_fma(w23, a23, f2_pack(vx.z, vx.w)));
+            val[k] = f2_lo(v01);
+            val[k + 1] = f2_hi(v01);
+            val[k + 2] = f2_lo(v23);
+            val[k + 3] = f2_hi(v23);
             mn = fmin3(mn, fminf(val[k], val[k + 1]), fminf(val[k + 2], val[k + 3]));
           }
           if (mn < tv[TC_K - 1]) {
@@ -394,10 +413,17 @@ __global__ void k_rerank_certify(RerankArgs R) {
 
 size_t tc_kb(int d, int precision) {
   const int esize = precision == 3 ? 1 : 2;
-  return (size_t)(((int64_t)d * esize + 31) / 32 * 32);
+  const int64_t values = (int64_t)d * fmt_parts(fmt_of_precision(precision));
+  return (size_t)((values * esize + 31) / 32 * 32);
 }
 
 int tc_bn(size_t kb) { return kb <= 384 ? 128 : 64; }
+
+bool tc_supported(int d, int precision) {
+  const size_t kb = tc_kb(d, precision);
+  const size_t a_bytes = (size_t)TC_BM * kb, b_bytes = (size_t)tc_bn(kb) * kb;
+  return a_bytes + b_bytes <= (size_t)TC_SMEM_BUDGET;
+}
 
 template <int FMT, int BN>
 static int launch_tc_t(const TcArgs& P, dim3 grid, size_t smem, cudaStream_t st) {
@@ -450,6 +476,9 @@ int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int preci
   if (T.ev0) cudaEventRecord(T.ev0, st);
   if (fmt == FMT_BF16)
     rc = bn == 128 ? launch_tc_t<FMT_BF16, 128>(P, grid, smem, st) : launch_tc_t<FMT_BF16, 64>(P, grid, smem, st);
+  else if (fmt == FMT_BF16X3)
+    rc = bn == 128 ? launch_tc_t<FMT_BF16X3, 128>(P, grid, smem, st)
+                   : launch_tc_t<FMT_BF16X3, 64>(P, grid, smem, st);
   else if (fmt == FMT_F16)
     rc = bn == 128 ? launch_tc_t<FMT_F16, 128>(P, grid, smem, st) : launch_tc_t<FMT_F16, 64>(P, grid, smem, st);
   else

@@ -24,14 +24,27 @@ namespace nnsemd {
 constexpr int TC_BM = 128;  // consumers per accumulator (MMA M)
 constexpr int TC_K = 16;    // candidates kept per consumer
 
-enum TcFmt : int { FMT_F16 = 0, FMT_BF16 = 1, FMT_E4M3 = 2 };
+// FMT_BF16X3: every coordinate v as a high part h = bf16(v) and a low part
+// l = bf16(v - h) (v - h is exact in FP32); a packed row holds 3d BF16
+// values, [h(y), h(y), l(y)] for a consumer and [h(x), l(x), h(x)] for a
+// supplier, so one BF16 contraction of length 3d gives
+// <h(x), h(y)> + <l(x), h(y)> + <h(x), l(y)>, which differs from <x, y> by at
+// most u^2 (3 + 2u + 2u^2) sum |x_k y_k| (u = 2^-8), against (2u + u^2) for
+// a single BF16 copy.
+enum TcFmt : int { FMT_F16 = 0, FMT_BF16 = 1, FMT_E4M3 = 2, FMT_BF16X3 = 3 };
 
 __host__ __device__ inline int fmt_of_precision(int precision) {
-  return precision == 1 ? FMT_BF16 : (precision == 2 ? FMT_F16 : FMT_E4M3);
+  return precision == 1 ? FMT_BF16 : (precision == 2 ? FMT_F16 : (precision == 4 ? FMT_BF16X3 : FMT_E4M3));
 }
 
+// BF16 operands (kind::f16 with the BF16 type) and no per-row scale
+__host__ __device__ constexpr bool fmt_is_bf16(int fmt) { return fmt == FMT_BF16 || fmt == FMT_BF16X3; }
+
+// Values per coordinate in a packed row.
+__host__ __device__ constexpr int fmt_parts(int fmt) { return fmt == FMT_BF16X3 ? 3 : 1; }
+
 NNS_DEV uint16_t to_bits16(float v, int fmt) {
-  if (fmt == FMT_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+  if (fmt_is_bf16(fmt)) return __bfloat16_as_ushort(__float2bfloat16_rn(v));
   return __half_as_ushort(__float2half_rn(v));
 }
 
@@ -40,7 +53,7 @@ NNS_DEV uint8_t to_e4m3(float v) { return (uint8_t)__nv_cvt_float_to_fp8(v, __NV
 // Per-row scale (a power of two) for FP16 / FP8: the largest |v| of the row
 // maps into [2^7, 2^8).  BF16 has FP32's exponent range and uses 1.
 NNS_DEV float row_scale(const float* row, int d, int fmt) {
-  if (!row || fmt == FMT_BF16) return 1.f;
+  if (!row || fmt_is_bf16(fmt)) return 1.f;
   float mx = 0.f;
   for (int k = 0; k < d; ++k) mx = fmaxf(mx, fabsf(row[k]));
   if (!(mx > 0.f)) return 1.f;
@@ -49,11 +62,30 @@ NNS_DEV float row_scale(const float* row, int d, int fmt) {
   return ldexpf(1.f, e - 8);
 }
 
+// Value k (0 <= k < 3d) of a BF16X3 packed row: segment k / d of [h, h, l]
+// (consumer, supplier = false) or [h, l, h] (supplier).
+NNS_DEV float bf16x3_part(const float* row, int d, int k, bool supplier) {
+  const int seg = k / d;
+  const float v = row[k - seg * d];
+  const float h = __bfloat162float(__float2bfloat16_rn(v));
+  const bool low = supplier ? seg == 1 : seg == 2;
+  return low ? v - h : h;
+}
+
 // Pack 16 bytes (block c) of one row into out (row r of tile t).  row == null
-// writes zeros (padding).
-NNS_DEV void pack_block(const float* row, int d, int c, float s, int fmt, uint8_t* tile_base, int tile_rows, int r) {
+// writes zeros (padding).  `supplier` picks the BF16X3 segment order.
+NNS_DEV void pack_block(const float* row, int d, int c, float s, int fmt, uint8_t* tile_base, int tile_rows, int r,
+                        bool supplier = false) {
   alignas(16) uint8_t bytes[16];
-  if (fmt == FMT_E4M3) {
+  if (fmt == FMT_BF16X3) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int k = c * 8 + e;
+      const uint16_t b = to_bits16((row && k < 3 * d) ? bf16x3_part(row, d, k, supplier) : 0.f, fmt);
+      bytes[2 * e] = (uint8_t)(b & 0xff);
+      bytes[2 * e + 1] = (uint8_t)(b >> 8);
+    }
+  } else if (fmt == FMT_E4M3) {
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const int k = c * 16 + e;
@@ -152,6 +184,33 @@ NNS_DEV void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// The same load without its wait: several loads go out back to back, then
+// one tmem_ld_wait.  The registers must not be read before that wait, so the
+// wait takes every destination block as an in/out operand of an (empty)
+// ordered asm, which keeps the compiler from moving a read above it.
+NNS_DEV void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+NNS_DEV void tmem_regs_after_wait(uint32_t (&r)[16]) {
+  asm volatile(""
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]));
+}
+
+template <int NB>
+NNS_DEV void tmem_ld_wait(uint32_t (&r)[NB][16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int b = 0; b < NB; ++b) tmem_regs_after_wait(r[b]);
+}
+
 // Make this thread's generic-proxy global writes visible to later bulk
 // copies (async proxy) issued after a barrier.
 NNS_DEV void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
@@ -189,9 +248,10 @@ NNS_DEV void topk_insert(float (&tv)[K], int (&tp)[K], float v, int p) {
 //
 // The epilogue ranks suppliers by a lower bound of the approximate distance:
 //   v'_ij = |x_i|^2 - 2 s_i s_j <x^_i, y^_j> - c_j |x_i|,
-//   c_j   = 2 (2u + u^2) |y_j|,
+//   c_j   = 2 Q |y_j|,
 // where the subtracted term bounds the quantisation error of the dot product
-// for this very pair (|<x~,y~> - <x,y>| <= (2u + u^2) |x| |y| by
+// for this very pair (|<x~,y~> - <x,y>| <= Q |x| |y|, Q = 2u + u^2 for one
+// rounded copy per side, u^2 (3 + 2u + 2u^2) for the BF16X3 split, by
 // Cauchy-Schwarz; it enters twice).  Every supplier outside the K candidates
 // has v' >= tau (the K-th smallest).  Its true squared distance d2 (of the
 // float inputs) is therefore >= ny + tau - E, with E bounding what remains:
@@ -199,7 +259,9 @@ NNS_DEV void topk_insert(float (&tv)[K], int (&tp)[K], float v, int p) {
 //   2 (eta terms)                             absolute rounding floor of the
 //                                             operand format (subnormals,
 //                                             times the row scale)
-//   2 d 2^-22 |x~| |y~|                       tensor-core accumulation
+//   2 K 2^-22 |x~| |y~|                       tensor-core accumulation
+//                                             (K = d, 3d for BF16X3; |x~|,
+//                                             |y~| the packed rows' norms)
 //   2 u32 (rx^2 + 2 |x~||y~| + c rx)          the epilogue's FP32 roundings
 // (u = the operand format's unit roundoff, u32 = 2^-24, rx = max |x_i|,
 // rx1 = max |x_i|_1 over the active suppliers).  Its FP32 key is >= d2 (1 -
@@ -210,13 +272,28 @@ NNS_DEV void topk_insert(float (&tv)[K], int (&tp)[K], float v, int p) {
 
 // (host and device: the CPU tests evaluate the certificate's arithmetic too)
 __host__ __device__ inline double quant_unit(int fmt) {
-  return fmt == FMT_BF16 ? 0x1p-8 : (fmt == FMT_F16 ? 0x1p-11 : 0x1p-4);
+  return fmt_is_bf16(fmt) ? 0x1p-8 : (fmt == FMT_F16 ? 0x1p-11 : 0x1p-4);
+}
+
+// Q with |<x~, y~> - <x, y>| <= Q sum |x_k y_k| <= Q |x| |y| for the dot
+// product the format computes: 2u + u^2 for one rounded copy of each side,
+// u^2 (3 + 2u + 2u^2) for the BF16X3 split (see FMT_BF16X3).
+__host__ __device__ inline double quant_err(int fmt) {
+  const double u = quant_unit(fmt);
+  return fmt == FMT_BF16X3 ? u * u * (3.0 + 2.0 * u + 2.0 * u * u) : 2.0 * u + u * u;
+}
+
+// Bound on |a| / |v| for a packed operand row a of a row v (rounding
+// only): 1 + u for one copy; the BF16X3 row [h, h, l] or [h, l, h] has
+// |a|^2 <= 2 (1 + u)^2 |v|^2 + (u + u^2)^2 |v|^2.
+__host__ __device__ inline double quant_norm_factor(int fmt) {
+  const double u = quant_unit(fmt);
+  return fmt == FMT_BF16X3 ? 1.4142135623731 * (1.0 + u) + u + u * u : 1.0 + u;
 }
 
 // c_j of the epilogue, from the consumer's FP32 squared norm (rounded up).
 NNS_DEV float quant_coeff(int fmt, float ny) {
-  const double uq = quant_unit(fmt);
-  return (float)(2.0 * (2.0 * uq + uq * uq) * sqrt((double)ny) * (1.0 + 1e-4));
+  return (float)(2.0 * quant_err(fmt) * sqrt((double)ny) * (1.0 + 1e-4));
 }
 
 // |x| rounded up, from the FP32 squared norm (sequential fma, relative error
@@ -232,13 +309,20 @@ __host__ __device__ inline double certify_floor(int fmt, int d, double ny, doubl
   const double u32 = 0x1p-24;
   const double uq = quant_unit(fmt);
   const double gam = d * u32 / (1.0 - d * u32);
-  const double eta_unit = fmt == FMT_BF16 ? 0x1p-134 : (fmt == FMT_F16 ? 0x1p-25 : 0x1p-10);
-  const double eta_x = eta_unit * (fmt == FMT_BF16 ? 1.0 : sxm);
-  const double eta_y = eta_unit * (fmt == FMT_BF16 ? 1.0 : sy);
-  const double dot_eta = eta_x * (yl1 + eta_y * d) + eta_y * rx1 + eta_x * uq * yl1 + eta_y * uq * rx1;
-  const double xt = (1 + uq) * rx + eta_x * sqrt((double)d), yt = (1 + uq) * yl2 + eta_y * sqrt((double)d);
-  const double dot_acc = d * 0x1p-22 * xt * yt;
-  const double c = 2.0 * (2.0 * uq + uq * uq) * yl2 * (1.0 + 1e-5);
+  const double kdim = (double)d * fmt_parts(fmt);  // length of the contraction
+  // absolute rounding floor of one packed value (subnormals; times the row
+  // scale for FP16 / FP8); BF16X3 rounds twice per coordinate
+  const double eta_unit =
+      fmt == FMT_BF16 ? 0x1p-134 : (fmt == FMT_BF16X3 ? 0x1p-132 : (fmt == FMT_F16 ? 0x1p-25 : 0x1p-10));
+  const double eta_x = eta_unit * (fmt_is_bf16(fmt) ? 1.0 : sxm);
+  const double eta_y = eta_unit * (fmt_is_bf16(fmt) ? 1.0 : sy);
+  const double dot_eta =
+      fmt == FMT_BF16X3 ? 3.0 * (eta_x * (2.0 * yl1 + eta_y * d) + 2.0 * eta_y * rx1)
+                        : eta_x * (yl1 + eta_y * d) + eta_y * rx1 + eta_x * uq * yl1 + eta_y * uq * rx1;
+  const double nf = quant_norm_factor(fmt);
+  const double xt = nf * rx + eta_x * sqrt(kdim), yt = nf * yl2 + eta_y * sqrt(kdim);
+  const double dot_acc = kdim * 0x1p-22 * xt * yt;
+  const double c = 2.0 * quant_err(fmt) * yl2 * (1.0 + 1e-5);
   const double E = gam * (ny + rx * rx) + 2.0 * (dot_eta + dot_acc) +
                    2.0 * u32 * (rx * rx + 2.0 * xt * yt + c * rx) + 1e-30;
   const double base = ny + (double)tau - E;  // <= 0: no key is certified (keys are >= 0)

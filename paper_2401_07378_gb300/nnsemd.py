@@ -26,7 +26,7 @@ NNSEMD_OK = 0
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NONFINITE", 3: "ZERO_MASS", 4: "CUDA", 5: "OOM",
           6: "TIMEOUT", 7: "ITER_LIMIT", 8: "UNSUPPORTED", 9: "CAPACITY"}
 METRIC = {"l2": 0, "sql2": 1, "l1": 2}
-PRECISION = {"fp32": 0, "bf16": 1, "fp16": 2, "fp8": 3}
+PRECISION = {"fp32": 0, "bf16": 1, "fp16": 2, "fp8": 3, "bf16x3": 4}
 FLAG_TIME_KERNELS = 1
 FLAG_AUTOTUNE = 2
 FLAG_GRAPH = 4
