@@ -379,7 +379,8 @@ def roofline(d: int, precision: str, pairs: int, launches: int, ms: float, total
         ops = pairs * 2 * d / max(launches, 1)
         basis = ("measured cuBLAS bf16 burst of MEASURED_PEAKS.json" +
                  (" x 2 (nominal fp8/bf16 ratio)" if precision == "fp8" else "") +
-                 "; work = 2d flops per supplier/consumer pair")
+                 "; work = 2d flops per supplier/consumer pair" +
+                 (" (the BF16X3 split runs 3 x 2d on the tensor pipe)" if precision == "bf16x3" else ""))
         bound = "tensor"
         kernel = f"k_nns_tc<{precision}> (tcgen05 contraction + top-8 epilogue)"
     achieved = ops / per_launch_s / 1e12 if ms > 0 else 0.0
@@ -675,7 +676,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="colour")
-    ap.add_argument("--precision", choices=["fp32", "bf16", "fp16", "fp8"], default=None)
+    ap.add_argument("--precision", choices=["fp32", "bf16", "fp16", "fp8", "bf16x3"], default=None)
     ap.add_argument("--proposal", choices=["none", "learned"], default=None,
                     help="gmm only (default learned): train a learned candidate proposal before timing")
     ap.add_argument("--no-plain", action="store_true", help="gmm: skip timing the plain FP32 form")

@@ -49,6 +49,7 @@ struct BtcScratch {
   float* sy_o;
   double* yl2_o;
   double* yl1_o;
+  double* e_o;      // per original consumer: E of the certificate (certify_E)
 };
 
 __host__ __device__ inline size_t btc_slot_layout(uint8_t* base, int cap, int kb, int bn, BtcScratch* out,
@@ -78,6 +79,7 @@ __host__ __device__ inline size_t btc_slot_layout(uint8_t* base, int cap, int kb
   s.sy_o = (float*)take(kc_cap ? (size_t)cap * sizeof(float) : 0);
   s.yl2_o = (double*)take(kc_cap ? (size_t)cap * sizeof(double) : 0);
   s.yl1_o = (double*)take(kc_cap ? (size_t)cap * sizeof(double) : 0);
+  s.e_o = (double*)take(kc_cap ? (size_t)cap * sizeof(double) : 0);
   if (out) *out = s;
   return (off + 255) & ~(size_t)255;
 }
@@ -129,6 +131,7 @@ struct GeoTC {
   // pair's first round), the pair's supplier and consumer counts (the row
   // length and the number of rows)
   int kc_on, kc_ready, kc_m, kc_n;
+  double kc_gam;  // gamma_d of the certificate
   int fb[CAP];
   // staging: tensor-core operand tiles or FP32 fallback tiles (never both at
   // once); the launch reserves max(sizeof(tiles), A + stages * B) bytes
@@ -167,7 +170,6 @@ struct GeoTC {
   NNS_DEV const unsigned long long* nns_cached(CtaCore<C>& S, int mt, int nt) {
     const int tid = threadIdx.x, T = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const double rx = __uint_as_float(stat_rx), rx1 = __uint_as_float(stat_rx1), sxm = __uint_as_float(stat_sx);
     const int K = rk < mt ? rk : mt;
     for (int q = warp; q < nt; q += T / 32) {
       const int j = S.jidx[q];
@@ -179,7 +181,18 @@ struct GeoTC {
       int tp[BTC_K];
 #pragma unroll
       for (int k = 0; k < BTC_K; ++k) { tv[k] = CUDART_INF_F; tp[k] = -1; }
-      for (int p = lane; p < mt; p += 32) topk_insert(tv, tp, vrow[S.iidx[p]], p);
+      // four loads in flight per lane before the insertions that use them
+      for (int p0 = lane; p0 < mt; p0 += 128) {
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int p = p0 + 32 * u;
+          v[u] = p < mt ? vrow[S.iidx[p]] : CUDART_INF_F;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (p0 + 32 * u < mt) topk_insert(tv, tp, v[u], p0 + 32 * u);
+      }
       unsigned long long sel = ~0ULL, first = ~0ULL, kth = ~0ULL;
       for (int k = 0; k < K; ++k) {
         const unsigned long long mine =
@@ -224,9 +237,11 @@ struct GeoTC {
       bool cert = false;
       if (lane == 0) {
         const unsigned tb = (unsigned)(kth >> 32);
+        // (E of this consumer was computed once, when the cache was filled)
         const float tau = mt > K ? __uint_as_float((tb & 0x80000000u) ? (tb & 0x7fffffffu) : ~tb) : CUDART_INF_F;
-        cert = best != ~0ULL && certify(fmt, d, scr.ny_o[j], scr.yl2_o[j], scr.yl1_o[j], scr.sy_o[j], rx, rx1, sxm,
-                                        tau, __uint_as_float((unsigned)(best >> 32)));
+        cert = best != ~0ULL &&
+               (mt <= K || (double)__uint_as_float((unsigned)(best >> 32)) <
+                               certify_floor_from_E(scr.ny_o[j], tau, scr.e_o[j], kc_gam));
       }
       cert = __shfl_sync(0xffffffffu, cert, 0);
       if (cert) {
@@ -287,24 +302,55 @@ struct GeoTC {
     }
     __syncthreads();
     {
-      // one thread per row: scale and norms once, then every 16-byte block
+      // one warp per row: the lanes take the row's coordinates and 16-byte
+      // blocks (coalesced loads, all in flight at once), and the scale and
+      // norms are warp reductions.  Any summation order keeps the FP32
+      // squared norm within gamma_d |v|^2, the bound the certificate uses.
       const int srows = stiles * bn, qrows = qtiles * TC_BM;
       const int total = srows + qrows;
-      for (int row_id = tid; row_id < total; row_id += T) {
+      for (int row_id = warp; row_id < total; row_id += T / 32) {
         const bool sup = row_id < srows;
         const int p = sup ? row_id : row_id - srows;
         const int cnt = sup ? mt : nt;
         const float* row = p < cnt ? (sup ? x + (size_t)S.iidx[p] * d : y + (size_t)S.jidx[p] * d) : nullptr;
-        const float s = row_scale(row, d, fmt);
+        float mx = 0.f, a2f = 0.f, a1f = 0.f;
+        double a2 = 0.0, a1 = 0.0;
+        const bool want64 = row && !sup && fill;
+        if (row)
+          for (int k = lane; k < d; k += 32) {
+            const float v = row[k];
+            mx = fmaxf(mx, fabsf(v));
+            a2f = __fmaf_rn(v, v, a2f);
+            a1f = __fadd_rn(a1f, fabsf(v));
+            if (want64) {
+              a2 += (double)v * v;
+              a1 += fabs((double)v);
+            }
+          }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+          a2f = __fadd_rn(a2f, __shfl_xor_sync(0xffffffffu, a2f, o));
+          a1f = __fadd_rn(a1f, __shfl_xor_sync(0xffffffffu, a1f, o));
+          if (want64) {
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+          }
+        }
+        float s = 1.f;  // the row scale of FP16 / FP8 (as row_scale), from the warp's maximum
+        if (row && !fmt_is_bf16(fmt) && mx > 0.f) {
+          int e;
+          frexpf(mx, &e);
+          s = ldexpf(1.f, e - 8);
+        }
         const int rows = sup ? bn : TC_BM;
         uint8_t* tile = (sup ? scr.B : scr.A) + (size_t)(p / rows) * rows * kb;
-        for (int c = 0; c < nblk; ++c) pack_block(row, d, c, s, fmt, tile, rows, p % rows, sup);
-        {
+        for (int c = lane; c < nblk; c += 32) pack_block(row, d, c, s, fmt, tile, rows, p % rows, sup);
+        if (lane == 0) {
           float* nrm = sup ? scr.nrm_x : scr.nrm_y;
           float* scl = sup ? scr.scale_x : scr.scale_y;
           if (row) {
-            float l2sq, l1;
-            row_norms(row, d, l2sq, l1);
+            const float l2sq = a2f, l1 = a1f;
             nrm[p] = l2sq;
             scl[p] = s;
             if (sup) {
@@ -315,11 +361,6 @@ struct GeoTC {
             } else if (fill) {
               // what the certificate needs of this consumer in every round
               const int j = S.jidx[p];
-              double a2 = 0.0, a1 = 0.0;
-              for (int k = 0; k < d; ++k) {
-                a2 += (double)row[k] * row[k];
-                a1 += fabs((double)row[k]);
-              }
               scr.ny_o[j] = l2sq;
               scr.sy_o[j] = s;
               scr.yl2_o[j] = sqrt(a2) * (1 + 1e-12);
@@ -448,8 +489,18 @@ struct GeoTC {
     if (tid == 64) epi_acc += (unsigned)(qtiles * stiles);
     if (fill) {
       // the cache holds every v' of the pair; this and every later round
-      // are answered from it
-      if (tid == 0) kc_ready = 1;
+      // are answered from it.  The certificate's E of every consumer, once:
+      // the supplier maxima of this first round bound every later round's.
+      const double rx = __uint_as_float(stat_rx), rx1 = __uint_as_float(stat_rx1);
+      const double sxm = __uint_as_float(stat_sx);
+      for (int q = tid; q < nt; q += T) {
+        const int j = S.jidx[q];
+        scr.e_o[j] = certify_E(fmt, d, scr.ny_o[j], scr.yl2_o[j], scr.yl1_o[j], scr.sy_o[j], rx, rx1, sxm);
+      }
+      if (tid == 0) {
+        kc_gam = certify_gamma(d);
+        kc_ready = 1;
+      }
       __syncthreads();
       return nns_cached(S, mt, nt);
     }

@@ -300,15 +300,20 @@ NNS_DEV float quant_coeff(int fmt, float ny) {
 // below 2e-5 for d <= 300 and far below 1e-4 for any d the kernels serve).
 NNS_DEV float norm_up(float l2sq) { return sqrtf(l2sq) * (1.f + 1e-4f); }
 
-// The bound a best exact FP32 key must stay strictly below to be certified:
-// (ny + tau - E)(1 - gamma)(1 - 2^-30) when positive (the last factor covers
-// the rounding of this double-precision evaluation), else the non-positive
-// ny + tau - E itself, which no key (>= 0) is below.
-__host__ __device__ inline double certify_floor(int fmt, int d, double ny, double yl2, double yl1, double sy,
-                                                double rx, double rx1, double sxm, float tau) {
+// gamma_d of the sequential FP32 key (relative rounding bound).
+__host__ __device__ inline double certify_gamma(int d) {
+  const double u32 = 0x1p-24;
+  return d * u32 / (1.0 - d * u32);
+}
+
+// E of the certificate: everything but ny + tau, for one consumer against
+// suppliers with the given maxima (it does not depend on tau, so a solver
+// whose maxima stay fixed can compute it once per consumer).
+__host__ __device__ inline double certify_E(int fmt, int d, double ny, double yl2, double yl1, double sy, double rx,
+                                            double rx1, double sxm) {
   const double u32 = 0x1p-24;
   const double uq = quant_unit(fmt);
-  const double gam = d * u32 / (1.0 - d * u32);
+  const double gam = certify_gamma(d);
   const double kdim = (double)d * fmt_parts(fmt);  // length of the contraction
   // absolute rounding floor of one packed value (subnormals; times the row
   // scale for FP16 / FP8); BF16X3 rounds twice per coordinate
@@ -323,10 +328,22 @@ __host__ __device__ inline double certify_floor(int fmt, int d, double ny, doubl
   const double xt = nf * rx + eta_x * sqrt(kdim), yt = nf * yl2 + eta_y * sqrt(kdim);
   const double dot_acc = kdim * 0x1p-22 * xt * yt;
   const double c = 2.0 * quant_err(fmt) * yl2 * (1.0 + 1e-5);
-  const double E = gam * (ny + rx * rx) + 2.0 * (dot_eta + dot_acc) +
-                   2.0 * u32 * (rx * rx + 2.0 * xt * yt + c * rx) + 1e-30;
+  return gam * (ny + rx * rx) + 2.0 * (dot_eta + dot_acc) + 2.0 * u32 * (rx * rx + 2.0 * xt * yt + c * rx) +
+         1e-30;
+}
+
+// The bound a best exact FP32 key must stay strictly below to be certified:
+// (ny + tau - E)(1 - gamma)(1 - 2^-30) when positive (the last factor covers
+// the rounding of this double-precision evaluation), else the non-positive
+// ny + tau - E itself, which no key (>= 0) is below.
+__host__ __device__ inline double certify_floor_from_E(double ny, float tau, double E, double gam) {
   const double base = ny + (double)tau - E;  // <= 0: no key is certified (keys are >= 0)
   return base > 0.0 ? base * (1.0 - gam) * (1.0 - 0x1p-30) : base;
+}
+
+__host__ __device__ inline double certify_floor(int fmt, int d, double ny, double yl2, double yl1, double sy,
+                                                double rx, double rx1, double sxm, float tau) {
+  return certify_floor_from_E(ny, tau, certify_E(fmt, d, ny, yl2, yl1, sy, rx, rx1, sxm), certify_gamma(d));
 }
 
 __host__ __device__ inline bool certify(int fmt, int d, double ny, double yl2, double yl1, double sy, double rx,

@@ -34,7 +34,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "tests", "native", "certify_host.cu")
 BUILD = os.path.join(ROOT, "tests", "_build")
-FMT_F16, FMT_BF16, FMT_E4M3 = 0, 1, 2
+FMT_F16, FMT_BF16, FMT_E4M3, FMT_BF16X3 = 0, 1, 2, 3
 U32 = Fr(1, 2 ** 24)
 
 
@@ -59,7 +59,15 @@ def lib():
 
 
 def quant_unit(fmt):
-    return {FMT_BF16: Fr(1, 2 ** 8), FMT_F16: Fr(1, 2 ** 11), FMT_E4M3: Fr(1, 2 ** 4)}[fmt]
+    return {FMT_BF16: Fr(1, 2 ** 8), FMT_BF16X3: Fr(1, 2 ** 8), FMT_F16: Fr(1, 2 ** 11),
+            FMT_E4M3: Fr(1, 2 ** 4)}[fmt]
+
+
+def quant_err(fmt):
+    """Q with |<x~, y~> - <x, y>| <= Q sum |x_k y_k| (derived in the module
+    docstring of the emulation below for BF16X3)."""
+    u = quant_unit(fmt)
+    return u * u * (3 + 2 * u + 2 * u * u) if fmt == FMT_BF16X3 else 2 * u + u * u
 
 
 def exact_floor(fmt, d, ny, yl2, yl1, sy, rx, rx1, sxm, tau):
@@ -67,16 +75,24 @@ def exact_floor(fmt, d, ny, yl2, yl1, sy, rx, rx1, sxm, tau):
     only lowers the bound)."""
     ny, yl2, yl1, sy, rx, rx1, sxm, tau = (Fr(v) for v in (ny, yl2, yl1, sy, rx, rx1, sxm, tau))
     uq = quant_unit(fmt)
+    bf = fmt in (FMT_BF16, FMT_BF16X3)
     gam = d * U32 / (1 - d * U32)
-    eta_unit = {FMT_BF16: Fr(1, 2 ** 134), FMT_F16: Fr(1, 2 ** 25), FMT_E4M3: Fr(1, 2 ** 10)}[fmt]
-    eta_x = eta_unit * (1 if fmt == FMT_BF16 else sxm)
-    eta_y = eta_unit * (1 if fmt == FMT_BF16 else sy)
-    sqd = Fr(math.sqrt(d)) * (1 + Fr(1, 2 ** 50))
-    dot_eta = eta_x * (yl1 + eta_y * d) + eta_y * rx1 + eta_x * uq * yl1 + eta_y * uq * rx1
-    xt = (1 + uq) * rx + eta_x * sqd
-    yt = (1 + uq) * yl2 + eta_y * sqd
-    dot_acc = d * Fr(1, 2 ** 22) * xt * yt
-    c = 2 * (2 * uq + uq * uq) * yl2 * (1 + Fr(1, 10 ** 5))
+    kdim = 3 * d if fmt == FMT_BF16X3 else d
+    eta_unit = {FMT_BF16: Fr(1, 2 ** 134), FMT_BF16X3: Fr(1, 2 ** 132), FMT_F16: Fr(1, 2 ** 25),
+                FMT_E4M3: Fr(1, 2 ** 10)}[fmt]
+    eta_x = eta_unit * (1 if bf else sxm)
+    eta_y = eta_unit * (1 if bf else sy)
+    sqd = Fr(math.sqrt(kdim)) * (1 + Fr(1, 2 ** 50))
+    if fmt == FMT_BF16X3:
+        dot_eta = 3 * (eta_x * (2 * yl1 + eta_y * d) + 2 * eta_y * rx1)
+        nf = Fr(1.4142135623731) * (1 + uq) + uq + uq * uq   # >= sqrt(2) (1 + u) + u + u^2
+    else:
+        dot_eta = eta_x * (yl1 + eta_y * d) + eta_y * rx1 + eta_x * uq * yl1 + eta_y * uq * rx1
+        nf = 1 + uq
+    xt = nf * rx + eta_x * sqd
+    yt = nf * yl2 + eta_y * sqd
+    dot_acc = kdim * Fr(1, 2 ** 22) * xt * yt
+    c = 2 * quant_err(fmt) * yl2 * (1 + Fr(1, 10 ** 5))
     E = gam * (ny + rx * rx) + 2 * (dot_eta + dot_acc) + 2 * U32 * (rx * rx + 2 * xt * yt + c * rx) + Fr(1e-30)
     base = ny + tau - E
     return base * (1 - gam) if base > 0 else base
@@ -88,13 +104,13 @@ def random_inputs(rng, fmt, d):
     yl1 = yl2 * math.sqrt(d) * rng.uniform(0.3, 1.0)
     rx = float(np.float32(rng.uniform(0.1, 300.0)))
     rx1 = rx * math.sqrt(d) * rng.uniform(0.3, 1.0)
-    sy = 2.0 ** int(rng.integers(-8, 4)) if fmt != FMT_BF16 else 1.0
-    sxm = 2.0 ** int(rng.integers(-8, 4)) if fmt != FMT_BF16 else 1.0
+    sy = 2.0 ** int(rng.integers(-8, 4)) if fmt in (FMT_F16, FMT_E4M3) else 1.0
+    sxm = 2.0 ** int(rng.integers(-8, 4)) if fmt in (FMT_F16, FMT_E4M3) else 1.0
     tau = float(np.float32(rng.uniform(-2 * rx * yl2, rx * rx)))
     return ny, yl2, yl1, sy, rx, rx1, sxm, tau
 
 
-@pytest.mark.parametrize("fmt", [FMT_BF16, FMT_F16, FMT_E4M3])
+@pytest.mark.parametrize("fmt", [FMT_BF16, FMT_F16, FMT_E4M3, FMT_BF16X3])
 @pytest.mark.parametrize("d", [9, 64, 128, 300])
 def test_double_evaluation_stays_below_the_exact_bound(lib, fmt, d):
     rng = np.random.default_rng(fmt * 1000 + d)
@@ -109,7 +125,7 @@ def test_double_evaluation_stays_below_the_exact_bound(lib, fmt, d):
         assert abs(Fr(got) - want) <= abs(want) * Fr(1, 2 ** 28), (args, got, float(want))
 
 
-@pytest.mark.parametrize("fmt", [FMT_BF16, FMT_F16, FMT_E4M3])
+@pytest.mark.parametrize("fmt", [FMT_BF16, FMT_F16, FMT_E4M3, FMT_BF16X3])
 def test_keys_at_the_floor_are_refused(lib, fmt):
     """Near-ties of the certificate itself: best keys at, just above and just
     below the floor."""
@@ -176,20 +192,36 @@ def norm2_32(v):
     return acc
 
 
-def emulated_step(rng, X, y, K):
+def packed_rows(x, y, split):
+    """The operand rows the tensor cores see: one BF16 copy of each side, or
+    for the BF16X3 split (h = bf16(v), l = bf16(v - h), v - h exact in FP32)
+    the supplier row [h, l, h] against the consumer row [h, h, l].  With
+    v = h + l + e, |v - h| <= u|v|, |e| <= u^2 |v| and |l| <= (u + u^2)|v|
+    (u = 2^-8), their product <h,h> + <l,h> + <h,l> = <x - e_x, y - e_y> -
+    <l_x, l_y> is within u^2 (3 + 2u + 2u^2) sum |x_k y_k| of <x, y>."""
+    if not split:
+        return [bf16(v) for v in x], [bf16(v) for v in y]
+    hx = [bf16(v) for v in x]
+    lx = [bf16(float(np.float32(Fr(float(v)) - h))) for v, h in zip(x, hx)]
+    hy = [bf16(v) for v in y]
+    ly = [bf16(float(np.float32(Fr(float(v)) - h))) for v, h in zip(y, hy)]
+    return hx + lx + hx, hy + hy + ly
+
+
+def emulated_step(rng, X, y, K, split=False):
     """One consumer's reduced-precision NNS over suppliers X: returns the
     certified supplier or None, and the exact keys."""
     d = X.shape[1]
+    fmt = FMT_BF16X3 if split else FMT_BF16
     ny = norm2_32(y)
-    yq = [bf16(v) for v in y]
-    cy = f32(Fr(float(np.float32(2 * (2 * 2 ** -8 + 2 ** -16) * math.sqrt(float(ny)) * (1 + 1e-4)))))
+    cy = f32(Fr(float(np.float32(2 * float(quant_err(fmt)) * math.sqrt(float(ny)) * (1 + 1e-4)))))
     vals = []
     for i in range(X.shape[0]):
-        xq = [bf16(v) for v in X[i]]
+        xq, yq = packed_rows(X[i], y, split)
         dot = sum(a * b for a, b in zip(xq, yq))
         nxq = math.sqrt(float(sum(a * a for a in xq)))
         nyq = math.sqrt(float(sum(b * b for b in yq)))
-        err = Fr(d) * Fr(1, 2 ** 22) * Fr(nxq) * Fr(nyq)
+        err = Fr(len(xq)) * Fr(1, 2 ** 22) * Fr(nxq) * Fr(nyq)
         acc = f32(dot + err * Fr(float(rng.uniform(-1, 1))))          # somewhere inside the assumed bound
         nx = norm2_32(X[i])
         ns = f32(Fr(float(np.float32(math.sqrt(float(nx)) * (1 + 1e-4)))))
@@ -206,11 +238,31 @@ def emulated_step(rng, X, y, K):
     yl1 = sum(abs(float(v)) for v in y)
     rx = max(float(np.float32(math.sqrt(float(norm2_32(X[i]))) * (1 + 1e-4))) for i in range(X.shape[0]))
     rx1 = max(float(np.float32(sum(abs(float(v)) for v in X[i]) * (1 + 1e-4))) for i in range(X.shape[0]))
-    fl = exact_floor(FMT_BF16, d, float(ny), yl2, yl1, 1.0, rx, rx1, 1.0, float(tau))
+    fl = exact_floor(fmt, d, float(ny), yl2, yl1, 1.0, rx, rx1, 1.0, float(tau))
     return (best if keys[best] < fl else None), keys, cand
 
 
-def test_emulated_bf16_step_certifies_only_the_strict_nearest():
+def test_split_bf16_dot_product_error_bound():
+    """The BF16X3 bound on the dot product itself, on random and adversarial
+    rows (values at BF16 rounding boundaries)."""
+    rng = np.random.default_rng(3)
+    u = Fr(1, 2 ** 8)
+    for trial in range(200):
+        d = int(rng.integers(1, 40))
+        x = rng.normal(0, 1, d).astype(np.float32)
+        y = rng.normal(0, 1, d).astype(np.float32)
+        if trial % 2:   # values just off a BF16 tie
+            x = (np.round(x * 256) / 256 + np.float32(2 ** -9 + 2 ** -20)).astype(np.float32)
+        a, b = packed_rows(x, y, True)
+        got = sum(p * q for p, q in zip(a, b))
+        exact = sum(Fr(float(p)) * Fr(float(q)) for p, q in zip(x, y))
+        bound = quant_err(FMT_BF16X3) * sum(abs(Fr(float(p)) * Fr(float(q))) for p, q in zip(x, y))
+        assert abs(got - exact) <= bound, trial
+        assert quant_err(FMT_BF16X3) < 4 * u * u
+
+
+@pytest.mark.parametrize("split", [False, True], ids=["bf16", "bf16x3"])
+def test_emulated_bf16_step_certifies_only_the_strict_nearest(split):
     rng = np.random.default_rng(11)
     certified = 0
     for trial in range(30):
@@ -225,7 +277,7 @@ def test_emulated_bf16_step_certifies_only_the_strict_nearest():
         X[1] = base
         X[2] = (base + np.float32(1e-6)).astype(np.float32)
         X = X[rng.permutation(m)]
-        got, keys, cand = emulated_step(rng, X, y, K=4)
+        got, keys, cand = emulated_step(rng, X, y, K=4, split=split)
         if got is None:
             continue
         certified += 1

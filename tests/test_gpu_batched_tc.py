@@ -44,6 +44,15 @@ def test_batched_documents_reduced_precision(ctx, precision):
     assert stats["certified"] + stats["fallbacks"] > 0
 
 
+def test_batched_bf16x3_small_pairs(ctx):
+    batch = wl.random_batch(20, seed=12, d=48, lo=20, hi=400)
+    costs, stats = run_batch(ctx, batch, "l2", "bf16x3")
+    costs = costs.cpu().numpy()
+    for k in range(batch.num_pairs):
+        assert costs[k] == oracle.solve_pair(batch.pair(k), "l2").cost, k
+    assert stats["fallbacks"] <= 0.01 * (stats["certified"] + stats["fallbacks"]), stats
+
+
 @pytest.mark.parametrize("precision", ["bf16", "fp16", "fp8"])
 def test_batched_retrieval_reduced_precision(ctx, precision):
     batch = wl.retrieval(num_pairs=5, seed=9, lo=600, hi=2048)

@@ -311,7 +311,7 @@ def gpu_solve_prec(ctx, x, a, y, b, metric, precision):
                      metric=metric, precision=precision, plan=True)
 
 
-@pytest.mark.parametrize("precision", ["bf16", "fp16", "fp8"])
+@pytest.mark.parametrize("precision", ["bf16", "fp16", "fp8", "bf16x3"])
 def test_reduced_precision_small_pair(ctx, precision):
     p = wl.uniform_pair(300, 260, 64, 31, "dirichlet")
     ref = oracle.solve_pair(p, "l2")
@@ -319,9 +319,11 @@ def test_reduced_precision_small_pair(ctx, precision):
     assert_parity(res, ref)
 
 
-@pytest.mark.parametrize("precision", ["bf16", "fp16", "fp8"])
+@pytest.mark.parametrize("precision", ["bf16", "fp16", "fp8", "bf16x3"])
 @pytest.mark.parametrize("shape", ["gmm64", "sift128", "words300"])
 def test_reduced_precision_equals_fp32(ctx, precision, shape):
+    if precision == "bf16x3" and shape == "words300":
+        pytest.skip("BF16X3 serves d <= 128 (test_bf16x3_beyond_its_dimension_is_unsupported)")
     if shape == "gmm64":
         p = wl.gmm_pair(seed=2, n=5000, d=64)
     elif shape == "sift128":
@@ -337,6 +339,33 @@ def test_reduced_precision_equals_fp32(ctx, precision, shape):
         assert s["certified"] + s["fallbacks"] > 0
         if precision in ("bf16", "fp16") and shape != "words300":
             assert s["certified"] >= 0.5 * (s["certified"] + s["fallbacks"]), s
+
+
+def test_bf16x3_certifies_where_bf16_cannot(ctx):
+    # points far from the origin relative to their spread (a common offset
+    # of 20 against unit noise in d = 16): the error of one BF16 copy,
+    # about 2^-7 |x||y|, dwarfs the distance gaps and leaves the searches to
+    # the FP32 rescan; the split form's 3 * 2^-16 |x||y| certifies them
+    p = wl.uniform_pair(3000, 2500, 16, 4, "dirichlet")
+    rng = np.random.default_rng(4)
+    p.x = (20.0 + rng.normal(0, 1, p.x.shape)).astype(np.float32)
+    p.y = (20.0 + rng.normal(0, 1, p.y.shape)).astype(np.float32)
+    ref = oracle.solve_pair(p, "l2")
+    one = gpu_solve_prec(ctx, p.x, p.a, p.y, p.b, "l2", "bf16")
+    split = gpu_solve_prec(ctx, p.x, p.a, p.y, p.b, "l2", "bf16x3")
+    assert_parity(one, ref)
+    assert_parity(split, ref)
+    s = split.stats
+    assert s["fallbacks"] <= 0.05 * (s["certified"] + s["fallbacks"]), s
+    assert one.stats["fallbacks"] >= 0.5 * (one.stats["certified"] + one.stats["fallbacks"]), one.stats
+
+
+def test_bf16x3_beyond_its_dimension_is_unsupported(ctx):
+    from paper_2401_07378_gb300.nnsemd import NNSEMDError
+    p = wl.uniform_pair(40, 30, 300, 8)
+    with pytest.raises(NNSEMDError) as e:
+        gpu_solve_prec(ctx, p.x, p.a, p.y, p.b, "l2", "bf16x3")
+    assert e.value.status == 8
 
 
 def test_reduced_precision_rejections(ctx):
