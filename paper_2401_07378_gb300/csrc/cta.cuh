@@ -75,6 +75,9 @@ struct CtaCore {
   int mt, nt;
   unsigned nflow;
   double total;
+  // running totals handed back by the one-warp rounds (warp_rounds)
+  unsigned long long w_nnz;
+  long long w_rounds, w_pe;
 };
 
 struct CtaOut {
@@ -116,10 +119,17 @@ struct CtaOut {
 template <int D, int DP, bool L1, int CAP>
 struct GeoSmem {
   static constexpr int kDP = DP;
+  static constexpr int kD = D;
   static constexpr int kThreads = FIN_THREADS;  // threads of the CTA
   float xs[CAP * DP];
   float ys[CAP * DP];
   struct PX { float v[DP]; };
+
+  // FP32 decision key of supplier coordinates xv against consumer
+  // coordinates yv (the metric of this policy)
+  static NNS_DEV float key_pair(const float* xv, const float* yv) {
+    return L1 ? key32<METRIC_L1>(xv, yv, D) : key32<METRIC_SQL2>(xv, yv, D);
+  }
 
   NNS_DEV void load_x(int p, PX& r) const {
 #pragma unroll
@@ -496,8 +506,229 @@ NNS_DEV int block_scan_array(const int* in, int* out, int n, int* wt) {
   return tot;
 }
 
+// Active sets both at most warp_cap<Geo>() points go to warp_rounds (two
+// per lane).  128 (four per lane) was measured slower on the colour-transfer
+// tail than the 16-CTA cluster rounds for sets of 65..128 points (483 against
+// 517 pairs/s for the whole solve).
+template <class Geo>
+NNS_DEV constexpr int warp_cap() { return 64; }
+
+// The remaining rounds of a pair whose active sets both hold at most
+// warp_cap<Geo>() points, run by the calling warp alone (shared-memory
+// coordinates, kDP > 0): with a few dozen points left, a round of the
+// block-wide steps below is mostly barrier latency, and one warp needs none.
+// The same steps in the same arithmetic as cta_rounds, so every result is
+// identical:
+//   NNS     lane = consumer (q = lane, lane + 32, ...), a scan of every
+//           active supplier in ascending position, first minimum kept;
+//   order   every consumer's rank by (supplier position, serving key,
+//           position), counted against all consumers; the members of a
+//           group then lie in serving order, groups in supplier order;
+//   flow    lane = supplier, the FP64 residual chain over its group;
+//   compact ballots keep the points with residual left, in order.
+template <int CAP, class Geo>
+NNS_DEV void warp_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, unsigned long long& nnz,
+                         long long& rounds, long long& pair_evals, long long round_limit) {
+  constexpr int D = Geo::kD;
+  constexpr int WH = warp_cap<Geo>() / 32;  // points per lane
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const bool deferred = O.fl_i != nullptr;
+  for (;;) {
+    const int mt = S.mt, nt = S.nt;
+    if (mt == 0 || nt == 0) break;
+    if (rounds >= round_limit) {
+      if (lane == 0) atomicOr(O.err, EF_ITER);
+      break;
+    }
+    if (lane == 0) S.nflow = 0;
+    // ---- NNS: one pass over the suppliers (each read once, a broadcast)
+    // for all WH consumers of the lane
+    {
+      float yv[WH][D], best[WH];
+      int bp[WH];
+#pragma unroll
+      for (int h = 0; h < WH; ++h) {
+        const int q = lane + 32 * h;
+#pragma unroll
+        for (int k = 0; k < D; ++k) yv[h][k] = q < nt ? G.ys[q * Geo::kDP + k] : 0.f;
+        best[h] = CUDART_INF_F;
+        bp[h] = -1;
+      }
+      for (int p = 0; p < mt; ++p) {
+        float xv[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) xv[k] = G.xs[p * Geo::kDP + k];
+#pragma unroll
+        for (int h = 0; h < WH; ++h) {
+          const float v = Geo::key_pair(xv, yv[h]);
+          if (bp[h] < 0 || v < best[h]) { best[h] = v; bp[h] = p; }
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < WH; ++h) {
+        const int q = lane + 32 * h;
+        if (q < nt) S.nnk[q] = pack_key(best[h], (unsigned)bp[h]);
+      }
+    }
+    __syncwarp();
+    // ---- order: the serving key of every consumer, then its rank
+#pragma unroll
+    for (int h = 0; h < WH; ++h) {
+      const int q = lane + 32 * h;
+      if (q < nt) {
+        const unsigned long long key = S.nnk[q];
+        const unsigned ord = O.protocol == 1 ? rp_key32(O.seed, O.round_base + rounds, S.jidx[q])
+                                             : (unsigned)(key >> 32);
+        S.mem[q] = ((key & 0xffffffffULL) << 32) | ord;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < WH; ++h) {
+      const int q = lane + 32 * h;
+      if (q < nt) {
+        const unsigned long long mine = S.mem[q];
+        int rank = 0;
+        for (int u = 0; u < nt; ++u) {
+          const unsigned long long o = S.mem[u];
+          rank += (o < mine) | ((o == mine) & (u < q));
+        }
+        S.mem2[rank] = (unsigned long long)(unsigned)q;
+      }
+    }
+    // group bounds of every supplier: members of lower suppliers, its own
+#pragma unroll
+    for (int h = 0; h < WH; ++h) {
+      const int p = lane + 32 * h;
+      if (p < mt) {
+        int lo = 0, len = 0;
+        for (int u = 0; u < nt; ++u) {
+          const int pp = (int)(S.mem[u] >> 32);
+          lo += pp < p;
+          len += pp == p;
+        }
+        S.off[p] = lo;
+        S.cnt[p] = len;
+      }
+    }
+    __syncwarp();
+    // ---- flow, one supplier per lane
+#pragma unroll
+    for (int h = 0; h < WH; ++h) {
+      const int p = lane + 32 * h;
+      if (p < mt && S.cnt[p] > 0) {
+        const int b = S.off[p], en = b + S.cnt[p];
+        double s = S.sres[p];
+        for (int r = b; r < en; ++r) {
+          if (!residual_positive(s)) break;
+          const int q = (int)(S.mem2[r] & 0xffffffffULL);
+          double c = S.cres[q];
+          const double f = greedy_step(s, c);
+          S.cres[q] = c;
+          const unsigned k = atomicAdd(&S.nflow, 1u);
+          if (O.quiet) {
+          } else if (deferred) {
+            const unsigned long long slot = nnz + k;
+            if (O.fl_cap && (long long)slot >= O.fl_cap) {
+              atomicOr(O.err, EF_CAPACITY);
+              continue;
+            }
+            O.fl_i[slot] = S.iidx[p];
+            O.fl_j[slot] = S.jidx[q];
+            O.fl_f[slot] = f;
+            if (O.c_glob) O.c_glob[S.jidx[q]] = c;
+          } else {
+            // (mem and nnk are free again: the order is in mem2)
+            S.mem[k] = ((unsigned long long)p << 32) | (unsigned)q;
+            S.nnk[k] = (unsigned long long)__double_as_longlong(f);
+          }
+        }
+        S.sres[p] = s;
+        if (O.s_glob) O.s_glob[S.iidx[p]] = s;
+      }
+    }
+    __syncwarp();
+    const unsigned nflow = S.nflow;
+    if (!(deferred || O.quiet)) {
+      for (unsigned k = lane; k < nflow; k += 32) {
+        const unsigned long long pq = S.mem[k];
+        const int p = (int)(pq >> 32), q = (int)(pq & 0xffffffffULL);
+        const double f = __longlong_as_double((long long)S.nnk[k]);
+        const double term = __dmul_rn(f, G.dist64(S, p, q, metric));
+        const unsigned long long slot = nnz + k;
+        if (O.acc) xs_add(O.acc, term);
+        if (O.plan_i) {
+          if ((long long)slot < O.plan_cap) {
+            O.plan_i[slot] = S.iidx[p];
+            O.plan_j[slot] = S.jidx[q];
+            O.plan_f[slot] = f;
+          } else {
+            atomicOr(O.err, EF_CAPACITY);
+          }
+        }
+        if (O.c_glob) O.c_glob[S.jidx[q]] = S.cres[q];
+      }
+      __syncwarp();
+    }
+    nnz += nflow;
+    rounds += 1;
+    pair_evals += (long long)mt * nt;
+    // ---- compaction: every kept value is read before any is written
+    double sv[WH], cv[WH];
+    int iv[WH], jv[WH];
+    typename Geo::PX px[WH], py[WH];
+    unsigned bs[WH], bc[WH];
+#pragma unroll
+    for (int h = 0; h < WH; ++h) {
+      const int i = lane + 32 * h;
+      bool ks = false, kc = false;
+      if (i < mt) {
+        sv[h] = S.sres[i];
+        ks = residual_positive(sv[h]);
+        if (ks) { iv[h] = S.iidx[i]; G.load_x(i, px[h]); }
+      }
+      if (i < nt) {
+        cv[h] = S.cres[i];
+        kc = residual_positive(cv[h]);
+        if (kc) { jv[h] = S.jidx[i]; G.load_y(i, py[h]); }
+      }
+      bs[h] = __ballot_sync(0xffffffffu, ks);
+      bc[h] = __ballot_sync(0xffffffffu, kc);
+    }
+    __syncwarp();
+    int ps = 0, pc = 0;
+#pragma unroll
+    for (int h = 0; h < WH; ++h) {
+      if ((bs[h] >> lane) & 1u) {
+        const int dd = ps + __popc(bs[h] & lt);
+        S.sres[dd] = sv[h];
+        S.iidx[dd] = iv[h];
+        G.store_x(dd, px[h]);
+      }
+      if ((bc[h] >> lane) & 1u) {
+        const int dd = pc + __popc(bc[h] & lt);
+        S.cres[dd] = cv[h];
+        S.jidx[dd] = jv[h];
+        G.store_y(dd, py[h]);
+      }
+      ps += __popc(bs[h]);
+      pc += __popc(bc[h]);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      S.mt = ps;
+      S.nt = pc;
+    }
+    __syncwarp();
+  }
+}
+
 // Rounds of Alg. 1 until one active side is empty.  nnz, rounds and
 // pair_evals are running totals (identical in every thread on return).
+// With shared-memory coordinates, the rounds after both active sets fit
+// warp_cap<Geo>() run in warp 0 alone (warp_rounds) while the other warps
+// wait.
 template <int CAP, class Geo>
 NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, unsigned long long& nnz,
                         long long& rounds, long long& pair_evals, long long round_limit) {
@@ -510,6 +741,23 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
     if (rounds >= round_limit) {
       if (tid == 0) atomicOr(O.err, EF_ITER);
       break;
+    }
+    if constexpr (Geo::kDP > 0) {
+      if (mt <= warp_cap<Geo>() && nt <= warp_cap<Geo>()) {
+        if (tid < 32) {
+          warp_rounds(S, G, metric, O, nnz, rounds, pair_evals, round_limit);
+          if (tid == 0) {
+            S.w_nnz = nnz;
+            S.w_rounds = rounds;
+            S.w_pe = pair_evals;
+          }
+        }
+        __syncthreads();
+        nnz = S.w_nnz;
+        rounds = S.w_rounds;
+        pair_evals = S.w_pe;
+        break;
+      }
     }
     // group counters of this round (the NNS step ends with a barrier)
     for (int p = tid; p < mt; p += T) S.cnt[p] = 0;
