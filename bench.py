@@ -85,9 +85,9 @@ WORKLOADS = {
                    metric="l2", precision="fp32", batched=False),
     "gmm": dict(d=64, desc=("GMM pair: 262,144 x 262,144 points, d=64, 256-component mixture (means N(0,4I), "
                       "cov 0.25I), Dirichlet(0.5) weights, Euclidean, full plan; learned candidate proposal "
-                      "(MLP 64-256-256-4096 cells, trained on 200 seeded plain runs), BF16 contraction for the "
-                      "consumers it cannot certify"),
-                metric="l2", precision="bf16", batched=False, proposal="learned", steps=5),
+                      "(MLP 64-256-256-4096 cells, trained on 200 seeded plain runs), BF16 contraction (split "
+                      "high/low BF16 parts, BF16X3) for the consumers it cannot certify"),
+                metric="l2", precision="bf16x3", batched=False, proposal="learned", steps=5),
     "docs": dict(d=300, desc=("document kNN: 1 query vs 4,096 documents, word vectors d=300 N(0,1) L2-normalised "
                        "(50k vocabulary), lengths LogNormal(ln 60, 0.6) clipped to [20,500], Zipf(1.1) weights, "
                        "Euclidean, BF16 distances + FP32 re-rank, one persistent launch replayed as a CUDA graph"),

@@ -446,6 +446,7 @@ struct GeoTC {
         for (int st = 0; st < stiles; ++st, ++ea) {
           const unsigned b = ea & 1, v = ea >> 1;
           if (ok) ok = mbar_wait_bounded(&bar_acc_full[b], v & 1);
+          ok = __all_sync(0xffffffffu, ok);  // warp-uniform: the fill below synchronises the warp
           tc_fence_after();
           if (ok) {
             const float* nx = scr.nrm_x + (size_t)st * bn;
@@ -456,16 +457,41 @@ struct GeoTC {
             for (int c0 = 0; c0 < bn; c0 += 16) {
               uint32_t r[16];
               tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + b * (uint32_t)bn + (uint32_t)c0, r);
+              float val[16];
 #pragma unroll
               for (int e = 0; e < 16; ++e) {
                 const float acc = __uint_as_float(r[e]);
                 const float w = fmt_is_bf16(fmt) ? -2.f : -2.f * sy * sx[c0 + e];
-                const float val = __fmaf_rn(-cy, ns[c0 + e], __fmaf_rn(w, acc, nx[c0 + e]));
+                val[e] = __fmaf_rn(-cy, ns[c0 + e], __fmaf_rn(w, acc, nx[c0 + e]));
+              }
+              if (!fill) {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) topk_insert(tv, tp, val[e], st * bn + c0 + e);
+              } else if constexpr (CAP >= 2048) {
+                // transpose the warp's 32 rows x 16 columns through the
+                // fallback list's buffer (unused while the cache fills), so
+                // that each store instruction writes 16 consecutive columns of
+                // two rows instead of one column of 32 rows (XOR-swizzled:
+                // no bank conflicts either way)
+                float* tb = reinterpret_cast<float*>(fb) + (warp - 2) * 512;
+#pragma unroll
+                for (int e = 0; e < 16; ++e) tb[e * 32 + (lane ^ e)] = val[e];
+                __syncwarp();
+                const int e = lane & 15;
                 const int col = st * bn + c0 + e;
-                if (fill) {
-                  if (vrow && col < mt) vrow[S.iidx[col]] = val;
-                } else {
-                  topk_insert(tv, tp, val, col);
+                const int icol = col < mt ? S.iidx[col] : 0;
+#pragma unroll 4
+                for (int it = 0; it < 16; ++it) {
+                  const int rr = 2 * it + (lane >> 4);
+                  const int qq = qt * TC_BM + quarter * 32 + rr;
+                  if (qq < nt && col < mt) scr.vcache[(size_t)S.jidx[qq] * kc_m + icol] = tb[e * 32 + (rr ^ e)];
+                }
+                __syncwarp();
+              } else {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                  const int col = st * bn + c0 + e;
+                  if (vrow && col < mt) vrow[S.iidx[col]] = val[e];
                 }
               }
             }
