@@ -86,8 +86,9 @@ WORKLOADS = {
     "gmm": dict(d=64, desc=("GMM pair: 262,144 x 262,144 points, d=64, 256-component mixture (means N(0,4I), "
                       "cov 0.25I), Dirichlet(0.5) weights, Euclidean, full plan; learned candidate proposal "
                       "(MLP 64-256-256-4096 cells, trained on 200 seeded plain runs), BF16 contraction (split "
-                      "high/low BF16 parts, BF16X3) for the consumers it cannot certify"),
-                metric="l2", precision="bf16x3", batched=False, proposal="learned", steps=5),
+                      "high/low BF16 parts, BF16X3, top-8 candidates re-ranked in FP32) for the consumers it "
+                      "cannot certify"),
+                metric="l2", precision="bf16x3", batched=False, proposal="learned", steps=5, rerank_k=8),
     "docs": dict(d=300, desc=("document kNN: 1 query vs 4,096 documents, word vectors d=300 N(0,1) L2-normalised "
                        "(50k vocabulary), lengths LogNormal(ln 60, 0.6) clipped to [20,500], Zipf(1.1) weights, "
                        "Euclidean, BF16 distances + FP32 re-rank, one persistent launch replayed as a CUDA graph"),
@@ -360,7 +361,7 @@ def peaks():
         return {}
 
 
-def roofline(d: int, precision: str, pairs: int, launches: int, ms: float, total_ms: float, lowd: bool,
+def roofline(d: int, precision: str, rk: int, pairs: int, launches: int, ms: float, total_ms: float, lowd: bool,
              sms: int) -> dict:
     pk = peaks()
     per_launch_s = ms / 1e3 / max(launches, 1)
@@ -382,7 +383,7 @@ def roofline(d: int, precision: str, pairs: int, launches: int, ms: float, total
                  "; work = 2d flops per supplier/consumer pair" +
                  (" (the BF16X3 split runs 3 x 2d on the tensor pipe)" if precision == "bf16x3" else ""))
         bound = "tensor"
-        kernel = f"k_nns_tc<{precision}> (tcgen05 contraction + top-8 epilogue)"
+        kernel = f"k_nns_tc<{precision}> (tcgen05 contraction + top-{8 if 1 <= rk <= 8 else 16} epilogue)"
     achieved = ops / per_launch_s / 1e12 if ms > 0 else 0.0
     return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak if peak else None, "traffic": measured_traffic() if lowd else None,
@@ -390,6 +391,13 @@ def roofline(d: int, precision: str, pairs: int, launches: int, ms: float, total
             "share_of_step": ms / total_ms if total_ms else None}
 
 
+
+
+def rerank_k(args) -> int:
+    """Reduced-precision candidates re-ranked per consumer (0: the library's 16)."""
+    if getattr(args, "rerank_k", None) is not None:
+        return args.rerank_k
+    return WORKLOADS[args.workload].get("rerank_k", 0)
 
 
 def bench_config(args, ws: int) -> dict:
@@ -403,8 +411,8 @@ def bench_config(args, ws: int) -> dict:
     else:
         par = f"{ws} independent pairs, one per GPU"
     return {"workload": spec["desc"], "name": args.workload, "d": spec["d"], "metric": spec["metric"],
-            "precision": precision, "protocol": args.protocol, "l2": "flushed before every step (256 MiB write)",
-            "parallelism": par}
+            "precision": precision, "rerank_k": rerank_k(args), "protocol": args.protocol,
+            "l2": "flushed before every step (256 MiB write)", "parallelism": par}
 
 
 def run_ours(args) -> dict | None:
@@ -416,6 +424,7 @@ def run_ours(args) -> dict | None:
     precision = args.precision or spec["precision"]
     metric = spec["metric"]
     proposal = args.proposal or spec.get("proposal", "none")
+    rk = rerank_k(args)
     rank, ws, local = world()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -446,12 +455,13 @@ def run_ours(args) -> dict | None:
         bflags = ((nnsemd.FLAG_GRAPH if spec.get("graph") else 0) |
                   (nnsemd.FLAG_AUTOTUNE if spec.get("autotune") else 0))
         step = lambda: ctx.solve_batched(x, a, inp.x_off, y, b, inp.y_off, metric=metric, precision=precision,
-                                         costs=costs, stats=True, flags=bflags, protocol=args.protocol)[1]
+                                         rerank_k=rk, costs=costs, stats=True, flags=bflags,
+                                         protocol=args.protocol)[1]
         units = P
     else:
         def step():
-            r = ctx.solve(x, a, y, b, metric=metric, precision=precision, plan=True, flags=T, proposal=prop,
-                          protocol=args.protocol)
+            r = ctx.solve(x, a, y, b, metric=metric, precision=precision, rerank_k=rk, plan=True, flags=T,
+                          proposal=prop, protocol=args.protocol)
             return dict(r.stats, cost=r.cost)
         units = 1
 
@@ -506,7 +516,7 @@ def run_ours(args) -> dict | None:
             for dv, hv in ((dx, hx), (da, ha), (dy, hy), (db, hb)):
                 dv.copy_(hv, non_blocking=True)
             ctx.solve_batched(dx, da, inp.x_off, dy, db, inp.y_off, metric=metric, precision=precision,
-                              costs=costs, flags=bflags, protocol=args.protocol)
+                              rerank_k=rk, costs=costs, flags=bflags, protocol=args.protocol)
             hcosts.copy_(costs, non_blocking=True)
 
         for _ in range(min(args.warmup, 2)):
@@ -533,8 +543,8 @@ def run_ours(args) -> dict | None:
         plan_out = (torch.empty(cap, dtype=torch.int32).pin_memory(),
                     torch.empty(cap, dtype=torch.int32).pin_memory(),
                     torch.empty(cap, dtype=torch.float64).pin_memory())
-        host_step = lambda: ctx.solve_host(hx, ha, hy, hb, metric=metric, precision=precision, plan=True,
-                                           plan_out=plan_out, proposal=prop, protocol=args.protocol)
+        host_step = lambda: ctx.solve_host(hx, ha, hy, hb, metric=metric, precision=precision, rerank_k=rk,
+                                           plan=True, plan_out=plan_out, proposal=prop, protocol=args.protocol)
         for _ in range(min(args.warmup, 2)):
             host_step()
         torch.cuda.synchronize()
@@ -562,7 +572,8 @@ def run_ours(args) -> dict | None:
     if spec["batched"]:
         # the persistent batched kernel is the step: its NNS work against the
         # FP32 pipe, or the tensor pipe when the contraction runs there
-        rl = roofline(d, precision, agg.get("nns_kernel_pairs", 0) or (last or {}).get("pair_evals", 0) * args.steps,
+        rl = roofline(d, precision, rk,
+                      agg.get("nns_kernel_pairs", 0) or (last or {}).get("pair_evals", 0) * args.steps,
                       args.steps, total_ms, total_ms, lowd, sms)
         if precision == "fp32":
             rl["kernel"] = ("k_batched_lowd" if lowd else
@@ -573,13 +584,13 @@ def run_ours(args) -> dict | None:
     elif agg["nns_kernel_launches"] == 0 and agg["tail_kernel_ms"] > 0:
         # a pair small enough for one launch (k_solve_small): that kernel runs
         # every round, so its NNS work over its own time
-        rl = roofline(d, precision, (last or {}).get("pair_evals", 0) * args.steps, args.steps,
+        rl = roofline(d, precision, rk, (last or {}).get("pair_evals", 0) * args.steps, args.steps,
                       agg["tail_kernel_ms"], total_ms, lowd, sms)
         rl["kernel"] = "k_solve_small (the whole pair in one launch: every round's NNS, grouping, flow, compaction)"
         rl["traffic"] = None
         rl["note"] = "latency-bound: the NNS work is a small part of each round"
     else:
-        rl = roofline(d, precision, agg["nns_kernel_pairs"], agg["nns_kernel_launches"], agg["nns_kernel_ms"],
+        rl = roofline(d, precision, rk, agg["nns_kernel_pairs"], agg["nns_kernel_launches"], agg["nns_kernel_ms"],
                       total_ms, lowd, sms)
         if prop is not None:
             # the learned step scans candidates only: its rate is the full scan's work over its time
@@ -687,6 +698,8 @@ def main(argv=None):
     ap.add_argument("--pairs", type=int, default=None,
                     help="docs/retrieval: number of pairs (default the full workload; smaller is for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rerank-k", type=int, default=None,
+                    help="reduced precision: candidates re-ranked per consumer (default: the workload's)")
     args = ap.parse_args(argv)
     if args.steps is None:
         args.steps = WORKLOADS[args.workload].get("steps", 200)

@@ -115,9 +115,10 @@ typedef struct {
   int32_t rerank_k;             /* reduced precision: approximate candidates per consumer re-ranked with the
                                    exact FP32 key, 0..NNSEMD_MAX_RERANK_K (0 = all the scan keeps: 16 per
                                    supplier chunk in nnsemd_solve, 8 per pair in the batched kernel, which
-                                   also caps larger values at 8).  Fewer candidates make the re-rank
-                                   cheaper and the certificate weaker (more FP32 rescans); results never
-                                   change.  Outside the range: INVALID_ARG. */
+                                   also caps larger values at 8; with 1..8 the nnsemd_solve scan keeps
+                                   8 per chunk, half the list upkeep).  Fewer candidates make the scan
+                                   and the re-rank cheaper and the certificate weaker (more FP32
+                                   rescans); results never change.  Outside the range: INVALID_ARG. */
   int32_t flags;                /* NNSEMD_FLAG_* bits, 0 for none */
   const void *proposal;         /* learned candidate proposal, NULL = full scan */
   int32_t protocol;             /* nnsemd_protocol (0 = greedy) */

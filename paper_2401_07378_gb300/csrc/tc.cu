@@ -16,10 +16,12 @@
 // K2 k_nns_tc: a CTA owns 128 consumers (the MMA's M) and streams supplier
 // tiles of BN rows.  Warp 0 issues 1-D bulk copies (TMA) of the packed tiles
 // into a ring of shared-memory stages; warp 1 allocates tensor memory and
-// one elected thread issues tcgen05.mma for each tile into one of two FP32
-// accumulators (BN columns each); warps 2..5 read each accumulator row back
-// with tcgen05.ld (one consumer per thread) and update its top-K.  Every wait
-// on an mbarrier is bounded and raises EF_TIMEOUT instead of hanging.
+// one elected thread issues tcgen05.mma for each tile into a ring of
+// TC_NACC FP32 accumulators (BN columns each); warp 2 copies each tile's
+// column norms into a ring of its own; warps 3..10 read each accumulator
+// row back with tcgen05.ld (one consumer per thread, two warps per row, half
+// the columns each) and update its top-K.  Every wait on an mbarrier is
+// bounded and raises EF_TIMEOUT instead of hanging.
 #include <algorithm>
 
 #include "common.cuh"
@@ -32,7 +34,9 @@ namespace nnsemd {
 // epilogue warps (two per TMEM lane quarter)
 constexpr int TC_EPI_WARPS = 8;
 constexpr int TC_THREADS = 32 * (3 + TC_EPI_WARPS);
-constexpr int TC_SMEM_BUDGET = 180 * 1024;  // dynamic: A tile + B stages (static: norms, lists, staging)
+constexpr int TC_SMEM_BUDGET = 168 * 1024;  // dynamic: A tile + B stages (static: norms, lists, staging)
+constexpr int TC_NACC = 4;                  // FP32 accumulators in tensor memory (a ring of tiles in flight)
+constexpr int TC_NNRM = 8;                  // column-norm slots (a ring of its own, loaded ahead)
 
 // One thread per point (consecutive threads write consecutive 16-byte rows
 // of each column block).  Also writes, per point, the FP32 squared norm, the
@@ -91,25 +95,28 @@ struct TcArgs {
   int tiles_per_chunk;
   int num_tiles;           // supplier tiles in total
   int nt_pad;              // consumer count rounded up to TC_BM
-  float* cand_v;           // [chunks][nt_pad][TC_K] approximate values (v = |x|^2 - 2 <x~,y~>)
-  int* cand_p;             // [chunks][nt_pad][TC_K] supplier positions
+  float* cand_v;           // [chunks][nt_pad][KL] approximate values (v = |x|^2 - 2 <x~,y~>)
+  int* cand_p;             // [chunks][nt_pad][KL] supplier positions
   unsigned* err;
   const int* nq_dev;       // packed consumer rows in use (nullable: nt); tiles past it exit
 };
 
-template <int FMT, int BN>
+// KL: the length of each consumer's list (TC_K, or TC_K / 2 when at most
+// that many candidates are re-ranked: half the insertion work)
+template <int FMT, int BN, int KL>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t bar_full[8];
   __shared__ __align__(8) uint64_t bar_empty[8];
-  __shared__ __align__(8) uint64_t bar_acc_full[2];
-  __shared__ __align__(8) uint64_t bar_acc_empty[2];
-  __shared__ __align__(8) uint64_t bar_nrm_full[2];
+  __shared__ __align__(8) uint64_t bar_acc_full[TC_NACC];
+  __shared__ __align__(8) uint64_t bar_acc_empty[TC_NACC];
+  __shared__ __align__(8) uint64_t bar_nrm_full[TC_NNRM];
+  __shared__ __align__(8) uint64_t bar_nrm_empty[TC_NNRM];
   __shared__ __align__(8) uint64_t bar_a;
   __shared__ uint32_t tmem_slot;
-  __shared__ __align__(16) float nrm_buf[2][3][BN];     // per accumulator: |x|^2, |x| rounded up, scale
-  __shared__ float merge_v[TC_K][TC_BM];                // second-half top-K lists, merged at the end
-  __shared__ int merge_p[TC_K][TC_BM];
+  __shared__ __align__(16) float nrm_buf[TC_NNRM][3][BN];  // per tile in flight: |x|^2, |x| rounded up, scale
+  __shared__ float merge_v[KL][TC_BM];                  // second-half top-K lists, merged at the end
+  __shared__ int merge_p[KL][TC_BM];
   __shared__ float stage[16][TC_EPI_WARPS * 32];         // per epilogue thread: one 16-column block
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -125,8 +132,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
   uint8_t* sA = smem;
   uint8_t* sB = smem + a_bytes;
   const int NST = P.nstage;
-  constexpr uint32_t NCOLS = 2 * BN;  // two accumulators
+  constexpr uint32_t NCOLS = TC_NACC * BN;  // the accumulator ring
   constexpr uint32_t TMEM_ALLOC = NCOLS < 32 ? 32 : NCOLS;
+  static_assert(NCOLS <= 512 && (NCOLS & (NCOLS - 1)) == 0, "tensor memory holds 512 columns");
   constexpr uint32_t NRM_BYTES = 3 * BN * sizeof(float);
 
   if (threadIdx.x == 0) {
@@ -134,10 +142,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
       mbar_init(&bar_full[s], 1);
       mbar_init(&bar_empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < TC_NACC; ++b) {
       mbar_init(&bar_acc_full[b], 1);
-      mbar_init(&bar_acc_empty[b], TC_EPI_WARPS * 32);
-      mbar_init(&bar_nrm_full[b], 1);
+      mbar_init(&bar_acc_empty[b], TC_EPI_WARPS);  // one arrival per epilogue warp
+    }
+    for (int n = 0; n < TC_NNRM; ++n) {
+      mbar_init(&bar_nrm_full[n], 1);
+      mbar_init(&bar_nrm_empty[n], TC_EPI_WARPS);
     }
     mbar_init(&bar_a, 1);
     mbar_fence_init();
@@ -156,7 +167,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
       tma_load_1d(sA, P.A + (size_t)qtile * a_bytes, a_bytes, &bar_a);
       for (int t = 0; t < ntiles && ok; ++t) {
         const int s = t % NST, u = t / NST;
-        ok = mbar_wait_backoff(&bar_empty[s], (u & 1) ^ 1);
+        ok = mbar_wait_sleep(&bar_empty[s], (u & 1) ^ 1);
         if (!ok) break;
         mbar_expect_tx(&bar_full[s], b_bytes);
         tma_load_1d(sB + (size_t)s * b_bytes, P.B + (size_t)(t0 + t) * b_bytes, b_bytes, &bar_full[s]);
@@ -172,9 +183,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
       const uint32_t a0 = smem_u32(sA);
       for (int t = 0; t < ntiles && ok; ++t) {
         const int s = t % NST, u = t / NST;
-        const int b = t & 1, v = t >> 1;
-        ok = mbar_wait_backoff(&bar_full[s], u & 1);
-        if (ok) ok = mbar_wait_backoff(&bar_acc_empty[b], (v & 1) ^ 1);
+        const int b = t % TC_NACC, v = t / TC_NACC;
+        ok = mbar_wait_sleep(&bar_full[s], u & 1);
+        if (ok) ok = mbar_wait_sleep(&bar_acc_empty[b], (v & 1) ^ 1);
         if (!ok) break;
         tc_fence_after();
         const uint32_t b0 = smem_u32(sB + (size_t)s * b_bytes);
@@ -189,17 +200,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
       }
     }
   } else if (warp == 2) {
-    // ---------------- producer: the column norms of each tile, per accumulator ----------------
+    // ---------------- producer: the column norms of each tile, a ring of their own ----------------
     if (lane == 0) {
       for (int t = 0; t < ntiles && ok; ++t) {
-        const int b = t & 1, v = t >> 1;
-        ok = mbar_wait_backoff(&bar_acc_empty[b], (v & 1) ^ 1);
+        const int n = t % TC_NNRM, w = t / TC_NNRM;
+        ok = mbar_wait_sleep(&bar_nrm_empty[n], (w & 1) ^ 1);
         if (!ok) break;
         const size_t col = (size_t)(t0 + t) * BN;
-        mbar_expect_tx(&bar_nrm_full[b], NRM_BYTES);
-        tma_load_1d(nrm_buf[b][0], P.nrm_x + col, BN * sizeof(float), &bar_nrm_full[b]);
-        tma_load_1d(nrm_buf[b][1], P.nrm_sx + col, BN * sizeof(float), &bar_nrm_full[b]);
-        tma_load_1d(nrm_buf[b][2], P.scale_x + col, BN * sizeof(float), &bar_nrm_full[b]);
+        mbar_expect_tx(&bar_nrm_full[n], NRM_BYTES);
+        tma_load_1d(nrm_buf[n][0], P.nrm_x + col, BN * sizeof(float), &bar_nrm_full[n]);
+        tma_load_1d(nrm_buf[n][1], P.nrm_sx + col, BN * sizeof(float), &bar_nrm_full[n]);
+        tma_load_1d(nrm_buf[n][2], P.scale_x + col, BN * sizeof(float), &bar_nrm_full[n]);
       }
     }
   } else {
@@ -214,21 +225,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
     const int q = qtile * TC_BM + row;
     const float sy = (q < P.nt) ? P.scale_y[q] : 1.f;
     const float cy = quant_coeff(FMT, (q < P.nt) ? P.nrm_y[q] : 0.f);
-    float tv[TC_K];
-    int tp[TC_K];
+    float tv[KL];
+    int tp[KL];
 #pragma unroll
-    for (int k = 0; k < TC_K; ++k) { tv[k] = CUDART_INF_F; tp[k] = -1; }
+    for (int k = 0; k < KL; ++k) { tv[k] = CUDART_INF_F; tp[k] = -1; }
     constexpr int HALF = BN / 2;
     for (int t = 0; t < ntiles; ++t) {
-      const int b = t & 1, v = t >> 1;
-      if (ok) ok = mbar_wait_bounded(&bar_acc_full[b], v & 1);
-      if (ok) ok = mbar_wait_bounded(&bar_nrm_full[b], v & 1);
+      const int b = t % TC_NACC, v = t / TC_NACC;
+      const int n = t % TC_NNRM, w = t / TC_NNRM;
+      if (ok) ok = mbar_wait_sleep(&bar_acc_full[b], v & 1, 200u);
+      if (ok) ok = mbar_wait_sleep(&bar_nrm_full[n], w & 1, 200u);
       tc_fence_after();
       if (ok) {
         const int tile = t0 + t;
-        const float* nx = nrm_buf[b][0];
-        const float* ns = nrm_buf[b][1];
-        const float* sx = nrm_buf[b][2];
+        const float* nx = nrm_buf[n][0];
+        const float* ns = nrm_buf[n][1];
+        const float* sx = nrm_buf[n][2];
         // all of this warp's columns of the accumulator at once (one wait
         // for NB loads in flight), then two columns per packed FP32x2 step
         constexpr int NB = HALF / 16;
@@ -246,7 +258,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
           const int c0 = half * HALF + 16 * bb;
           const uint32_t(&r)[16] = rr[bb];
           float val[16];
-          float mn = CUDART_INF_F;
 #pragma unroll
           for (int k = 0; k < 16; k += 4) {
             const float4 vx = *reinterpret_cast<const float4*>(nx + c0 + k);
@@ -266,12 +277,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
             val[k + 1] = f2_hi(v01);
             val[k + 2] = f2_lo(v23);
             val[k + 3] = f2_hi(v23);
-            mn = fmin3(mn, fminf(val[k], val[k + 1]), fminf(val[k + 2], val[k + 3]));
           }
-          if (mn < tv[TC_K - 1]) {
+          // the block's minimum as a tree of three-input minima (8 for 16)
+          const float mn =
+              fminf(fmin3(fmin3(val[0], val[1], val[2]), fmin3(val[3], val[4], val[5]), fmin3(val[6], val[7], val[8])),
+                    fmin3(fmin3(val[9], val[10], val[11]), fmin3(val[12], val[13], val[14]), val[15]));
+          if (mn < tv[KL - 1]) {
             // the few columns that beat the current K-th value: park the
             // block's values, then one (rolled) insertion per such column
-            const float thr = tv[TC_K - 1];
+            const float thr = tv[KL - 1];
             unsigned msk = 0;
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
@@ -288,12 +302,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
         }
       }
       tc_fence_before();
-      mbar_arrive(&bar_acc_empty[b]);
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&bar_acc_empty[b]);
+        mbar_arrive(&bar_nrm_empty[n]);
+      }
     }
     // merge: the second-half warps hand their lists to the first-half warps
     if (half == 1) {
 #pragma unroll
-      for (int k = 0; k < TC_K; ++k) {
+      for (int k = 0; k < KL; ++k) {
         merge_v[k][row] = tv[k];
         merge_p[k][row] = tp[k];
       }
@@ -301,11 +319,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
     asm volatile("bar.sync 1, %0;" ::"r"(TC_EPI_WARPS * 32) : "memory");
     if (half == 0) {
 #pragma unroll
-      for (int k = 0; k < TC_K; ++k) topk_insert(tv, tp, merge_v[k][row], merge_p[k][row]);
+      for (int k = 0; k < KL; ++k) topk_insert(tv, tp, merge_v[k][row], merge_p[k][row]);
       if (q < P.nt) {
-        const size_t o = ((size_t)blockIdx.y * P.nt_pad + q) * TC_K;
+        const size_t o = ((size_t)blockIdx.y * P.nt_pad + q) * KL;
 #pragma unroll
-        for (int k = 0; k < TC_K; ++k) {
+        for (int k = 0; k < KL; ++k) {
           P.cand_v[o + k] = tv[k];
           P.cand_p[o + k] = tp[k];
         }
@@ -342,7 +360,8 @@ struct RerankArgs {
   unsigned long long* nnear;  // consumers whose exact best differs from the approximate best
   const int* sel;       // packed row -> consumer position (nullable: identity)
   const int* nq_dev;    // rows in use (nullable: nt)
-  int rk;               // candidates of each chunk re-ranked (1 .. TC_K)
+  int rk;               // candidates of each chunk re-ranked (1 .. kl)
+  int kl;               // list length of each chunk (the stride of cand_v / cand_p)
 };
 
 // One warp per packed consumer row.  The first rk candidates of every chunk
@@ -363,7 +382,7 @@ __global__ void k_rerank_certify(RerankArgs R) {
   float tau = CUDART_INF_F;  // smallest chunk threshold (rk-th value of each chunk)
   for (int c = lane; c < ncand; c += 32) {
     const int chunk = c / rk, k = c % rk;
-    const size_t o = ((size_t)chunk * R.nt_pad + r) * TC_K + k;
+    const size_t o = ((size_t)chunk * R.nt_pad + r) * R.kl + k;
     const int p = R.cand_p[o];
     if (k == rk - 1) tau = fminf(tau, R.cand_v[o]);
     if (p < 0) continue;
@@ -425,12 +444,19 @@ bool tc_supported(int d, int precision) {
   return a_bytes + b_bytes <= (size_t)TC_SMEM_BUDGET;
 }
 
-template <int FMT, int BN>
+template <int FMT, int BN, int KL>
 static int launch_tc_t(const TcArgs& P, dim3 grid, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_nns_tc<FMT, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_nns_tc<FMT, BN, KL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return -1;
-  k_nns_tc<FMT, BN><<<grid, TC_THREADS, smem, st>>>(P);
+  k_nns_tc<FMT, BN, KL><<<grid, TC_THREADS, smem, st>>>(P);
   return 0;
+}
+
+template <int FMT>
+static int launch_tc_f(const TcArgs& P, int bn, int kl, dim3 grid, size_t smem, cudaStream_t st) {
+  if (bn == 128) return kl == TC_K ? launch_tc_t<FMT, 128, TC_K>(P, grid, smem, st)
+                                   : launch_tc_t<FMT, 128, TC_K / 2>(P, grid, smem, st);
+  return kl == TC_K ? launch_tc_t<FMT, 64, TC_K>(P, grid, smem, st) : launch_tc_t<FMT, 64, TC_K / 2>(P, grid, smem, st);
 }
 
 // With sel / nsel_dev the consumers are the positions sel[0 .. *nsel_dev)
@@ -467,6 +493,9 @@ int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int preci
   if (nstage > 4) nstage = 4;
   if (nstage < 1) return -2;
   const int nt_pad = qtiles * TC_BM;
+  // candidates re-ranked per chunk; the scan keeps half the lists when that suffices
+  const int rk = T.rerank_k >= 1 && T.rerank_k <= TC_K ? T.rerank_k : TC_K;
+  const int kl = rk <= TC_K / 2 ? TC_K / 2 : TC_K;
   TcArgs P{T.A,      T.B,      T.nrm_x,    T.nrm_sx, T.nrm_y,  T.scale_x,  T.scale_y, nt, mt,
            kb,       bn,       nstage,     per,      stiles,   nt_pad,     T.cand_v,  T.cand_p, &B.st->err,
            nsel_dev};
@@ -475,23 +504,21 @@ int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int preci
   int rc;
   if (T.ev0) cudaEventRecord(T.ev0, st);
   if (fmt == FMT_BF16)
-    rc = bn == 128 ? launch_tc_t<FMT_BF16, 128>(P, grid, smem, st) : launch_tc_t<FMT_BF16, 64>(P, grid, smem, st);
+    rc = launch_tc_f<FMT_BF16>(P, bn, kl, grid, smem, st);
   else if (fmt == FMT_BF16X3)
-    rc = bn == 128 ? launch_tc_t<FMT_BF16X3, 128>(P, grid, smem, st)
-                   : launch_tc_t<FMT_BF16X3, 64>(P, grid, smem, st);
+    rc = launch_tc_f<FMT_BF16X3>(P, bn, kl, grid, smem, st);
   else if (fmt == FMT_F16)
-    rc = bn == 128 ? launch_tc_t<FMT_F16, 128>(P, grid, smem, st) : launch_tc_t<FMT_F16, 64>(P, grid, smem, st);
+    rc = launch_tc_f<FMT_F16>(P, bn, kl, grid, smem, st);
   else
-    rc = bn == 128 ? launch_tc_t<FMT_E4M3, 128>(P, grid, smem, st) : launch_tc_t<FMT_E4M3, 64>(P, grid, smem, st);
+    rc = launch_tc_f<FMT_E4M3>(P, bn, kl, grid, smem, st);
   if (rc) return rc;
   if (T.ev1) cudaEventRecord(T.ev1, st);
   // exact re-rank and certificate
   if (cudaMemsetAsync(T.nfallback, 0, sizeof(int), st) != cudaSuccess) return -1;
-  const int rk = T.rerank_k >= 1 && T.rerank_k <= TC_K ? T.rerank_k : TC_K;
   RerankArgs R{B.x,      B.y,        B.ia[B.cur], B.ja[B.cur], B.d,       nt,          nt_pad,
                chunks,   fmt,        T.cand_v,    T.cand_p,    T.nrm_y,   T.scale_y,   T.stats,
                B.nnkey,  T.fallback, T.nfallback, &B.st->certified, &B.st->fallbacks, &B.st->near_ties,
-               sel,      nsel_dev,   rk};
+               sel,      nsel_dev,   rk,          kl};
   k_rerank_certify<<<(nt + 7) / 8, 256, 0, st>>>(R);
   // FP32 scan of the consumers that were not certified
   launch_nns_f32(B, mt, nt, T.fallback, T.nfallback, st);

@@ -156,6 +156,23 @@ NNS_DEV void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
+// Wait for a phase, suspended in the barrier between polls: each try_wait
+// carries a time hint of hint_ns, so the thread sleeps until the phase
+// completes (and wakes at once then) or the hint runs out.  Gives up after
+// `limit` polls (about a second with the default hint).
+NNS_DEV bool mbar_wait_sleep(uint64_t* bar, unsigned parity, unsigned hint_ns = 1000u, unsigned limit = 1u << 20) {
+  for (unsigned it = 0; it < limit; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
 NNS_DEV void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
