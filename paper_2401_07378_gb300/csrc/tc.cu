@@ -18,10 +18,10 @@
 // into a ring of shared-memory stages; warp 1 allocates tensor memory and
 // one elected thread issues tcgen05.mma for each tile into a ring of
 // TC_NACC FP32 accumulators (BN columns each); warp 2 copies each tile's
-// column norms into a ring of its own; warps 3..10 read each accumulator
-// row back with tcgen05.ld (one consumer per thread, two warps per row, half
-// the columns each) and update its top-K.  Every wait on an mbarrier is
-// bounded and raises EF_TIMEOUT instead of hanging.
+// column norms into a ring of its own; the warps from 3 on read each
+// accumulator row back with tcgen05.ld (one consumer per thread, two or four
+// warps per row, a share of the columns each) and update its top-K.  Every
+// wait on an mbarrier is bounded and raises EF_TIMEOUT instead of hanging.
 #include <algorithm>
 
 #include "common.cuh"
@@ -31,12 +31,18 @@
 namespace nnsemd {
 
 // warp 0 operand copies, warp 1 MMA, warp 2 column-norm copies, then the
-// epilogue warps (two per TMEM lane quarter)
-constexpr int TC_EPI_WARPS = 8;
-constexpr int TC_THREADS = 32 * (3 + TC_EPI_WARPS);
-constexpr int TC_SMEM_BUDGET = 168 * 1024;  // dynamic: A tile + B stages (static: norms, lists, staging)
+// epilogue warps (EW / 4 per TMEM lane quarter, each a share of the columns).
+// Sixteen epilogue warps (more latency hidden) where their registers fit:
+// BF16 operands (no per-column scale) and lists of 8.
+__host__ __device__ constexpr int tc_epi_warps(int fmt, int kl) { return fmt_is_bf16(fmt) && kl <= 8 ? 16 : 8; }
+__host__ __device__ constexpr int tc_threads(int fmt, int kl) { return 32 * (3 + tc_epi_warps(fmt, kl)); }
+// A tile + one B stage must fit in this much dynamic shared memory (what
+// every instantiation has left beside its static arrays); more stages use
+// what the instantiation actually has left.
+constexpr int TC_SMEM_BUDGET = 150 * 1024;
+constexpr int TC_SMEM_MAX = 227 * 1024;  // per block, static + dynamic
 constexpr int TC_NACC = 4;                  // FP32 accumulators in tensor memory (a ring of tiles in flight)
-constexpr int TC_NNRM = 8;                  // column-norm slots (a ring of its own, loaded ahead)
+constexpr int TC_NNRM = 4;                  // column-norm slots (a ring of its own, loaded ahead)
 
 // One thread per point (consecutive threads write consecutive 16-byte rows
 // of each column block).  Also writes, per point, the FP32 squared norm, the
@@ -104,7 +110,11 @@ struct TcArgs {
 // KL: the length of each consumer's list (TC_K, or TC_K / 2 when at most
 // that many candidates are re-ranked: half the insertion work)
 template <int FMT, int BN, int KL>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
+__global__ void __launch_bounds__(tc_threads(FMT, KL), 1) k_nns_tc(TcArgs P) {
+  constexpr int EW = tc_epi_warps(FMT, KL);
+  constexpr int PARTS = EW / 4;      // epilogue warps per TMEM lane quarter
+  constexpr int CPART = BN / PARTS;  // columns of a tile per epilogue warp
+  static_assert(CPART % 16 == 0, "whole 16-column blocks per epilogue warp");
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t bar_full[8];
   __shared__ __align__(8) uint64_t bar_empty[8];
@@ -115,9 +125,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
   __shared__ __align__(8) uint64_t bar_a;
   __shared__ uint32_t tmem_slot;
   __shared__ __align__(16) float nrm_buf[TC_NNRM][3][BN];  // per tile in flight: |x|^2, |x| rounded up, scale
-  __shared__ float merge_v[KL][TC_BM];                  // second-half top-K lists, merged at the end
-  __shared__ int merge_p[KL][TC_BM];
-  __shared__ float stage[16][TC_EPI_WARPS * 32];         // per epilogue thread: one 16-column block
+  // per epilogue thread: one 16-column block (at the end: the lists of
+  // parts 1.. of each row, merged into part 0's)
+  __shared__ __align__(16) float stage[16][EW * 32];
+  __shared__ int tag_pos[TagList<KL>::NTAG][EW * 32];  // per epilogue thread: tag -> position
+  static_assert(2 * (PARTS - 1) * KL * TC_BM <= 16 * EW * 32, "the merge lists fit in the staging area");
+  float* const merge_v = &stage[0][0];                                              // [PARTS-1][KL][TC_BM]
+  int* const merge_p = reinterpret_cast<int*>(&stage[0][0]) + (PARTS - 1) * KL * TC_BM;  // same shape
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int qtile = blockIdx.x;
@@ -144,11 +158,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
     }
     for (int b = 0; b < TC_NACC; ++b) {
       mbar_init(&bar_acc_full[b], 1);
-      mbar_init(&bar_acc_empty[b], TC_EPI_WARPS);  // one arrival per epilogue warp
+      mbar_init(&bar_acc_empty[b], EW);  // one arrival per epilogue warp
     }
     for (int n = 0; n < TC_NNRM; ++n) {
       mbar_init(&bar_nrm_full[n], 1);
-      mbar_init(&bar_nrm_empty[n], TC_EPI_WARPS);
+      mbar_init(&bar_nrm_empty[n], EW);
     }
     mbar_init(&bar_a, 1);
     mbar_fence_init();
@@ -215,21 +229,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
     }
   } else {
     // ---------------- epilogue: TMEM -> top-K per consumer ----------------
-    // Two warps per TMEM lane quarter; each takes half of the tile's columns
-    // and keeps its own top-K, and the halves merge at the end.
+    // PARTS warps per TMEM lane quarter; each takes CPART of the tile's
+    // columns and keeps its own top-K, and the parts merge at the end.
     const int e = warp - 3;
     const int etid = e * 32 + lane;
     const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
-    const int half = e >> 2;
+    const int part = e >> 2;
     const int row = quarter * 32 + lane;
     const int q = qtile * TC_BM + row;
     const float sy = (q < P.nt) ? P.scale_y[q] : 1.f;
     const float cy = quant_coeff(FMT, (q < P.nt) ? P.nrm_y[q] : 0.f);
+    // the list: tagged values (tc_common.cuh), ascending, +inf while not full
     float tv[KL];
-    int tp[KL];
+    unsigned used = 0u;  // tags held by entries of the list
 #pragma unroll
-    for (int k = 0; k < KL; ++k) { tv[k] = CUDART_INF_F; tp[k] = -1; }
-    constexpr int HALF = BN / 2;
+    for (int k = 0; k < KL; ++k) tv[k] = CUDART_INF_F;
+    int* const table = &tag_pos[0][etid];
+    constexpr int TSTRIDE = EW * 32;
     for (int t = 0; t < ntiles; ++t) {
       const int b = t % TC_NACC, v = t / TC_NACC;
       const int n = t % TC_NNRM, w = t / TC_NNRM;
@@ -243,11 +259,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
         const float* sx = nrm_buf[n][2];
         // all of this warp's columns of the accumulator at once (one wait
         // for NB loads in flight), then two columns per packed FP32x2 step
-        constexpr int NB = HALF / 16;
+        constexpr int NB = CPART / 16;
         uint32_t rr[NB][16];
 #pragma unroll
         for (int bb = 0; bb < NB; ++bb)
-          tmem_ld16_async(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + half * HALF + 16 * bb),
+          tmem_ld16_async(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN + part * CPART + 16 * bb),
                           rr[bb]);
         tmem_ld_wait(rr);
         const unsigned long long mcy2 = f2_pack(-cy, -cy);
@@ -255,7 +271,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
         const unsigned long long wsy2 = f2_pack(-2.f * sy, -2.f * sy);
 #pragma unroll
         for (int bb = 0; bb < NB; ++bb) {
-          const int c0 = half * HALF + 16 * bb;
+          const int c0 = part * CPART + 16 * bb;
           const uint32_t(&r)[16] = rr[bb];
           float val[16];
 #pragma unroll
@@ -283,8 +299,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
               fminf(fmin3(fmin3(val[0], val[1], val[2]), fmin3(val[3], val[4], val[5]), fmin3(val[6], val[7], val[8])),
                     fmin3(fmin3(val[9], val[10], val[11]), fmin3(val[12], val[13], val[14]), val[15]));
           if (mn < tv[KL - 1]) {
-            // the few columns that beat the current K-th value: park the
+            // the few columns that beat the current K-th entry: park the
             // block's values, then one (rolled) insertion per such column
+            // that still beats it
             const float thr = tv[KL - 1];
             unsigned msk = 0;
 #pragma unroll
@@ -296,7 +313,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
             while (msk) {
               const int k = __ffs(msk) - 1;
               msk &= msk - 1;
-              topk_insert(tv, tp, stage[k][etid], tile * BN + c0 + k);
+              const float vk = stage[k][etid];
+              if (vk < tv[KL - 1]) tag_insert<KL>(tv, used, table, TSTRIDE, vk, tile * BN + c0 + k);
             }
           }
         }
@@ -308,18 +326,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_nns_tc(TcArgs P) {
         mbar_arrive(&bar_nrm_empty[n]);
       }
     }
-    // merge: the second-half warps hand their lists to the first-half warps
-    if (half == 1) {
+    // untag: positions from the table, values floored to lower bounds of
+    // the exact approximate values (every bound taken from a list is then
+    // at most the value it stands for)
+    int tp[KL];
+#pragma unroll
+    for (int k = 0; k < KL; ++k) {
+      const bool real = tv[k] != CUDART_INF_F;
+      tp[k] = real ? table[(__float_as_uint(tv[k]) & TagList<KL>::MASK) * TSTRIDE] : -1;
+      if (real) tv[k] = tag_floor(tv[k], TagList<KL>::MASK);
+    }
+    // merge: parts 1.. hand their lists to part 0 (through the staging
+    // area, once every epilogue warp has left it)
+    asm volatile("bar.sync 1, %0;" ::"r"(EW * 32) : "memory");
+    if (part > 0) {
+      const int o = (part - 1) * KL * TC_BM;
 #pragma unroll
       for (int k = 0; k < KL; ++k) {
-        merge_v[k][row] = tv[k];
-        merge_p[k][row] = tp[k];
+        merge_v[o + k * TC_BM + row] = tv[k];
+        merge_p[o + k * TC_BM + row] = tp[k];
       }
     }
-    asm volatile("bar.sync 1, %0;" ::"r"(TC_EPI_WARPS * 32) : "memory");
-    if (half == 0) {
+    asm volatile("bar.sync 1, %0;" ::"r"(EW * 32) : "memory");
+    if (part == 0) {
+      for (int pp = 0; pp < PARTS - 1; ++pp) {
+        const int o = pp * KL * TC_BM;
 #pragma unroll
-      for (int k = 0; k < KL; ++k) topk_insert(tv, tp, merge_v[k][row], merge_p[k][row]);
+        for (int k = 0; k < KL; ++k) topk_insert(tv, tp, merge_v[o + k * TC_BM + row], merge_p[o + k * TC_BM + row]);
+      }
       if (q < P.nt) {
         const size_t o = ((size_t)blockIdx.y * P.nt_pad + q) * KL;
 #pragma unroll
@@ -444,19 +478,32 @@ bool tc_supported(int d, int precision) {
   return a_bytes + b_bytes <= (size_t)TC_SMEM_BUDGET;
 }
 
+// B stages (up to 4) in what the instantiation leaves beside its static
+// shared memory; the first launch of each instantiation sets the attribute.
 template <int FMT, int BN, int KL>
-static int launch_tc_t(const TcArgs& P, dim3 grid, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_nns_tc<FMT, BN, KL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return -1;
-  k_nns_tc<FMT, BN, KL><<<grid, TC_THREADS, smem, st>>>(P);
+static int launch_tc_t(TcArgs P, dim3 grid, size_t a_bytes, size_t b_bytes, cudaStream_t st) {
+  static const int static_smem = [] {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, k_nns_tc<FMT, BN, KL>) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(k_nns_tc<FMT, BN, KL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TC_SMEM_MAX - 1024 - (int)fa.sharedSizeBytes) != cudaSuccess)
+      return -1;
+    return (int)fa.sharedSizeBytes;
+  }();
+  if (static_smem < 0) return -1;
+  const size_t avail = (size_t)(TC_SMEM_MAX - 1024 - static_smem);
+  if (a_bytes + b_bytes > avail) return -2;
+  P.nstage = (int)std::min<size_t>(4, (avail - a_bytes) / b_bytes);
+  const size_t smem = a_bytes + (size_t)P.nstage * b_bytes;
+  k_nns_tc<FMT, BN, KL><<<grid, tc_threads(FMT, KL), smem, st>>>(P);
   return 0;
 }
 
 template <int FMT>
-static int launch_tc_f(const TcArgs& P, int bn, int kl, dim3 grid, size_t smem, cudaStream_t st) {
-  if (bn == 128) return kl == TC_K ? launch_tc_t<FMT, 128, TC_K>(P, grid, smem, st)
-                                   : launch_tc_t<FMT, 128, TC_K / 2>(P, grid, smem, st);
-  return kl == TC_K ? launch_tc_t<FMT, 64, TC_K>(P, grid, smem, st) : launch_tc_t<FMT, 64, TC_K / 2>(P, grid, smem, st);
+static int launch_tc_f(const TcArgs& P, int bn, int kl, dim3 grid, size_t a, size_t b, cudaStream_t st) {
+  if (bn == 128) return kl == TC_K ? launch_tc_t<FMT, 128, TC_K>(P, grid, a, b, st)
+                                   : launch_tc_t<FMT, 128, TC_K / 2>(P, grid, a, b, st);
+  return kl == TC_K ? launch_tc_t<FMT, 64, TC_K>(P, grid, a, b, st) : launch_tc_t<FMT, 64, TC_K / 2>(P, grid, a, b, st);
 }
 
 // With sel / nsel_dev the consumers are the positions sel[0 .. *nsel_dev)
@@ -489,28 +536,24 @@ int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int preci
   const int per = (stiles + chunks - 1) / chunks;
   chunks = (stiles + per - 1) / per;
   const size_t a_bytes = (size_t)TC_BM * kb, b_bytes = (size_t)bn * kb;
-  int nstage = (int)((TC_SMEM_BUDGET - a_bytes) / b_bytes);
-  if (nstage > 4) nstage = 4;
-  if (nstage < 1) return -2;
   const int nt_pad = qtiles * TC_BM;
   // candidates re-ranked per chunk; the scan keeps half the lists when that suffices
   const int rk = T.rerank_k >= 1 && T.rerank_k <= TC_K ? T.rerank_k : TC_K;
   const int kl = rk <= TC_K / 2 ? TC_K / 2 : TC_K;
   TcArgs P{T.A,      T.B,      T.nrm_x,    T.nrm_sx, T.nrm_y,  T.scale_x,  T.scale_y, nt, mt,
-           kb,       bn,       nstage,     per,      stiles,   nt_pad,     T.cand_v,  T.cand_p, &B.st->err,
+           kb,       bn,       0,          per,      stiles,   nt_pad,     T.cand_v,  T.cand_p, &B.st->err,
            nsel_dev};
-  const size_t smem = a_bytes + (size_t)nstage * b_bytes;
   dim3 grid(qtiles, chunks);
   int rc;
   if (T.ev0) cudaEventRecord(T.ev0, st);
   if (fmt == FMT_BF16)
-    rc = launch_tc_f<FMT_BF16>(P, bn, kl, grid, smem, st);
+    rc = launch_tc_f<FMT_BF16>(P, bn, kl, grid, a_bytes, b_bytes, st);
   else if (fmt == FMT_BF16X3)
-    rc = launch_tc_f<FMT_BF16X3>(P, bn, kl, grid, smem, st);
+    rc = launch_tc_f<FMT_BF16X3>(P, bn, kl, grid, a_bytes, b_bytes, st);
   else if (fmt == FMT_F16)
-    rc = launch_tc_f<FMT_F16>(P, bn, kl, grid, smem, st);
+    rc = launch_tc_f<FMT_F16>(P, bn, kl, grid, a_bytes, b_bytes, st);
   else
-    rc = launch_tc_f<FMT_E4M3>(P, bn, kl, grid, smem, st);
+    rc = launch_tc_f<FMT_E4M3>(P, bn, kl, grid, a_bytes, b_bytes, st);
   if (rc) return rc;
   if (T.ev1) cudaEventRecord(T.ev1, st);
   // exact re-rank and certificate

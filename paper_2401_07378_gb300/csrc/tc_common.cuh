@@ -13,6 +13,8 @@
 
 #include <math_constants.h>
 
+#include <cstring>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -258,6 +260,77 @@ NNS_DEV void topk_insert(float (&tv)[K], int (&tp)[K], float v, int p) {
       np = fp;
     }
   }
+}
+
+// Tagged top-K lists (the K2 epilogue).  A list entry is its approximate
+// value with the low TAG bits of the FP32 pattern replaced by a tag; the tag
+// names a slot of a per-thread table that holds the supplier position.  Tags
+// of the entries in the list are distinct, so entries never compare equal
+// and the list is kept by minima and maxima alone (no positions to move).
+// The tag moves a value by less than 2^TAG units in the last place; every
+// bound read from a list goes through tag_floor, the smallest value that
+// shares the entry's other bits, which is at most the entry's exact value.
+template <int KL>
+struct TagList {
+  static constexpr int TAG = KL <= 8 ? 4 : 5;  // 2^TAG >= KL + 1 tags
+  static constexpr int NTAG = 1 << TAG;
+  static constexpr unsigned MASK = NTAG - 1;
+};
+
+// FP32 bit patterns on either side (the host build serves the CPU tests)
+__host__ __device__ inline unsigned f32_bits(float v) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(v);
+#else
+  unsigned u;
+  memcpy(&u, &v, sizeof u);
+  return u;
+#endif
+}
+
+__host__ __device__ inline float f32_of_bits(unsigned u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float v;
+  memcpy(&v, &u, sizeof v);
+  return v;
+#endif
+}
+
+__host__ __device__ inline float tag_floor(float v, unsigned mask) {
+  const unsigned u = f32_bits(v);
+  return f32_of_bits((u & 0x80000000u) ? (u | mask) : (u & ~mask));
+}
+
+// Insert value v (finite) of supplier position pos: a free tag takes the
+// position, the tagged value c enters the ascending list, and the entry
+// pushed out (+inf while the list is not full, or c itself when it is above
+// every entry) frees its tag.  All comparisons with c are taken first (the
+// list is ascending and its entries distinct, so they read false ... false,
+// true ... true), then every slot picks its new entry at once: a shallow
+// chain instead of one comparison after another.  `table` points at this
+// thread's tag 0 slot; slots are `stride` apart.
+template <int KL>
+__host__ __device__ inline void tag_insert(float (&tv)[KL], unsigned& used, int* table, int stride, float v,
+                                           int pos) {
+  using T = TagList<KL>;
+#ifdef __CUDA_ARCH__
+  const unsigned t = (unsigned)__ffs(~used) - 1u;
+#else
+  const unsigned t = (unsigned)__builtin_ffs((int)~used) - 1u;
+#endif
+  used |= 1u << t;
+  table[t * stride] = pos;
+  const float c = f32_of_bits((f32_bits(v) & ~T::MASK) | t);
+  bool before[KL];
+#pragma unroll
+  for (int k = 0; k < KL; ++k) before[k] = c < tv[k];
+  const float out = before[KL - 1] ? tv[KL - 1] : c;
+#pragma unroll
+  for (int k = KL - 1; k > 0; --k) tv[k] = before[k] ? (before[k - 1] ? tv[k - 1] : c) : tv[k];
+  tv[0] = before[0] ? c : tv[0];
+  if (!(out > 3.402823466e38f)) used &= ~(1u << (f32_bits(out) & T::MASK));
 }
 
 // --------------------------------------------------------------------------

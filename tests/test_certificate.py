@@ -54,6 +54,10 @@ def lib():
     L.certify_floor_host.restype = D
     L.certify_host.argtypes = L.certify_floor_host.argtypes + [ctypes.c_float]
     L.certify_host.restype = ctypes.c_int
+    P = ctypes.POINTER
+    L.tag_list_host.argtypes = [P(ctypes.c_float), ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_float),
+                                P(ctypes.c_int)]
+    L.tag_list_host.restype = ctypes.c_int
     yield L
     os.unlink(so)
 
@@ -285,3 +289,76 @@ def test_emulated_bf16_step_certifies_only_the_strict_nearest(split):
             if i != got:
                 assert keys[i] > keys[got] or (keys[i] == keys[got] and i > got), (trial, i, got)
     assert certified > 5
+
+
+# ---------------------------------------------------------------------------
+# the K2 epilogue's tagged lists
+# ---------------------------------------------------------------------------
+
+def tag_list(lib, vals, kl, floor=True):
+    vals = np.ascontiguousarray(vals, dtype=np.float32)
+    out_v = np.empty(kl, np.float32)
+    out_p = np.empty(kl, np.int32)
+    F, I = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)
+    assert lib.tag_list_host(vals.ctypes.data_as(F), len(vals), kl, int(floor), out_v.ctypes.data_as(F),
+                             out_p.ctypes.data_as(I)) == 0
+    return out_v, out_p
+
+
+def tag_streams():
+    rng = np.random.default_rng(11)
+    yield rng.normal(-240.0, 6.0, 5000)                     # GMM-like: negative values near one another
+    yield rng.normal(0.0, 1.0, 3000)                        # both signs, values near zero
+    yield np.repeat(rng.normal(5.0, 1.0, 300), 7)           # many exact ties
+    yield np.sort(rng.normal(0.0, 1.0, 1000))[::-1]         # descending: every value enters the list
+    yield np.concatenate([[0.0, -0.0] * 20, rng.normal(0.0, 1e-30, 200)])  # zeros and subnormal-sized
+    base = np.float32(-123.4567)                            # one high-bit pattern, every tag order
+    bits = base.view(np.uint32) & np.uint32(~31 & 0xFFFFFFFF)
+    yield np.array([np.uint32(bits | k).view(np.float32) for k in rng.permutation(32)], np.float32)
+    yield rng.normal(0.0, 1.0, 5)                           # shorter than the list
+
+
+@pytest.mark.parametrize("kl", [8, 16])
+def test_tagged_list_bounds_every_excluded_value(lib, kl):
+    """The floored K-th entry is a lower bound of every value left out (the
+    certificate's tau), each entry's floored value is at most its own value,
+    positions are distinct, and the list holds the kl smallest values up to
+    the tag's perturbation (2^5 units in the last place at most)."""
+    for vals in tag_streams():
+        vals = np.asarray(vals, np.float32)
+        v, p = tag_list(lib, vals, kl)
+        n = len(vals)
+        real = p >= 0
+        assert real.sum() == min(n, kl)
+        assert len(set(p[real].tolist())) == real.sum()
+        assert np.all(v[real] <= vals[p[real]])
+        assert np.all(np.diff(v[real]) >= 0)
+        if n <= kl:
+            assert sorted(p[real].tolist()) == list(range(n))
+            continue
+        tau = v[kl - 1]
+        out = np.setdiff1d(np.arange(n), p)
+        assert np.all(vals[out] >= tau)
+        kth = np.sort(vals)[kl - 1]
+        slack = 64 * np.spacing(np.abs(kth).astype(np.float32)) + np.float32(1e-44)
+        assert np.all(vals[p] <= kth + slack)
+
+
+def test_tagged_list_needs_its_floor(lib):
+    """Without the floor a tagged entry can stand above a value it pushed
+    out (same high bits, the larger tag on the smaller value): the unfloored
+    K-th entry then fails as a bound, the floored one holds."""
+    kl = 8
+    base = np.float32(1000.0).view(np.uint32) & np.uint32(~15 & 0xFFFFFFFF)
+    # 8 values take tags 0..7 in arrival order; a ninth, smaller in exact
+    # terms than the eighth, gets tag 8 and so compares above it
+    vals = [np.uint32(base | k).view(np.float32) for k in (15, 14, 13, 12, 11, 10, 9, 8)]
+    vals.append(np.uint32(base | 0).view(np.float32))
+    vals = np.array(vals, np.float32)
+    raw_v, raw_p = tag_list(lib, vals, kl, floor=False)
+    flo_v, flo_p = tag_list(lib, vals, kl, floor=True)
+    out_raw = np.setdiff1d(np.arange(len(vals)), raw_p)
+    assert len(out_raw) == 1
+    assert vals[out_raw].min() < raw_v[kl - 1]
+    out = np.setdiff1d(np.arange(len(vals)), flo_p)
+    assert np.all(vals[out] >= flo_v[kl - 1])
