@@ -72,6 +72,37 @@ NNS_DEV float key32(const float* x, const float* y, int d) {
   return acc;
 }
 
+// The FP32 key of key32<SQL2> (t = x_k - y_k, acc = t_0 t_0, then
+// acc = fma(t_k, t_k, acc) in ascending k), read four coordinates at a time:
+// x a 16-byte aligned global row, y a 16-byte aligned row (global or
+// shared memory), d % 4 == 0.
+NNS_DEV float key32_sql2_v4(const float* __restrict__ x, const float* y, int d) {
+  const float4* x4 = reinterpret_cast<const float4*>(x);
+  const float4* y4 = reinterpret_cast<const float4*>(y);
+  float4 a = __ldg(x4), b = y4[0];
+  float t = __fsub_rn(a.x, b.x);
+  float acc = __fmul_rn(t, t);
+  t = __fsub_rn(a.y, b.y);
+  acc = __fmaf_rn(t, t, acc);
+  t = __fsub_rn(a.z, b.z);
+  acc = __fmaf_rn(t, t, acc);
+  t = __fsub_rn(a.w, b.w);
+  acc = __fmaf_rn(t, t, acc);
+  for (int i = 1; i < (d >> 2); ++i) {
+    a = __ldg(x4 + i);
+    b = y4[i];
+    t = __fsub_rn(a.x, b.x);
+    acc = __fmaf_rn(t, t, acc);
+    t = __fsub_rn(a.y, b.y);
+    acc = __fmaf_rn(t, t, acc);
+    t = __fsub_rn(a.z, b.z);
+    acc = __fmaf_rn(t, t, acc);
+    t = __fsub_rn(a.w, b.w);
+    acc = __fmaf_rn(t, t, acc);
+  }
+  return acc;
+}
+
 // FP64 ground distance D_ij of the cost: the same steps in double, sqrt for L2.
 NNS_DEV double cost_dist64(const float* x, const float* y, int d, int metric) {
   double acc;

@@ -584,36 +584,6 @@ struct LearnedArgs {
 
 constexpr int LN_YMAX = 256;  // consumer rows up to this d are staged in shared memory
 
-// The FP32 key of key32<SQL2> (t = x_k - y_k, acc = t_0 t_0, then
-// acc = fma(t_k, t_k, acc) in ascending k), read four coordinates at a time:
-// x a 16-byte aligned global row, y a row in shared memory, d % 4 == 0.
-NNS_DEV float key32_sql2_v4(const float* __restrict__ x, const float* y, int d) {
-  const float4* x4 = reinterpret_cast<const float4*>(x);
-  const float4* y4 = reinterpret_cast<const float4*>(y);
-  float4 a = __ldg(x4), b = y4[0];
-  float t = __fsub_rn(a.x, b.x);
-  float acc = __fmul_rn(t, t);
-  t = __fsub_rn(a.y, b.y);
-  acc = __fmaf_rn(t, t, acc);
-  t = __fsub_rn(a.z, b.z);
-  acc = __fmaf_rn(t, t, acc);
-  t = __fsub_rn(a.w, b.w);
-  acc = __fmaf_rn(t, t, acc);
-  for (int i = 1; i < (d >> 2); ++i) {
-    a = __ldg(x4 + i);
-    b = y4[i];
-    t = __fsub_rn(a.x, b.x);
-    acc = __fmaf_rn(t, t, acc);
-    t = __fsub_rn(a.y, b.y);
-    acc = __fmaf_rn(t, t, acc);
-    t = __fsub_rn(a.z, b.z);
-    acc = __fmaf_rn(t, t, acc);
-    t = __fsub_rn(a.w, b.w);
-    acc = __fmaf_rn(t, t, acc);
-  }
-  return acc;
-}
-
 // One warp per active consumer.  When d % 4 == 0, d <= LN_YMAX and the
 // coordinates are 16-byte aligned, the consumer's row is staged in shared
 // memory (every lane reads it: broadcast) and the supplier rows are read

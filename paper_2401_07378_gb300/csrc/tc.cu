@@ -56,6 +56,7 @@ __global__ void k_pack_tc(const float* __restrict__ pts, const int* __restrict__
                           float* __restrict__ scale, unsigned* __restrict__ stats) {
   const int nblk = kb / 16;
   const int count = cnt_dev ? min(*cnt_dev, cnt) : cnt;
+  unsigned m0 = 0u, m1 = 0u, m2 = 0u;  // this thread's maxima (float bits of values >= 0)
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < rows_pad; p += gridDim.x * blockDim.x) {
     const float* row = p < count ? pts + (size_t)idx[sel ? sel[p] : p] * d : nullptr;
     const float s = row_scale(row, d, fmt);
@@ -69,15 +70,25 @@ __global__ void k_pack_tc(const float* __restrict__ pts, const int* __restrict__
         nrm[p] = l2sq;
         if (nrm_s) nrm_s[p] = norm_up(l2sq);
         scale[p] = s;
-        atomicMax(stats + 0, __float_as_uint(norm_up(l2sq)));
-        atomicMax(stats + 1, __float_as_uint(l1 * (1.f + 1e-4f)));
-        atomicMax(stats + 2, __float_as_uint(s));
+        m0 = max(m0, __float_as_uint(norm_up(l2sq)));
+        m1 = max(m1, __float_as_uint(l1 * (1.f + 1e-4f)));
+        m2 = max(m2, __float_as_uint(s));
       } else {
         nrm[p] = CUDART_INF_F;
         if (nrm_s) nrm_s[p] = 0.f;
         scale[p] = 1.f;
       }
     }
+  }
+  // the maxima: over the warp first, then one atomic per warp (every
+  // thread of the block reaches this point: the loop above has no exit)
+  m0 = __reduce_max_sync(0xffffffffu, m0);
+  m1 = __reduce_max_sync(0xffffffffu, m1);
+  m2 = __reduce_max_sync(0xffffffffu, m2);
+  if ((threadIdx.x & 31) == 0 && (m0 | m1 | m2)) {
+    atomicMax(stats + 0, m0);
+    atomicMax(stats + 1, m1);
+    atomicMax(stats + 2, m2);
   }
 }
 
@@ -412,6 +423,8 @@ __global__ void k_rerank_certify(RerankArgs R) {
   const float* yrow = R.y + (size_t)R.ja[q] * R.d;
   const int rk = R.rk;
   const int ncand = R.chunks * rk;
+  // rows read 16 bytes at a time where d and both bases allow it
+  const bool vec = (R.d & 3) == 0 && ((reinterpret_cast<uintptr_t>(R.x) | reinterpret_cast<uintptr_t>(R.y)) & 15) == 0;
   unsigned long long best = ~0ULL, abest = ~0ULL;
   float tau = CUDART_INF_F;  // smallest chunk threshold (rk-th value of each chunk)
   for (int c = lane; c < ncand; c += 32) {
@@ -425,7 +438,8 @@ __global__ void k_rerank_certify(RerankArgs R) {
       abest = ak < abest ? ak : abest;
     }
     // squared-Euclidean FP32 key (the contraction has no L1 form)
-    const float acc = key32<METRIC_SQL2>(R.x + (size_t)R.ia[p] * R.d, yrow, R.d);
+    const float* xr = R.x + (size_t)R.ia[p] * R.d;
+    const float acc = vec ? key32_sql2_v4(xr, yrow, R.d) : key32<METRIC_SQL2>(xr, yrow, R.d);
     const unsigned long long key = pack_key(acc, (unsigned)p);
     best = key < best ? key : best;
   }
