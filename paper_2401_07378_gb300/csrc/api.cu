@@ -164,6 +164,8 @@ size_t layout_solve(void* base, int64_t m, int64_t n, int d, SolveBufs& B, int p
     L->tmp = C.take<float>((size_t)2 * L->chunk * h);
     L->tmp2 = C.take<float>((size_t)L->chunk * K);
     L->tmp3 = C.take<float>((size_t)L->chunk * d);
+    L->sel_over = C.take<int>(L->chunk);
+    L->nsel_over = C.take<int>(1);
   }
   if (precision != NNSEMD_FP32) {
     const size_t kb = tc_kb(d, precision);

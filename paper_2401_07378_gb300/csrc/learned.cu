@@ -342,17 +342,22 @@ NNS_DEV unsigned ordered_bits(float v) {
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-// LARGEST: keep the K largest values; otherwise the K smallest.
+// LARGEST: keep the K largest values; otherwise the K smallest.  One block
+// per row: a radix select over all of the row's keys.  With row_list /
+// n_rows it serves the rows row_list[0 .. *n_rows) (blocks past the count
+// leave at once): the rows the one-warp selection below hands over.
 template <bool LARGEST>
 __global__ void __launch_bounds__(256) k_select_rows(const float* __restrict__ V, int rows, int cols, int* __restrict__ out_idx,
-                                                     float* __restrict__ out_val, int out_stride) {
+                                                     float* __restrict__ out_val, int out_stride,
+                                                     const int* __restrict__ row_list, const int* __restrict__ n_rows) {
   extern __shared__ unsigned sk[];  // cols keys
   __shared__ unsigned hist[256];
   __shared__ unsigned s_prefix, s_mask, s_need;
   __shared__ int s_cnt;
   __shared__ unsigned sel_key[PROP_LIST];
   __shared__ int sel_idx[PROP_LIST];
-  const int r = blockIdx.x;
+  if (row_list && (int)blockIdx.x >= *n_rows) return;
+  const int r = row_list ? row_list[blockIdx.x] : blockIdx.x;
   const int tid = threadIdx.x;
   for (int c = tid; c < cols; c += blockDim.x) {
     const unsigned o = ordered_bits(V[(size_t)r * cols + c]);
@@ -424,6 +429,113 @@ __global__ void __launch_bounds__(256) k_select_rows(const float* __restrict__ V
   }
 }
 
+constexpr int SEL_WARPS = 8;   // rows per block of the one-warp selection
+constexpr int SEL_CAP = 256;   // candidates a warp keeps in shared memory
+
+// The same selection (the PROP_LIST largest keys, lowest column first among
+// equal keys, written in that order), one warp per row, with no atomics:
+//  1. the row's columns fall into 64 groups (lane x half of the row); the
+//     two largest keys of every group form a set S, and T is the 64th
+//     largest key of S, so at least 64 keys of the row are >= T;
+//  2. the keys > T are gathered in column order; with fewer than 64 of
+//     them, the first keys == T in column order complete the 64 (exactly
+//     the selection's tie rule), else the 64 are among the gathered ones;
+//  3. each gathered key's rank by (key descending, column ascending) places
+//     the 64 first.
+// A row with more than SEL_CAP keys > T is left to k_select_rows through
+// over_rows / n_over.  Needs cols >= 2 * PROP_LIST.
+template <bool LARGEST>
+__global__ void __launch_bounds__(32 * SEL_WARPS) k_select_rows_warp(const float* __restrict__ V, int rows, int cols,
+                                                                   int* __restrict__ out_idx, float* __restrict__ out_val,
+                                                                   int out_stride, int* __restrict__ over_rows,
+                                                                   int* __restrict__ n_over) {
+  __shared__ unsigned s_key[SEL_WARPS][4 * 32];
+  __shared__ unsigned c_key[SEL_WARPS][SEL_CAP];
+  __shared__ int c_col[SEL_WARPS][SEL_CAP];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = blockIdx.x * SEL_WARPS + w;
+  if (r >= rows) return;
+  const float* row = V + (size_t)r * cols;
+  auto key = [&](int c) -> unsigned {
+    const unsigned o = ordered_bits(row[c]);
+    return LARGEST ? o : ~o;
+  };
+  // 1. the two largest keys of each group (lane, half); every group holds
+  // at least two columns (cols >= 128), so all 128 entries are real keys
+  const int half = cols / 2;
+  for (int h = 0; h < 2; ++h) {
+    unsigned a1 = 0u, a2 = 0u;
+    int n = 0;
+    for (int c = h * half + lane; c < (h ? cols : half); c += 32) {
+      const unsigned k = key(c);
+      if (n == 0 || k > a1) {
+        a2 = a1;
+        a1 = k;
+      } else if (n == 1 || k > a2) {
+        a2 = k;
+      }
+      ++n;
+    }
+    s_key[w][h * 64 + lane] = a1;
+    s_key[w][h * 64 + 32 + lane] = a2;
+  }
+  __syncwarp();
+  // T: the largest key of S with at least 64 keys of S at or above it
+  unsigned T = 0u;
+  for (int i = lane; i < 128; i += 32) {
+    const unsigned ki = s_key[w][i];
+    int ge = 0;
+    for (int j = 0; j < 128; ++j) ge += s_key[w][j] >= ki;
+    if (ge >= PROP_LIST && ki > T) T = ki;
+  }
+  T = __reduce_max_sync(0xffffffffu, T);
+  // 2. keys > T in column order
+  int n = 0;
+  for (int base = 0; base < cols; base += 32) {
+    const int c = base + lane;
+    const unsigned k = c < cols ? key(c) : 0u;
+    const bool p = c < cols && k > T;
+    const unsigned bal = __ballot_sync(0xffffffffu, p);
+    const int pos = n + __popc(bal & ((1u << lane) - 1u));
+    if (p && pos < SEL_CAP) {
+      c_key[w][pos] = k;
+      c_col[w][pos] = c;
+    }
+    n += __popc(bal);
+  }
+  if (n > SEL_CAP) {
+    if (lane == 0) over_rows[atomicAdd(n_over, 1)] = r;
+    return;
+  }
+  // ... completed by the first keys == T when fewer than 64 exceed it
+  for (int base = 0; base < cols && n < PROP_LIST; base += 32) {
+    const int c = base + lane;
+    const bool p = c < cols && key(c) == T;
+    const unsigned bal = __ballot_sync(0xffffffffu, p);
+    const int pos = n + __popc(bal & ((1u << lane) - 1u));
+    if (p && pos < PROP_LIST) {
+      c_key[w][pos] = T;
+      c_col[w][pos] = c;
+    }
+    n = min(PROP_LIST, n + __popc(bal));
+  }
+  __syncwarp();
+  // 3. ranks; the first PROP_LIST are written
+  for (int i = lane; i < n; i += 32) {
+    const unsigned ki = c_key[w][i];
+    const int ci = c_col[w][i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const unsigned kj = c_key[w][j];
+      rank += (kj > ki) || (kj == ki && c_col[w][j] < ci);
+    }
+    if (rank < PROP_LIST) {
+      out_idx[(size_t)r * out_stride + rank] = ci;
+      if (out_val) out_val[(size_t)r * out_stride + rank] = row[ci];
+    }
+  }
+}
+
 // --------------------------------------------------------------------------
 // per-solve preparation
 // --------------------------------------------------------------------------
@@ -439,10 +551,17 @@ __global__ void k_cell_radius(const float* __restrict__ pts, int64_t N, int d, c
   }
 }
 
-// Squared distances between rows Y[rows][d] and centroids MU[cells][d] (FP32
-// direct differences, 4 x 4 per thread), out[rows][cells].
-__global__ void __launch_bounds__(256) k_centroid_d2(const float* __restrict__ Y, int rows, const float* __restrict__ MU,
-                                                     int cells, int d, float* __restrict__ out) {
+// Lower bounds of the squared distance from each row of Y [rows][d] to any
+// supplier of each cell, out[rows][cells]: max(0, |y - mu_c| - r_c)^2.
+// |y - mu_c|^2 is computed in FP32 (direct differences, fma in ascending k,
+// 4 x 4 per thread); the computed D satisfies D <= |y - mu|^2 (1 + gamma_{d+1})
+// (each difference adds a relative error of at most u = 2^-24 before it is
+// squared, the d-term sum at most gamma_{d-1}), so |y - mu| >=
+// sqrt(D (1 - gamma_{d+2})); every later step rounds down (r_c is rounded up
+// when it is formed), so the result is at most the bound it stands for.
+__global__ void __launch_bounds__(256) k_centroid_lb(const float* __restrict__ Y, int rows, const float* __restrict__ MU,
+                                                     int cells, int d, const unsigned* __restrict__ radius_bits,
+                                                     float* __restrict__ out) {
   __shared__ float Ys[TG_K][TG_PAD];
   __shared__ float Ms[TG_K][TG_PAD];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -469,28 +588,37 @@ __global__ void __launch_bounds__(256) k_centroid_d2(const float* __restrict__ Y
     }
     __syncthreads();
   }
+  const double ud = (d + 2) * 0x1p-24;
+  const float shrink = __double2float_rd(1.0 - ud / (1.0 - ud));  // 1 - gamma_{d+2}, rounded down
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int j = 0; j < 4; ++j) {
+    const int c = c0 + tx * 4 + j;
+    if (c >= cells) continue;
+    const float rc = __uint_as_float(radius_bits[c]);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int r = r0 + ty * 4 + i, c = c0 + tx * 4 + j;
-      if (r < rows && c < cells) out[(size_t)r * cells + c] = acc[i][j];
+    for (int i = 0; i < 4; ++i) {
+      const int r = r0 + ty * 4 + i;
+      if (r >= rows) continue;
+      const float gap = __fsub_rd(__fsqrt_rd(__fmul_rd(acc[i][j], shrink)), rc);
+      out[(size_t)r * cells + c] = gap > 0.f ? __fmul_rd(gap, gap) : 0.f;
     }
+  }
 }
 
-// In place: d2 -> lower bound of the squared distance to any point of cell c:
-// max(0, |y - mu| - r_c)^2, with |y - mu| rounded down (the FP32 squared
-// distance has relative error <= gamma_d) and the result rounded down.
-__global__ void k_cell_lower_bound(float* __restrict__ D, int rows, int cells, int d,
-                                   const unsigned* __restrict__ radius_bits) {
-  const double gam = d * 0x1p-24 / (1.0 - d * 0x1p-24);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)rows * cells;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(i % cells);
-    const double r = __uint_as_float(radius_bits[c]);
-    const double dist = sqrt((double)D[i] * (1.0 - gam)) * (1.0 - 1e-9);
-    const double gap = dist - r;
-    D[i] = gap > 0.0 ? (float)(gap * gap * (1.0 - 1e-6)) : 0.f;
+// The PROP_LIST best of every row of V [rows][cols]: one warp per row
+// (k_select_rows_warp), the rows it hands over by the block selection.
+template <bool LARGEST>
+static void select_rows(const float* V, int rows, int cols, int* out_idx, float* out_val, const LearnedBufs& L,
+                        cudaStream_t st) {
+  if (cols >= 2 * PROP_LIST) {
+    cudaMemsetAsync(L.nsel_over, 0, sizeof(int), st);
+    k_select_rows_warp<LARGEST><<<(rows + SEL_WARPS - 1) / SEL_WARPS, 32 * SEL_WARPS, 0, st>>>(
+        V, rows, cols, out_idx, out_val, PROP_LIST, L.sel_over, L.nsel_over);
+    k_select_rows<LARGEST><<<rows, 256, cols * sizeof(unsigned), st>>>(V, rows, cols, out_idx, out_val, PROP_LIST,
+                                                                       L.sel_over, L.nsel_over);
+  } else {
+    k_select_rows<LARGEST><<<rows, 256, cols * sizeof(unsigned), st>>>(V, rows, cols, out_idx, out_val, PROP_LIST,
+                                                                       nullptr, nullptr);
   }
 }
 
@@ -511,14 +639,11 @@ int learned_prepare(const LearnedBufs& L, const float* x, int64_t m, const float
     float* Z = L.tmp2;               // rows x K
     k_standardise<<<num_sms() * 4, 256, 0, st>>>(yc, rows, d, P->in_mean, P->in_scale, Xs);
     mlp_forward(P, Xs, rows, H1, H2, Z, st);
-    k_select_rows<true><<<rows, 256, K * sizeof(unsigned), st>>>(Z, rows, K, L.prop_cells + r0 * PROP_LIST, nullptr,
-                                                                 PROP_LIST);
+    select_rows<true>(Z, rows, K, L.prop_cells + r0 * PROP_LIST, nullptr, L, st);
     // bounds: the cells with the smallest lower bound
     dim3 g2((K + 63) / 64, (rows + 63) / 64);
-    k_centroid_d2<<<g2, 256, 0, st>>>(yc, rows, P->centroids, K, d, Z);
-    k_cell_lower_bound<<<num_sms() * 8, 256, 0, st>>>(Z, rows, K, d, reinterpret_cast<const unsigned*>(L.radius));
-    k_select_rows<false><<<rows, 256, K * sizeof(unsigned), st>>>(Z, rows, K, L.bound_cells + r0 * PROP_LIST,
-                                                                  L.bound_vals + r0 * PROP_LIST, PROP_LIST);
+    k_centroid_lb<<<g2, 256, 0, st>>>(yc, rows, P->centroids, K, d, reinterpret_cast<const unsigned*>(L.radius), Z);
+    select_rows<false>(Z, rows, K, L.bound_cells + r0 * PROP_LIST, L.bound_vals + r0 * PROP_LIST, L, st);
   }
   (void)h;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;

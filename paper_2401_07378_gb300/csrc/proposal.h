@@ -59,6 +59,8 @@ struct LearnedBufs {
   float* tmp;           // [chunk][max(cells, hidden)] and friends
   float* tmp2;
   float* tmp3;
+  int* sel_over;        // [chunk] rows the one-warp selection hands to the block selection
+  int* nsel_over;
   int chunk;            // consumers per pass
 };
 
