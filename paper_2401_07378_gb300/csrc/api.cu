@@ -166,6 +166,16 @@ size_t layout_solve(void* base, int64_t m, int64_t n, int d, SolveBufs& B, int p
     L->tmp3 = C.take<float>((size_t)L->chunk * d);
     L->sel_over = C.take<int>(L->chunk);
     L->nsel_over = C.take<int>(1);
+    L->lc_cand = C.take<int>((size_t)n * PROP_TAKE);
+    L->lc_slot = C.take<int>((size_t)n * PROP_TAKE);
+    L->lc_ncand = C.take<int>(n);
+    L->lc_bound = C.take<float>(n);
+    L->lc_qcnt = C.take<int>(K);
+    L->lc_qoff = C.take<int>(K + 1);
+    L->lc_work = C.take<int>(K + 1);
+    L->lc_nwork = C.take<int>(1);
+    L->lc_qlist = C.take<int>((size_t)n * PROP_TAKE);
+    L->lc_best = C.take<unsigned long long>(n);
   }
   if (precision != NNSEMD_FP32) {
     const size_t kb = tc_kb(d, precision);
@@ -353,7 +363,10 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
     // once per solve: supplier cells and radii, consumer proposals and bounds
     if (learned_prepare(*learned, B.x, B.m, B.y, B.n, B.d, st))
       return drained(fail(ctx, NNSEMD_ERR_CUDA, "proposal preparation"));
-    L += 8 + 8 * ((B.n + learned->chunk - 1) / learned->chunk);
+    // per chunk: standardisation, three GEMMs, the centroid bounds and two
+    // selections (one-warp + block pass each, or the block pass alone)
+    const int sel = learned->P->cells >= 2 * PROP_LIST ? 2 : 1;
+    L += 8 + (5 + 2 * sel) * ((B.n + learned->chunk - 1) / learned->chunk);
   }
   while (mt > 0 && nt > 0) {
     const bool tail = clcap ? (mt <= clcap && nt <= clcap)
@@ -379,7 +392,7 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
       if (timed) CKD(cudaEventRecord(ctx->ev[0], st));
       nrc = launch_nns_learned(B, *learned, mt, nt, st);
       if (timed) CKD(cudaEventRecord(ctx->ev[1], st));
-      L += 6;
+      L += learned_cell_scan(B.d, B.x, B.y) ? 10 : 6;
     } else if (B.precision != NNSEMD_FP32) {
       // tensor-core candidates + exact re-rank + certificate + FP32 rescan;
       // the timing events bracket the tensor-core kernel alone

@@ -445,7 +445,7 @@ constexpr int SEL_CAP = 256;   // candidates a warp keeps in shared memory
 // A row with more than SEL_CAP keys > T is left to k_select_rows through
 // over_rows / n_over.  Needs cols >= 2 * PROP_LIST.
 template <bool LARGEST>
-__global__ void __launch_bounds__(32 * SEL_WARPS) k_select_rows_warp(const float* __restrict__ V, int rows, int cols,
+__global__ void __launch_bounds__(32 * SEL_WARPS, 4) k_select_rows_warp(const float* __restrict__ V, int rows, int cols,
                                                                    int* __restrict__ out_idx, float* __restrict__ out_val,
                                                                    int out_stride, int* __restrict__ over_rows,
                                                                    int* __restrict__ n_over) {
@@ -485,6 +485,7 @@ __global__ void __launch_bounds__(32 * SEL_WARPS) k_select_rows_warp(const float
   for (int i = lane; i < 128; i += 32) {
     const unsigned ki = s_key[w][i];
     int ge = 0;
+#pragma unroll 8
     for (int j = 0; j < 128; ++j) ge += s_key[w][j] >= ki;
     if (ge >= PROP_LIST && ki > T) T = ki;
   }
@@ -779,6 +780,231 @@ __global__ void __launch_bounds__(256) k_learned_nns(LearnedArgs A) {
   }
 }
 
+// --------------------------------------------------------------------------
+// The same step, cell by cell (d of 32, 64 or 128, 16-byte aligned rows): the
+// candidate cells and the bound of every consumer first (k_learned_plan), the
+// consumers grouped by candidate cell (k_lc_offsets, k_lc_group), then one
+// CTA per (cell, up to LC_THREADS of its consumers) stages the cell's active
+// suppliers in shared memory once for all of them (k_lc_keys), and the
+// certificate last (k_learned_cert).  Candidates, keys, bound and
+// certificate are those of k_learned_nns, so the results are the same.
+// --------------------------------------------------------------------------
+
+constexpr int LC_THREADS = 256;  // consumers of one cell per work item (one per thread)
+constexpr int LC_TILE = 64;      // suppliers staged at a time
+
+struct LcArgs {
+  const float* x;
+  const float* y;
+  const int* ia;
+  const int* ja;
+  int d, nt, cells;
+  const int* prop_cells;
+  const int* bound_cells;
+  const float* bound_vals;
+  const int* cell_off;     // [K+1] active suppliers by cell
+  const int* members;
+  int* cand;               // [nt][PROP_TAKE] candidate cells of each consumer
+  int* slot;               // [nt][PROP_TAKE] the consumer's place in each candidate cell's list
+  int* ncand;              // [nt]
+  float* bound;            // [nt] smallest bound of a non-candidate cell holding active suppliers
+  int* qcnt;               // [K] consumers per cell
+  int* qoff;               // [K+1]
+  int* work_off;           // [K+1] work items (chunks of LC_THREADS consumers) before each cell
+  int* nwork;
+  int* qlist;              // consumers grouped by cell
+  unsigned long long* best;  // [nt] smallest packed key over the candidates (all ones on entry)
+  unsigned long long* nnkey;
+  int* fallback;
+  int* nfallback;
+  unsigned long long* ncert;
+  unsigned long long* nfall;
+};
+
+// One warp per active consumer: the first PROP_TAKE proposed cells that
+// still hold active suppliers, their places in the cells' lists, and the
+// bound of the other cells (as k_learned_nns takes them).
+__global__ void __launch_bounds__(256) k_learned_plan(LcArgs A) {
+  __shared__ int cand[8][PROP_TAKE];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int q = blockIdx.x * 8 + wib;
+  if (q >= A.nt) return;
+  const int j = A.ja[q];
+  const int* pl = A.prop_cells + (size_t)j * PROP_LIST;
+  int ncand = 0;
+  for (int base = 0; base < PROP_LIST && ncand < PROP_TAKE; base += 32) {
+    const int c = pl[base + lane];
+    const bool ne = A.cell_off[c + 1] > A.cell_off[c];
+    const unsigned bal = __ballot_sync(0xffffffffu, ne);
+    const int pos = ncand + __popc(bal & ((1u << lane) - 1u));
+    if (ne && pos < PROP_TAKE) {
+      cand[wib][pos] = c;
+      A.cand[(size_t)q * PROP_TAKE + pos] = c;
+      A.slot[(size_t)q * PROP_TAKE + pos] = atomicAdd(A.qcnt + c, 1);
+    }
+    ncand = min(PROP_TAKE, ncand + __popc(bal));
+  }
+  __syncwarp();
+  const int* bl = A.bound_cells + (size_t)j * PROP_LIST;
+  const float* bv = A.bound_vals + (size_t)j * PROP_LIST;
+  float bound = bv[PROP_LIST - 1];
+  for (int base = 0; base < PROP_LIST; base += 32) {
+    const int c = bl[base + lane];
+    bool ok = A.cell_off[c + 1] > A.cell_off[c];
+    for (int k = 0; k < ncand && ok; ++k) ok = cand[wib][k] != c;
+    const float v = ok ? bv[base + lane] : CUDART_INF_F;
+    float mn = v;
+    for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    bound = fminf(bound, mn);
+  }
+  if (lane == 0) {
+    A.ncand[q] = ncand;
+    A.bound[q] = bound;
+  }
+}
+
+// Single block: qoff = exclusive scan of qcnt, work_off = exclusive scan of
+// the work items per cell (ceil(qcnt / LC_THREADS)), *nwork = their total.
+__global__ void k_lc_offsets(LcArgs A) {
+  __shared__ int wt[33];
+  __shared__ int carry_q, carry_w;
+  if (threadIdx.x == 0) carry_q = carry_w = 0;
+  __syncthreads();
+  for (int base = 0; base < A.cells; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int v = i < A.cells ? A.qcnt[i] : 0;
+    const int wv = (v + LC_THREADS - 1) / LC_THREADS;
+    int tot, wtot;
+    const int ex = block_scan_excl(v, wt, tot);
+    __syncthreads();
+    const int wex = block_scan_excl(wv, wt, wtot);
+    if (i < A.cells) {
+      A.qoff[i] = carry_q + ex;
+      A.work_off[i] = carry_w + wex;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      carry_q += tot;
+      carry_w += wtot;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    A.qoff[A.cells] = carry_q;
+    A.work_off[A.cells] = carry_w;
+    *A.nwork = carry_w;
+  }
+}
+
+// One thread per (consumer, candidate): the consumer into its cell's list.
+__global__ void k_lc_group(LcArgs A) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= (int64_t)A.nt * PROP_TAKE) return;
+  const int q = (int)(i / PROP_TAKE), k = (int)(i % PROP_TAKE);
+  if (k >= A.ncand[q]) return;
+  const int c = A.cand[i];
+  A.qlist[A.qoff[c] + A.slot[i]] = q;
+}
+
+// The cell scan.  CTAs take work items in turn; a work item is up to
+// LC_THREADS consumers of one cell, one per thread, each with its row in
+// registers; the cell's active suppliers pass through shared memory
+// LC_TILE rows at a time and every thread runs the key32<SQL2> chain of
+// four suppliers at once against its row.
+template <int D>
+__global__ void __launch_bounds__(LC_THREADS) k_lc_keys(LcArgs A) {
+  __shared__ __align__(16) float xs[LC_TILE][D];
+  __shared__ int ps[LC_TILE];
+  const int tid = threadIdx.x;
+  const int nw = *A.nwork;
+  for (int wi = blockIdx.x; wi < nw; wi += gridDim.x) {
+    // the cell of this work item: the last c with work_off[c] <= wi
+    int lo = 0, hi = A.cells;  // work_off[lo] <= wi < work_off[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (A.work_off[mid] <= wi) lo = mid; else hi = mid;
+    }
+    const int c = lo;
+    const int qi = (wi - A.work_off[c]) * LC_THREADS + tid;
+    const bool has = qi < A.qoff[c + 1] - A.qoff[c];
+    const int q = has ? A.qlist[A.qoff[c] + qi] : 0;
+    float yr[D];
+    if (has) {
+      const float4* y4 = reinterpret_cast<const float4*>(A.y + (size_t)A.ja[q] * D);
+#pragma unroll
+      for (int k = 0; k < D / 4; ++k) {
+        const float4 v = y4[k];
+        yr[4 * k] = v.x;
+        yr[4 * k + 1] = v.y;
+        yr[4 * k + 2] = v.z;
+        yr[4 * k + 3] = v.w;
+      }
+    }
+    unsigned long long best = ~0ULL;
+    const int s0 = A.cell_off[c], ns = A.cell_off[c + 1] - s0;
+    for (int t0 = 0; t0 < ns; t0 += LC_TILE) {
+      const int tn = min(LC_TILE, ns - t0);
+      __syncthreads();
+      for (int i = tid; i < tn * (D / 4); i += LC_THREADS) {
+        const int r = i / (D / 4), k4 = i % (D / 4);
+        const int p = A.members[s0 + t0 + r];
+        reinterpret_cast<float4*>(xs[r])[k4] = reinterpret_cast<const float4*>(A.x + (size_t)A.ia[p] * D)[k4];
+        if (k4 == 0) ps[r] = p;
+      }
+      __syncthreads();
+      if (has) {
+        for (int r = 0; r < tn; r += 4) {
+          const float4* row[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) row[u] = reinterpret_cast<const float4*>(xs[min(r + u, tn - 1)]);
+          float acc[4];
+#pragma unroll
+          for (int k4 = 0; k4 < D / 4; ++k4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float4 xv = row[u][k4];
+              const float xk[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float t = __fsub_rn(xk[e], yr[4 * k4 + e]);
+                acc[u] = (k4 == 0 && e == 0) ? __fmul_rn(t, t) : __fmaf_rn(t, t, acc[u]);
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (r + u < tn) {
+              const unsigned long long kk = pack_key(acc[u], (unsigned)ps[r + u]);
+              best = kk < best ? kk : best;
+            }
+        }
+      }
+    }
+    if (has) atomicMin(A.best + q, best);
+  }
+}
+
+// One thread per active consumer: the certificate of k_learned_nns.
+__global__ void k_learned_cert(LcArgs A) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= A.nt) return;
+  const unsigned long long best = A.best[q];
+  const double gam = A.d * 0x1p-24 / (1.0 - A.d * 0x1p-24);
+  const bool certified = best != ~0ULL && (double)__uint_as_float((unsigned)(best >> 32)) <
+                                              (double)A.bound[q] * (1.0 - gam) * (1.0 - 0x1p-30);
+  if (certified) {
+    A.nnkey[q] = best;
+    atomicAdd(A.ncert, 1ULL);
+  } else {
+    A.fallback[atomicAdd(A.nfallback, 1)] = q;
+    if (A.nfall) atomicAdd(A.nfall, 1ULL);
+  }
+}
+
+bool learned_cell_scan(int d, const float* x, const float* y) {
+  return (d == 32 || d == 64 || d == 128) && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) == 0;
+}
+
 // The consumers the proposal cannot certify are scanned in full: in FP32,
 // or with a reduced-precision solve precision by the tensor-core scan (its
 // own certificate and FP32 rescan), restricted to them.
@@ -790,11 +1016,28 @@ int launch_nns_learned(const SolveBufs& B, const LearnedBufs& L, int mt, int nt,
   k_cell_scan<<<1, 1024, 0, st>>>(L.cell_cnt, K, L.cell_off, L.cell_fill);
   k_cell_scatter<<<(mt + 255) / 256, 256, 0, st>>>(ia, mt, L.cell_of_x, L.cell_off, L.cell_fill, L.cell_members);
   cudaMemsetAsync(L.nfallback, 0, sizeof(int), st);
-  LearnedArgs A{B.x,          B.y,          ia,          B.ja[B.cur], B.d,       nt,
-                L.prop_cells, L.bound_cells, L.bound_vals, L.cell_off, L.cell_members, B.nnkey,
-                L.fallback,   L.nfallback,   &B.st->certified,
-                B.precision == 0 ? &B.st->fallbacks : nullptr};
-  k_learned_nns<<<(nt + 7) / 8, 256, 0, st>>>(A);
+  unsigned long long* nfall = B.precision == 0 ? &B.st->fallbacks : nullptr;
+  if (learned_cell_scan(B.d, B.x, B.y)) {
+    LcArgs C{B.x,        B.y,          ia,          B.ja[B.cur], B.d,       nt,        K,
+             L.prop_cells, L.bound_cells, L.bound_vals, L.cell_off, L.cell_members, L.lc_cand, L.lc_slot,
+             L.lc_ncand,   L.lc_bound,   L.lc_qcnt,   L.lc_qoff,  L.lc_work,  L.lc_nwork, L.lc_qlist,
+             L.lc_best,    B.nnkey,      L.fallback,  L.nfallback, &B.st->certified, nfall};
+    cudaMemsetAsync(L.lc_qcnt, 0, K * sizeof(int), st);
+    cudaMemsetAsync(L.lc_best, 0xff, (size_t)nt * sizeof(unsigned long long), st);
+    k_learned_plan<<<(nt + 7) / 8, 256, 0, st>>>(C);
+    k_lc_offsets<<<1, 1024, 0, st>>>(C);
+    k_lc_group<<<(int)(((int64_t)nt * PROP_TAKE + 255) / 256), 256, 0, st>>>(C);
+    const int g = num_sms() * 4;
+    if (B.d == 32) k_lc_keys<32><<<g, LC_THREADS, 0, st>>>(C);
+    else if (B.d == 64) k_lc_keys<64><<<g, LC_THREADS, 0, st>>>(C);
+    else k_lc_keys<128><<<g, LC_THREADS, 0, st>>>(C);
+    k_learned_cert<<<(nt + 255) / 256, 256, 0, st>>>(C);
+  } else {
+    LearnedArgs A{B.x,          B.y,          ia,          B.ja[B.cur], B.d,       nt,
+                  L.prop_cells, L.bound_cells, L.bound_vals, L.cell_off, L.cell_members, B.nnkey,
+                  L.fallback,   L.nfallback,   &B.st->certified, nfall};
+    k_learned_nns<<<(nt + 7) / 8, 256, 0, st>>>(A);
+  }
   if (B.precision == 0) {  // FP32
     launch_nns_f32(B, mt, nt, L.fallback, L.nfallback, st);
   } else {

@@ -61,6 +61,17 @@ struct LearnedBufs {
   float* tmp3;
   int* sel_over;        // [chunk] rows the one-warp selection hands to the block selection
   int* nsel_over;
+  // the cell-by-cell scan (learned.cu)
+  int* lc_cand;         // [n][PROP_TAKE]
+  int* lc_slot;         // [n][PROP_TAKE]
+  int* lc_ncand;        // [n]
+  float* lc_bound;      // [n]
+  int* lc_qcnt;         // [cells]
+  int* lc_qoff;         // [cells + 1]
+  int* lc_work;         // [cells + 1]
+  int* lc_nwork;
+  int* lc_qlist;        // [n * PROP_TAKE]
+  unsigned long long* lc_best;  // [n]
   int chunk;            // consumers per pass
 };
 
@@ -71,6 +82,10 @@ int learned_prepare(const LearnedBufs& L, const float* x, int64_t m, const float
 // One round: CSR of active suppliers by cell, candidate scan + certificate,
 // FP32 rescan of the rest.  Writes B.nnkey (all ones on entry).
 int launch_nns_learned(const SolveBufs& B, const LearnedBufs& L, int mt, int nt, cudaStream_t st);
+// Whether a round takes the cell-by-cell scan (d of 32, 64 or 128, 16-byte
+// aligned coordinates; else one warp per consumer): 10 launches per round
+// before any fallback, against 5.
+bool learned_cell_scan(int d, const float* x, const float* y);
 
 // Training / inference building blocks (learned.cu).
 int mlp_forward(const nnsemd_proposal* P, const float* X, int rows, float* H1, float* H2, float* Z, cudaStream_t st);
