@@ -176,6 +176,8 @@ size_t layout_solve(void* base, int64_t m, int64_t n, int d, SolveBufs& B, int p
     L->lc_nwork = C.take<int>(1);
     L->lc_qlist = C.take<int>((size_t)n * PROP_TAKE);
     L->lc_best = C.take<unsigned long long>(n);
+    L->w3p = C.take<uint8_t>(linear_tc_supported(h) ? linear_tc_packed_bytes(K, h) : 0);
+    L->h2p = C.take<uint8_t>(linear_tc_supported(h) ? linear_tc_packed_bytes(L->chunk, h) : 0);
   }
   if (precision != NNSEMD_FP32) {
     const size_t kb = tc_kb(d, precision);
@@ -361,12 +363,13 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
   const int clcap = lowd ? finish_cluster_cap(B.d, B.metric) : 0;
   if (learned) {
     // once per solve: supplier cells and radii, consumer proposals and bounds
-    if (learned_prepare(*learned, B.x, B.m, B.y, B.n, B.d, st))
+    if (learned_prepare(*learned, B.x, B.m, B.y, B.n, B.d, &B.st->err, st))
       return drained(fail(ctx, NNSEMD_ERR_CUDA, "proposal preparation"));
     // per chunk: standardisation, three GEMMs, the centroid bounds and two
     // selections (one-warp + block pass each, or the block pass alone)
     const int sel = learned->P->cells >= 2 * PROP_LIST ? 2 : 1;
-    L += 8 + (5 + 2 * sel) * ((B.n + learned->chunk - 1) / learned->chunk);
+    L += 8 + (linear_tc_supported(learned->P->hidden) ? 1 : 0) +
+         (5 + 2 * sel) * ((B.n + learned->chunk - 1) / learned->chunk);
   }
   while (mt > 0 && nt > 0) {
     const bool tail = clcap ? (mt <= clcap && nt <= clcap)

@@ -164,6 +164,17 @@ void launch_check_finite(const float* v, int64_t count, unsigned* err, cudaStrea
 size_t tc_kb(int d, int precision);  // packed bytes per row
 int tc_bn(size_t kb);                // supplier rows per tile
 bool tc_supported(int d, int precision);  // the operand tiles of K2 fit its shared memory
+
+// A BF16 linear layer on the tensor cores (tc.cu): Z [rows][N] = X W^T + b
+// with FP32 accumulation, X [rows][K] and W [N][K] packed by
+// pack_rows_bf16 into linear_tc_packed_bytes(rows, K) bytes each; K a
+// multiple of 16 up to 256 (linear_tc_supported).  A wait that gives up
+// sets EF_TIMEOUT in *err.
+bool linear_tc_supported(int K);
+size_t linear_tc_packed_bytes(int rows, int K);
+int pack_rows_bf16(const float* src, int rows, int K, uint8_t* out, cudaStream_t st);
+int linear_tc(const uint8_t* X, int rows, int K, const uint8_t* W, const float* bias, int N, float* Z, unsigned* err,
+              cudaStream_t st);
 // NNS of every active consumer: tensor-core candidates, exact FP32 re-rank,
 // certificate, FP32 rescan of the rest.  Writes B.nnkey (must be all ones).
 int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int precision, cudaStream_t st,

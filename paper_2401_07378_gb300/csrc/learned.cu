@@ -623,10 +623,15 @@ static void select_rows(const float* V, int rows, int cols, int* out_idx, float*
   }
 }
 
-int learned_prepare(const LearnedBufs& L, const float* x, int64_t m, const float* y, int64_t n, int d,
+int learned_prepare(const LearnedBufs& L, const float* x, int64_t m, const float* y, int64_t n, int d, unsigned* err,
                     cudaStream_t st) {
   const nnsemd_proposal* P = L.P;
   const int K = P->cells, h = P->hidden;
+  // the scoring layer (hidden -> cells, the widest) runs on the tensor
+  // cores in BF16 where its width allows: its scores only rank the cells a
+  // consumer scans, every choice is still certified with exact keys
+  const bool tc3 = linear_tc_supported(h);
+  if (tc3 && pack_rows_bf16(P->params + P->off_W3(), K, h, L.w3p, st)) return -1;
   if (assign_cells(P, x, m, L.cell_of_x, st)) return -1;
   cudaMemsetAsync(L.radius, 0, K * sizeof(float), st);
   k_cell_radius<<<num_sms() * 4, 256, 0, st>>>(x, m, d, L.cell_of_x, P->centroids, reinterpret_cast<unsigned*>(L.radius));
@@ -639,7 +644,15 @@ int learned_prepare(const LearnedBufs& L, const float* x, int64_t m, const float
     float* H2 = L.tmp + (size_t)L.chunk * h;
     float* Z = L.tmp2;               // rows x K
     k_standardise<<<num_sms() * 4, 256, 0, st>>>(yc, rows, d, P->in_mean, P->in_scale, Xs);
-    mlp_forward(P, Xs, rows, H1, H2, Z, st);
+    if (tc3) {
+      const float* p = P->params;
+      gemm<false, true, EPI_BIAS_RELU>(Xs, d, p + P->off_W1(), d, H1, h, rows, h, d, p + P->off_b1(), st);
+      gemm<false, true, EPI_BIAS_RELU>(H1, h, p + P->off_W2(), h, H2, h, rows, h, h, p + P->off_b2(), st);
+      if (pack_rows_bf16(H2, rows, h, L.h2p, st) || linear_tc(L.h2p, rows, h, L.w3p, p + P->off_b3(), K, Z, err, st))
+        return -1;
+    } else {
+      mlp_forward(P, Xs, rows, H1, H2, Z, st);
+    }
     select_rows<true>(Z, rows, K, L.prop_cells + r0 * PROP_LIST, nullptr, L, st);
     // bounds: the cells with the smallest lower bound
     dim3 g2((K + 63) / 64, (rows + 63) / 64);

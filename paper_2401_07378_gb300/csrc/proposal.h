@@ -72,12 +72,14 @@ struct LearnedBufs {
   int* lc_nwork;
   int* lc_qlist;        // [n * PROP_TAKE]
   unsigned long long* lc_best;  // [n]
+  uint8_t* w3p;         // the scoring layer's weights packed for linear_tc
+  uint8_t* h2p;         // [chunk] hidden rows packed for linear_tc
   int chunk;            // consumers per pass
 };
 
 // Per-solve preparation: supplier cells and radii, consumer proposals and
 // cell bounds (x, y original coordinates, d; m suppliers, n consumers).
-int learned_prepare(const LearnedBufs& L, const float* x, int64_t m, const float* y, int64_t n, int d,
+int learned_prepare(const LearnedBufs& L, const float* x, int64_t m, const float* y, int64_t n, int d, unsigned* err,
                     cudaStream_t st);
 // One round: CSR of active suppliers by cell, candidate scan + certificate,
 // FP32 rescan of the rest.  Writes B.nnkey (all ones on entry).

@@ -582,4 +582,129 @@ int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int preci
   return 0;
 }
 
+// --------------------------------------------------------------------------
+// A plain BF16 linear layer on the tensor cores, Z = X W^T + b (FP32
+// accumulation): the learned proposal's widest layer at inference.  Both
+// operands are packed like K2's (K-major, no swizzle, tiles of 128 rows).
+// --------------------------------------------------------------------------
+
+constexpr int LIN_TILE = 128;  // rows of X and of W per tile
+constexpr int LIN_MAX_K = 256;
+
+// Rows [0, rows) of src [rows][K] as BF16 tiles of LIN_TILE rows (padding
+// rows up to the next tile are zero); one thread per row.
+__global__ void k_pack_rows_bf16(const float* __restrict__ src, int rows, int rows_pad, int K,
+                                 uint8_t* __restrict__ out) {
+  const int kb = 2 * K;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < rows_pad; p += gridDim.x * blockDim.x) {
+    const float* row = p < rows ? src + (size_t)p * K : nullptr;
+    const int t = p / LIN_TILE, r = p % LIN_TILE;
+    for (int c = 0; c < kb / 16; ++c) pack_block(row, K, c, 1.f, FMT_BF16, out + (size_t)t * LIN_TILE * kb, LIN_TILE, r);
+  }
+}
+
+// One CTA per 128 x 128 block of Z: both tiles by one bulk copy each, K / 16
+// MMAs into a 128-column accumulator, then every thread adds the bias to
+// its row's 128 values and stores those inside [rows) x [N).
+__global__ void __launch_bounds__(128, 1) k_linear_tc(const uint8_t* __restrict__ X, const uint8_t* __restrict__ W,
+                                                      int K, const float* __restrict__ bias, int rows, int N,
+                                                      float* __restrict__ Z, unsigned* err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t bar_ld;
+  __shared__ __align__(8) uint64_t bar_mma;
+  __shared__ uint32_t tslot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t tile_bytes = LIN_TILE * 2 * K;
+  uint8_t* sX = smem;
+  uint8_t* sW = smem + tile_bytes;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar_ld, 1);
+    mbar_init(&bar_mma, 1);
+    mbar_fence_init();
+  }
+  if (warp == 0) tmem_alloc(&tslot, LIN_TILE);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tslot;
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar_ld, 2 * tile_bytes);
+    tma_load_1d(sX, X + (size_t)blockIdx.y * tile_bytes, tile_bytes, &bar_ld);
+    tma_load_1d(sW, W + (size_t)blockIdx.x * tile_bytes, tile_bytes, &bar_ld);
+    if (mbar_wait_bounded(&bar_ld, 0)) {
+      tc_fence_after();
+      const uint32_t idesc = make_idesc(1, LIN_TILE, LIN_TILE);
+      const uint32_t x0 = smem_u32(sX), w0 = smem_u32(sW);
+      for (int k = 0; k < K / 16; ++k)
+        mma_issue<FMT_BF16>(tmem, make_desc(x0 + k * 2 * LIN_TILE * 16, LIN_TILE * 16, 128),
+                            make_desc(w0 + k * 2 * LIN_TILE * 16, LIN_TILE * 16, 128), idesc, k > 0 ? 1u : 0u);
+      mma_commit(&bar_mma);
+    }
+  }
+  // the accumulator (every lane of a warp agrees before the aligned loads)
+  const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar_mma, 0));
+  tc_fence_after();
+  if (ok) {
+    const int row = blockIdx.y * LIN_TILE + warp * 32 + lane;
+    const int n0 = blockIdx.x * LIN_TILE;
+#pragma unroll 1
+    for (int cb = 0; cb < LIN_TILE; cb += 64) {
+      uint32_t rr[4][16];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) tmem_ld16_async(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb + 16 * b), rr[b]);
+      tmem_ld_wait(rr);
+      if (row < rows) {
+        float* zr = Z + (size_t)row * N;
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+          for (int e = 0; e < 16; e += 4) {
+            const int n = n0 + cb + 16 * b + e;
+            if ((N & 3) == 0 && n + 3 < N) {
+              const float4 bv = *reinterpret_cast<const float4*>(bias + n);
+              *reinterpret_cast<float4*>(zr + n) =
+                  make_float4(__uint_as_float(rr[b][e]) + bv.x, __uint_as_float(rr[b][e + 1]) + bv.y,
+                              __uint_as_float(rr[b][e + 2]) + bv.z, __uint_as_float(rr[b][e + 3]) + bv.w);
+            } else {
+#pragma unroll
+              for (int f = 0; f < 4; ++f)
+                if (n + f < N) zr[n + f] = __uint_as_float(rr[b][e + f]) + bias[n + f];
+            }
+          }
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    atomicOr(err, EF_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, LIN_TILE);
+}
+
+bool linear_tc_supported(int K) { return K >= 16 && K <= LIN_MAX_K && K % 16 == 0; }
+
+size_t linear_tc_packed_bytes(int rows, int K) {
+  return (size_t)(rows + LIN_TILE - 1) / LIN_TILE * LIN_TILE * 2 * K;
+}
+
+int pack_rows_bf16(const float* src, int rows, int K, uint8_t* out, cudaStream_t st) {
+  const int rows_pad = (rows + LIN_TILE - 1) / LIN_TILE * LIN_TILE;
+  const int g = std::max(1, std::min((rows_pad + 255) / 256, num_sms() * 8));
+  k_pack_rows_bf16<<<g, 256, 0, st>>>(src, rows, rows_pad, K, out);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int linear_tc(const uint8_t* X, int rows, int K, const uint8_t* W, const float* bias, int N, float* Z, unsigned* err,
+              cudaStream_t st) {
+  if (!linear_tc_supported(K) || rows <= 0 || N <= 0) return -2;
+  const int smem = 2 * LIN_TILE * 2 * LIN_MAX_K;
+  static const bool attr = cudaFuncSetAttribute(k_linear_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+                           cudaSuccess;
+  if (!attr) return -1;
+  dim3 grid((N + LIN_TILE - 1) / LIN_TILE, (rows + LIN_TILE - 1) / LIN_TILE);
+  k_linear_tc<<<grid, 128, 2 * LIN_TILE * 2 * K, st>>>(X, W, K, bias, rows, N, Z, err);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 }  // namespace nnsemd
