@@ -594,7 +594,8 @@ def run_ours(args) -> dict | None:
                       total_ms, lowd, sms)
         if prop is not None:
             # the learned step scans candidates only: its rate is the full scan's work over its time
-            rl["kernel"] = "learned NNS step (cell bookkeeping, k_learned_nns, FP32 rescan of the uncertified)"
+            rl["kernel"] = ("learned NNS step (cell lists, candidate plan, k_lc_keys cell-by-cell exact scan, "
+                            "certificate, tensor-core scan + re-rank of the uncertified)")
             rl["note"] = "achieved counts the full scan's 2d ops per pair: an effective rate, not pipe utilisation"
     line = {
         "metric": METRIC, "value": args.steps * total_units / (max_ms / 1e3), "unit": "pairs/s", "n_gpus": ws,

@@ -178,6 +178,12 @@ size_t layout_solve(void* base, int64_t m, int64_t n, int d, SolveBufs& B, int p
     L->lc_best = C.take<unsigned long long>(n);
     L->w3p = C.take<uint8_t>(linear_tc_supported(h) ? linear_tc_packed_bytes(K, h) : 0);
     L->h2p = C.take<uint8_t>(linear_tc_supported(h) ? linear_tc_packed_bytes(L->chunk, h) : 0);
+    L->assign_chunk = 65536;
+    const bool tca = linear_tc_supported(d);
+    L->mup = C.take<uint8_t>(tca ? linear_tc_packed_bytes(K, d) : 0);
+    L->mu_bias = C.take<float>(tca ? K : 0);
+    L->xp = C.take<uint8_t>(tca ? linear_tc_packed_bytes(L->assign_chunk, d) : 0);
+    L->apart = C.take<unsigned long long>(tca ? (size_t)L->assign_chunk * ((K + 127) / 128) : 0);
   }
   if (precision != NNSEMD_FP32) {
     const size_t kb = tc_kb(d, precision);
@@ -368,7 +374,10 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
     // per chunk: standardisation, three GEMMs, the centroid bounds and two
     // selections (one-warp + block pass each, or the block pass alone)
     const int sel = learned->P->cells >= 2 * PROP_LIST ? 2 : 1;
-    L += 8 + (linear_tc_supported(learned->P->hidden) ? 1 : 0) +
+    // supplier cells: on the tensor cores two set-up kernels, three per pass,
+    // and the radii
+    const int64_t passes = (B.m + learned->assign_chunk - 1) / learned->assign_chunk;
+    L += (linear_tc_supported(B.d) ? 3 + 3 * passes : 8) + (linear_tc_supported(learned->P->hidden) ? 1 : 0) +
          (5 + 2 * sel) * ((B.n + learned->chunk - 1) / learned->chunk);
   }
   while (mt > 0 && nt > 0) {

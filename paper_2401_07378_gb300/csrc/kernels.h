@@ -175,6 +175,11 @@ size_t linear_tc_packed_bytes(int rows, int K);
 int pack_rows_bf16(const float* src, int rows, int K, uint8_t* out, cudaStream_t st);
 int linear_tc(const uint8_t* X, int rows, int K, const uint8_t* W, const float* bias, int N, float* Z, unsigned* err,
               cudaStream_t st);
+// The same layer reduced per row: out[row] = the column of the row's largest
+// value of X W^T + b (lowest column on ties); part holds rows x
+// ceil(N / 128) partial keys.
+int linear_tc_argmax(const uint8_t* X, int rows, int K, const uint8_t* W, const float* bias, int N,
+                     unsigned long long* part, int* out, unsigned* err, cudaStream_t st);
 // NNS of every active consumer: tensor-core candidates, exact FP32 re-rank,
 // certificate, FP32 rescan of the rest.  Writes B.nnkey (must be all ones).
 int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int precision, cudaStream_t st,

@@ -552,6 +552,15 @@ __global__ void k_cell_radius(const float* __restrict__ pts, int64_t N, int d, c
   }
 }
 
+// bias[c] = -|mu_c|^2 / 2 (FP32), the offset of the supplier-to-cell scores
+__global__ void k_half_sq_norms(const float* __restrict__ mu, int cells, int d, float* __restrict__ bias) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cells) return;
+  float s = 0.f;
+  for (int k = 0; k < d; ++k) s = fmaf(mu[(size_t)c * d + k], mu[(size_t)c * d + k], s);
+  bias[c] = -0.5f * s;
+}
+
 // Lower bounds of the squared distance from each row of Y [rows][d] to any
 // supplier of each cell, out[rows][cells]: max(0, |y - mu_c| - r_c)^2.
 // |y - mu_c|^2 is computed in FP32 (direct differences, fma in ascending k,
@@ -632,7 +641,21 @@ int learned_prepare(const LearnedBufs& L, const float* x, int64_t m, const float
   // consumer scans, every choice is still certified with exact keys
   const bool tc3 = linear_tc_supported(h);
   if (tc3 && pack_rows_bf16(P->params + P->off_W3(), K, h, L.w3p, st)) return -1;
-  if (assign_cells(P, x, m, L.cell_of_x, st)) return -1;
+  // the cell of each supplier: any assignment keeps the bounds sound (the
+  // radii below are taken over the cells as assigned), so on the tensor
+  // cores in BF16 where d allows: the largest <x, mu_c> - |mu_c|^2 / 2
+  if (linear_tc_supported(d)) {
+    k_half_sq_norms<<<(K + 255) / 256, 256, 0, st>>>(P->centroids, K, d, L.mu_bias);
+    if (pack_rows_bf16(P->centroids, K, d, L.mup, st)) return -1;
+    for (int64_t r0 = 0; r0 < m; r0 += L.assign_chunk) {
+      const int rows = (int)std::min<int64_t>(L.assign_chunk, m - r0);
+      if (pack_rows_bf16(x + (size_t)r0 * d, rows, d, L.xp, st) ||
+          linear_tc_argmax(L.xp, rows, d, L.mup, L.mu_bias, K, L.apart, L.cell_of_x + r0, err, st))
+        return -1;
+    }
+  } else if (assign_cells(P, x, m, L.cell_of_x, st)) {
+    return -1;
+  }
   cudaMemsetAsync(L.radius, 0, K * sizeof(float), st);
   k_cell_radius<<<num_sms() * 4, 256, 0, st>>>(x, m, d, L.cell_of_x, P->centroids, reinterpret_cast<unsigned*>(L.radius));
   for (int64_t r0 = 0; r0 < n; r0 += L.chunk) {

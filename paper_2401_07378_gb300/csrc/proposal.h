@@ -74,6 +74,12 @@ struct LearnedBufs {
   unsigned long long* lc_best;  // [n]
   uint8_t* w3p;         // the scoring layer's weights packed for linear_tc
   uint8_t* h2p;         // [chunk] hidden rows packed for linear_tc
+  // the supplier-to-cell assignment on the tensor cores
+  int assign_chunk;     // suppliers per pass
+  uint8_t* mup;         // centroids packed for linear_tc
+  float* mu_bias;       // [cells] -|mu_c|^2 / 2
+  uint8_t* xp;          // [assign_chunk] supplier rows packed
+  unsigned long long* apart;  // [assign_chunk][cells / 128] partial row maxima
   int chunk;            // consumers per pass
 };
 

@@ -605,10 +605,14 @@ __global__ void k_pack_rows_bf16(const float* __restrict__ src, int rows, int ro
 
 // One CTA per 128 x 128 block of Z: both tiles by one bulk copy each, K / 16
 // MMAs into a 128-column accumulator, then every thread adds the bias to
-// its row's 128 values and stores those inside [rows) x [N).
+// its row's 128 values and stores those inside [rows) x [N) (ARGMAX: keeps
+// instead the largest of them, lowest column on ties, as a packed key in
+// part[row][column tile]).
+template <bool ARGMAX>
 __global__ void __launch_bounds__(128, 1) k_linear_tc(const uint8_t* __restrict__ X, const uint8_t* __restrict__ W,
                                                       int K, const float* __restrict__ bias, int rows, int N,
-                                                      float* __restrict__ Z, unsigned* err) {
+                                                      float* __restrict__ Z, unsigned long long* __restrict__ part,
+                                                      unsigned* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t bar_ld;
   __shared__ __align__(8) uint64_t bar_mma;
@@ -647,13 +651,26 @@ __global__ void __launch_bounds__(128, 1) k_linear_tc(const uint8_t* __restrict_
   if (ok) {
     const int row = blockIdx.y * LIN_TILE + warp * 32 + lane;
     const int n0 = blockIdx.x * LIN_TILE;
+    unsigned long long best = 0ULL;
 #pragma unroll 1
     for (int cb = 0; cb < LIN_TILE; cb += 64) {
       uint32_t rr[4][16];
 #pragma unroll
       for (int b = 0; b < 4; ++b) tmem_ld16_async(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb + 16 * b), rr[b]);
       tmem_ld_wait(rr);
-      if (row < rows) {
+      if (ARGMAX) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int n = n0 + cb + 16 * b + e;
+            if (n < N) {
+              const unsigned long long key = ((unsigned long long)ordered_bits(__uint_as_float(rr[b][e]) + bias[n])
+                                              << 32) | (0xffffffffu - (unsigned)n);
+              best = key > best ? key : best;
+            }
+          }
+      } else if (row < rows) {
         float* zr = Z + (size_t)row * N;
 #pragma unroll
         for (int b = 0; b < 4; ++b)
@@ -673,6 +690,7 @@ __global__ void __launch_bounds__(128, 1) k_linear_tc(const uint8_t* __restrict_
           }
       }
     }
+    if (ARGMAX && row < rows) part[(size_t)row * gridDim.x + blockIdx.x] = best;
   } else if (threadIdx.x == 0) {
     atomicOr(err, EF_TIMEOUT);
   }
@@ -695,15 +713,38 @@ int pack_rows_bf16(const float* src, int rows, int K, uint8_t* out, cudaStream_t
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int linear_tc(const uint8_t* X, int rows, int K, const uint8_t* W, const float* bias, int N, float* Z, unsigned* err,
-              cudaStream_t st) {
+template <bool ARGMAX>
+static int launch_linear_tc(const uint8_t* X, int rows, int K, const uint8_t* W, const float* bias, int N, float* Z,
+                            unsigned long long* part, unsigned* err, cudaStream_t st) {
   if (!linear_tc_supported(K) || rows <= 0 || N <= 0) return -2;
   const int smem = 2 * LIN_TILE * 2 * LIN_MAX_K;
-  static const bool attr = cudaFuncSetAttribute(k_linear_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
-                           cudaSuccess;
+  static const bool attr =
+      cudaFuncSetAttribute(k_linear_tc<ARGMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
   if (!attr) return -1;
   dim3 grid((N + LIN_TILE - 1) / LIN_TILE, (rows + LIN_TILE - 1) / LIN_TILE);
-  k_linear_tc<<<grid, 128, 2 * LIN_TILE * 2 * K, st>>>(X, W, K, bias, rows, N, Z, err);
+  k_linear_tc<ARGMAX><<<grid, 128, 2 * LIN_TILE * 2 * K, st>>>(X, W, K, bias, rows, N, Z, part, err);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int linear_tc(const uint8_t* X, int rows, int K, const uint8_t* W, const float* bias, int N, float* Z, unsigned* err,
+              cudaStream_t st) {
+  return launch_linear_tc<false>(X, rows, K, W, bias, N, Z, nullptr, err, st);
+}
+
+// out[row] = the column of the row's largest partial key
+__global__ void k_argmax_parts(const unsigned long long* __restrict__ part, int rows, int tiles, int* __restrict__ out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  unsigned long long best = 0ULL;
+  for (int t = 0; t < tiles; ++t) best = max(best, part[(size_t)r * tiles + t]);
+  out[r] = (int)(0xffffffffu - (unsigned)(best & 0xffffffffu));
+}
+
+int linear_tc_argmax(const uint8_t* X, int rows, int K, const uint8_t* W, const float* bias, int N,
+                     unsigned long long* part, int* out, unsigned* err, cudaStream_t st) {
+  const int rc = launch_linear_tc<true>(X, rows, K, W, bias, N, nullptr, part, err, st);
+  if (rc) return rc;
+  k_argmax_parts<<<(rows + 255) / 256, 256, 0, st>>>(part, rows, (N + LIN_TILE - 1) / LIN_TILE, out);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
