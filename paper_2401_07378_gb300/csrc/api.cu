@@ -184,6 +184,13 @@ size_t layout_solve(void* base, int64_t m, int64_t n, int d, SolveBufs& B, int p
     L->mu_bias = C.take<float>(tca ? K : 0);
     L->xp = C.take<uint8_t>(tca ? linear_tc_packed_bytes(L->assign_chunk, d) : 0);
     L->apart = C.take<unsigned long long>(tca ? (size_t)L->assign_chunk * ((K + 127) / 128) : 0);
+    const bool tcb = cell_bounds_tc_supported(d);
+    L->mup3 = C.take<uint8_t>(tcb ? linear_tc_packed_bytes(K, 3 * d) : 0);
+    L->mu_sq_lo = C.take<float>(tcb ? K : 0);
+    L->mu_nrm_up = C.take<float>(tcb ? K : 0);
+    L->yp3 = C.take<uint8_t>(tcb ? linear_tc_packed_bytes(L->chunk, 3 * d) : 0);
+    L->y_sq_lo = C.take<float>(tcb ? L->chunk : 0);
+    L->y_nrm_up = C.take<float>(tcb ? L->chunk : 0);
   }
   if (precision != NNSEMD_FP32) {
     const size_t kb = tc_kb(d, precision);
@@ -377,8 +384,9 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
     // supplier cells: on the tensor cores two set-up kernels, three per pass,
     // and the radii
     const int64_t passes = (B.m + learned->assign_chunk - 1) / learned->assign_chunk;
+    const bool tcb = cell_bounds_tc_supported(B.d);
     L += (linear_tc_supported(B.d) ? 3 + 3 * passes : 8) + (linear_tc_supported(learned->P->hidden) ? 1 : 0) +
-         (5 + 2 * sel) * ((B.n + learned->chunk - 1) / learned->chunk);
+         (tcb ? 2 : 0) + (5 + (tcb ? 2 : 0) + 2 * sel) * ((B.n + learned->chunk - 1) / learned->chunk);
   }
   while (mt > 0 && nt > 0) {
     const bool tail = clcap ? (mt <= clcap && nt <= clcap)

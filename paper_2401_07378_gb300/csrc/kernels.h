@@ -180,6 +180,20 @@ int linear_tc(const uint8_t* X, int rows, int K, const uint8_t* W, const float* 
 // ceil(N / 128) partial keys.
 int linear_tc_argmax(const uint8_t* X, int rows, int K, const uint8_t* W, const float* bias, int N,
                      unsigned long long* part, int* out, unsigned* err, cudaStream_t st);
+// Lower bounds of the squared distance from each row y of [rows][d] to any
+// point of each cell (centre mu_c, radius r_c): out[row][c] =
+// max(0, |y - mu_c| - r_c)^2 with |y - mu_c| bounded from below through a
+// BF16X3 contraction and its error bound, rounded toward the bound.  The
+// cells are packed once (cell_bounds_tc_cells: packed into
+// linear_tc_packed_bytes(cells, 3d) bytes, |mu|^2 down and |mu| up); the
+// rows use scratch of linear_tc_packed_bytes(rows, 3d) bytes and 2 x rows
+// floats.  d a multiple of 16 with 3d <= 256 (cell_bounds_tc_supported).
+bool cell_bounds_tc_supported(int d);
+int cell_bounds_tc_cells(const float* mu, int cells, int d, uint8_t* packed, float* sq_lo, float* nrm_up,
+                         cudaStream_t st);
+int cell_bounds_tc(const float* y, int rows, int d, uint8_t* packed_y, float* y_sq_lo, float* y_nrm_up,
+                   const uint8_t* packed_mu, const float* mu_sq_lo, const float* mu_nrm_up, const float* radius,
+                   int cells, float* out, unsigned* err, cudaStream_t st);
 // NNS of every active consumer: tensor-core candidates, exact FP32 re-rank,
 // certificate, FP32 rescan of the rest.  Writes B.nnkey (must be all ones).
 int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int precision, cudaStream_t st,

@@ -658,6 +658,10 @@ int learned_prepare(const LearnedBufs& L, const float* x, int64_t m, const float
   }
   cudaMemsetAsync(L.radius, 0, K * sizeof(float), st);
   k_cell_radius<<<num_sms() * 4, 256, 0, st>>>(x, m, d, L.cell_of_x, P->centroids, reinterpret_cast<unsigned*>(L.radius));
+  // the cell bounds on the tensor cores (a BF16X3 contraction with its error
+  // bound) where d allows, else by FP32 direct differences
+  const bool tcb = cell_bounds_tc_supported(d);
+  if (tcb && cell_bounds_tc_cells(P->centroids, K, d, L.mup3, L.mu_sq_lo, L.mu_nrm_up, st)) return -1;
   for (int64_t r0 = 0; r0 < n; r0 += L.chunk) {
     const int rows = (int)std::min<int64_t>(L.chunk, n - r0);
     const float* yc = y + (size_t)r0 * d;
@@ -678,8 +682,14 @@ int learned_prepare(const LearnedBufs& L, const float* x, int64_t m, const float
     }
     select_rows<true>(Z, rows, K, L.prop_cells + r0 * PROP_LIST, nullptr, L, st);
     // bounds: the cells with the smallest lower bound
-    dim3 g2((K + 63) / 64, (rows + 63) / 64);
-    k_centroid_lb<<<g2, 256, 0, st>>>(yc, rows, P->centroids, K, d, reinterpret_cast<const unsigned*>(L.radius), Z);
+    if (tcb) {
+      if (cell_bounds_tc(yc, rows, d, L.yp3, L.y_sq_lo, L.y_nrm_up, L.mup3, L.mu_sq_lo, L.mu_nrm_up, L.radius, K, Z,
+                         err, st))
+        return -1;
+    } else {
+      dim3 g2((K + 63) / 64, (rows + 63) / 64);
+      k_centroid_lb<<<g2, 256, 0, st>>>(yc, rows, P->centroids, K, d, reinterpret_cast<const unsigned*>(L.radius), Z);
+    }
     select_rows<false>(Z, rows, K, L.bound_cells + r0 * PROP_LIST, L.bound_vals + r0 * PROP_LIST, L, st);
   }
   (void)h;

@@ -80,6 +80,13 @@ struct LearnedBufs {
   float* mu_bias;       // [cells] -|mu_c|^2 / 2
   uint8_t* xp;          // [assign_chunk] supplier rows packed
   unsigned long long* apart;  // [assign_chunk][cells / 128] partial row maxima
+  // the cell bounds on the tensor cores
+  uint8_t* mup3;        // centroids packed as BF16X3 splits
+  float* mu_sq_lo;      // [cells]
+  float* mu_nrm_up;     // [cells]
+  uint8_t* yp3;         // [chunk] consumer rows packed as BF16X3 splits
+  float* y_sq_lo;       // [chunk]
+  float* y_nrm_up;      // [chunk]
   int chunk;            // consumers per pass
 };
 

@@ -23,6 +23,7 @@
 // warps per row, a share of the columns each) and update its top-K.  Every
 // wait on an mbarrier is bounded and raises EF_TIMEOUT instead of hanging.
 #include <algorithm>
+#include <cmath>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -583,42 +584,70 @@ int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int preci
 }
 
 // --------------------------------------------------------------------------
-// A plain BF16 linear layer on the tensor cores, Z = X W^T + b (FP32
-// accumulation): the learned proposal's widest layer at inference.  Both
-// operands are packed like K2's (K-major, no swizzle, tiles of 128 rows).
+// A plain BF16 contraction on the tensor cores, S = X W^T with FP32
+// accumulation (rows of X against rows of W), for the learned proposal's
+// per-solve passes.  Both operands are packed like K2's (K-major, no
+// swizzle, tiles of 128 rows).  The epilogue either stores S + b (a linear
+// layer), keeps each row's largest S + b (an assignment), or turns S into a
+// lower bound of a squared distance (below).
 // --------------------------------------------------------------------------
 
 constexpr int LIN_TILE = 128;  // rows of X and of W per tile
-constexpr int LIN_MAX_K = 256;
+constexpr int LIN_MAX_K = 256; // packed values per row
 
-// Rows [0, rows) of src [rows][K] as BF16 tiles of LIN_TILE rows (padding
-// rows up to the next tile are zero); one thread per row.
-__global__ void k_pack_rows_bf16(const float* __restrict__ src, int rows, int rows_pad, int K,
-                                 uint8_t* __restrict__ out) {
-  const int kb = 2 * K;
+enum LinMode : int { LIN_STORE = 0, LIN_ARGMAX = 1, LIN_LOWER = 2 };
+
+struct LinArgs {
+  const uint8_t* X;
+  const uint8_t* W;
+  int K;                     // packed values per row
+  int rows, N;
+  const float* bias;         // STORE / ARGMAX: [N]
+  float* Z;                  // STORE / LOWER: [rows][N]
+  unsigned long long* part;  // ARGMAX: [rows][ceil(N / 128)]
+  // LOWER: the rows and columns as points; X and W hold BF16X3 copies
+  const float* row_sq_lo;    // [rows] |y|^2 rounded down
+  const float* row_nrm_up;   // [rows] |y| rounded up
+  const float* col_sq_lo;    // [N] |mu|^2 rounded down
+  const float* col_nrm_up;   // [N] |mu| rounded up
+  const float* col_radius;   // [N] r_c (rounded up when formed)
+  float err_coeff;           // |S - <y, mu>| <= err_coeff |y| |mu| + 1e-30
+  unsigned* err;
+};
+
+// Rows [0, rows) of src [rows][d] packed in tiles of LIN_TILE rows (padding
+// rows zero): BF16 copies (fmt FMT_BF16), or BF16X3 splits (FMT_BF16X3;
+// `supplier` picks the segment order) of 3d values per row.
+__global__ void k_pack_rows(const float* __restrict__ src, int rows, int rows_pad, int d, int fmt, bool supplier,
+                            uint8_t* __restrict__ out) {
+  const int kb = 2 * d * fmt_parts(fmt);
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < rows_pad; p += gridDim.x * blockDim.x) {
-    const float* row = p < rows ? src + (size_t)p * K : nullptr;
+    const float* row = p < rows ? src + (size_t)p * d : nullptr;
     const int t = p / LIN_TILE, r = p % LIN_TILE;
-    for (int c = 0; c < kb / 16; ++c) pack_block(row, K, c, 1.f, FMT_BF16, out + (size_t)t * LIN_TILE * kb, LIN_TILE, r);
+    for (int c = 0; c < kb / 16; ++c)
+      pack_block(row, d, c, 1.f, fmt, out + (size_t)t * LIN_TILE * kb, LIN_TILE, r, supplier);
   }
 }
 
-// One CTA per 128 x 128 block of Z: both tiles by one bulk copy each, K / 16
-// MMAs into a 128-column accumulator, then every thread adds the bias to
-// its row's 128 values and stores those inside [rows) x [N) (ARGMAX: keeps
-// instead the largest of them, lowest column on ties, as a packed key in
-// part[row][column tile]).
-template <bool ARGMAX>
-__global__ void __launch_bounds__(128, 1) k_linear_tc(const uint8_t* __restrict__ X, const uint8_t* __restrict__ W,
-                                                      int K, const float* __restrict__ bias, int rows, int N,
-                                                      float* __restrict__ Z, unsigned long long* __restrict__ part,
-                                                      unsigned* err) {
+// One CTA per 128 x 128 block of S: both tiles by one bulk copy each, K / 16
+// MMAs into a 128-column accumulator, then every thread takes its row's 128
+// values through the mode's epilogue (columns >= N and rows >= rows are
+// skipped; ARGMAX keeps the largest S + b, lowest column on ties, as a
+// packed key in part[row][column tile]).
+//
+// LOWER: with S~ the computed <y~, mu~> of the BF16X3 copies, |S~ - <y, mu>|
+// <= err_coeff |y| |mu| (+ 1e-30 for the subnormal floors), so
+//   |y - mu|^2 >= |y|^2_lo + |mu|^2_lo - 2 (S~ + err_coeff |y|_up |mu|_up),
+// and the bound on the squared distance to any point of cell `col` is
+// max(0, sqrt(that) - r_col)^2, every step rounded toward the bound.
+template <int MODE>
+__global__ void __launch_bounds__(128, 1) k_linear_tc(LinArgs A) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t bar_ld;
   __shared__ __align__(8) uint64_t bar_mma;
   __shared__ uint32_t tslot;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t tile_bytes = LIN_TILE * 2 * K;
+  const uint32_t tile_bytes = LIN_TILE * 2 * A.K;
   uint8_t* sX = smem;
   uint8_t* sW = smem + tile_bytes;
   if (threadIdx.x == 0) {
@@ -633,13 +662,13 @@ __global__ void __launch_bounds__(128, 1) k_linear_tc(const uint8_t* __restrict_
   const uint32_t tmem = tslot;
   if (threadIdx.x == 0) {
     mbar_expect_tx(&bar_ld, 2 * tile_bytes);
-    tma_load_1d(sX, X + (size_t)blockIdx.y * tile_bytes, tile_bytes, &bar_ld);
-    tma_load_1d(sW, W + (size_t)blockIdx.x * tile_bytes, tile_bytes, &bar_ld);
+    tma_load_1d(sX, A.X + (size_t)blockIdx.y * tile_bytes, tile_bytes, &bar_ld);
+    tma_load_1d(sW, A.W + (size_t)blockIdx.x * tile_bytes, tile_bytes, &bar_ld);
     if (mbar_wait_bounded(&bar_ld, 0)) {
       tc_fence_after();
       const uint32_t idesc = make_idesc(1, LIN_TILE, LIN_TILE);
       const uint32_t x0 = smem_u32(sX), w0 = smem_u32(sW);
-      for (int k = 0; k < K / 16; ++k)
+      for (int k = 0; k < A.K / 16; ++k)
         mma_issue<FMT_BF16>(tmem, make_desc(x0 + k * 2 * LIN_TILE * 16, LIN_TILE * 16, 128),
                             make_desc(w0 + k * 2 * LIN_TILE * 16, LIN_TILE * 16, 128), idesc, k > 0 ? 1u : 0u);
       mma_commit(&bar_mma);
@@ -651,6 +680,12 @@ __global__ void __launch_bounds__(128, 1) k_linear_tc(const uint8_t* __restrict_
   if (ok) {
     const int row = blockIdx.y * LIN_TILE + warp * 32 + lane;
     const int n0 = blockIdx.x * LIN_TILE;
+    const bool live = row < A.rows;
+    float ysq = 0.f, ynr = 0.f;
+    if (MODE == LIN_LOWER && live) {
+      ysq = A.row_sq_lo[row];
+      ynr = A.row_nrm_up[row];
+    }
     unsigned long long best = 0ULL;
 #pragma unroll 1
     for (int cb = 0; cb < LIN_TILE; cb += 64) {
@@ -658,77 +693,52 @@ __global__ void __launch_bounds__(128, 1) k_linear_tc(const uint8_t* __restrict_
 #pragma unroll
       for (int b = 0; b < 4; ++b) tmem_ld16_async(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb + 16 * b), rr[b]);
       tmem_ld_wait(rr);
-      if (ARGMAX) {
+      if (!live) continue;
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
+      for (int b = 0; b < 4; ++b)
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int n = n0 + cb + 16 * b + e;
-            if (n < N) {
-              const unsigned long long key = ((unsigned long long)ordered_bits(__uint_as_float(rr[b][e]) + bias[n])
-                                              << 32) | (0xffffffffu - (unsigned)n);
+        for (int e = 0; e < 16; e += 4) {
+          const int nq = n0 + cb + 16 * b + e;
+          float out[4];
+#pragma unroll
+          for (int f = 0; f < 4; ++f) {
+            const int n = nq + f;
+            const float sv = __uint_as_float(rr[b][e + f]);
+            out[f] = 0.f;
+            if (n >= A.N) continue;
+            if (MODE == LIN_ARGMAX) {
+              const unsigned long long key =
+                  ((unsigned long long)ordered_bits(sv + A.bias[n]) << 32) | (0xffffffffu - (unsigned)n);
               best = key > best ? key : best;
+            } else if (MODE == LIN_STORE) {
+              out[f] = sv + A.bias[n];
+            } else {
+              const float eb = __fmaf_ru(A.err_coeff, __fmul_ru(ynr, A.col_nrm_up[n]), 1e-30f);
+              const float d2 = __fsub_rd(__fadd_rd(ysq, A.col_sq_lo[n]), __fmul_ru(2.f, __fadd_ru(sv, eb)));
+              const float gap = __fsub_rd(__fsqrt_rd(fmaxf(d2, 0.f)), A.col_radius[n]);
+              out[f] = gap > 0.f ? __fmul_rd(gap, gap) : 0.f;
             }
           }
-      } else if (row < rows) {
-        float* zr = Z + (size_t)row * N;
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-#pragma unroll
-          for (int e = 0; e < 16; e += 4) {
-            const int n = n0 + cb + 16 * b + e;
-            if ((N & 3) == 0 && n + 3 < N) {
-              const float4 bv = *reinterpret_cast<const float4*>(bias + n);
-              *reinterpret_cast<float4*>(zr + n) =
-                  make_float4(__uint_as_float(rr[b][e]) + bv.x, __uint_as_float(rr[b][e + 1]) + bv.y,
-                              __uint_as_float(rr[b][e + 2]) + bv.z, __uint_as_float(rr[b][e + 3]) + bv.w);
+          if (MODE != LIN_ARGMAX) {
+            float* zr = A.Z + (size_t)row * A.N;
+            if ((A.N & 3) == 0 && nq + 3 < A.N) {
+              *reinterpret_cast<float4*>(zr + nq) = make_float4(out[0], out[1], out[2], out[3]);
             } else {
 #pragma unroll
               for (int f = 0; f < 4; ++f)
-                if (n + f < N) zr[n + f] = __uint_as_float(rr[b][e + f]) + bias[n + f];
+                if (nq + f < A.N) zr[nq + f] = out[f];
             }
           }
-      }
+        }
     }
-    if (ARGMAX && row < rows) part[(size_t)row * gridDim.x + blockIdx.x] = best;
+    if (MODE == LIN_ARGMAX && live) A.part[(size_t)row * gridDim.x + blockIdx.x] = best;
   } else if (threadIdx.x == 0) {
-    atomicOr(err, EF_TIMEOUT);
+    atomicOr(A.err, EF_TIMEOUT);
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   if (warp == 0) tmem_dealloc(tmem, LIN_TILE);
-}
-
-bool linear_tc_supported(int K) { return K >= 16 && K <= LIN_MAX_K && K % 16 == 0; }
-
-size_t linear_tc_packed_bytes(int rows, int K) {
-  return (size_t)(rows + LIN_TILE - 1) / LIN_TILE * LIN_TILE * 2 * K;
-}
-
-int pack_rows_bf16(const float* src, int rows, int K, uint8_t* out, cudaStream_t st) {
-  const int rows_pad = (rows + LIN_TILE - 1) / LIN_TILE * LIN_TILE;
-  const int g = std::max(1, std::min((rows_pad + 255) / 256, num_sms() * 8));
-  k_pack_rows_bf16<<<g, 256, 0, st>>>(src, rows, rows_pad, K, out);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
-}
-
-template <bool ARGMAX>
-static int launch_linear_tc(const uint8_t* X, int rows, int K, const uint8_t* W, const float* bias, int N, float* Z,
-                            unsigned long long* part, unsigned* err, cudaStream_t st) {
-  if (!linear_tc_supported(K) || rows <= 0 || N <= 0) return -2;
-  const int smem = 2 * LIN_TILE * 2 * LIN_MAX_K;
-  static const bool attr =
-      cudaFuncSetAttribute(k_linear_tc<ARGMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
-  if (!attr) return -1;
-  dim3 grid((N + LIN_TILE - 1) / LIN_TILE, (rows + LIN_TILE - 1) / LIN_TILE);
-  k_linear_tc<ARGMAX><<<grid, 128, 2 * LIN_TILE * 2 * K, st>>>(X, W, K, bias, rows, N, Z, part, err);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
-}
-
-int linear_tc(const uint8_t* X, int rows, int K, const uint8_t* W, const float* bias, int N, float* Z, unsigned* err,
-              cudaStream_t st) {
-  return launch_linear_tc<false>(X, rows, K, W, bias, N, Z, nullptr, err, st);
 }
 
 // out[row] = the column of the row's largest partial key
@@ -740,12 +750,92 @@ __global__ void k_argmax_parts(const unsigned long long* __restrict__ part, int 
   out[r] = (int)(0xffffffffu - (unsigned)(best & 0xffffffffu));
 }
 
+// Per point: |p|^2 (sequential fma, relative error <= gamma_d) rounded down
+// and |p| rounded up.
+__global__ void k_point_norms(const float* __restrict__ pts, int n, int d, float* __restrict__ sq_lo,
+                              float* __restrict__ nrm_up) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s = 0.f;
+  for (int k = 0; k < d; ++k) s = __fmaf_rn(pts[(size_t)i * d + k], pts[(size_t)i * d + k], s);
+  const double g = certify_gamma(d);
+  sq_lo[i] = __fmul_rd(s, __double2float_rd(1.0 - g));
+  nrm_up[i] = __fsqrt_ru(__fmul_ru(s, __double2float_ru(1.0 + g / (1.0 - g))));
+}
+
+bool linear_tc_supported(int K) { return K >= 16 && K <= LIN_MAX_K && K % 16 == 0; }
+
+size_t linear_tc_packed_bytes(int rows, int K) {
+  return (size_t)(rows + LIN_TILE - 1) / LIN_TILE * LIN_TILE * 2 * K;
+}
+
+static int pack_rows(const float* src, int rows, int d, int fmt, bool supplier, uint8_t* out, cudaStream_t st) {
+  const int rows_pad = (rows + LIN_TILE - 1) / LIN_TILE * LIN_TILE;
+  const int g = std::max(1, std::min((rows_pad + 255) / 256, num_sms() * 8));
+  k_pack_rows<<<g, 256, 0, st>>>(src, rows, rows_pad, d, fmt, supplier, out);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int pack_rows_bf16(const float* src, int rows, int K, uint8_t* out, cudaStream_t st) {
+  return pack_rows(src, rows, K, FMT_BF16, false, out, st);
+}
+
+template <int MODE>
+static int launch_linear_tc(const LinArgs& A, cudaStream_t st) {
+  if (!linear_tc_supported(A.K) || A.rows <= 0 || A.N <= 0) return -2;
+  const int smem = 2 * LIN_TILE * 2 * LIN_MAX_K;
+  static const bool attr =
+      cudaFuncSetAttribute(k_linear_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
+  if (!attr) return -1;
+  dim3 grid((A.N + LIN_TILE - 1) / LIN_TILE, (A.rows + LIN_TILE - 1) / LIN_TILE);
+  k_linear_tc<MODE><<<grid, 128, 2 * LIN_TILE * 2 * A.K, st>>>(A);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int linear_tc(const uint8_t* X, int rows, int K, const uint8_t* W, const float* bias, int N, float* Z, unsigned* err,
+              cudaStream_t st) {
+  LinArgs A{};
+  A.X = X, A.W = W, A.K = K, A.rows = rows, A.N = N, A.bias = bias, A.Z = Z, A.err = err;
+  return launch_linear_tc<LIN_STORE>(A, st);
+}
+
 int linear_tc_argmax(const uint8_t* X, int rows, int K, const uint8_t* W, const float* bias, int N,
                      unsigned long long* part, int* out, unsigned* err, cudaStream_t st) {
-  const int rc = launch_linear_tc<true>(X, rows, K, W, bias, N, nullptr, part, err, st);
+  LinArgs A{};
+  A.X = X, A.W = W, A.K = K, A.rows = rows, A.N = N, A.bias = bias, A.part = part, A.err = err;
+  const int rc = launch_linear_tc<LIN_ARGMAX>(A, st);
   if (rc) return rc;
   k_argmax_parts<<<(rows + 255) / 256, 256, 0, st>>>(part, rows, (N + LIN_TILE - 1) / LIN_TILE, out);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+bool cell_bounds_tc_supported(int d) { return d % 16 == 0 && linear_tc_supported(3 * d); }
+
+int cell_bounds_tc_cells(const float* mu, int cells, int d, uint8_t* packed, float* sq_lo, float* nrm_up,
+                         cudaStream_t st) {
+  k_point_norms<<<(cells + 255) / 256, 256, 0, st>>>(mu, cells, d, sq_lo, nrm_up);
+  return pack_rows(mu, cells, d, FMT_BF16X3, true, packed, st);
+}
+
+int cell_bounds_tc(const float* y, int rows, int d, uint8_t* packed_y, float* y_sq_lo, float* y_nrm_up,
+                   const uint8_t* packed_mu, const float* mu_sq_lo, const float* mu_nrm_up, const float* radius,
+                   int cells, float* out, unsigned* err, cudaStream_t st) {
+  k_point_norms<<<(rows + 255) / 256, 256, 0, st>>>(y, rows, d, y_sq_lo, y_nrm_up);
+  if (pack_rows(y, rows, d, FMT_BF16X3, false, packed_y, st)) return -1;
+  // |<y~, mu~> - <y, mu>| <= (Q + K 2^-22 nf^2) |y| |mu| for the BF16X3
+  // copies (the certificate's quantisation and accumulation terms, K = 3d
+  // packed values), with a little slack for this single-precision use
+  const int K = 3 * d;
+  const double nf = quant_norm_factor(FMT_BF16X3);
+  const double c = (quant_err(FMT_BF16X3) + K * 0x1p-22 * nf * nf) * (1.0 + 1e-3);
+  LinArgs A{};
+  A.X = packed_y, A.W = packed_mu, A.K = K, A.rows = rows, A.N = cells, A.Z = out, A.err = err;
+  A.row_sq_lo = y_sq_lo, A.row_nrm_up = y_nrm_up, A.col_sq_lo = mu_sq_lo, A.col_nrm_up = mu_nrm_up;
+  A.col_radius = radius;
+  float cf = (float)c;
+  if ((double)cf < c) cf = std::nextafter(cf, 2.f * cf);  // rounded up
+  A.err_coeff = cf;
+  return launch_linear_tc<LIN_LOWER>(A, st);
 }
 
 }  // namespace nnsemd
