@@ -617,15 +617,18 @@ struct LinArgs {
 
 // Rows [0, rows) of src [rows][d] packed in tiles of LIN_TILE rows (padding
 // rows zero): BF16 copies (fmt FMT_BF16), or BF16X3 splits (FMT_BF16X3;
-// `supplier` picks the segment order) of 3d values per row.
+// `supplier` picks the segment order) of 3d values per row.  One thread per
+// 16-byte block of a row; consecutive threads write consecutive rows of one
+// block column.
 __global__ void k_pack_rows(const float* __restrict__ src, int rows, int rows_pad, int d, int fmt, bool supplier,
                             uint8_t* __restrict__ out) {
   const int kb = 2 * d * fmt_parts(fmt);
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < rows_pad; p += gridDim.x * blockDim.x) {
+  const int64_t total = (int64_t)rows_pad * (kb / 16);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i / rows_pad), p = (int)(i % rows_pad);
     const float* row = p < rows ? src + (size_t)p * d : nullptr;
     const int t = p / LIN_TILE, r = p % LIN_TILE;
-    for (int c = 0; c < kb / 16; ++c)
-      pack_block(row, d, c, 1.f, fmt, out + (size_t)t * LIN_TILE * kb, LIN_TILE, r, supplier);
+    pack_block(row, d, c, 1.f, fmt, out + (size_t)t * LIN_TILE * kb, LIN_TILE, r, supplier);
   }
 }
 
@@ -646,8 +649,20 @@ __global__ void __launch_bounds__(128, 1) k_linear_tc(LinArgs A) {
   __shared__ __align__(8) uint64_t bar_ld;
   __shared__ __align__(8) uint64_t bar_mma;
   __shared__ uint32_t tslot;
+  __shared__ float col_a[LIN_TILE], col_b[LIN_TILE], col_c[LIN_TILE];  // the tile's per-column terms
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t tile_bytes = LIN_TILE * 2 * A.K;
+  {
+    const int n = blockIdx.x * LIN_TILE + threadIdx.x;
+    const bool in = n < A.N;
+    if (MODE == LIN_LOWER) {
+      col_a[threadIdx.x] = in ? A.col_sq_lo[n] : 0.f;
+      col_b[threadIdx.x] = in ? A.col_nrm_up[n] : 0.f;
+      col_c[threadIdx.x] = in ? A.col_radius[n] : 0.f;
+    } else {
+      col_a[threadIdx.x] = in ? A.bias[n] : 0.f;
+    }
+  }
   uint8_t* sX = smem;
   uint8_t* sW = smem + tile_bytes;
   if (threadIdx.x == 0) {
@@ -706,16 +721,17 @@ __global__ void __launch_bounds__(128, 1) k_linear_tc(LinArgs A) {
             const float sv = __uint_as_float(rr[b][e + f]);
             out[f] = 0.f;
             if (n >= A.N) continue;
+            const int cl = n - n0;
             if (MODE == LIN_ARGMAX) {
               const unsigned long long key =
-                  ((unsigned long long)ordered_bits(sv + A.bias[n]) << 32) | (0xffffffffu - (unsigned)n);
+                  ((unsigned long long)ordered_bits(sv + col_a[cl]) << 32) | (0xffffffffu - (unsigned)n);
               best = key > best ? key : best;
             } else if (MODE == LIN_STORE) {
-              out[f] = sv + A.bias[n];
+              out[f] = sv + col_a[cl];
             } else {
-              const float eb = __fmaf_ru(A.err_coeff, __fmul_ru(ynr, A.col_nrm_up[n]), 1e-30f);
-              const float d2 = __fsub_rd(__fadd_rd(ysq, A.col_sq_lo[n]), __fmul_ru(2.f, __fadd_ru(sv, eb)));
-              const float gap = __fsub_rd(__fsqrt_rd(fmaxf(d2, 0.f)), A.col_radius[n]);
+              const float eb = __fmaf_ru(A.err_coeff, __fmul_ru(ynr, col_b[cl]), 1e-30f);
+              const float d2 = __fsub_rd(__fadd_rd(ysq, col_a[cl]), __fmul_ru(2.f, __fadd_ru(sv, eb)));
+              const float gap = __fsub_rd(__fsqrt_rd(fmaxf(d2, 0.f)), col_c[cl]);
               out[f] = gap > 0.f ? __fmul_rd(gap, gap) : 0.f;
             }
           }
@@ -771,7 +787,8 @@ size_t linear_tc_packed_bytes(int rows, int K) {
 
 static int pack_rows(const float* src, int rows, int d, int fmt, bool supplier, uint8_t* out, cudaStream_t st) {
   const int rows_pad = (rows + LIN_TILE - 1) / LIN_TILE * LIN_TILE;
-  const int g = std::max(1, std::min((rows_pad + 255) / 256, num_sms() * 8));
+  const int64_t work = (int64_t)rows_pad * (2 * d * fmt_parts(fmt) / 16);
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, num_sms() * 16));
   k_pack_rows<<<g, 256, 0, st>>>(src, rows, rows_pad, d, fmt, supplier, out);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
