@@ -478,6 +478,8 @@ def run_ours(args) -> dict | None:
     agg = {"nns_kernel_ms": 0.0, "tail_kernel_ms": 0.0, "nns_kernel_pairs": 0, "nns_kernel_launches": 0,
            "kernel_launches": 0, "certified": 0, "fallbacks": 0, "near_ties": 0}
     last = None
+    # the timed steps alone for a profiler started with --profile-from-start off
+    torch.cuda.cudart().cudaProfilerStart()
     for k in range(args.steps):
         flush.zero_()
         starts[k].record()
@@ -487,6 +489,7 @@ def run_ours(args) -> dict | None:
             agg[key] += s.get(key, 0) or 0
         last = s
     torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
     dist_barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
