@@ -198,6 +198,36 @@ NNS_DEV void xs_add(unsigned long long* acc, double v) {
   if (c2) atomicAdd(acc + L + 2, c2);
 }
 
+// The same add for the 32 lanes of a warp at once: every lane calls it (a
+// lane with nothing to add passes 0).  Lanes whose values start at the same
+// limb sum their digits by shuffles first (at most 32 digits below 2^32
+// each: no overflow), then one of them adds the sums, so values that share
+// an exponent cost three atomics per warp, not per lane.
+NNS_DEV void xs_add_warp(unsigned long long* acc, double v) {
+  int L = -1;
+  unsigned long long c0 = 0, c1 = 0, c2 = 0;
+  if (v > 0.0) xs_digits(v, L, c0, c1, c2);
+  const int lane = threadIdx.x & 31;
+  const unsigned grp = __match_any_sync(0xffffffffu, L);
+  unsigned long long s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll 4
+  for (int k = 0; k < 32; ++k) {
+    const unsigned long long a0 = __shfl_sync(0xffffffffu, c0, k);
+    const unsigned long long a1 = __shfl_sync(0xffffffffu, c1, k);
+    const unsigned long long a2 = __shfl_sync(0xffffffffu, c2, k);
+    if ((grp >> k) & 1u) {
+      s0 += a0;
+      s1 += a1;
+      s2 += a2;
+    }
+  }
+  if (L >= 0 && lane == __ffs(grp) - 1) {
+    if (s0) atomicAdd(acc + L, s0);
+    if (s1) atomicAdd(acc + L + 1, s1);
+    if (s2) atomicAdd(acc + L + 2, s2);
+  }
+}
+
 NNS_DEV unsigned long long xs_limb(const unsigned long long* a, int L) {
   return (L >= 0 && L < XS_LIMBS) ? a[L] : 0ULL;
 }

@@ -651,23 +651,27 @@ NNS_DEV void warp_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, u
     __syncwarp();
     const unsigned nflow = S.nflow;
     if (!(deferred || O.quiet)) {
-      for (unsigned k = lane; k < nflow; k += 32) {
-        const unsigned long long pq = S.mem[k];
-        const int p = (int)(pq >> 32), q = (int)(pq & 0xffffffffULL);
-        const double f = __longlong_as_double((long long)S.nnk[k]);
-        const double term = __dmul_rn(f, G.dist64(S, p, q, metric));
-        const unsigned long long slot = nnz + k;
-        if (O.acc) xs_add(O.acc, term);
-        if (O.plan_i) {
-          if ((long long)slot < O.plan_cap) {
-            O.plan_i[slot] = S.iidx[p];
-            O.plan_j[slot] = S.jidx[q];
-            O.plan_f[slot] = f;
-          } else {
-            atomicOr(O.err, EF_CAPACITY);
+      for (unsigned base = 0; base < nflow; base += 32) {  // the whole warp (xs_add_warp)
+        const unsigned k = base + lane;
+        double term = 0.0;
+        if (k < nflow) {
+          const unsigned long long pq = S.mem[k];
+          const int p = (int)(pq >> 32), q = (int)(pq & 0xffffffffULL);
+          const double f = __longlong_as_double((long long)S.nnk[k]);
+          term = __dmul_rn(f, G.dist64(S, p, q, metric));
+          const unsigned long long slot = nnz + k;
+          if (O.plan_i) {
+            if ((long long)slot < O.plan_cap) {
+              O.plan_i[slot] = S.iidx[p];
+              O.plan_j[slot] = S.jidx[q];
+              O.plan_f[slot] = f;
+            } else {
+              atomicOr(O.err, EF_CAPACITY);
+            }
           }
+          if (O.c_glob) O.c_glob[S.jidx[q]] = S.cres[q];
         }
-        if (O.c_glob) O.c_glob[S.jidx[q]] = S.cres[q];
+        if (O.acc) xs_add_warp(O.acc, term);  // one call site for the whole warp
       }
       __syncwarp();
     }
@@ -831,23 +835,27 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
     __syncthreads();
     // ---- cost terms and plan entries of the round's flows, one per thread
     const unsigned nflow = S.nflow;
-    for (unsigned k = (deferred || O.quiet) ? nflow : tid; k < nflow; k += T) {
-      const unsigned long long pq = S.mem[k];
-      const int p = (int)(pq >> 32), q = (int)(pq & 0xffffffffULL);
-      const double f = __longlong_as_double((long long)S.nnk[k]);
-      const double term = __dmul_rn(f, G.dist64(S, p, q, metric));
-      const unsigned long long slot = nnz + k;
-      if (O.acc) xs_add(O.acc, term);
-      if (O.plan_i) {
-        if ((long long)slot < O.plan_cap) {
-          O.plan_i[slot] = S.iidx[p];
-          O.plan_j[slot] = S.jidx[q];
-          O.plan_f[slot] = f;
-        } else {
-          atomicOr(O.err, EF_CAPACITY);
+    for (unsigned base = (deferred || O.quiet) ? nflow : 0; base < nflow; base += T) {  // whole warps
+      const unsigned k = base + tid;
+      double term = 0.0;
+      if (k < nflow) {
+        const unsigned long long pq = S.mem[k];
+        const int p = (int)(pq >> 32), q = (int)(pq & 0xffffffffULL);
+        const double f = __longlong_as_double((long long)S.nnk[k]);
+        term = __dmul_rn(f, G.dist64(S, p, q, metric));
+        const unsigned long long slot = nnz + k;
+        if (O.plan_i) {
+          if ((long long)slot < O.plan_cap) {
+            O.plan_i[slot] = S.iidx[p];
+            O.plan_j[slot] = S.jidx[q];
+            O.plan_f[slot] = f;
+          } else {
+            atomicOr(O.err, EF_CAPACITY);
+          }
         }
+        if (O.c_glob) O.c_glob[S.jidx[q]] = S.cres[q];
       }
-      if (O.c_glob) O.c_glob[S.jidx[q]] = S.cres[q];
+      if (O.acc) xs_add_warp(O.acc, term);  // one call site for the whole warp
     }
     // (the compaction rewrites what this loop reads; with the loop empty
     // the flow step's barrier suffices)
@@ -861,20 +869,24 @@ NNS_DEV void cta_rounds(CtaCore<CAP>& S, Geo& G, int metric, const CtaOut& O, un
   if (O.fl_i && (O.acc || O.plan_i)) {
     // deferred costing: the terms and plan entries of every flow of the loop
     // (a solve whose later pass costs all its flows records them only)
-    for (unsigned long long k = nnz0 + tid; k < nnz; k += T) {
-      const int i = O.fl_i[k], j = O.fl_j[k];
-      const double f = O.fl_f[k];
-      const double term = __dmul_rn(f, cost_dist64(O.x + (size_t)i * O.d, O.y + (size_t)j * O.d, O.d, metric));
-      if (O.acc) xs_add(O.acc, term);
-      if (O.plan_i) {
-        if ((long long)k < O.plan_cap) {
-          O.plan_i[k] = i;
-          O.plan_j[k] = j;
-          O.plan_f[k] = f;
-        } else {
-          atomicOr(O.err, EF_CAPACITY);
+    for (unsigned long long base = nnz0; base < nnz; base += T) {  // whole warps (xs_add_warp)
+      const unsigned long long k = base + tid;
+      double term = 0.0;
+      if (k < nnz) {
+        const int i = O.fl_i[k], j = O.fl_j[k];
+        const double f = O.fl_f[k];
+        term = __dmul_rn(f, cost_dist64(O.x + (size_t)i * O.d, O.y + (size_t)j * O.d, O.d, metric));
+        if (O.plan_i) {
+          if ((long long)k < O.plan_cap) {
+            O.plan_i[k] = i;
+            O.plan_j[k] = j;
+            O.plan_f[k] = f;
+          } else {
+            atomicOr(O.err, EF_CAPACITY);
+          }
         }
       }
+      if (O.acc) xs_add_warp(O.acc, term);  // one call site for the whole warp
     }
     __syncthreads();
   }
@@ -890,7 +902,10 @@ NNS_DEV bool cta_load_side(const float* pts, const double* w, int cnt, int d, fl
   for (int i = tid; i < XS_LIMBS; i += blockDim.x) S.acc[i] = 0ULL;
   __syncthreads();
   bool nonfinite = false, negative = false;
-  for (int p = tid; p < cnt; p += blockDim.x) {
+  for (int base = 0; base < cnt; base += blockDim.x) {  // whole warps (xs_add_warp)
+    const int p = base + tid;
+    double add = 0.0;
+    if (p < cnt) {
     if (DP > 0) {
 #pragma unroll
       for (int k = 0; k < (DP > 0 ? DP : 1); ++k) {
@@ -907,7 +922,9 @@ NNS_DEV bool cta_load_side(const float* pts, const double* w, int cnt, int d, fl
     else if (wv < 0.0) negative = true;
     res[p] = wv;
     idx[p] = p;
-    if (isfinite(wv) && wv > 0.0) xs_add(S.acc, wv);
+    add = isfinite(wv) && wv > 0.0 ? wv : 0.0;
+    }
+    xs_add_warp(S.acc, add);  // one call site for the whole warp
   }
   nonfinite = __syncthreads_or(nonfinite);
   negative = __syncthreads_or(negative);

@@ -558,8 +558,10 @@ __global__ void __launch_bounds__(FIN_THREADS, 1) k_solve_small(SolveBufs B, con
   __syncthreads();
   for (int i = tid; i < XS_LIMBS; i += blockDim.x) S.acc[i] = 0ULL;
   __syncthreads();
-  for (int p = tid; p < S.mt; p += blockDim.x) xs_add(S.acc, S.sres[p]);
-  for (int q = tid; q < S.nt; q += blockDim.x) xs_add(S.acc, S.cres[q]);
+  for (int base = 0; base < S.mt; base += blockDim.x)  // whole warps (xs_add_warp)
+    xs_add_warp(S.acc, base + tid < S.mt ? S.sres[base + tid] : 0.0);
+  for (int base = 0; base < S.nt; base += blockDim.x)
+    xs_add_warp(S.acc, base + tid < S.nt ? S.cres[base + tid] : 0.0);
   __syncthreads();
   if (tid == 0) {
     B.st->leftover = xs_round(S.acc);
