@@ -209,6 +209,20 @@ NNS_DEV void xs_add_warp(unsigned long long* acc, double v) {
   if (v > 0.0) xs_digits(v, L, c0, c1, c2);
   const int lane = threadIdx.x & 31;
   const unsigned grp = __match_any_sync(0xffffffffu, L);
+  if (grp == 0xffffffffu) {  // one limb for the whole warp (the same for every lane)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+      c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+      c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+    }
+    if (L >= 0 && lane == 0) {
+      if (c0) atomicAdd(acc + L, c0);
+      if (c1) atomicAdd(acc + L + 1, c1);
+      if (c2) atomicAdd(acc + L + 2, c2);
+    }
+    return;
+  }
   unsigned long long s0 = 0, s1 = 0, s2 = 0;
 #pragma unroll 4
   for (int k = 0; k < 32; ++k) {

@@ -57,14 +57,24 @@ __global__ void __launch_bounds__(XS_THREADS) k_xs_accum_multi(XsJob j0, XsJob j
   const int64_t n2 = njobs > 2 ? (j2.n_dev ? (int64_t)*j2.n_dev : j2.n) : 0;
   const int64_t e1 = n0, e2 = n0 + n1, e3 = n0 + n1 + n2;
   const int w = threadIdx.x >> 5;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < e3; i += (int64_t)gridDim.x * blockDim.x) {
-    const int j = i < e1 ? 0 : (i < e2 ? 1 : 2);
-    const double v = j == 0 ? j0.v[i] : (j == 1 ? j1.v[i - e1] : j2.v[i - e2]);
-    if (check) {
-      if (!isfinite(v)) { atomicOr(err, EF_NONFINITE); continue; }
-      if (v < 0.0) { atomicOr(err, EF_NEGATIVE); continue; }
+  // whole warps per step (xs_add_warp): a lane past the end adds nothing
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < e3; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    int j = -1;
+    double v = 0.0;
+    if (i < e3) {
+      j = i < e1 ? 0 : (i < e2 ? 1 : 2);
+      v = j == 0 ? j0.v[i] : (j == 1 ? j1.v[i - e1] : j2.v[i - e2]);
+      if (check && !isfinite(v)) {
+        atomicOr(err, EF_NONFINITE);
+        v = 0.0;
+      } else if (check && v < 0.0) {
+        atomicOr(err, EF_NEGATIVE);
+        v = 0.0;
+      }
     }
-    xs_add(sacc[j][w], v);
+    for (int jj = 0; jj < njobs; ++jj)
+      if (__any_sync(0xffffffffu, j == jj)) xs_add_warp(sacc[jj][w], j == jj ? v : 0.0);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < njobs * XS_LIMBS; i += blockDim.x) {
@@ -111,24 +121,29 @@ __global__ void __launch_bounds__(XS_THREADS) k_final_sums(FinalArgs A) {
   const int64_t e1 = A.m, e2 = A.m + A.n, e3 = e2 + (int64_t)*A.nnz;
   const int w = threadIdx.x >> 5;
   bool over = false;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < e3; i += (int64_t)gridDim.x * blockDim.x) {
+  // whole warps per step (xs_add_warp): a lane past the end adds nothing
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < e3; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    double left = 0.0, term = 0.0;
     if (i < e2) {
-      xs_add(sacc[0][w], i < e1 ? A.s[i] : A.c[i - e1]);
-      continue;
-    }
-    const int64_t k = i - e2;
-    const int fi = A.fl_i[k], fj = A.fl_j[k];
-    const double f = A.fl_f[k];
-    xs_add(sacc[1][w], __dmul_rn(f, cost_dist64(A.x + (size_t)fi * A.d, A.y + (size_t)fj * A.d, A.d, A.metric)));
-    if (A.plan_i) {
-      if (k < A.plan_cap) {
-        A.plan_i[k] = fi;
-        A.plan_j[k] = fj;
-        A.plan_f[k] = f;
-      } else {
-        over = true;
+      left = i < e1 ? A.s[i] : A.c[i - e1];
+    } else if (i < e3) {
+      const int64_t k = i - e2;
+      const int fi = A.fl_i[k], fj = A.fl_j[k];
+      const double f = A.fl_f[k];
+      term = __dmul_rn(f, cost_dist64(A.x + (size_t)fi * A.d, A.y + (size_t)fj * A.d, A.d, A.metric));
+      if (A.plan_i) {
+        if (k < A.plan_cap) {
+          A.plan_i[k] = fi;
+          A.plan_j[k] = fj;
+          A.plan_f[k] = f;
+        } else {
+          over = true;
+        }
       }
     }
+    if (__any_sync(0xffffffffu, i < e2)) xs_add_warp(sacc[0][w], left);
+    if (__any_sync(0xffffffffu, i >= e2 && i < e3)) xs_add_warp(sacc[1][w], term);
   }
   if (over) atomicOr(A.err, EF_CAPACITY);
   __syncthreads();
