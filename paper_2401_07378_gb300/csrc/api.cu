@@ -173,7 +173,7 @@ size_t layout_solve(void* base, int64_t m, int64_t n, int d, SolveBufs& B, int p
     L->lc_qcnt = C.take<int>(K);
     L->lc_qoff = C.take<int>(K + 1);
     L->lc_work = C.take<int>(K + 1);
-    L->lc_nwork = C.take<int>(1);
+    L->lc_nwork = C.take<int>(2);  // the work items' count, then the counter of the next one
     L->lc_qlist = C.take<int>((size_t)n * PROP_TAKE);
     L->lc_best = C.take<unsigned long long>(n);
     L->w3p = C.take<uint8_t>(linear_tc_supported(h) ? linear_tc_packed_bytes(K, h) : 0);

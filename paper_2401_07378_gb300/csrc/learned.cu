@@ -462,19 +462,35 @@ __global__ void __launch_bounds__(32 * SEL_WARPS, 4) k_select_rows_warp(const fl
   };
   // 1. the two largest keys of each group (lane, half); every group holds
   // at least two columns (cols >= 128), so all 128 entries are real keys
+  // (starting both at 0, the smallest key, gives the two largest of any
+  // group of two or more keys).  Rows whose columns split into whole
+  // 16-byte vectors per lane and half are read 16 bytes at a time (the
+  // group of a lane is then its vectors in that half).
   const int half = cols / 2;
+  const bool vec = (cols & 255) == 0 && (reinterpret_cast<uintptr_t>(row) & 15) == 0;
+  auto top2 = [](unsigned k, unsigned& a1, unsigned& a2) {
+    if (k > a1) {
+      a2 = a1;
+      a1 = k;
+    } else if (k > a2) {
+      a2 = k;
+    }
+  };
   for (int h = 0; h < 2; ++h) {
     unsigned a1 = 0u, a2 = 0u;
-    int n = 0;
-    for (int c = h * half + lane; c < (h ? cols : half); c += 32) {
-      const unsigned k = key(c);
-      if (n == 0 || k > a1) {
-        a2 = a1;
-        a1 = k;
-      } else if (n == 1 || k > a2) {
-        a2 = k;
+    if (vec) {
+      const float4* r4 = reinterpret_cast<const float4*>(row);
+      for (int f = h * (half / 4) + lane; f < (h + 1) * (half / 4); f += 32) {
+        const float4 v = r4[f];
+        const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const unsigned o = ordered_bits(e[u]);
+          top2(LARGEST ? o : ~o, a1, a2);
+        }
       }
-      ++n;
+    } else {
+      for (int c = h * half + lane; c < (h ? cols : half); c += 32) top2(key(c), a1, a2);
     }
     s_key[w][h * 64 + lane] = a1;
     s_key[w][h * 64 + 32 + lane] = a2;
@@ -492,17 +508,52 @@ __global__ void __launch_bounds__(32 * SEL_WARPS, 4) k_select_rows_warp(const fl
   T = __reduce_max_sync(0xffffffffu, T);
   // 2. keys > T in column order
   int n = 0;
-  for (int base = 0; base < cols; base += 32) {
-    const int c = base + lane;
-    const unsigned k = c < cols ? key(c) : 0u;
-    const bool p = c < cols && k > T;
-    const unsigned bal = __ballot_sync(0xffffffffu, p);
-    const int pos = n + __popc(bal & ((1u << lane) - 1u));
-    if (p && pos < SEL_CAP) {
-      c_key[w][pos] = k;
-      c_col[w][pos] = c;
+  if (vec) {
+    // four consecutive columns per lane: a lane's place is the count of the
+    // lanes before it (a warp scan) plus its own earlier columns
+    const float4* r4 = reinterpret_cast<const float4*>(row);
+    for (int f0 = 0; f0 < cols / 4; f0 += 32) {
+      const float4 v = r4[f0 + lane];
+      const float e[4] = {v.x, v.y, v.z, v.w};
+      unsigned k4[4];
+      int cnt = 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const unsigned o = ordered_bits(e[u]);
+        k4[u] = LARGEST ? o : ~o;
+        cnt += k4[u] > T;
+      }
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      int pos = n + incl - cnt;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (k4[u] > T) {
+          if (pos < SEL_CAP) {
+            c_key[w][pos] = k4[u];
+            c_col[w][pos] = 4 * (f0 + lane) + u;
+          }
+          ++pos;
+        }
+      n += __shfl_sync(0xffffffffu, incl, 31);
     }
-    n += __popc(bal);
+  } else {
+    for (int base = 0; base < cols; base += 32) {
+      const int c = base + lane;
+      const unsigned k = c < cols ? key(c) : 0u;
+      const bool p = c < cols && k > T;
+      const unsigned bal = __ballot_sync(0xffffffffu, p);
+      const int pos = n + __popc(bal & ((1u << lane) - 1u));
+      if (p && pos < SEL_CAP) {
+        c_key[w][pos] = k;
+        c_col[w][pos] = c;
+      }
+      n += __popc(bal);
+    }
   }
   if (n > SEL_CAP) {
     if (lane == 0) over_rows[atomicAdd(n_over, 1)] = r;
@@ -858,6 +909,7 @@ struct LcArgs {
   int* qoff;               // [K+1]
   int* work_off;           // [K+1] work items (chunks of LC_THREADS consumers) before each cell
   int* nwork;
+  int* work_next;          // the next work item to take (zero at launch)
   int* qlist;              // consumers grouped by cell
   unsigned long long* best;  // [nt] smallest packed key over the candidates (all ones on entry)
   unsigned long long* nnkey;
@@ -952,7 +1004,7 @@ __global__ void k_lc_group(LcArgs A) {
   A.qlist[A.qoff[c] + A.slot[i]] = q;
 }
 
-// The cell scan.  CTAs take work items in turn; a work item is up to
+// The cell scan.  CTAs take work items from a counter; a work item is up to
 // LC_THREADS consumers of one cell, one per thread, each with its row in
 // registers; the cell's active suppliers pass through shared memory
 // LC_TILE rows at a time and every thread runs the key32<SQL2> chain of
@@ -961,9 +1013,15 @@ template <int D>
 __global__ void __launch_bounds__(LC_THREADS) k_lc_keys(LcArgs A) {
   __shared__ __align__(16) float xs[LC_TILE][D];
   __shared__ int ps[LC_TILE];
+  __shared__ int s_wi;
   const int tid = threadIdx.x;
   const int nw = *A.nwork;
-  for (int wi = blockIdx.x; wi < nw; wi += gridDim.x) {
+  for (;;) {
+    __syncthreads();  // the previous item's reads of s_wi and of the tiles are done
+    if (tid == 0) s_wi = atomicAdd(A.work_next, 1);
+    __syncthreads();
+    const int wi = s_wi;
+    if (wi >= nw) break;
     // the cell of this work item: the last c with work_off[c] <= wi
     int lo = 0, hi = A.cells;  // work_off[lo] <= wi < work_off[hi]
     while (hi - lo > 1) {
@@ -1030,6 +1088,18 @@ __global__ void __launch_bounds__(LC_THREADS) k_lc_keys(LcArgs A) {
   }
 }
 
+// As many CTAs of the cell scan as the GPU holds at once (they take work
+// items from a counter until none is left).
+template <int D>
+static int lc_grid() {
+  static const int per_sm = [] {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_lc_keys<D>, LC_THREADS, 0) != cudaSuccess || b < 1) b = 1;
+    return b;
+  }();
+  return per_sm * num_sms();
+}
+
 // One thread per active consumer: the certificate of k_learned_nns.
 __global__ void k_learned_cert(LcArgs A) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1066,17 +1136,17 @@ int launch_nns_learned(const SolveBufs& B, const LearnedBufs& L, int mt, int nt,
   if (learned_cell_scan(B.d, B.x, B.y)) {
     LcArgs C{B.x,        B.y,          ia,          B.ja[B.cur], B.d,       nt,        K,
              L.prop_cells, L.bound_cells, L.bound_vals, L.cell_off, L.cell_members, L.lc_cand, L.lc_slot,
-             L.lc_ncand,   L.lc_bound,   L.lc_qcnt,   L.lc_qoff,  L.lc_work,  L.lc_nwork, L.lc_qlist,
-             L.lc_best,    B.nnkey,      L.fallback,  L.nfallback, &B.st->certified, nfall};
+             L.lc_ncand,   L.lc_bound,   L.lc_qcnt,   L.lc_qoff,  L.lc_work,  L.lc_nwork, L.lc_nwork + 1,
+             L.lc_qlist,   L.lc_best,    B.nnkey,     L.fallback, L.nfallback, &B.st->certified, nfall};
     cudaMemsetAsync(L.lc_qcnt, 0, K * sizeof(int), st);
+    cudaMemsetAsync(L.lc_nwork + 1, 0, sizeof(int), st);
     cudaMemsetAsync(L.lc_best, 0xff, (size_t)nt * sizeof(unsigned long long), st);
     k_learned_plan<<<(nt + 7) / 8, 256, 0, st>>>(C);
     k_lc_offsets<<<1, 1024, 0, st>>>(C);
     k_lc_group<<<(int)(((int64_t)nt * PROP_TAKE + 255) / 256), 256, 0, st>>>(C);
-    const int g = num_sms() * 4;
-    if (B.d == 32) k_lc_keys<32><<<g, LC_THREADS, 0, st>>>(C);
-    else if (B.d == 64) k_lc_keys<64><<<g, LC_THREADS, 0, st>>>(C);
-    else k_lc_keys<128><<<g, LC_THREADS, 0, st>>>(C);
+    if (B.d == 32) k_lc_keys<32><<<lc_grid<32>(), LC_THREADS, 0, st>>>(C);
+    else if (B.d == 64) k_lc_keys<64><<<lc_grid<64>(), LC_THREADS, 0, st>>>(C);
+    else k_lc_keys<128><<<lc_grid<128>(), LC_THREADS, 0, st>>>(C);
     k_learned_cert<<<(nt + 255) / 256, 256, 0, st>>>(C);
   } else {
     LearnedArgs A{B.x,          B.y,          ia,          B.ja[B.cur], B.d,       nt,

@@ -69,7 +69,7 @@ struct LearnedBufs {
   int* lc_qcnt;         // [cells]
   int* lc_qoff;         // [cells + 1]
   int* lc_work;         // [cells + 1]
-  int* lc_nwork;
+  int* lc_nwork;         // [2]: work items, next work item
   int* lc_qlist;        // [n * PROP_TAKE]
   unsigned long long* lc_best;  // [n]
   uint8_t* w3p;         // the scoring layer's weights packed for linear_tc
