@@ -476,7 +476,7 @@ def run_ours(args) -> dict | None:
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     agg = {"nns_kernel_ms": 0.0, "tail_kernel_ms": 0.0, "nns_kernel_pairs": 0, "nns_kernel_launches": 0,
-           "kernel_launches": 0, "certified": 0, "fallbacks": 0, "near_ties": 0}
+           "kernel_launches": 0, "certified": 0, "fallbacks": 0, "near_ties": 0, "widened": 0}
     last = None
     # the timed steps alone for a profiler started with --profile-from-start off
     torch.cuda.cudart().cudaProfilerStart()
@@ -611,7 +611,8 @@ def run_ours(args) -> dict | None:
         "tail_kernel_share": agg["tail_kernel_ms"] / total_ms if total_ms else None,
         "gpu_launches": launches_all,
         "rounds_per_step": (last or {}).get("rounds"), "pair_evals_per_step": (last or {}).get("pair_evals"),
-        "certified": agg["certified"], "fallbacks": agg["fallbacks"], "near_ties_reduced_precision": agg["near_ties"],
+        "certified": agg["certified"], "certified_by_second_tier": agg["widened"], "fallbacks": agg["fallbacks"],
+        "near_ties_reduced_precision": agg["near_ties"],
         "cost": float(gpu_costs[0]) if not spec["batched"] else None,
         "proposal": prop_info,
         "clocks": clocks,

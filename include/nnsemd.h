@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define NNSEMD_ABI_VERSION 3
+#define NNSEMD_ABI_VERSION 4
 
 typedef enum {
   NNSEMD_OK = 0,
@@ -150,6 +150,10 @@ typedef struct {
                                    first (ties at that precision).  0 on the FP32 paths: their decisions
                                    are the FP32 decisions themselves (the FP32 / FP64 near-ties of the
                                    method are the oracle's to count). */
+  int64_t widened;              /* learned proposal: consumer searches certified by the second tier (the
+                                   cells of the bound list beyond the proposed candidates, in bound order);
+                                   included in `certified`.  certified - widened is what the proposal's
+                                   own candidates certified. */
 } nnsemd_stats;
 
 /* Create a context bound to cfg->device and cfg->stream.  *out receives the

@@ -161,6 +161,8 @@ size_t layout_solve(void* base, int64_t m, int64_t n, int d, SolveBufs& B, int p
     L->cell_members = C.take<int>(m);
     L->fallback = C.take<int>(n);
     L->nfallback = C.take<int>(1);
+    L->fallback2 = C.take<int>(n);
+    L->nfallback2 = C.take<int>(1);
     L->tmp = C.take<float>((size_t)2 * L->chunk * h);
     L->tmp2 = C.take<float>((size_t)L->chunk * K);
     L->tmp3 = C.take<float>((size_t)L->chunk * d);
@@ -412,7 +414,7 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
       if (timed) CKD(cudaEventRecord(ctx->ev[0], st));
       nrc = launch_nns_learned(B, *learned, mt, nt, st);
       if (timed) CKD(cudaEventRecord(ctx->ev[1], st));
-      L += learned_cell_scan(B.d, B.x, B.y) ? 10 : 6;
+      L += learned_cell_scan(B.d, B.x, B.y) ? 11 : 6;
     } else if (B.precision != NNSEMD_FP32) {
       // tensor-core candidates + exact re-rank + certificate + FP32 rescan;
       // the timing events bracket the tensor-core kernel alone
@@ -476,6 +478,7 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
     stats->certified = (int64_t)ctx->hstate->certified;
     stats->fallbacks = (int64_t)ctx->hstate->fallbacks;
     stats->near_ties = (int64_t)ctx->hstate->near_ties;
+    stats->widened = (int64_t)ctx->hstate->widened;
     stats->nns_kernel_ms = nns_ms;
     stats->nns_kernel_launches = nns_launches;
     stats->nns_kernel_pairs = nns_pairs;

@@ -47,6 +47,7 @@ struct DevState {
   unsigned long long certified;  // reduced precision: consumer searches settled by the certificate
   unsigned long long fallbacks;  // reduced precision: consumer searches redone in FP32
   unsigned long long near_ties;  // reduced precision: exact re-rank overturned the approximate first choice
+  unsigned long long widened;    // learned proposal: certified by the second tier
   unsigned ticket;               // blocks of the current compaction count done (reset by its last block)
 };
 

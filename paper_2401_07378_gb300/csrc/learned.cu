@@ -917,6 +917,7 @@ struct LcArgs {
   int* nfallback;
   unsigned long long* ncert;
   unsigned long long* nfall;
+  unsigned long long* nwiden;  // certified by the second tier
 };
 
 // One warp per active consumer: the first PROP_TAKE proposed cells that
@@ -1117,6 +1118,64 @@ __global__ void k_learned_cert(LcArgs A) {
   }
 }
 
+// One warp per consumer the cell scan left uncertified (list[0 .. count)):
+// the cells of its bound list (smallest bound first) that still hold active
+// suppliers and were not among its candidates are scanned one after another
+// with the same FP32 key, until the best key is strictly below the bound of
+// the next such cell (every cell not scanned then lies at or above that
+// bound, the ones outside the list at or above its last), or the list runs
+// out and the last bound decides.  The rest go to out_list for the full
+// scan.  The key, the packed minimum and the margin are those of
+// k_learned_cert, so a certified choice is the full scan's.
+__global__ void __launch_bounds__(256) k_learned_widen(LcArgs A, const int* __restrict__ list, int count,
+                                                       int* __restrict__ out_list, int* __restrict__ out_count) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int idx = blockIdx.x * 8 + wib;
+  if (idx >= count) return;
+  const int q = list[idx];
+  const int j = A.ja[q];
+  const float* yrow = A.y + (size_t)j * A.d;
+  const int nc = A.ncand[q];
+  static_assert(PROP_TAKE <= 32, "one candidate per lane");
+  const int mycand = lane < nc ? A.cand[(size_t)q * PROP_TAKE + lane] : -1;
+  const int* bl = A.bound_cells + (size_t)j * PROP_LIST;
+  const float* bv = A.bound_vals + (size_t)j * PROP_LIST;
+  const double gam = A.d * 0x1p-24 / (1.0 - A.d * 0x1p-24);
+  auto below = [&](unsigned long long key, float bound) {
+    return key != ~0ULL && (double)__uint_as_float((unsigned)(key >> 32)) < (double)bound * (1.0 - gam) * (1.0 - 0x1p-30);
+  };
+  unsigned long long best = A.best[q];
+  bool done = false;
+  for (int t = 0; t < PROP_LIST && !done; ++t) {
+    const int c = bl[t];
+    const int b = A.cell_off[c], e = A.cell_off[c + 1];
+    if (e == b || __any_sync(0xffffffffu, mycand == c)) continue;  // empty, or scanned already
+    if (below(best, bv[t])) {
+      done = true;
+      break;
+    }
+    for (int u = b + lane; u < e; u += 32) {
+      const int p = A.members[u];
+      const unsigned long long kk = pack_key(key32_sql2_v4(A.x + (size_t)A.ia[p] * A.d, yrow, A.d), (unsigned)p);
+      best = kk < best ? kk : best;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+      best = ob < best ? ob : best;
+    }
+  }
+  if (!done) done = below(best, bv[PROP_LIST - 1]);
+  if (lane != 0) return;
+  if (done) {
+    A.nnkey[q] = best;
+    atomicAdd(A.ncert, 1ULL);
+    atomicAdd(A.nwiden, 1ULL);
+  } else {
+    out_list[atomicAdd(out_count, 1)] = q;
+    if (A.nfall) atomicAdd(A.nfall, 1ULL);
+  }
+}
+
 bool learned_cell_scan(int d, const float* x, const float* y) {
   return (d == 32 || d == 64 || d == 128) && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) == 0;
 }
@@ -1137,7 +1196,8 @@ int launch_nns_learned(const SolveBufs& B, const LearnedBufs& L, int mt, int nt,
     LcArgs C{B.x,        B.y,          ia,          B.ja[B.cur], B.d,       nt,        K,
              L.prop_cells, L.bound_cells, L.bound_vals, L.cell_off, L.cell_members, L.lc_cand, L.lc_slot,
              L.lc_ncand,   L.lc_bound,   L.lc_qcnt,   L.lc_qoff,  L.lc_work,  L.lc_nwork, L.lc_nwork + 1,
-             L.lc_qlist,   L.lc_best,    B.nnkey,     L.fallback, L.nfallback, &B.st->certified, nfall};
+             L.lc_qlist,   L.lc_best,    B.nnkey,     L.fallback, L.nfallback, &B.st->certified, nfall,
+             &B.st->widened};
     cudaMemsetAsync(L.lc_qcnt, 0, K * sizeof(int), st);
     cudaMemsetAsync(L.lc_nwork + 1, 0, sizeof(int), st);
     cudaMemsetAsync(L.lc_best, 0xff, (size_t)nt * sizeof(unsigned long long), st);
@@ -1147,7 +1207,26 @@ int launch_nns_learned(const SolveBufs& B, const LearnedBufs& L, int mt, int nt,
     if (B.d == 32) k_lc_keys<32><<<lc_grid<32>(), LC_THREADS, 0, st>>>(C);
     else if (B.d == 64) k_lc_keys<64><<<lc_grid<64>(), LC_THREADS, 0, st>>>(C);
     else k_lc_keys<128><<<lc_grid<128>(), LC_THREADS, 0, st>>>(C);
-    k_learned_cert<<<(nt + 255) / 256, 256, 0, st>>>(C);
+    LcArgs Cc = C;
+    Cc.nfall = nullptr;  // the consumers it leaves are counted after the second tier
+    k_learned_cert<<<(nt + 255) / 256, 256, 0, st>>>(Cc);
+    // the second tier: more cells, in bound order, for the consumers left
+    int nf = 0;
+    if (cudaMemcpyAsync(&nf, L.nfallback, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return -1;
+    cudaMemsetAsync(L.nfallback2, 0, sizeof(int), st);
+    if (nf > 0) k_learned_widen<<<(nf + 7) / 8, 256, 0, st>>>(C, L.fallback, nf, L.fallback2, L.nfallback2);
+    if (B.precision == 0) {  // FP32
+      launch_nns_f32(B, mt, nt, L.fallback2, L.nfallback2, st);
+    } else {
+      int nf2 = 0;
+      if (nf > 0 && (cudaMemcpyAsync(&nf2, L.nfallback2, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                     cudaStreamSynchronize(st) != cudaSuccess))
+        return -1;
+      if (nf2 > 0 && launch_nns_tc(B, B.tc, mt, nf2, B.precision, st, L.fallback2, nullptr)) return -1;
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
   } else {
     LearnedArgs A{B.x,          B.y,          ia,          B.ja[B.cur], B.d,       nt,
                   L.prop_cells, L.bound_cells, L.bound_vals, L.cell_off, L.cell_members, B.nnkey,

@@ -55,6 +55,8 @@ struct LearnedBufs {
   int* cell_members;    // [m] active supplier positions grouped by cell
   int* fallback;        // [n]
   int* nfallback;
+  int* fallback2;       // [n] the consumers the second tier of the cell scan leaves
+  int* nfallback2;
   // scratch for the per-solve passes
   float* tmp;           // [chunk][max(cells, hidden)] and friends
   float* tmp2;

@@ -52,7 +52,7 @@ class nnsemd_stats(ctypes.Structure):
                 ("certified", ctypes.c_int64), ("fallbacks", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("nns_kernel_ms", ctypes.c_double), ("nns_kernel_launches", ctypes.c_int64),
                 ("nns_kernel_pairs", ctypes.c_int64), ("tail_kernel_ms", ctypes.c_double),
-                ("near_ties", ctypes.c_int64)]
+                ("near_ties", ctypes.c_int64), ("widened", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -121,7 +121,7 @@ def abi_version() -> int:
     return _lib.nnsemd_abi_version()
 
 
-ABI_VERSION = 3  # the nnsemd.h this binding mirrors
+ABI_VERSION = 4  # the nnsemd.h this binding mirrors
 if abi_version() != ABI_VERSION:
     raise ImportError(f"libnnsemd.so has ABI {abi_version()}, this binding expects {ABI_VERSION}: rebuild")
 

@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol():
     missing = [n for n in declared_functions() if not hasattr(lib, n)]
     assert not missing, missing
     lib.nnsemd_abi_version.restype = ctypes.c_int
-    assert lib.nnsemd_abi_version() == 3
+    assert lib.nnsemd_abi_version() == 4
     lib.nnsemd_status_string.restype = ctypes.c_char_p
     assert lib.nnsemd_status_string(0) == b"NNSEMD_OK"
     assert lib.nnsemd_status_string(9) == b"NNSEMD_ERR_CAPACITY"
@@ -44,10 +44,11 @@ def test_binding_loads_and_matches_struct_sizes():
     from paper_2401_07378_gb300 import nnsemd
     assert ctypes.sizeof(nnsemd.nnsemd_options) == 40
     assert ctypes.sizeof(nnsemd.nnsemd_plan) == 40
-    assert ctypes.sizeof(nnsemd.nnsemd_stats) == 88
+    assert ctypes.sizeof(nnsemd.nnsemd_stats) == 96
     assert nnsemd.nnsemd_stats.near_ties.offset == 80
+    assert nnsemd.nnsemd_stats.widened.offset == 88
     assert ctypes.sizeof(nnsemd.nnsemd_config) == 24
-    assert nnsemd.abi_version() == 3
+    assert nnsemd.abi_version() == 4
 
 
 def test_null_context_is_rejected_without_a_gpu():
