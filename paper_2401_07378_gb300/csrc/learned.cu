@@ -496,16 +496,16 @@ __global__ void __launch_bounds__(32 * SEL_WARPS, 4) k_select_rows_warp(const fl
     s_key[w][h * 64 + 32 + lane] = a2;
   }
   __syncwarp();
-  // T: the largest key of S with at least 64 keys of S at or above it
+  // T: the largest key of S with at least 64 keys of S at or above it,
+  // bit by bit from the top (the count of keys >= t only falls as t grows,
+  // so the largest t that keeps it at 64 is the 64th largest key of S)
+  const unsigned s0 = s_key[w][lane], s1 = s_key[w][32 + lane], s2 = s_key[w][64 + lane], s3 = s_key[w][96 + lane];
   unsigned T = 0u;
-  for (int i = lane; i < 128; i += 32) {
-    const unsigned ki = s_key[w][i];
-    int ge = 0;
-#pragma unroll 8
-    for (int j = 0; j < 128; ++j) ge += s_key[w][j] >= ki;
-    if (ge >= PROP_LIST && ki > T) T = ki;
+  for (int bit = 31; bit >= 0; --bit) {
+    const unsigned t = T | (1u << bit);
+    const unsigned ge = (s0 >= t) + (s1 >= t) + (s2 >= t) + (s3 >= t);
+    if (__reduce_add_sync(0xffffffffu, ge) >= PROP_LIST) T = t;
   }
-  T = __reduce_max_sync(0xffffffffu, T);
   // 2. keys > T in column order
   int n = 0;
   if (vec) {
@@ -1176,6 +1176,12 @@ __global__ void __launch_bounds__(256) k_learned_widen(LcArgs A, const int* __re
   }
 }
 
+// Consumers left after the second tier at or below which the full scan
+// runs in FP32 rather than on the tensor cores.
+constexpr int LC_TC_MIN = 256;
+
+__global__ void k_add_count(unsigned long long* ctr, unsigned long long v) { *ctr += v; }
+
 bool learned_cell_scan(int d, const float* x, const float* y) {
   return (d == 32 || d == 64 || d == 128) && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) == 0;
 }
@@ -1224,7 +1230,14 @@ int launch_nns_learned(const SolveBufs& B, const LearnedBufs& L, int mt, int nt,
       if (nf > 0 && (cudaMemcpyAsync(&nf2, L.nfallback2, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                      cudaStreamSynchronize(st) != cudaSuccess))
         return -1;
-      if (nf2 > 0 && launch_nns_tc(B, B.tc, mt, nf2, B.precision, st, L.fallback2, nullptr)) return -1;
+      if (nf2 > LC_TC_MIN) {
+        if (launch_nns_tc(B, B.tc, mt, nf2, B.precision, st, L.fallback2, nullptr)) return -1;
+      } else if (nf2 > 0) {
+        // a few consumers: the FP32 scan costs less than packing every
+        // active supplier for the tensor cores (counted as fallbacks)
+        k_add_count<<<1, 1, 0, st>>>(&B.st->fallbacks, (unsigned long long)nf2);
+        launch_nns_f32(B, mt, nt, L.fallback2, L.nfallback2, st);
+      }
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
   } else {
