@@ -180,6 +180,11 @@ size_t layout_solve(void* base, int64_t m, int64_t n, int d, SolveBufs& B, int p
     L->lc_best = C.take<unsigned long long>(n);
     L->w3p = C.take<uint8_t>(linear_tc_supported(h) ? linear_tc_packed_bytes(K, h) : 0);
     L->h2p = C.take<uint8_t>(linear_tc_supported(h) ? linear_tc_packed_bytes(L->chunk, h) : 0);
+    const bool tc_all = linear_tc_supported(h) && linear_tc_supported(d);
+    L->w1p = C.take<uint8_t>(tc_all ? linear_tc_packed_bytes(h, d) : 0);
+    L->w2p = C.take<uint8_t>(tc_all ? linear_tc_packed_bytes(h, h) : 0);
+    L->xp1 = C.take<uint8_t>(tc_all ? linear_tc_packed_bytes(L->chunk, d) : 0);
+    L->h1p = C.take<uint8_t>(tc_all ? linear_tc_packed_bytes(L->chunk, h) : 0);
     L->assign_chunk = 65536;
     const bool tca = linear_tc_supported(d);
     L->mup = C.take<uint8_t>(tca ? linear_tc_packed_bytes(K, d) : 0);
@@ -387,7 +392,8 @@ int run_solve(nnsemd_ctx* ctx, SolveBufs& B, const double* a, const double* b, d
     // and the radii
     const int64_t passes = (B.m + learned->assign_chunk - 1) / learned->assign_chunk;
     const bool tcb = cell_bounds_tc_supported(B.d);
-    L += (linear_tc_supported(B.d) ? 3 + 3 * passes : 8) + (linear_tc_supported(learned->P->hidden) ? 1 : 0) +
+    const bool tch = linear_tc_supported(learned->P->hidden);
+    L += (linear_tc_supported(B.d) ? 3 + 3 * passes : 8) + (tch ? 1 : 0) + (tch && linear_tc_supported(B.d) ? 2 : 0) +
          (tcb ? 2 : 0) + (5 + (tcb ? 2 : 0) + 2 * sel) * ((B.n + learned->chunk - 1) / learned->chunk);
   }
   while (mt > 0 && nt > 0) {

@@ -175,6 +175,10 @@ size_t linear_tc_packed_bytes(int rows, int K);
 int pack_rows_bf16(const float* src, int rows, int K, uint8_t* out, cudaStream_t st);
 int linear_tc(const uint8_t* X, int rows, int K, const uint8_t* W, const float* bias, int N, float* Z, unsigned* err,
               cudaStream_t st);
+// The same layer with ReLU, written as the next layer's packed X (BF16,
+// tiles of 128 rows, padding rows zero; N a multiple of 16).
+int linear_tc_pack_relu(const uint8_t* X, int rows, int K, const uint8_t* W, const float* bias, int N, uint8_t* out,
+                        unsigned* err, cudaStream_t st);
 // The same layer reduced per row: out[row] = the column of the row's largest
 // value of X W^T + b (lowest column on ties); part holds rows x
 // ceil(N / 128) partial keys.

@@ -437,7 +437,7 @@ constexpr int SEL_CAP = 256;   // candidates a warp keeps in shared memory
 //  1. the row's columns fall into 64 groups (lane x half of the row); the
 //     two largest keys of every group form a set S, and T is the 64th
 //     largest key of S, so at least 64 keys of the row are >= T;
-//  2. the keys > T are gathered in column order; with fewer than 64 of
+//  2. the keys > T are gathered; with fewer than 64 of
 //     them, the first keys == T in column order complete the 64 (exactly
 //     the selection's tie rule), else the 64 are among the gathered ones;
 //  3. each gathered key's rank by (key descending, column ascending) places
@@ -452,6 +452,7 @@ __global__ void __launch_bounds__(32 * SEL_WARPS, 4) k_select_rows_warp(const fl
   __shared__ unsigned s_key[SEL_WARPS][4 * 32];
   __shared__ unsigned c_key[SEL_WARPS][SEL_CAP];
   __shared__ int c_col[SEL_WARPS][SEL_CAP];
+  __shared__ int s_cnt[SEL_WARPS];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = blockIdx.x * SEL_WARPS + w;
   if (r >= rows) return;
@@ -506,41 +507,33 @@ __global__ void __launch_bounds__(32 * SEL_WARPS, 4) k_select_rows_warp(const fl
     const unsigned ge = (s0 >= t) + (s1 >= t) + (s2 >= t) + (s3 >= t);
     if (__reduce_add_sync(0xffffffffu, ge) >= PROP_LIST) T = t;
   }
-  // 2. keys > T in column order
+  // 2. keys > T (ranked in step 3, so their order here does not matter)
   int n = 0;
   if (vec) {
-    // four consecutive columns per lane: a lane's place is the count of the
-    // lanes before it (a warp scan) plus its own earlier columns
+    // four consecutive columns per lane; the keys above T go to the list in
+    // any order (step 3 ranks them by key and column), each lane taking
+    // its places from a shared counter
+    if (lane == 0) s_cnt[w] = 0;
+    __syncwarp();
     const float4* r4 = reinterpret_cast<const float4*>(row);
-    for (int f0 = 0; f0 < cols / 4; f0 += 32) {
-      const float4 v = r4[f0 + lane];
+    for (int f = lane; f < cols / 4; f += 32) {
+      const float4 v = r4[f];
       const float e[4] = {v.x, v.y, v.z, v.w};
-      unsigned k4[4];
-      int cnt = 0;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const unsigned o = ordered_bits(e[u]);
-        k4[u] = LARGEST ? o : ~o;
-        cnt += k4[u] > T;
-      }
-      int incl = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-      }
-      int pos = n + incl - cnt;
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (k4[u] > T) {
+        const unsigned k = LARGEST ? o : ~o;
+        if (k > T) {
+          const int pos = atomicAdd(&s_cnt[w], 1);
           if (pos < SEL_CAP) {
-            c_key[w][pos] = k4[u];
-            c_col[w][pos] = 4 * (f0 + lane) + u;
+            c_key[w][pos] = k;
+            c_col[w][pos] = 4 * f + u;
           }
-          ++pos;
         }
-      n += __shfl_sync(0xffffffffu, incl, 31);
+      }
     }
+    __syncwarp();
+    n = s_cnt[w];
   } else {
     for (int base = 0; base < cols; base += 32) {
       const int c = base + lane;
@@ -692,6 +685,12 @@ int learned_prepare(const LearnedBufs& L, const float* x, int64_t m, const float
   // consumer scans, every choice is still certified with exact keys
   const bool tc3 = linear_tc_supported(h);
   if (tc3 && pack_rows_bf16(P->params + P->off_W3(), K, h, L.w3p, st)) return -1;
+  // with d on the tensor cores too, all three layers run there, each
+  // writing the next one's packed BF16 input (ReLU applied)
+  const bool tc_all = tc3 && linear_tc_supported(d);
+  if (tc_all && (pack_rows_bf16(P->params + P->off_W1(), h, d, L.w1p, st) ||
+                 pack_rows_bf16(P->params + P->off_W2(), h, h, L.w2p, st)))
+    return -1;
   // the cell of each supplier: any assignment keeps the bounds sound (the
   // radii below are taken over the cells as assigned), so on the tensor
   // cores in BF16 where d allows: the largest <x, mu_c> - |mu_c|^2 / 2
@@ -722,7 +721,14 @@ int learned_prepare(const LearnedBufs& L, const float* x, int64_t m, const float
     float* H2 = L.tmp + (size_t)L.chunk * h;
     float* Z = L.tmp2;               // rows x K
     k_standardise<<<num_sms() * 4, 256, 0, st>>>(yc, rows, d, P->in_mean, P->in_scale, Xs);
-    if (tc3) {
+    if (tc_all) {
+      const float* p = P->params;
+      if (pack_rows_bf16(Xs, rows, d, L.xp1, st) ||
+          linear_tc_pack_relu(L.xp1, rows, d, L.w1p, p + P->off_b1(), h, L.h1p, err, st) ||
+          linear_tc_pack_relu(L.h1p, rows, h, L.w2p, p + P->off_b2(), h, L.h2p, err, st) ||
+          linear_tc(L.h2p, rows, h, L.w3p, p + P->off_b3(), K, Z, err, st))
+        return -1;
+    } else if (tc3) {
       const float* p = P->params;
       gemm<false, true, EPI_BIAS_RELU>(Xs, d, p + P->off_W1(), d, H1, h, rows, h, d, p + P->off_b1(), st);
       gemm<false, true, EPI_BIAS_RELU>(H1, h, p + P->off_W2(), h, H2, h, rows, h, h, p + P->off_b2(), st);

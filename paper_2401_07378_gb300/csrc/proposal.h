@@ -76,6 +76,10 @@ struct LearnedBufs {
   unsigned long long* lc_best;  // [n]
   uint8_t* w3p;         // the scoring layer's weights packed for linear_tc
   uint8_t* h2p;         // [chunk] hidden rows packed for linear_tc
+  uint8_t* w1p;         // the two narrow layers' weights packed for linear_tc
+  uint8_t* w2p;
+  uint8_t* xp1;         // [chunk] standardised inputs packed
+  uint8_t* h1p;         // [chunk] first hidden layer packed
   // the supplier-to-cell assignment on the tensor cores
   int assign_chunk;     // suppliers per pass
   uint8_t* mup;         // centroids packed for linear_tc

@@ -595,7 +595,7 @@ int launch_nns_tc(const SolveBufs& B, const TcBufs& T, int mt, int nt, int preci
 constexpr int LIN_TILE = 128;  // rows of X and of W per tile
 constexpr int LIN_MAX_K = 256; // packed values per row
 
-enum LinMode : int { LIN_STORE = 0, LIN_ARGMAX = 1, LIN_LOWER = 2 };
+enum LinMode : int { LIN_STORE = 0, LIN_ARGMAX = 1, LIN_LOWER = 2, LIN_PACK_RELU = 3 };
 
 struct LinArgs {
   const uint8_t* X;
@@ -604,6 +604,7 @@ struct LinArgs {
   int rows, N;
   const float* bias;         // STORE / ARGMAX: [N]
   float* Z;                  // STORE / LOWER: [rows][N]
+  uint8_t* P;                // PACK_RELU: relu(S + b) packed in BF16 as the next layer's X (N values a row)
   unsigned long long* part;  // ARGMAX: [rows][ceil(N / 128)]
   // LOWER: the rows and columns as points; X and W hold BF16X3 copies
   const float* row_sq_lo;    // [rows] |y|^2 rounded down
@@ -708,6 +709,28 @@ __global__ void __launch_bounds__(128, 1) k_linear_tc(LinArgs A) {
 #pragma unroll
       for (int b = 0; b < 4; ++b) tmem_ld16_async(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb + 16 * b), rr[b]);
       tmem_ld_wait(rr);
+      if (MODE == LIN_PACK_RELU) {
+        // 16 columns = two 16-byte blocks of the next layer's packed row
+        // (zeros for padding rows, so the next tile holds no garbage)
+        const int kb = 2 * A.N;
+        uint8_t* base = A.P + (size_t)(row / LIN_TILE) * LIN_TILE * kb + (size_t)(row % LIN_TILE) * 16;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int nb = n0 + cb + 16 * b;
+          if (nb >= A.N) continue;
+          uint32_t w[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const float lo = live ? fmaxf(__uint_as_float(rr[b][2 * e]) + col_a[nb - n0 + 2 * e], 0.f) : 0.f;
+            const float hi = live ? fmaxf(__uint_as_float(rr[b][2 * e + 1]) + col_a[nb - n0 + 2 * e + 1], 0.f) : 0.f;
+            w[e] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+          }
+          *reinterpret_cast<uint4*>(base + (size_t)(nb / 8) * LIN_TILE * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+          *reinterpret_cast<uint4*>(base + (size_t)(nb / 8 + 1) * LIN_TILE * 16) = make_uint4(w[4], w[5], w[6], w[7]);
+        }
+        continue;
+      }
       if (!live) continue;
 #pragma unroll
       for (int b = 0; b < 4; ++b)
@@ -814,6 +837,14 @@ int linear_tc(const uint8_t* X, int rows, int K, const uint8_t* W, const float* 
   LinArgs A{};
   A.X = X, A.W = W, A.K = K, A.rows = rows, A.N = N, A.bias = bias, A.Z = Z, A.err = err;
   return launch_linear_tc<LIN_STORE>(A, st);
+}
+
+int linear_tc_pack_relu(const uint8_t* X, int rows, int K, const uint8_t* W, const float* bias, int N, uint8_t* out,
+                        unsigned* err, cudaStream_t st) {
+  if (N % 16) return -2;
+  LinArgs A{};
+  A.X = X, A.W = W, A.K = K, A.rows = rows, A.N = N, A.bias = bias, A.P = out, A.err = err;
+  return launch_linear_tc<LIN_PACK_RELU>(A, st);
 }
 
 int linear_tc_argmax(const uint8_t* X, int rows, int K, const uint8_t* W, const float* bias, int N,
