@@ -754,7 +754,11 @@ __global__ void __launch_bounds__(128, 1) k_linear_tc(LinArgs A) {
             } else {
               const float eb = __fmaf_ru(A.err_coeff, __fmul_ru(ynr, col_b[cl]), 1e-30f);
               const float d2 = __fsub_rd(__fadd_rd(ysq, col_a[cl]), __fmul_ru(2.f, __fadd_ru(sv, eb)));
-              const float gap = __fsub_rd(__fsqrt_rd(fmaxf(d2, 0.f)), col_c[cl]);
+              // sqrt from below: x * rsqrtf(x) is within 2^-22 of sqrt(x)
+              // (rsqrtf is documented to 2 ulp), and the factor 1 - 2^-20
+              // takes it under; tiny or non-positive x gives 0
+              const float dist = d2 > 1e-30f ? __fmul_rd(__fmul_rd(d2, rsqrtf(d2)), 0.99999905f) : 0.f;
+              const float gap = __fsub_rd(dist, col_c[cl]);
               out[f] = gap > 0.f ? __fmul_rd(gap, gap) : 0.f;
             }
           }
