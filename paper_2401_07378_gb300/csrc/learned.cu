@@ -1071,15 +1071,19 @@ __global__ void __launch_bounds__(LC_THREADS) k_lc_keys(LcArgs A) {
           float acc[4];
 #pragma unroll
           for (int k4 = 0; k4 < D / 4; ++k4) {
+            const unsigned long long y01 = f2_pack(yr[4 * k4], yr[4 * k4 + 1]);
+            const unsigned long long y23 = f2_pack(yr[4 * k4 + 2], yr[4 * k4 + 3]);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
+              // the differences two coordinates per packed FP32x2 step (each
+              // lane rounds as the scalar form), the squares in order
               const float4 xv = row[u][k4];
-              const float xk[4] = {xv.x, xv.y, xv.z, xv.w};
+              const unsigned long long t01 = f2_sub(f2_pack(xv.x, xv.y), y01);
+              const unsigned long long t23 = f2_sub(f2_pack(xv.z, xv.w), y23);
+              const float t[4] = {f2_lo(t01), f2_hi(t01), f2_lo(t23), f2_hi(t23)};
 #pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                const float t = __fsub_rn(xk[e], yr[4 * k4 + e]);
-                acc[u] = (k4 == 0 && e == 0) ? __fmul_rn(t, t) : __fmaf_rn(t, t, acc[u]);
-              }
+              for (int e = 0; e < 4; ++e)
+                acc[u] = (k4 == 0 && e == 0) ? __fmul_rn(t[e], t[e]) : __fmaf_rn(t[e], t[e], acc[u]);
             }
           }
 #pragma unroll
