@@ -128,3 +128,26 @@ def test_learned_host_entry_point(ctx, small_prop):
     p = wl.gmm_pair(seed=2, n=3000, d=64)
     res = ctx.solve_host(p.x, p.a, p.y, p.b, metric="l2", proposal=prop)
     assert res.cost == oracle.solve_pair(p, "l2").cost
+
+
+@pytest.mark.parametrize("d,precision", [(48, "fp32"), (48, "bf16x3"), (100, "fp32"), (100, "bf16")])
+def test_learned_solve_at_other_widths_equals_oracle(ctx, d, precision):
+    """The learned path's other branches: at d = 48 the scan runs one warp
+    per consumer while the network, the assignment and the cell bounds run
+    on the tensor cores; at d = 100 (not a multiple of 16) the network's two
+    narrow layers, the assignment and the cell bounds take their FP32 forms.
+    Either way the result is the oracle's, bit for bit."""
+    from paper_2401_07378_gb300 import proposal_training
+    prop, _ = proposal_training.build_gmm_proposal(ctx, d=d, cells=128, hidden=64, runs=12, n_per_run=1024,
+                                                    fit_runs=1, fit_n=8192, epochs=3, batch=1024, lr=3e-3)
+    p = wl.gmm_pair(seed=3, n=3000, d=d)
+    t = lambda v: torch.from_numpy(v).cuda()
+    res = ctx.solve(t(p.x), t(p.a), t(p.y), t(p.b), metric="l2", precision=precision, plan=True, proposal=prop)
+    ref = oracle.solve_pair(p, "l2")
+    assert res.cost == ref.cost
+    assert res.stats["rounds"] == ref.rounds
+    gi = np.lexsort((res.plan_j.cpu().numpy(), res.plan_i.cpu().numpy()))
+    oi = np.lexsort((ref.plan_j, ref.plan_i))
+    assert np.array_equal(res.plan_f.cpu().numpy()[gi], ref.plan_f[oi])
+    assert res.stats["certified"] > 0
+    prop.close()
