@@ -893,7 +893,7 @@ __global__ void __launch_bounds__(256) k_learned_nns(LearnedArgs A) {
 // certificate are those of k_learned_nns, so the results are the same.
 // --------------------------------------------------------------------------
 
-constexpr int LC_THREADS = 256;  // consumers of one cell per work item (one per thread)
+constexpr int LC_THREADS = 128;  // consumers of one cell per work item (one per thread)
 constexpr int LC_TILE = 64;      // suppliers staged at a time
 
 struct LcArgs {
