@@ -204,7 +204,7 @@ NNS_DEV void xs_add(unsigned long long* acc, double v) {
 // limb sum their digits by shuffles first (at most 32 digits below 2^32
 // each: no overflow), then one of them adds the sums, so values that share
 // an exponent cost three atomics per warp, not per lane.
-NNS_DEV void xs_add_warp(unsigned long long* acc, double v) {
+static __device__ __noinline__ void xs_add_warp(unsigned long long* acc, double v) {  // one copy per file, not inlined at every site
   int L = -1;
   unsigned long long c0 = 0, c1 = 0, c2 = 0;
   if (v > 0.0) xs_digits(v, L, c0, c1, c2);

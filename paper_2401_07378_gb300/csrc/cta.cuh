@@ -23,6 +23,7 @@
 #include <math_constants.h>
 
 #include "common.cuh"
+#include "kernels.h"
 
 namespace nnsemd {
 
@@ -940,6 +941,13 @@ NNS_DEV bool cta_load_side(const float* pts, const double* w, int cnt, int d, fl
   __syncthreads();
   return true;
 }
+
+// Shared memory of a one-CTA solver for d <= 8 (coordinates included).
+template <int D, int DP, bool L1>
+struct LowdSmem {
+  CtaCore<FIN_MAX> S;
+  GeoSmem<D, DP, L1, FIN_MAX> G;
+};
 
 // Whole pair in one CTA: load both sides, drop zero weights, run all rounds,
 // return R (correctly rounded) in thread 0.  Returns false on invalid input.
