@@ -323,8 +323,7 @@ int nnsemd_proposal_load(nnsemd_ctx *ctx, const char *path, nnsemd_proposal **ou
  * until the process exits; the kernel clears it at the start of each call.
  * The first call on a device does a one-time set-up with that device current:
  * it looks up the array's device address (cudaGetSymbolAddress) and sets the
- * kernel's shared-memory limit.  Make that first call on each device before
- * any stream capture begins there.  All calls share the array, so calls that
+ * kernel's shared-memory limit.  All calls share the array, so calls that
  * overlap on the GPU race: serialise them.  R equals nnsemd_solve's. */
 #define NNSEMD_NOALLOC_MAX_POINTS 1024
 #define NNSEMD_NOALLOC_MAX_D 8
