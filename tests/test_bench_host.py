@@ -1,5 +1,6 @@
 """Host-side logic of bench.py without a GPU: the multi-rank reductions
-(world size 2 over gloo on CPU) and the reference arm's JSON line."""
+(world size 2 over gloo on CPU), the reference arm's JSON line, the roofline
+arithmetic and the freshness rule of the recorded DRAM traffic."""
 import json
 import os
 import socket
@@ -83,3 +84,39 @@ def test_reference_arm_non_zero_rank_prints_nothing(monkeypatch, capsys):
     monkeypatch.setenv("WORLD_SIZE", "2")
     bench.main(["--impl", "reference", "--workload", "single", "--steps", "1", "--warmup", "0"])
     assert capsys.readouterr().out.strip() == ""
+
+
+def test_roofline_rates_against_hand_worked_figures(monkeypatch):
+    """The roofline field on made-up launches, worked by hand.  FP32: 7e9
+    pairs at d = 3 over 7 launches in 7 ms is 6e9 pipe ops per 1 ms launch,
+    6 T op/s, against 100 SMs x 128 lanes x 2,000 MHz = 25.6 T.  Tensor:
+    1e12 pairs at d = 64 over 10 launches in 100 ms is 1,280 TFLOP/s against
+    a 2,000 TFLOP/s bf16 peak (twice that for FP8)."""
+    import bench
+    monkeypatch.setattr(bench, "peaks", lambda: {"sm_max_mhz": 2000.0, "bf16_tflops": 2000.0})
+    monkeypatch.setattr(bench, "measured_traffic", lambda: 4.5e5)
+    r = bench.roofline(3, "fp32", 0, 7e9, 7, 7.0, 14.0, True, 100)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["peak"] == pytest.approx(25.6) and r["achieved"] == pytest.approx(6.0)
+    assert r["frac"] == pytest.approx(6.0 / 25.6) and r["share_of_step"] == pytest.approx(0.5)
+    assert r["traffic"] == 4.5e5 and r["kernel"] == "k_nns_lowd (K1)"
+    r = bench.roofline(64, "bf16", 8, 1e12, 10, 100.0, 100.0, False, 100)
+    assert r["bound"] == "tensor" and r["achieved"] == pytest.approx(1280.0)
+    assert r["frac"] == pytest.approx(0.64) and r["traffic"] is None and "top-8" in r["kernel"]
+    r = bench.roofline(64, "fp8", 16, 1e12, 10, 100.0, 100.0, False, 100)
+    assert r["peak"] == pytest.approx(4000.0) and r["frac"] == pytest.approx(0.32) and "top-16" in r["kernel"]
+
+
+def test_traffic_only_while_the_k1_source_matches(monkeypatch, tmp_path):
+    """The DRAM bytes recorded by an ncu capture are reported only while K1's
+    source still hashes to the value stored beside them."""
+    import bench
+    f = tmp_path / "counters.json"
+    f.write_text(json.dumps({"source_sha256": "abc", "dram_bytes_per_launch": 123.0}))
+    monkeypatch.setattr(bench, "COUNTERS_FILE", str(f))
+    monkeypatch.setattr(bench, "k1_source_hash", lambda: "abc")
+    assert bench.measured_traffic() == 123.0
+    monkeypatch.setattr(bench, "k1_source_hash", lambda: "abd")
+    assert bench.measured_traffic() is None
+    monkeypatch.setattr(bench, "COUNTERS_FILE", str(tmp_path / "missing.json"))
+    assert bench.measured_traffic() is None
